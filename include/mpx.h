@@ -1,0 +1,297 @@
+/*
+ * mpx.h -- MPI communication enqueued on CUDA streams, among R virtual ranks
+ * that share one GPU.  C ABI of libmpx.so.
+ *
+ * The operations follow "MPIX Stream: An Explicit Solution to Hybrid MPI+X
+ * Programming" (Zhou, Raffenetti, Guo, Thakur; EuroMPI/USA'22):
+ *   - MPIX stream: a local serial execution context, here a cudaStream_t bound
+ *     to one virtual rank (§3.1, MPIX_Stream_create / MPIX_Stream_free).
+ *   - stream communicator: one stream per rank (§3.3, MPIX_Stream_comm_create).
+ *   - enqueue operations with the MPI signatures (§3.4, MPIX_Send_enqueue,
+ *     MPIX_Recv_enqueue, MPIX_Isend_enqueue, MPIX_Irecv_enqueue,
+ *     MPIX_Wait_enqueue, MPIX_Waitall_enqueue) and their extension to
+ *     collectives (§3.4, last paragraph), here SUM allreduce.
+ * The paper's process ranks become virtual ranks of one world living on one
+ * GPU; the "network" is the GPU's own memory.  A device-resident engine
+ * (one cooperative kernel) ingests operations from per-stream submission
+ * rings, matches them, moves payloads with its own copy kernels and releases
+ * each CUDA stream in stream order, so the host never synchronises per
+ * message (§2.4, §5.2).
+ *
+ * Conventions for every call:
+ *   - Return value: MPX_SUCCESS (0) or an MPX_ERR_* code.  Errors detected at
+ *     enqueue time are returned synchronously and nothing is enqueued.
+ *     Errors found while an operation executes on the GPU go to its status
+ *     (if one was given) and to the sticky error of the stream and world
+ *     (mpx_stream_get_error / mpx_world_get_error).
+ *   - Buffers are device-accessible memory the caller owns (cudaMalloc,
+ *     PyTorch tensors, or mapped pinned host memory).  A buffer must stay valid
+ *     and unmodified (send) or untouched (receive) until its operation has
+ *     completed in stream order.
+ *   - mpx_status_t pointers passed to enqueue calls must be device-accessible
+ *     (device memory or mapped pinned host memory) and stay valid until the
+ *     operation completes; NULL (MPX_STATUS_IGNORE) discards the status.
+ *   - A stream (and everything enqueued through it) is used by at most one
+ *     host thread at a time (§3.1: the user guarantees serial use, so the
+ *     enqueue path takes no lock).  Different streams may be used from
+ *     different threads concurrently.
+ *   - Nothing here allocates per message.  Library memory is allocated at
+ *     mpx_world_create and mpx_stream_create.
+ */
+#ifndef MPX_H
+#define MPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                       /* cudaStream_t is a CUstream_st* */
+typedef struct CUstream_st* mpx_cuda_stream_t;
+
+typedef struct mpx_world_s* mpx_world_t;   /* R virtual ranks on this GPU (stands in for MPI_COMM_WORLD) */
+typedef struct mpx_stream_s* mpx_stream_t; /* MPIX_Stream */
+typedef struct mpx_comm_s* mpx_comm_t;     /* one rank's handle of a stream communicator */
+typedef int64_t mpx_request_t;             /* opaque: (world << 56) | (stream << 40) | seq; MPX_REQUEST_NULL = -1 */
+typedef int32_t mpx_datatype_t;
+
+typedef struct {
+  int32_t source; /* sender's rank in the communicator */
+  int32_t tag;    /* sender's tag */
+  int32_t error;  /* MPX_SUCCESS, MPX_ERR_TRUNCATE, MPX_ERR_TIMEOUT, ... */
+  int32_t pad;
+  int64_t bytes;  /* bytes delivered */
+} mpx_status_t;   /* 24 bytes */
+
+#define MPX_STATUS_IGNORE ((mpx_status_t*)0)
+#define MPX_STATUSES_IGNORE ((mpx_status_t*)0)
+#define MPX_IN_PLACE ((const void*)1)
+#define MPX_REQUEST_NULL ((mpx_request_t)-1)
+
+enum {
+  MPX_ANY_SOURCE = -2,
+  MPX_ANY_TAG = -1,
+  MPX_TAG_UB = (1 << 30) - 1,
+  MPX_UNDEFINED = -32766
+};
+
+/* predefined datatypes; derived ones come from mpx_type_vector */
+enum {
+  MPX_BYTE = 0, MPX_UINT8 = 0,
+  MPX_INT32 = 1,
+  MPX_INT64 = 2,
+  MPX_FLOAT = 3,
+  MPX_DOUBLE = 4
+};
+
+enum { MPX_SUM = 0 };
+
+/* allreduce summation order */
+enum {
+  MPX_REDUCE_FIXED = 0, /* left fold (((x0+x1)+x2)+...) in rank order: bit-reproducible */
+  MPX_REDUCE_TREE = 1   /* pairwise tree over ranks: tighter error bound */
+};
+
+/* stream flags */
+enum {
+  MPX_STREAM_DEFAULT = 0,
+  /* The caller promises that no other work is enqueued on the CUDA stream
+   * between these operations and that buffers are ready at enqueue time;
+   * the per-operation stream-order doorbell is then omitted. */
+  MPX_STREAM_EXCLUSIVE = 1
+};
+
+/* engine modes (mpx_world_config_t.engine_mode) */
+enum {
+  MPX_ENGINE_PERSISTENT = 0, /* one cooperative engine kernel stays resident; relaunched on demand */
+  MPX_ENGINE_DRAIN = 1,      /* the engine runs only inside mpx_world_progress(), in stream order */
+  MPX_ENGINE_PLAIN = 2       /* no engine: host matching, one copy or kernel per operation, host sync per wait */
+};
+
+enum {
+  MPX_SUCCESS = 0,
+  MPX_ERR_ARG = 1,         /* invalid argument */
+  MPX_ERR_RANK = 2,        /* destination/source rank out of range */
+  MPX_ERR_TAG = 3,         /* tag out of range */
+  MPX_ERR_TYPE = 4,        /* invalid datatype */
+  MPX_ERR_COMM = 5,        /* not a stream communicator with a GPU stream (§3.4) */
+  MPX_ERR_NO_ENDPOINT = 6, /* stream pool exhausted (§3.1) */
+  MPX_ERR_AGAIN = 7,       /* submission ring or request space full; retry */
+  MPX_ERR_STREAM = 8,      /* waitall requests on different streams (§3.4) */
+  MPX_ERR_PENDING = 9,     /* object still has operations in flight (§3.1, MPIX_Stream_free) */
+  MPX_ERR_CUDA = 10,       /* a CUDA runtime/driver call failed */
+  MPX_ERR_REQUEST = 11,    /* invalid request handle */
+  MPX_ERR_NO_MEM = 12,     /* allocation failed / budget exceeded / staging exhausted */
+  MPX_ERR_STATE = 13,      /* engine in a state that does not allow the call */
+  MPX_ERR_INTERN = 14,     /* internal error (device-side consistency check) */
+  MPX_ERR_TRUNCATE = 15,   /* message longer than the receive buffer: capacity delivered */
+  MPX_ERR_TIMEOUT = 16,    /* watchdog: no progress within watchdog_ns */
+  MPX_ERR_UNSUPPORTED = 17
+};
+
+typedef struct {
+  int32_t engine_mode;     /* MPX_ENGINE_* (default PERSISTENT) */
+  int32_t max_streams;     /* stream (endpoint) pool size, <= 1024 (default 64) */
+  int32_t ring_slots;      /* operations in flight per stream, power of two (default 4096) */
+  int32_t max_comms;       /* stream communicators created over the world's life (default 8) */
+  int32_t queue_slots;     /* matching queue capacity per (comm, rank) domain, power of two (default 4096) */
+  int32_t task_slots;      /* engine task ring, power of two (default 16384) */
+  int32_t engine_ctas;     /* engine CTAs; 0 = one per SM */
+  int32_t engine_threads;  /* threads per engine CTA, multiple of 32, <= 512 (default 256) */
+  int32_t tile_bytes;      /* copy tile, multiple of 16 (default 65536) */
+  int32_t bulk_min_bytes;  /* contiguous tiles at least this large move by TMA bulk copy (default 32768; 0 = never) */
+  int32_t reduce_mode;     /* default allreduce order, MPX_REDUCE_* (default FIXED) */
+  int32_t pad0;
+  int64_t staging_bytes;   /* eager-send staging arena (default 256 MiB) */
+  int64_t budget_bytes;    /* cap on library device memory; 0 = no cap */
+  int64_t watchdog_ns;     /* pending work with no progress this long fails with MPX_ERR_TIMEOUT (default 10 s) */
+  int64_t idle_exit_ns;    /* persistent engine exits after this long with nothing to do (default 100 ms) */
+  int64_t stage_delay_ns;  /* a stalled stream's undeliverable send is staged after this long (default 20 us) */
+} mpx_world_config_t;
+
+/* Fill *cfg with defaults, then apply MPX_* environment overrides. */
+int mpx_world_config_init(mpx_world_config_t* cfg);
+
+/* Create a world of `nranks` virtual ranks on the current CUDA device.
+ * cfg may be NULL (defaults).  Allocates rings and control words in pinned
+ * host memory and the engine state, matching queues and staging arena in
+ * device memory.  Errors: MPX_ERR_ARG, MPX_ERR_NO_MEM, MPX_ERR_CUDA. */
+int mpx_world_create(int nranks, const mpx_world_config_t* cfg, mpx_world_t* world);
+
+/* Stop the engine and free everything.  MPX_ERR_PENDING if streams or
+ * communicators are still alive (nothing is freed then). */
+int mpx_world_free(mpx_world_t* world);
+
+/* PERSISTENT mode: launch the engine now if it is not running (enqueue calls
+ * also do this on demand).  Errors: MPX_ERR_STATE in other modes. */
+int mpx_world_start(mpx_world_t world);
+
+/* PERSISTENT mode: ask the engine to exit once idle and wait (host side, at
+ * most timeout_ms) until it has exited.  MPX_ERR_TIMEOUT if it did not. */
+int mpx_world_stop(mpx_world_t world, int timeout_ms);
+
+/* DRAIN mode: enqueue one engine pass on `stream` (stream-ordered, may be
+ * captured in a CUDA graph).  The pass ingests every operation published
+ * so far, moves every payload whose both ends are ready, and returns when
+ * nothing more can complete without new operations.  A pass must not
+ * overlap another engine pass of the same world (enqueue them on one
+ * stream).  PLAIN mode: run host progress until nothing more can complete. */
+int mpx_world_progress(mpx_world_t world, mpx_cuda_stream_t stream);
+
+/* Failure recovery: mark the world failed and release every CUDA stream that
+ * waits on an operation of this world (from the host, without the engine).
+ * Pending operations complete with MPX_ERR_TIMEOUT and move no data; later
+ * enqueue calls return MPX_ERR_STATE.  Use it when a deadline passes. */
+int mpx_world_abort(mpx_world_t world);
+
+/* Sticky first asynchronous error of the world (MPX_SUCCESS if none). */
+int mpx_world_get_error(mpx_world_t world, int* first_error);
+
+/* Engine counters: [0] launches, [1] ticks, [2] messages completed,
+ * [3] payload bytes moved, [4] tasks, [5] staged sends, [6] rounds,
+ * [7] allreduce instances.  n is the array length (<= 8 filled). */
+int mpx_world_get_counters(mpx_world_t world, int64_t* out, int n);
+
+/* MPIX_Stream_create (§3.1) for virtual rank `rank`, backed by a CUDA
+ * stream the caller owns and keeps alive until mpx_stream_free.  Claims a
+ * dedicated endpoint (submission ring, doorbell and completion word) from
+ * the world's pool; MPX_ERR_NO_ENDPOINT when the pool is exhausted.
+ * flags: MPX_STREAM_DEFAULT or MPX_STREAM_EXCLUSIVE. */
+int mpx_stream_create(mpx_world_t world, int rank, mpx_cuda_stream_t cuda_stream, unsigned flags,
+                      mpx_stream_t* stream);
+
+/* MPIX_Stream_free (§3.1): fails with MPX_ERR_PENDING while operations
+ * enqueued on the stream have not completed; *stream is then unchanged. */
+int mpx_stream_free(mpx_stream_t* stream);
+
+/* Endpoint id of the stream (the order key used for matching ties). */
+int mpx_stream_get_id(mpx_stream_t stream, int* id);
+
+/* Sticky first asynchronous error of operations on this stream. */
+int mpx_stream_get_error(mpx_stream_t stream, int* first_error);
+
+/* Number of operations enqueued on the stream that have not completed. */
+int mpx_stream_pending(mpx_stream_t stream, int64_t* pending);
+
+/* MPIX_Stream_comm_create (§3.3), done for all R ranks at once because the
+ * ranks share one process: streams[r] is rank r's stream; comms_out[r]
+ * receives rank r's handle.  Each stream may serve in several comms. */
+int mpx_stream_comm_create(mpx_world_t parent, int nranks, const mpx_stream_t streams[],
+                           mpx_comm_t comms_out[]);
+
+/* Free one rank's handle; the communicator dies with its last handle. */
+int mpx_comm_free(mpx_comm_t* comm);
+int mpx_comm_rank(mpx_comm_t comm, int* rank);
+int mpx_comm_size(mpx_comm_t comm, int* size);
+/* Summation order for allreduce on this communicator (all ranks' handles). */
+int mpx_comm_set_reduce_mode(mpx_comm_t comm, int mode);
+
+/* MPI_Type_vector(count, blocklength, stride, oldtype): `count` blocks of
+ * `blocklength` old elements whose starts are `stride` elements apart.  One
+ * instance spans ((count-1)*stride+blocklength) elements (its extent);
+ * instance i of a message starts at i*extent.  oldtype must be predefined.
+ * Process-wide handle; stays valid until mpx_type_free. */
+int mpx_type_vector(int count, int blocklength, int stride, mpx_datatype_t oldtype,
+                    mpx_datatype_t* newtype);
+int mpx_type_free(mpx_datatype_t* type);
+/* bytes of data in one instance (gaps excluded) */
+int mpx_type_size(mpx_datatype_t type, int64_t* size);
+/* bytes from the start of one instance to the start of the next */
+int mpx_type_extent(mpx_datatype_t type, int64_t* extent);
+
+/* MPIX_Send_enqueue (§3.4): blocking in stream order.  Work enqueued on the
+ * stream after it runs once the send buffer may be reused (the payload was
+ * delivered or copied to the staging arena: eager protocol).  The buffer is
+ * read only after the work enqueued before the call has completed. */
+int mpx_send_enqueue(const void* buf, int64_t count, mpx_datatype_t datatype, int dest, int tag,
+                     mpx_comm_t comm);
+
+/* MPIX_Recv_enqueue (§3.4): blocking in stream order.  Work enqueued after it
+ * sees the received data; no cudaStreamSynchronize is needed.  source may be
+ * MPX_ANY_SOURCE, tag may be MPX_ANY_TAG.  A longer message delivers the
+ * buffer's capacity and reports MPX_ERR_TRUNCATE in the status. */
+int mpx_recv_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int source, int tag,
+                     mpx_comm_t comm, mpx_status_t* status);
+
+/* MPIX_Isend_enqueue / MPIX_Irecv_enqueue (§3.4): start in stream order and
+ * let later enqueued work proceed; complete with mpx_wait(all)_enqueue. */
+int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t datatype, int dest, int tag,
+                      mpx_comm_t comm, mpx_request_t* request);
+int mpx_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int source, int tag,
+                      mpx_comm_t comm, mpx_request_t* request);
+
+/* MPIX_Wait_enqueue (§3.4): enqueued on the request's stream; work enqueued
+ * after it runs once the request completed.  *request becomes
+ * MPX_REQUEST_NULL at enqueue time (a null request is a no-op). */
+int mpx_wait_enqueue(mpx_request_t* request, mpx_status_t* status);
+
+/* MPIX_Waitall_enqueue (§3.4): all non-null requests must belong to one
+ * stream (else MPX_ERR_STREAM).  statuses may be NULL, else n entries. */
+int mpx_waitall_enqueue(int n, mpx_request_t requests[], mpx_status_t statuses[]);
+
+/* Enqueued MPI_Allreduce (§3.4, last paragraph), op = MPX_SUM over a
+ * predefined datatype.  The k-th call on a communicator from every rank forms
+ * instance k.  Every rank's recvbuf receives the result; sendbuf may be
+ * MPX_IN_PLACE.  Blocking in stream order.  Integer sums wrap; float sums use
+ * the communicator's reduce mode. */
+int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                          mpx_datatype_t datatype, int op, mpx_comm_t comm);
+
+/* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
+int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);
+
+/* Listing 4's user compute kernel, for programs that interleave compute with
+ * enqueued communication: y[i] = a*x[i] + y[i] (fused multiply-add, one
+ * rounding) for i < n, launched on `stream`.  Not an MPI call. */
+int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y, mpx_cuda_stream_t stream);
+
+/* Library version (major*100+minor). */
+int mpx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPX_H */

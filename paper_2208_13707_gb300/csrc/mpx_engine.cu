@@ -1,0 +1,1782 @@
+// Device engine of libmpx: one cooperative kernel that completes operations
+// enqueued on CUDA streams (MPIX Stream, §3.4), without the host in the loop.
+//
+// CTA 0 is the control CTA.  Each tick it
+//   1. ingests new descriptors from every stream's submission ring,
+//   2. runs logical rounds: every stream advances past the operations that are
+//      not blocked, sends/receives get posted with key (round, stream, seq),
+//      and each (comm, destination) domain matches its posts in key order
+//      (a send takes the first posted receive that accepts it, a receive the
+//      first unexpected send) -- MPI's matching order and non-overtaking rule
+//      (§2.1); allreduce instances complete once all ranks arrived,
+//   3. turns matched pairs whose two streams have reached them (stream-order
+//      doorbells) into copy tasks, stages sends of stalled streams (eager
+//      protocol), and turns complete allreduce instances into reduce tasks,
+//   4. processes finished tasks, writes statuses, advances each stream's
+//      completion word (which releases the stream's cuStreamWaitValue64) and
+//      retires operations.
+// Every CTA (CTA 0 when it has nothing else to do) moves data: it claims
+// tiles of tasks from a ring and runs them with 16-byte coalesced accesses,
+// TMA bulk copies (cp.async.bulk) for large contiguous tiles, and strided
+// gather/scatter for MPI_Type_vector layouts.  Every wait is bounded; a
+// watchdog fails pending work with MPX_ERR_TIMEOUT instead of hanging.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpx_internal.h"
+
+namespace mpxi {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kAnySource = -2;
+constexpr int kAnyTag = -1;
+constexpr int kErrArg = 1;
+constexpr int kErrNoMem = 12;
+constexpr int kErrIntern = 14;
+constexpr int kErrTruncate = 15;
+constexpr int kErrTimeout = 16;
+constexpr int kMaxRoundsPerTick = 64;
+constexpr int kMaxStagePerTick = 128;
+constexpr int kTmaStages = 4;
+constexpr uint32_t kTmaChunk = 16384;
+constexpr int kMaxStreamsPerCta = 1024;
+
+// ------------------------------------------------------------------------
+// memory-model helpers
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint64_t ld_acq_sys(const void* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_rlx_sys(const void* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int32_t ld_acq_sys32(const void* p) {
+  int32_t v;
+  asm volatile("ld.acquire.sys.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rlx_sys(void* p, uint64_t v) {
+  asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel_sys(void* p, uint64_t v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel_sys32(void* p, int32_t v) {
+  asm volatile("st.release.sys.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acq_gpu(const void* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_acq_gpu32(const void* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_gpu(void* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel_gpu32(void* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int32_t ld_vol32(const void* p) {
+  return *reinterpret_cast<const volatile int32_t*>(p);
+}
+__device__ __forceinline__ void fence_sc_sys() { asm volatile("fence.sc.sys;" ::: "memory"); }
+
+// payload loads bypass L1: buffers change between uses inside one launch
+__device__ __forceinline__ uint4 ld_cg16(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_cg8(const void* p) {
+  uint2 v;
+  asm volatile("ld.global.cg.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_cg4(const void* p) {
+  uint32_t v;
+  asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint16_t ld_cg2(const void* p) {
+  uint16_t v;
+  asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint8_t ld_cg1(const void* p) {
+  uint32_t v;
+  asm volatile("ld.global.cg.u8 %0, [%1];" : "=r"(v) : "l"(p));
+  return (uint8_t)v;
+}
+__device__ __forceinline__ void st16(void* p, uint4 v) {
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st8(void* p, uint2 v) {
+  asm volatile("st.global.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
+}
+__device__ __forceinline__ void st4(void* p, uint32_t v) {
+  asm volatile("st.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st2(void* p, uint16_t v) {
+  asm volatile("st.global.u16 [%0], %1;" ::"l"(p), "h"(v) : "memory");
+}
+__device__ __forceinline__ void st1(void* p, uint8_t v) {
+  asm volatile("st.global.u8 [%0], %1;" ::"l"(p), "r"((uint32_t)v) : "memory");
+}
+// descriptor loads from pinned host memory: never served from L1
+__device__ __forceinline__ uint4 ld_vol16(const void* p) {
+  uint4 v;
+  asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
+  return v;
+}
+
+// ------------------------------------------------------------------------
+// TMA bulk copy helpers (non-multicast, this GPU's memory only)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_1d(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"(smem_u32(ssrc)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ------------------------------------------------------------------------
+// shared memory of every engine CTA
+// ------------------------------------------------------------------------
+struct CtaShared {
+  uint64_t bar[kTmaStages];
+  uint32_t phase;
+  int32_t flag;           // broadcast scalar
+  int64_t claim_task;     // task id claimed by this CTA (-1: none)
+  uint32_t claim_tile;
+  int32_t any;            // control: something happened
+  int32_t nstage;         // control: staging candidates
+  int32_t ntask_full;     // control: task ring full this tick
+  int32_t pending;        // control: some stream has unretired operations
+  uint64_t stage_ref[kMaxStagePerTick];
+  int32_t cnt[kMaxStreamsPerCta];
+  Task task;              // claimed task (copy)
+};
+
+__device__ __forceinline__ DOp* op_at(const EngineParams& P, int g, uint64_t seq) {
+  return P.ops + (((size_t)g << P.slots_log2) + ((seq - 1) & ((1ull << P.slots_log2) - 1)));
+}
+__device__ __forceinline__ DOp* op_ref(const EngineParams& P, uint64_t ref) {
+  return op_at(P, ref_stream(ref), ref_seq(ref));
+}
+__device__ __forceinline__ bool is_send(uint32_t k) { return k == K_SEND || k == K_ISEND; }
+__device__ __forceinline__ bool is_recv(uint32_t k) { return k == K_RECV || k == K_IRECV; }
+__device__ __forceinline__ bool is_blocking(uint32_t k) {
+  return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL || k == K_ALLREDUCE;
+}
+
+__device__ void set_error(const EngineParams& P, int g, int err) {
+  if (g >= 0) atomicCAS(&P.sctl[g].error, 0, err);
+  atomicCAS(&P.wctl->error, 0, err);
+}
+
+// Packed bytes carried by one operation's datatype.
+__device__ __forceinline__ int64_t op_bytes(const Desc& d) {
+  return d.count * (int64_t)d.vcount * (int64_t)d.blocklen * base_size(kw_base(d.kw));
+}
+
+__device__ void make_layout(Layout& L, uint64_t base, const Desc& d) {
+  const int64_t es = base_size(kw_base(d.kw));
+  const int64_t seg = (int64_t)d.blocklen * es;
+  const int64_t stride = (int64_t)d.stride * es;
+  const int64_t per = d.vcount;
+  const int64_t extent = ((per - 1) * stride + seg);
+  L.base = base;
+  bool contiguous = (per == 1 && extent == seg) || (stride == seg && extent == per * seg);
+  if (contiguous) {
+    L.seg = kContig;
+    L.stride = 0;
+    L.per = 1;
+    L.extent = 0;
+  } else {
+    L.seg = seg;
+    L.stride = stride;
+    L.per = per;
+    L.extent = extent;
+  }
+}
+
+__device__ int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// ------------------------------------------------------------------------
+// data movement
+// ------------------------------------------------------------------------
+// Position of a packed byte offset inside one side's layout, stepped by a
+// fixed number of bytes without dividing again.
+struct SideIter {
+  uint64_t base;
+  int64_t seg, stride, per, extent;
+  int64_t within, b, inst;
+  int64_t sw, sb, si;
+  __device__ void init(const Layout& L, int64_t p, int64_t step) {
+    base = L.base;
+    seg = L.seg;
+    stride = L.stride;
+    per = L.per;
+    extent = L.extent;
+    int64_t k = p / seg;
+    within = p - k * seg;
+    inst = k / per;
+    b = k - inst * per;
+    int64_t sk = step / seg;
+    sw = step - sk * seg;
+    si = sk / per;
+    sb = sk - si * per;
+  }
+  __device__ __forceinline__ uint64_t addr() const {
+    return base + (uint64_t)(inst * extent + b * stride + within);
+  }
+  __device__ __forceinline__ void step() {
+    within += sw;
+    b += sb;
+    inst += si;
+    if (within >= seg) {
+      within -= seg;
+      ++b;
+    }
+    if (b >= per) {
+      b -= per;
+      ++inst;
+    }
+  }
+};
+
+template <int U>
+__device__ __forceinline__ void copy_unit(uint64_t d, uint64_t s) {
+  if (U == 16) st16((void*)d, ld_cg16((const void*)s));
+  else if (U == 8) st8((void*)d, ld_cg8((const void*)s));
+  else if (U == 4) st4((void*)d, ld_cg4((const void*)s));
+  else if (U == 2) st2((void*)d, ld_cg2((const void*)s));
+  else st1((void*)d, ld_cg1((const void*)s));
+}
+
+// Strided gather/scatter: chunks of C bytes are contiguous on both sides.
+template <int U>
+__device__ void chunked_copy(const Task& T, int64_t p0, int64_t p1) {
+  const int64_t C = T.chunk;
+  const int64_t upc = C / U;
+  int L = 32;
+  if (upc < 32) {
+    L = 1;
+    while (L * 2 <= upc) L *= 2;
+  }
+  const int cpw = 32 / L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int sub = lane / L, ul = lane % L;
+  const int64_t nch = (p1 - p0 + C - 1) / C;
+  const int64_t D = (int64_t)nwarps * cpw;
+  int64_t c = (int64_t)warp * cpw + sub;
+  if (c >= nch) return;
+  SideIter si, di;
+  si.init(T.src, p0 + c * C, D * C);
+  di.init(T.dst, p0 + c * C, D * C);
+  for (; c < nch; c += D) {
+    const int64_t p = p0 + c * C;
+    const int64_t n = (p1 - p) < C ? (p1 - p) : C;
+    const uint64_t s = si.addr(), d = di.addr();
+    const int64_t full = n / U;
+#pragma unroll 4
+    for (int64_t u = ul; u < full; u += L) copy_unit<U>(d + u * U, s + u * U);
+    if (U > 1 && ul == 0) {
+      for (int64_t q = full * U; q < n; ++q) copy_unit<1>(d + q, s + q);
+    }
+    si.step();
+    di.step();
+  }
+}
+
+__device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t src,
+                                int64_t n, const EngineParams& P) {
+  // one thread drives the bulk copies: loads into kTmaStages smem buffers,
+  // stores back out, keeping up to kTmaStages-1 loads in flight
+  if (threadIdx.x != 0) return;
+  const uint32_t nch = (uint32_t)((n + kTmaChunk - 1) / kTmaChunk);
+  uint32_t phase = sm.phase;
+  auto issue = [&](uint32_t j) {
+    const uint32_t s = j % kTmaStages;
+    const uint64_t off = (uint64_t)j * kTmaChunk;
+    const uint32_t bytes = (uint32_t)((n - (int64_t)off) < (int64_t)kTmaChunk ? (n - off) : kTmaChunk);
+    mbar_expect_tx(&sm.bar[s], bytes);
+    tma_load_1d(buf + (size_t)s * kTmaChunk, (const void*)(src + off), bytes, &sm.bar[s]);
+  };
+  uint32_t issued = 0;
+  while (issued < nch && issued < (uint32_t)kTmaStages) issue(issued++);
+  for (uint32_t j = 0; j < nch; ++j) {
+    const uint32_t s = j % kTmaStages;
+    const uint32_t par = (phase >> s) & 1u;
+    uint32_t spins = 0;
+    bool landed = true;
+    while (!mbar_try_wait(&sm.bar[s], par)) {
+      if (++spins > (1u << 22)) {  // a bulk load that never lands: report and give up
+        set_error(P, -1, kErrIntern);
+        landed = false;
+        break;
+      }
+    }
+    if (!landed) {
+      tma_wait_all();
+      return;
+    }
+    phase ^= (1u << s);
+    const uint64_t off = (uint64_t)j * kTmaChunk;
+    const uint32_t bytes = (uint32_t)((n - (int64_t)off) < (int64_t)kTmaChunk ? (n - off) : kTmaChunk);
+    tma_store_1d((void*)(dst + off), buf + (size_t)s * kTmaChunk, bytes);
+    tma_commit();
+    if (issued < nch) {
+      tma_wait_read_all();  // stage s is free again once the store has read it
+      issue(issued++);
+    }
+  }
+  tma_wait_all();
+  sm.phase = phase;
+}
+
+__device__ void contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t src, int64_t n,
+                            const EngineParams& P) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (n <= 0) return;
+  if (((src | dst) & 15) == 0 && P.bulk_min > 0 && n >= P.bulk_min) {
+    const int64_t n16 = n & ~(int64_t)15;
+    tma_contig_copy(sm, buf, dst, src, n16, P);
+    for (int64_t q = n16 + tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+    return;
+  }
+  if (((src ^ dst) & 15) == 0) {
+    int64_t head = (int64_t)((16 - (src & 15)) & 15);
+    if (head > n) head = n;
+    for (int64_t q = tid; q < head; q += nt) copy_unit<1>(dst + q, src + q);
+    const uint64_t s = src + head, d = dst + head;
+    const int64_t nv = (n - head) >> 4;
+    int64_t i = tid;
+    for (; i + 3 * nt < nv; i += 4 * nt) {
+      uint4 a = ld_cg16((const void*)(s + 16 * i));
+      uint4 b = ld_cg16((const void*)(s + 16 * (i + nt)));
+      uint4 c = ld_cg16((const void*)(s + 16 * (i + 2 * nt)));
+      uint4 e = ld_cg16((const void*)(s + 16 * (i + 3 * nt)));
+      st16((void*)(d + 16 * i), a);
+      st16((void*)(d + 16 * (i + nt)), b);
+      st16((void*)(d + 16 * (i + 2 * nt)), c);
+      st16((void*)(d + 16 * (i + 3 * nt)), e);
+    }
+    for (; i < nv; i += nt) st16((void*)(d + 16 * i), ld_cg16((const void*)(s + 16 * i)));
+    const int64_t tail0 = head + (nv << 4);
+    for (int64_t q = tail0 + tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+    return;
+  }
+  if (((src ^ dst) & 3) == 0) {
+    int64_t head = (int64_t)((4 - (src & 3)) & 3);
+    if (head > n) head = n;
+    for (int64_t q = tid; q < head; q += nt) copy_unit<1>(dst + q, src + q);
+    const int64_t nw = (n - head) >> 2;
+    for (int64_t i = tid; i < nw; i += nt) copy_unit<4>(dst + head + 4 * i, src + head + 4 * i);
+    for (int64_t q = head + (nw << 2) + tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+    return;
+  }
+  for (int64_t q = tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+}
+
+__device__ void copy_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
+                          const EngineParams& P) {
+  const int64_t p0 = (int64_t)k * T.tile;
+  const int64_t p1 = (p0 + T.tile) < T.bytes ? (p0 + T.tile) : T.bytes;
+  if (p1 <= p0) return;
+  if (T.chunk == kContig) {
+    contig_copy(sm, buf, T.dst.base + p0, T.src.base + p0, p1 - p0, P);
+    return;
+  }
+  switch (T.unit) {
+    case 16: chunked_copy<16>(T, p0, p1); break;
+    case 8: chunked_copy<8>(T, p0, p1); break;
+    case 4: chunked_copy<4>(T, p0, p1); break;
+    case 2: chunked_copy<2>(T, p0, p1); break;
+    default: chunked_copy<1>(T, p0, p1); break;
+  }
+}
+
+// --- reductions: SUM over nr inputs, written to nr outputs ---
+struct AddF32 {
+  __device__ static uint32_t add(uint32_t a, uint32_t b) {
+    return __float_as_uint(__fadd_rn(__uint_as_float(a), __uint_as_float(b)));
+  }
+};
+struct AddI32 {
+  __device__ static uint32_t add(uint32_t a, uint32_t b) { return a + b; }
+};
+struct AddU8 {
+  __device__ static uint32_t add(uint32_t a, uint32_t b) { return __vadd4(a, b); }
+};
+
+template <class Op>
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b) {
+  return make_uint4(Op::add(a.x, b.x), Op::add(a.y, b.y), Op::add(a.z, b.z), Op::add(a.w, b.w));
+}
+__device__ __forceinline__ uint4 add4_i64(uint4 a, uint4 b) {
+  uint64_t x0 = ((uint64_t)a.y << 32 | a.x) + ((uint64_t)b.y << 32 | b.x);
+  uint64_t x1 = ((uint64_t)a.w << 32 | a.z) + ((uint64_t)b.w << 32 | b.z);
+  return make_uint4((uint32_t)x0, (uint32_t)(x0 >> 32), (uint32_t)x1, (uint32_t)(x1 >> 32));
+}
+__device__ __forceinline__ uint4 add4_f64(uint4 a, uint4 b) {
+  double x0 = __hiloint2double((int)a.y, (int)a.x), y0 = __hiloint2double((int)b.y, (int)b.x);
+  double x1 = __hiloint2double((int)a.w, (int)a.z), y1 = __hiloint2double((int)b.w, (int)b.z);
+  double r0 = __dadd_rn(x0, y0), r1 = __dadd_rn(x1, y1);
+  return make_uint4((uint32_t)__double2loint(r0), (uint32_t)__double2hiint(r0),
+                    (uint32_t)__double2loint(r1), (uint32_t)__double2hiint(r1));
+}
+__device__ __forceinline__ uint4 vadd(uint32_t dtype, uint4 a, uint4 b) {
+  switch (dtype) {
+    case 0: return add4<AddU8>(a, b);
+    case 1: return add4<AddI32>(a, b);
+    case 2: return add4_i64(a, b);
+    case 3: return add4<AddF32>(a, b);
+    default: return add4_f64(a, b);
+  }
+}
+// scalar element add on raw bits (esz bytes)
+__device__ __forceinline__ uint64_t sadd(uint32_t dtype, uint64_t a, uint64_t b) {
+  switch (dtype) {
+    case 0: return (uint8_t)(a + b);
+    case 1: return (uint32_t)(a + b);
+    case 2: return a + b;
+    case 3: return __float_as_uint(__fadd_rn(__uint_as_float((uint32_t)a), __uint_as_float((uint32_t)b)));
+    default: return (uint64_t)__double_as_longlong(
+        __dadd_rn(__longlong_as_double((long long)a), __longlong_as_double((long long)b)));
+  }
+}
+
+// Pairwise tree over ranks, built like a binary counter: x0+x1, x2+x3, then
+// (x0+x1)+(x2+x3), ...; leftovers fold from the top of the stack.
+template <class V, class Load, class Add>
+__device__ __forceinline__ V tree_sum(int nr, Load load, Add add) {
+  V stack[16];
+  int depth[16];
+  int sp = 0;
+  for (int k = 0; k < nr; ++k) {
+    V cur = load(k);
+    int dd = 0;
+    while (sp > 0 && depth[sp - 1] == dd) {
+      cur = add(stack[sp - 1], cur);
+      --sp;
+      ++dd;
+    }
+    stack[sp] = cur;
+    depth[sp] = dd;
+    ++sp;
+  }
+  V res = stack[sp - 1];
+  for (int i = sp - 2; i >= 0; --i) res = add(stack[i], res);
+  return res;
+}
+
+__device__ void reduce_tile(const Task& T, uint32_t k) {
+  const int64_t e0 = (int64_t)k * T.tile;
+  const int64_t e1 = (e0 + T.tile) < T.bytes ? (e0 + T.tile) : T.bytes;
+  if (e1 <= e0) return;
+  const uint64_t* ptrs = (const uint64_t*)T.ptrs;
+  const int nr = (int)T.nr;
+  const uint32_t dt = T.dtype;
+  const int64_t es = base_size(dt);
+  const bool tree = (T.mode == 1) && (dt == 3 || dt == 4);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int64_t vstart = e0, vend = e0;
+  if (T.unit == 16) {
+    const int64_t per = 16 / es;
+    vend = e0 + ((e1 - e0) / per) * per;
+    const int64_t nv = (vend - e0) / per;
+    for (int64_t v = tid; v < nv; v += nt) {
+      const int64_t boff = (e0 + v * per) * es;
+      uint4 acc;
+      if (tree) {
+        acc = tree_sum<uint4>(
+            nr, [&](int r) { return ld_cg16((const void*)(ptrs[r] + boff)); },
+            [&](uint4 a, uint4 b) { return vadd(dt, a, b); });
+      } else {
+        acc = ld_cg16((const void*)(ptrs[0] + boff));
+        int r = 1;
+        for (; r + 3 < nr; r += 4) {
+          uint4 a = ld_cg16((const void*)(ptrs[r] + boff));
+          uint4 b = ld_cg16((const void*)(ptrs[r + 1] + boff));
+          uint4 c = ld_cg16((const void*)(ptrs[r + 2] + boff));
+          uint4 d = ld_cg16((const void*)(ptrs[r + 3] + boff));
+          acc = vadd(dt, acc, a);
+          acc = vadd(dt, acc, b);
+          acc = vadd(dt, acc, c);
+          acc = vadd(dt, acc, d);
+        }
+        for (; r < nr; ++r) acc = vadd(dt, acc, ld_cg16((const void*)(ptrs[r] + boff)));
+      }
+      for (int r = 0; r < nr; ++r) st16((void*)(ptrs[nr + r] + boff), acc);
+    }
+    vstart = vend;
+  }
+  for (int64_t e = vstart + tid; e < e1; e += nt) {
+    const int64_t boff = e * es;
+    auto ld = [&](int r) -> uint64_t {
+      const uint64_t a = ptrs[r] + boff;
+      if (es == 1) return ld_cg1((const void*)a);
+      if (es == 4) return ld_cg4((const void*)a);
+      uint2 v = ld_cg8((const void*)a);
+      return ((uint64_t)v.y << 32) | v.x;
+    };
+    uint64_t acc;
+    if (tree) {
+      acc = tree_sum<uint64_t>(nr, ld, [&](uint64_t a, uint64_t b) { return sadd(dt, a, b); });
+    } else {
+      acc = ld(0);
+      for (int r = 1; r < nr; ++r) acc = sadd(dt, acc, ld(r));
+    }
+    for (int r = 0; r < nr; ++r) {
+      const uint64_t a = ptrs[nr + r] + boff;
+      if (es == 1) st1((void*)a, (uint8_t)acc);
+      else if (es == 4) st4((void*)a, (uint32_t)acc);
+      else st8((void*)a, make_uint2((uint32_t)acc, (uint32_t)(acc >> 32)));
+    }
+  }
+}
+
+// Claim one tile: thread 0 walks the task ring from task_head.
+// Returns false when there is no claimable tile right now.
+__device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
+  if (threadIdx.x == 0) {
+    sm.claim_task = -1;
+    Shared* sh = P.sh;
+    const uint64_t mask = (1ull << P.tq_log2) - 1;
+    for (int tries = 0; tries < 64; ++tries) {
+      const uint64_t i = ld_acq_gpu(&sh->task_head);
+      const uint64_t a = ld_acq_gpu(&sh->task_alloc);
+      if (i >= a) break;
+      Task* T = &P.tasks[i & mask];
+      const uint64_t c = ld_acq_gpu(&T->claim);
+      if ((uint32_t)(c >> 32) != (uint32_t)i) break;  // not published yet
+      const uint32_t k = (uint32_t)c;
+      const uint32_t nt = *(volatile uint32_t*)&T->ntiles;
+      if (k >= nt) {
+        atomicCAS((unsigned long long*)&sh->task_head, (unsigned long long)i,
+                  (unsigned long long)(i + 1));
+        continue;
+      }
+      if (atomicCAS((unsigned long long*)&T->claim, (unsigned long long)c,
+                    (unsigned long long)(c + 1)) == c) {
+        sm.claim_task = (int64_t)i;
+        sm.claim_tile = k;
+        sm.task = *T;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return sm.claim_task >= 0;
+}
+
+__device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
+  const Task& T = sm.task;
+  if (T.type == T_COPY) copy_tile(sm, buf, T, sm.claim_tile, P);
+  else if (T.type == T_REDUCE) reduce_tile(T, sm.claim_tile);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint64_t mask = (1ull << P.tq_log2) - 1;
+    atomicAdd(&P.tasks[(uint64_t)sm.claim_task & mask].tiles_done, 1u);
+  }
+}
+
+// ------------------------------------------------------------------------
+// control CTA
+// ------------------------------------------------------------------------
+struct Ctl {
+  const EngineParams& P;
+  CtaShared& sm;
+  int64_t round;
+  __device__ Ctl(const EngineParams& p, CtaShared& s) : P(p), sm(s), round(0) {}
+
+  __device__ uint64_t slots_mask() const { return (1ull << P.slots_log2) - 1; }
+
+  // --- 1. ingest: every thread polls one ring tail, then a warp per stream
+  // with new entries copies the descriptors ---
+  __device__ bool ingest() {
+    for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
+      SState& S = P.ss[g];
+      const int32_t flags = ld_acq_sys32(&P.sctl[g].flags);
+      S.flags = flags;
+      S.rank = ((volatile int32_t*)&P.sctl[g].rank)[0];
+      uint64_t tail = 0;
+      if (flags & SF_ACTIVE) tail = ld_acq_sys(&P.sctl[g].tail);
+      sm.cnt[g] = (flags & SF_ACTIVE) && tail > S.ingested ? (int32_t)(tail - S.ingested) : 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    bool any = false;
+    for (int g = warp; g < P.max_streams; g += nw) {
+      if (sm.cnt[g] == 0) continue;
+      SState& S = P.ss[g];
+      const uint64_t ing = S.ingested;
+      const uint64_t tail = ing + (uint64_t)sm.cnt[g];
+      any = true;
+      const int64_t n = (int64_t)(tail - ing);
+      const uint64_t t0 = now_ns();
+      for (int64_t i = lane; i < n; i += 32) {
+        const uint64_t seq = ing + 1 + (uint64_t)i;
+        const Desc* src = P.rings + (((size_t)g << P.slots_log2) + ((seq - 1) & slots_mask()));
+        DOp* o = op_at(P, g, seq);
+        uint4* dd = reinterpret_cast<uint4*>(&o->d);
+        const uint4* ss = reinterpret_cast<const uint4*>(src);
+        uint4 v0 = ld_vol16(ss), v1 = ld_vol16(ss + 1), v2 = ld_vol16(ss + 2), v3 = ld_vol16(ss + 3);
+        dd[0] = v0;
+        dd[1] = v1;
+        dd[2] = v2;
+        dd[3] = v3;
+        o->partner = 0;
+        o->bytes = op_bytes(o->d);
+        o->stage = 0;
+        o->lstate = 0;
+        o->lround = 0;
+        o->pflags = 0;
+        o->err = 0;
+        o->msrc = 0;
+        o->mtag = 0;
+        o->wscan = 0;
+        o->pscan = 0;
+        o->t_ingest = (int64_t)t0;
+      }
+      __syncwarp();
+      if (lane == 0) S.ingested = tail;
+    }
+    return any;
+  }
+
+  // --- 2a. logical advance (thread per stream) ---
+  __device__ bool done_before(const DOp* o) const { return o->lstate == 2 && o->lround < round; }
+
+  __device__ bool arrive(int g, DOp* o, uint64_t seq) {
+    const int c = o->d.comm, r = o->d.rank;
+    int64_t* ni = &P.next_inst[(size_t)c * P.nranks + r];
+    const int64_t k = *ni;
+    InstSlot* slot = &P.inst[(size_t)c * P.iw + (k % P.iw)];
+    const unsigned long long want = (unsigned long long)(k + 1);
+    unsigned long long old = atomicCAS((unsigned long long*)&slot->k1, 0ull, want);
+    if (old != 0 && old != want) return false;  // window full: try again next round
+    P.inst_refs[((size_t)c * P.iw + (k % P.iw)) * P.nranks + r] = make_ref(g, seq);
+    *ni = k + 1;
+    __threadfence_block();
+    atomicAdd(&slot->arrived, 1);
+    return true;
+  }
+
+  __device__ bool advance_stream(int g) {
+    SState& S = P.ss[g];
+    int n = 0;
+    bool arrived = false;
+    uint64_t cur = S.cursor;
+    uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+    const int ndomains_per_comm = P.nranks;
+    while (cur <= S.ingested) {
+      DOp* o = op_at(P, g, cur);
+      const uint32_t k = kw_kind(o->d.kw);
+      if (is_send(k)) {
+        o->lstate = 2;  // eager: complete at post
+        o->lround = (int32_t)round;
+        const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.peer;
+        posts[n++] = (dom << 40) | cur;
+        ++cur;
+        continue;
+      }
+      if (k == K_IRECV) {
+        o->lstate = 1;
+        const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank;
+        posts[n++] = (dom << 40) | cur;
+        ++cur;
+        continue;
+      }
+      if (k == K_RECV) {
+        if (o->lstate == 0) {
+          o->lstate = 1;
+          const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank;
+          posts[n++] = (dom << 40) | cur;
+          break;
+        }
+        if (done_before(o)) {
+          ++cur;
+          continue;
+        }
+        break;
+      }
+      if (k == K_WAIT) {
+        const DOp* q = op_at(P, g, o->d.aux);
+        if (o->d.aux == 0 || done_before(q)) {
+          o->lstate = 2;
+          o->lround = (int32_t)round;
+          ++cur;
+          continue;
+        }
+        break;
+      }
+      if (k == K_WAITALL) {
+        const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+        const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+        uint32_t w = o->wscan;
+        while (w < (uint32_t)o->d.n32) {
+          const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
+          if (rs != 0 && !done_before(op_at(P, g, rs))) break;
+          ++w;
+        }
+        o->wscan = w;
+        if (w >= (uint32_t)o->d.n32) {
+          o->lstate = 2;
+          o->lround = (int32_t)round;
+          ++cur;
+          continue;
+        }
+        break;
+      }
+      if (k == K_ALLREDUCE) {
+        if (o->lstate == 0) {
+          if (arrive(g, o, cur)) {
+            o->lstate = 1;
+            arrived = true;
+          }
+          break;
+        }
+        if (done_before(o)) {
+          ++cur;
+          continue;
+        }
+        break;
+      }
+      // unknown kind: fail the op, skip it
+      o->err = kErrArg;
+      o->lstate = 2;
+      o->lround = (int32_t)round;
+      o->pflags |= PF_COMPLETE | PF_DELIVERED | PF_WAITED;
+      set_error(P, g, kErrArg);
+      ++cur;
+    }
+    const bool moved = (cur != S.cursor) || n > 0 || arrived;
+    S.cursor = cur;
+    S.nposts = n;
+    sm.cnt[g] = n;
+    if (moved) sm.any = 1;
+    return moved;
+  }
+
+  // --- 2b. matching (warp per domain) ---
+  __device__ int64_t q_find(const QEntry* q, const QHead& h, uint32_t qmask, bool is_send_post,
+                            int32_t src, int32_t tag) {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32) {
+      const uint32_t idx = base + (uint32_t)lane;
+      bool hit = false;
+      if ((int32_t)(h.tail - idx) > 0) {
+        const QEntry e = q[idx & qmask];
+        if (e.ref != 0) {
+          if (is_send_post)  // looking for a posted receive accepting (src, tag)
+            hit = (e.src == kAnySource || e.src == src) && (e.tag == kAnyTag || e.tag == tag);
+          else  // looking for an unexpected send the receive (src, tag) accepts
+            hit = (src == kAnySource || src == e.src) && (tag == kAnyTag || tag == e.tag);
+        }
+      }
+      const unsigned b = __ballot_sync(FULL, hit);
+      if (b) return (int64_t)(base + (uint32_t)(__ffs(b) - 1));
+    }
+    return -1;
+  }
+
+  __device__ void q_remove(QEntry* q, QHead& h, uint32_t qmask, uint32_t idx) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) q[idx & qmask].ref = 0;
+    __syncwarp();
+    if (idx != h.head) return;
+    // advance head over tombstones
+    uint32_t head = h.head;
+    while ((int32_t)(h.tail - head) > 0) {
+      const uint32_t i = head + (uint32_t)lane;
+      const bool live = (int32_t)(h.tail - i) > 0 && q[i & qmask].ref != 0;
+      const bool inrange = (int32_t)(h.tail - i) > 0;
+      const unsigned b = __ballot_sync(FULL, live);
+      const unsigned r = __ballot_sync(FULL, inrange);
+      if (b) {
+        head += (uint32_t)(__ffs(b) - 1);
+        break;
+      }
+      head += (uint32_t)__popc(r);
+    }
+    if (lane == 0) h.head = head;
+    __syncwarp();
+  }
+
+  __device__ bool q_push(QEntry* q, QHead& h, uint32_t qmask, QEntry e) {
+    if ((h.tail - h.head) > qmask) return false;
+    if ((threadIdx.x & 31) == 0) {
+      q[h.tail & qmask] = e;
+      h.tail = h.tail + 1;
+    }
+    __syncwarp();
+    return true;
+  }
+
+  __device__ void pair(uint64_t sref, uint64_t rref) {
+    if ((threadIdx.x & 31) != 0) return;
+    DOp* s = op_ref(P, sref);
+    DOp* r = op_ref(P, rref);
+    const int64_t sent = s->bytes;
+    const int64_t cap = op_bytes(r->d);
+    r->partner = sref;
+    r->bytes = sent < cap ? sent : cap;
+    r->err = sent > cap ? kErrTruncate : 0;
+    r->msrc = s->d.rank;
+    r->mtag = s->d.tag;
+    r->lstate = 2;
+    r->lround = (int32_t)round;
+    s->partner = rref;
+    atomicOr(&r->pflags, PF_MATCHED);
+    atomicOr(&s->pflags, PF_MATCHED);
+  }
+
+  __device__ void match_domain(uint32_t d) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t qmask = (1u << P.qcap_log2) - 1;
+    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
+    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
+    QHead ph = P.pqh[d], uh = P.uqh[d];
+    for (int g = 0; g < P.max_streams; ++g) {
+      const int n = sm.cnt[g];
+      if (n == 0) continue;
+      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        uint64_t pv = 0;
+        bool mine = false;
+        if (i < n) {
+          pv = posts[i];
+          mine = (uint32_t)(pv >> 40) == d;
+        }
+        unsigned b = __ballot_sync(FULL, mine);
+        while (b) {
+          const int src_lane = __ffs(b) - 1;
+          b &= b - 1;
+          const uint64_t seq = __shfl_sync(FULL, pv, src_lane) & ((1ull << 40) - 1);
+          const DOp* o = op_at(P, g, seq);
+          const uint32_t kind = kw_kind(o->d.kw);
+          const uint64_t ref = make_ref(g, seq);
+          if (is_send(kind)) {
+            const int32_t src = o->d.rank, tag = o->d.tag;
+            const int64_t hit = q_find(pq, ph, qmask, true, src, tag);
+            if (hit >= 0) {
+              const uint64_t rref = pq[(uint32_t)hit & qmask].ref;
+              q_remove(pq, ph, qmask, (uint32_t)hit);
+              pair(ref, rref);
+            } else if (!q_push(uq, uh, qmask, QEntry{ref, src, tag})) {
+              if (lane == 0) set_error(P, g, kErrNoMem);
+            }
+          } else {
+            const int32_t src = o->d.peer, tag = o->d.tag;
+            const int64_t hit = q_find(uq, uh, qmask, false, src, tag);
+            if (hit >= 0) {
+              const uint64_t sref = uq[(uint32_t)hit & qmask].ref;
+              q_remove(uq, uh, qmask, (uint32_t)hit);
+              pair(sref, ref);
+            } else if (!q_push(pq, ph, qmask, QEntry{ref, src, tag})) {
+              if (lane == 0) set_error(P, g, kErrNoMem);
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (lane == 0) {
+      P.pqh[d] = ph;
+      P.uqh[d] = uh;
+    }
+  }
+
+  // --- 2c. collectives (thread per instance slot) ---
+  __device__ void collectives() {
+    const int nslots = P.max_comms * P.iw;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+      InstSlot* s = &P.inst[i];
+      if (s->k1 == 0 || s->state != 0) continue;
+      if (*(volatile int32_t*)&s->arrived < P.nranks) continue;
+      const uint64_t* refs = P.inst_refs + (size_t)i * P.nranks;
+      // all arrivals must agree on count, type and mode
+      const DOp* o0 = op_ref(P, refs[0]);
+      int err = 0;
+      for (int r = 1; r < P.nranks; ++r) {
+        const DOp* o = op_ref(P, refs[r]);
+        if (o->d.count != o0->d.count || o->d.kw != o0->d.kw) err = kErrArg;
+      }
+      s->err = err;
+      for (int r = 0; r < P.nranks; ++r) {
+        DOp* o = op_ref(P, refs[r]);
+        o->lstate = 2;
+        o->lround = (int32_t)round;
+        o->err = err;
+      }
+      s->state = 1;
+      sm.any = 1;
+    }
+  }
+
+  // --- task creation ---
+  // Allocate a task id; fails when the ring is full.  task_retire only moves
+  // in a phase of its own, so a CAS on task_alloc suffices.
+  __device__ Task* task_new(uint64_t& id) {
+    Shared* sh = P.sh;
+    const uint64_t cap = 1ull << P.tq_log2;
+    const uint64_t r = *(volatile uint64_t*)&sh->task_retire;
+    uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+    for (;;) {
+      if (a - r >= cap) {
+        sm.ntask_full = 1;
+        return nullptr;
+      }
+      const uint64_t old = atomicCAS((unsigned long long*)&sh->task_alloc, (unsigned long long)a,
+                                     (unsigned long long)(a + 1));
+      if (old == a) break;
+      a = old;
+    }
+    id = a;
+    return &P.tasks[id & (cap - 1)];
+  }
+  __device__ void task_publish(Task* T, uint64_t id) {
+    T->tiles_done = 0;
+    __threadfence();
+    st_rel_gpu(&T->claim, (id << 32));
+  }
+
+  __device__ void fill_copy(Task* T, const Layout& src, const Layout& dst, int64_t bytes) {
+    T->type = T_COPY;
+    T->src = src;
+    T->dst = dst;
+    T->bytes = bytes;
+    int64_t C;
+    if (src.seg == kContig && dst.seg == kContig) C = kContig;
+    else if (src.seg == kContig) C = dst.seg;
+    else if (dst.seg == kContig) C = src.seg;
+    else C = gcd64(src.seg, dst.seg);
+    T->chunk = C;
+    uint32_t U = 16;
+    if (C != kContig) {
+      auto bad = [&](uint32_t u) {
+        if ((C % u) || (src.base % u) || (dst.base % u)) return true;
+        if (src.seg != kContig && ((src.stride % u) || (src.extent % u))) return true;
+        if (dst.seg != kContig && ((dst.stride % u) || (dst.extent % u))) return true;
+        return false;
+      };
+      while (U > 1 && bad(U)) U >>= 1;
+    }
+    T->unit = U;
+    int64_t tile = P.tile_bytes;
+    if (C != kContig) tile = C >= tile ? C : (tile / C) * C;
+    T->tile = tile;
+    T->ntiles = (uint32_t)((bytes + tile - 1) / tile);
+  }
+
+  // deliver send s (payload in its buffer or in staging) into recv r
+  __device__ bool create_deliver(uint64_t sref, uint64_t rref, bool from_stage) {
+    DOp* s = op_ref(P, sref);
+    DOp* r = op_ref(P, rref);
+    Layout src, dst;
+    if (from_stage) {
+      src.base = (uint64_t)(P.stage + (s->stage - 1));
+      src.seg = kContig;
+      src.stride = 0;
+      src.per = 1;
+      src.extent = 0;
+    } else {
+      make_layout(src, s->d.buf, s->d);
+    }
+    make_layout(dst, r->d.buf, r->d);
+    const int64_t bytes = r->bytes;
+    atomicOr(&r->pflags, PF_SCHED);
+    if (bytes <= 0) {  // nothing to move: complete now
+      atomicOr(&r->pflags, PF_DELIVERED | PF_COMPLETE);
+      if (from_stage) stage_free(s);
+      atomicOr(&s->pflags, PF_DELIVERED | PF_COMPLETE);
+      sm.any = 1;
+      return true;
+    }
+    uint64_t id;
+    Task* T = task_new(id);
+    if (!T) {
+      atomicAnd(&r->pflags, ~PF_SCHED);
+      return false;
+    }
+    fill_copy(T, src, dst, bytes);
+    T->action = from_stage ? A_DELIVER_STAGED : A_DELIVER;
+    T->ref_s = sref;
+    T->ref_r = rref;
+    task_publish(T, id);
+    sm.any = 1;
+    return true;
+  }
+
+  // --- staging arena (thread 0 only) ---
+  __device__ bool stage_alloc(uint64_t size, uint64_t& off) {
+    Shared* sh = P.sh;
+    const uint64_t cap = (uint64_t)P.stage_bytes;
+    const uint64_t srmask = (1ull << P.sr_log2) - 1;
+    size = (size + 255) & ~255ull;
+    if (size > cap) return false;
+    if (sh->sr_head - sh->sr_tail + 2 > srmask + 1) return false;
+    uint64_t head = sh->st_head;
+    uint64_t pos = head % cap;
+    if (pos + size > cap) {  // skip the tail end of the arena
+      const uint64_t pad = cap - pos;
+      if ((head + pad + size) - sh->st_tail > cap) return false;
+      StageRec& d = P.srec[sh->sr_head & srmask];
+      d.off = head;
+      d.size = pad;
+      d.freed = 1;
+      sh->sr_head++;
+      head += pad;
+      pos = 0;
+    }
+    if ((head + size) - sh->st_tail > cap) return false;
+    StageRec& rec = P.srec[sh->sr_head & srmask];
+    rec.off = head;
+    rec.size = size;
+    rec.freed = 0;
+    sh->sr_head++;
+    sh->st_head = head + size;
+    off = pos;
+    return true;
+  }
+  __device__ void stage_free(DOp* s) {
+    // mark the record whose arena position holds this payload; records are
+    // found by offset (the staging offset is unique among live records)
+    Shared* sh = P.sh;
+    const uint64_t srmask = (1ull << P.sr_log2) - 1;
+    const uint64_t cap = (uint64_t)P.stage_bytes;
+    const uint64_t want = s->stage - 1;
+    for (uint64_t i = sh->sr_tail; i != sh->sr_head; ++i) {
+      StageRec& rec = P.srec[i & srmask];
+      if (!rec.freed && (rec.off % cap) == want) {
+        atomicExch(&rec.freed, 1);
+        break;
+      }
+    }
+    s->stage = 0;
+  }
+  __device__ void stage_reclaim() {
+    Shared* sh = P.sh;
+    const uint64_t srmask = (1ull << P.sr_log2) - 1;
+    while (sh->sr_tail != sh->sr_head) {
+      StageRec& rec = P.srec[sh->sr_tail & srmask];
+      if (!*(volatile int32_t*)&rec.freed) break;
+      sh->st_tail = rec.off + rec.size;
+      sh->sr_tail++;
+    }
+  }
+
+  // --- 3a. per stream: physical completion, completion word, retirement ---
+  __device__ void write_status(uint64_t addr, int32_t src, int32_t tag, int32_t err, int64_t bytes) {
+    if (!addr) return;
+    int32_t* p = (int32_t*)addr;
+    p[0] = src;
+    p[1] = tag;
+    p[2] = err;
+    p[3] = 0;
+    *(int64_t*)(p + 4) = bytes;
+  }
+  __device__ void request_status(uint64_t addr, const DOp* q) {
+    if (is_recv(kw_kind(q->d.kw))) write_status(addr, q->msrc, q->mtag, q->err, q->bytes);
+    else write_status(addr, kAnySource, kAnyTag, q->err, 0);
+  }
+
+  __device__ bool phys_done(int g, DOp* o, uint64_t seq) {
+    const uint32_t k = kw_kind(o->d.kw);
+    if (k == K_SEND || k == K_RECV || k == K_ALLREDUCE) return (o->pflags & PF_COMPLETE) != 0;
+    if (k == K_WAIT) {
+      if (o->d.aux == 0) return true;
+      return (op_at(P, g, o->d.aux)->pflags & PF_COMPLETE) != 0;
+    }
+    if (k == K_WAITALL) {
+      const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+      const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+      uint32_t w = o->pscan;
+      while (w < (uint32_t)o->d.n32) {
+        const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
+        if (rs != 0 && !(op_at(P, g, rs)->pflags & PF_COMPLETE)) break;
+        ++w;
+      }
+      o->pscan = w;
+      return w >= (uint32_t)o->d.n32;
+    }
+    return true;
+  }
+
+  __device__ void finish_blocking(int g, DOp* o) {
+    const uint32_t k = kw_kind(o->d.kw);
+    if (k == K_RECV) {
+      write_status(o->d.status, o->msrc, o->mtag, o->err, o->bytes);
+      if (o->err) set_error(P, g, o->err);
+    } else if (k == K_WAIT) {
+      if (o->d.aux) {
+        DOp* q = op_at(P, g, o->d.aux);
+        request_status(o->d.status, q);
+        if (q->err) set_error(P, g, q->err);
+        atomicOr(&q->pflags, PF_WAITED);
+      }
+    } else if (k == K_WAITALL) {
+      const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+      const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+      for (uint32_t w = 0; w < (uint32_t)o->d.n32; ++w) {
+        const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
+        if (rs == 0) {
+          if (o->d.status) write_status(o->d.status + 24ull * w, kAnySource, kAnyTag, 0, 0);
+          continue;
+        }
+        DOp* q = op_at(P, g, rs);
+        if (o->d.status) request_status(o->d.status + 24ull * w, q);
+        if (q->err) set_error(P, g, q->err);
+        atomicOr(&q->pflags, PF_WAITED);
+      }
+    } else if (k == K_ALLREDUCE || k == K_SEND) {
+      if (o->err) set_error(P, g, o->err);
+    }
+    // a blocking send stays unfinished until its payload is delivered
+    atomicOr(&o->pflags, PF_COMPLETE);
+  }
+
+  __device__ bool finished(const DOp* o) const {
+    const uint32_t k = kw_kind(o->d.kw);
+    const int32_t f = o->pflags;
+    switch (k) {
+      case K_SEND: return (f & PF_DELIVERED) != 0;
+      case K_ISEND: return (f & PF_DELIVERED) && (f & PF_WAITED);
+      case K_RECV: return (f & PF_COMPLETE) != 0;
+      case K_IRECV: return (f & PF_COMPLETE) && (f & PF_WAITED);
+      default: return (f & PF_COMPLETE) != 0;
+    }
+  }
+
+  __device__ bool stream_physical(int g, int64_t now) {
+    SState& S = P.ss[g];
+    if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return false;
+    bool prog = false;
+    // completion word: blocking ops complete in order
+    uint64_t pc = S.pc;
+    uint64_t newdone = S.done;
+    while (pc <= S.ingested) {
+      DOp* o = op_at(P, g, pc);
+      const uint32_t k = kw_kind(o->d.kw);
+      if (!is_blocking(k)) {
+        ++pc;
+        continue;
+      }
+      if (!phys_done(g, o, pc)) break;
+      finish_blocking(g, o);
+      newdone = pc;
+      ++pc;
+    }
+    if (pc != S.pc) prog = true;
+    S.pc = pc;
+    if (newdone != S.done) {
+      S.done = newdone;
+      fence_sc_sys();
+      st_rlx_sys(&P.done[g], newdone);
+      st_rlx_sys(&P.sctl[g].done, newdone);
+      prog = true;
+    }
+    // how far the stream has executed
+    if (S.flags & SF_EXCLUSIVE) {
+      S.reached = pc <= S.ingested ? pc : S.ingested;
+    } else {
+      uint64_t db = ld_rlx_sys(&P.doorbell[g]);
+      S.reached = db;
+    }
+    // stall clock: the stream sits at blocking op pc
+    const bool stalled = pc <= S.ingested && S.reached >= pc;
+    if (stalled) {
+      if (S.stall_t0 == 0) S.stall_t0 = now;
+    } else {
+      S.stall_t0 = 0;
+    }
+    // retire in order
+    uint64_t rt = S.retire;
+    uint64_t wlr = S.wl_retired;
+    while (rt < S.ingested && rt + 1 < S.cursor) {
+      const DOp* o = op_at(P, g, rt + 1);
+      if (!finished(o)) break;
+      if (kw_kind(o->d.kw) == K_WAITALL) wlr = o->d.aux + (uint64_t)o->d.n32;
+      ++rt;
+    }
+    if (rt != S.retire) {
+      S.retire = rt;
+      S.wl_retired = wlr;
+      st_rlx_sys(&P.sctl[g].wl_retired, wlr);
+      st_rel_sys(&P.sctl[g].retired, rt);
+      prog = true;
+    }
+    return prog;
+  }
+
+  // --- 3b. per stream: schedule deliveries and stage stalled sends ---
+  __device__ void stream_schedule(int g, int64_t now) {
+    SState& S = P.ss[g];
+    if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return;
+    const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+    uint64_t sc = S.sched > S.retire ? S.sched : S.retire + 1;
+    bool advancing = true;
+    for (uint64_t seq = sc; seq <= lim; ++seq) {
+      DOp* o = op_at(P, g, seq);
+      const uint32_t k = kw_kind(o->d.kw);
+      bool settled = true;
+      if (is_recv(k)) {
+        const int32_t f = o->pflags;
+        if (!(f & PF_SCHED)) {
+          settled = false;
+          if (f & PF_MATCHED) {
+            const uint64_t sref = o->partner;
+            DOp* s = op_ref(P, sref);
+            const int32_t sf = *(volatile int32_t*)&s->pflags;
+            if (sf & PF_STAGED) {
+              settled = create_deliver(sref, make_ref(g, seq), true);
+            } else if (!(sf & PF_SCHED)) {
+              const SState& SS = P.ss[ref_stream(sref)];
+              if (*(volatile uint64_t*)&SS.reached >= ref_seq(sref)) {
+                const int32_t old = atomicOr(&s->pflags, PF_SCHED);
+                if (!(old & PF_SCHED)) {
+                  settled = create_deliver(sref, make_ref(g, seq), false);
+                  if (!settled) atomicAnd(&s->pflags, ~PF_SCHED);
+                }
+              }
+            }
+          }
+        }
+      } else if (is_send(k)) {
+        const int32_t f = o->pflags;
+        if (!(f & (PF_SCHED | PF_COMPLETE))) {
+          settled = false;
+          // stage when the stream sits at a blocking op at or after this send
+          if (S.stall_t0 != 0 && now - S.stall_t0 >= P.stage_delay_ns && seq <= S.pc) {
+            const int32_t old = atomicOr(&o->pflags, PF_SCHED);
+            if (!(old & PF_SCHED)) {
+              const int slot = atomicAdd(&sm.nstage, 1);
+              if (slot < kMaxStagePerTick) {
+                sm.stage_ref[slot] = make_ref(g, seq);
+              } else {
+                atomicAnd(&o->pflags, ~PF_SCHED);
+              }
+            }
+          }
+        }
+      }
+      if (advancing && settled) sc = seq + 1;
+      else advancing = false;
+    }
+    S.sched = sc;
+  }
+
+  // thread 0: create staging tasks for the collected sends
+  __device__ void make_stage_tasks() {
+    const int n = sm.nstage < kMaxStagePerTick ? sm.nstage : kMaxStagePerTick;
+    for (int i = 0; i < n; ++i) {
+      const uint64_t sref = sm.stage_ref[i];
+      DOp* s = op_ref(P, sref);
+      const int64_t bytes = s->bytes;
+      uint64_t off = 0;
+      if (bytes > 0 && !stage_alloc((uint64_t)bytes, off)) {
+        atomicAnd(&s->pflags, ~PF_SCHED);  // arena full: retry next tick
+        continue;
+      }
+      if (bytes <= 0) {
+        s->stage = 1;
+        atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
+        atomicAnd(&s->pflags, ~PF_SCHED);
+        continue;
+      }
+      s->stage = off + 1;
+      Layout src, dst;
+      make_layout(src, s->d.buf, s->d);
+      dst.base = (uint64_t)(P.stage + off);
+      dst.seg = kContig;
+      dst.stride = 0;
+      dst.per = 1;
+      dst.extent = 0;
+      uint64_t id;
+      Task* T = task_new(id);
+      if (!T) {
+        stage_free(s);
+        atomicAnd(&s->pflags, ~PF_SCHED);
+        continue;
+      }
+      fill_copy(T, src, dst, bytes);
+      T->action = A_STAGE;
+      T->ref_s = sref;
+      T->ref_r = 0;
+      task_publish(T, id);
+      atomicOr(&s->pflags, PF_STAGING);
+      atomicAdd((unsigned long long*)&P.wctl->counters[5], 1ull);
+    }
+    sm.nstage = 0;
+  }
+
+  // --- 3c. allreduce instances whose ranks have all reached them ---
+  __device__ void schedule_reduce() {
+    const int nslots = P.max_comms * P.iw;
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+      InstSlot* s = &P.inst[i];
+      if (s->k1 == 0 || s->state != 1) continue;
+      const uint64_t* refs = P.inst_refs + (size_t)i * P.nranks;
+      bool ready = true;
+      for (int r = 0; r < P.nranks && ready; ++r) {
+        const uint64_t ref = refs[r];
+        if (*(volatile uint64_t*)&P.ss[ref_stream(ref)].reached < ref_seq(ref)) ready = false;
+      }
+      if (!ready) continue;
+      const DOp* o0 = op_ref(P, refs[0]);
+      const int64_t n = o0->d.count;
+      if (s->err || n <= 0) {
+        for (int r = 0; r < P.nranks; ++r) atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+        s->state = 0;
+        s->arrived = 0;
+        __threadfence();
+        atomicExch((unsigned long long*)&s->k1, 0ull);
+        sm.any = 1;
+        continue;
+      }
+      uint64_t* ptrs = P.reduce_ptrs + (size_t)i * 2 * P.nranks;
+      bool aligned = true;
+      for (int r = 0; r < P.nranks; ++r) {
+        const DOp* o = op_ref(P, refs[r]);
+        ptrs[r] = o->d.buf;
+        ptrs[P.nranks + r] = o->d.aux;
+        if (((o->d.buf | o->d.aux) & 15) != 0) aligned = false;
+      }
+      const uint32_t dt = kw_base(o0->d.kw);
+      const int64_t es = base_size(dt);
+      uint64_t id;
+      Task* T = task_new(id);
+      if (!T) continue;
+      T->type = T_REDUCE;
+      T->action = A_REDUCE;
+      T->bytes = n;
+      int64_t tile = P.tile_bytes / (es * (P.nranks < 8 ? 1 : P.nranks / 8));
+      tile = tile < 256 ? 256 : (tile & ~(int64_t)15);
+      T->tile = tile;
+      T->ntiles = (uint32_t)((n + tile - 1) / tile);
+      T->nr = (uint32_t)P.nranks;
+      T->dtype = dt;
+      T->mode = kw_mode(o0->d.kw);
+      T->unit = aligned ? 16u : (uint32_t)es;
+      T->ptrs = (uint64_t)ptrs;
+      T->ref_s = (uint64_t)i;
+      T->ref_r = 0;
+      T->chunk = 0;
+      s->state = 2;
+      task_publish(T, id);
+      atomicAdd((unsigned long long*)&P.wctl->counters[7], 1ull);
+      sm.any = 1;
+    }
+  }
+
+  // --- 4. finished tasks (thread per task in flight) ---
+  __device__ void complete_tasks() {
+    Shared* sh = P.sh;
+    const uint64_t mask = (1ull << P.tq_log2) - 1;
+    const uint64_t r0 = *(volatile uint64_t*)&sh->task_retire;
+    const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+    for (uint64_t id = r0 + threadIdx.x; id < a; id += blockDim.x) {
+      Task* T = &P.tasks[id & mask];
+      if (T->type == 0) continue;  // already processed
+      if ((uint32_t)(ld_acq_gpu(&T->claim) >> 32) != (uint32_t)id) continue;
+      if (ld_acq_gpu32(&T->tiles_done) < T->ntiles) continue;
+      if (T->type == T_COPY) {
+        DOp* s = op_ref(P, T->ref_s);
+        if (T->action == A_STAGE) {
+          atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
+          atomicAnd(&s->pflags, ~(PF_SCHED | PF_STAGING));
+        } else {
+          DOp* r = op_ref(P, T->ref_r);
+          if (T->action == A_DELIVER_STAGED) stage_free(s);
+          atomicOr(&r->pflags, PF_DELIVERED | PF_COMPLETE);
+          atomicOr(&s->pflags, PF_DELIVERED | PF_COMPLETE);
+          atomicAdd((unsigned long long*)&P.wctl->counters[2], 1ull);
+        }
+        atomicAdd((unsigned long long*)&P.wctl->counters[3], (unsigned long long)T->bytes);
+      } else if (T->type == T_REDUCE) {
+        InstSlot* s = &P.inst[T->ref_s];
+        const uint64_t* refs = P.inst_refs + (size_t)T->ref_s * P.nranks;
+        for (int r = 0; r < P.nranks; ++r)
+          atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+        s->state = 0;
+        s->arrived = 0;
+        __threadfence();
+        atomicExch((unsigned long long*)&s->k1, 0ull);
+        atomicAdd((unsigned long long*)&P.wctl->counters[3],
+                  (unsigned long long)(T->bytes * base_size(T->dtype) * P.nranks));
+      }
+      atomicAdd((unsigned long long*)&P.wctl->counters[4], 1ull);
+      T->type = 0;
+      sm.any = 1;
+    }
+  }
+};
+
+// Release every stream's waiters without moving data (watchdog / failed world).
+__device__ void release_all(const EngineParams& P, int err) {
+  for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
+    SState& S = P.ss[g];
+    if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) continue;
+    for (uint64_t seq = S.retire + 1; seq <= S.ingested; ++seq) {
+      DOp* o = op_at(P, g, seq);
+      if (!(o->pflags & PF_COMPLETE)) {
+        o->err = err;
+        if (kw_kind(o->d.kw) == K_RECV || kw_kind(o->d.kw) == K_WAIT || kw_kind(o->d.kw) == K_WAITALL) {
+          if (o->d.status && kw_kind(o->d.kw) != K_WAITALL) {
+            int32_t* p = (int32_t*)o->d.status;
+            p[2] = err;
+          }
+        }
+      }
+      o->pflags |= PF_COMPLETE | PF_DELIVERED | PF_WAITED;
+    }
+    S.pc = S.ingested + 1;
+    S.cursor = S.ingested + 1;
+    S.sched = S.ingested + 1;
+    S.done = S.ingested;
+    S.retire = S.ingested;
+    fence_sc_sys();
+    st_rlx_sys(&P.done[g], S.ingested);
+    st_rlx_sys(&P.sctl[g].done, S.ingested);
+    st_rel_sys(&P.sctl[g].retired, S.ingested);
+    if (P.sctl[g].error == 0) atomicCAS(&P.sctl[g].error, 0, err);
+  }
+}
+
+__device__ void grid_barrier(const EngineParams& P, int nctas) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Shared* sh = P.sh;
+    const uint32_t gen = ld_acq_gpu32(&sh->bar_gen);
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&sh->bar_count, 1u);
+    if (arrived == (uint32_t)nctas - 1) {
+      sh->bar_count = 0;
+      __threadfence();
+      st_rel_gpu32(&sh->bar_gen, gen + 1);
+    } else {
+      const uint64_t t0 = now_ns();
+      while (ld_acq_gpu32(&sh->bar_gen) == gen) {
+        __nanosleep(200);
+        if ((int64_t)(now_ns() - t0) > P.watchdog_ns) {
+          set_error(P, -1, kErrTimeout);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
+  Ctl C(P, sm);
+  Shared* sh = P.sh;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    C.round = (int64_t)sh->round;
+    sm.nstage = 0;
+  }
+  __syncthreads();
+  C.round = (int64_t)*(volatile uint64_t*)&sh->round;
+  int64_t last_prog = (int64_t)now_ns();
+  int64_t idle_since = last_prog;
+  uint64_t ticks = 0;
+  const bool failed_at_start = ld_acq_sys32(&P.wctl->failed) != 0;
+  for (;;) {
+    ++ticks;
+    const int64_t now = (int64_t)now_ns();
+    if (tid == 0) {
+      sm.any = 0;
+      sm.ntask_full = 0;
+      st_rlx_sys(&P.wctl->heartbeat, (uint64_t)now);
+    }
+    __syncthreads();
+    // 1. ingest
+    const bool ing = C.ingest();
+    if (ing) sm.any = 1;
+    __syncthreads();
+    if (failed_at_start || ld_vol32(&P.wctl->failed)) {
+      if (tid == 0) sm.pending = 0;
+      release_all(P, kErrTimeout);
+      __syncthreads();
+    } else {
+      // 2. logical rounds
+      for (int r = 0; r < kMaxRoundsPerTick; ++r) {
+        if (tid == 0) sm.flag = 0;
+        for (int g = tid; g < P.max_streams; g += blockDim.x) sm.cnt[g] = 0;
+        __syncthreads();
+        int local_any = 0;
+        for (int g = tid; g < P.max_streams; g += blockDim.x) {
+          SState& S = P.ss[g];
+          if (!(S.flags & SF_ACTIVE) && S.cursor > S.ingested) continue;
+          if (C.advance_stream(g)) local_any = 1;
+        }
+        if (local_any) atomicOr(&sm.flag, 1);
+        __syncthreads();
+        const bool moved = sm.flag != 0;
+        if (moved) {
+          const int warp = tid >> 5, nw = blockDim.x >> 5;
+          const uint32_t nd = (uint32_t)(P.max_comms * P.nranks);
+          for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
+          __syncthreads();
+        }
+        C.collectives();
+        __syncthreads();
+        if (tid == 0) {
+          sh->round = (uint64_t)(C.round + 1);
+          if (moved) atomicAdd((unsigned long long*)&P.wctl->counters[6], 1ull);
+        }
+        C.round += 1;
+        __syncthreads();
+        if (!moved) break;
+      }
+      // 3. finished tasks, then per-stream completion and retirement
+      C.complete_tasks();
+      __syncthreads();
+      if (tid == 0) {
+        const uint64_t mask = (1ull << P.tq_log2) - 1;
+        uint64_t r0 = sh->task_retire;
+        const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+        while (r0 < a && P.tasks[r0 & mask].type == 0 &&
+               (uint32_t)(P.tasks[r0 & mask].claim >> 32) == (uint32_t)r0)
+          ++r0;
+        sh->task_retire = r0;
+        C.stage_reclaim();
+      }
+      __syncthreads();
+      int phys = 0, pend = 0;
+      if (tid == 0) sm.pending = 0;
+      __syncthreads();
+      for (int g = tid; g < P.max_streams; g += blockDim.x) {
+        if (C.stream_physical(g, now)) phys = 1;
+        const SState& S = P.ss[g];
+        if (S.retire < S.ingested) pend = 1;
+      }
+      if (phys) atomicOr(&sm.any, 1);
+      if (pend) atomicOr(&sm.pending, 1);
+      __syncthreads();
+      for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
+      __syncthreads();
+      C.schedule_reduce();
+      if (tid == 0) C.make_stage_tasks();
+      __syncthreads();
+    }
+    // 4. bookkeeping and exit decisions (thread 0)
+    if (tid == 0) {
+      int decision = 0;  // 0 continue, 1 exit
+      const bool any = sm.any != 0;
+      if (any) last_prog = now;
+      const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+      const uint64_t rt = sh->task_retire;
+      const bool tasks_live = rt != a;
+      const bool pending = tasks_live || sm.pending != 0;
+      const bool new_in_ring = false;  // rings were drained at the start of this tick
+      if (pending || new_in_ring || any) idle_since = now;
+      if (ld_vol32(&P.wctl->failed) && !tasks_live && !new_in_ring) decision = 1;
+      if (!decision && pending && !any && now - last_prog > P.watchdog_ns) {
+        // nothing moved for too long: fail the pending work and release waiters
+        atomicCAS(&P.wctl->error, 0, kErrTimeout);
+        st_rel_sys32(&P.wctl->failed, 1);
+        decision = 2;
+      }
+      if (!decision) {
+        if (P.mode == 1) {  // drain pass
+          if (!pending && !new_in_ring) decision = 1;
+          else if (!any && !tasks_live && now - last_prog > P.idle_ns) decision = 1;
+        } else {
+          const bool stop = ld_vol32(&P.wctl->stop) != 0;
+          if (!pending && !new_in_ring && (stop || now - idle_since > P.idle_ns)) {
+            // leave, unless the host published something meanwhile
+            st_rel_sys32(&P.wctl->state, ENG_EXITING);
+            fence_sc_sys();
+            bool fresh = false;
+            for (int g = 0; g < P.max_streams; ++g) {
+              if (!(P.ss[g].flags & SF_ACTIVE) && !(ld_acq_sys32(&P.sctl[g].flags) & SF_ACTIVE)) continue;
+              if (ld_acq_sys(&P.sctl[g].tail) > P.ss[g].ingested) fresh = true;
+            }
+            if (fresh) st_rel_sys32(&P.wctl->state, ENG_RUNNING);
+            else decision = 1;
+          }
+        }
+      }
+      sm.flag = decision;
+      atomicAdd((unsigned long long*)&P.wctl->counters[1], 1ull);
+    }
+    __syncthreads();
+    if (sm.flag == 1) break;
+    if (sm.flag == 2) {
+      release_all(P, kErrTimeout);
+      __syncthreads();
+      continue;
+    }
+    // 5. help with data movement, or back off when there is nothing to do
+    if (claim_tile(P, sm)) {
+      run_claimed(P, sm, buf);
+    } else if (!sm.any) {
+      if (tid == 0) __nanosleep(2000);
+    }
+    __syncthreads();
+  }
+  // let the movers go; tasks in flight were finished before deciding to exit
+  if (tid == 0) {
+    st_rel_gpu32(&sh->exit_flag, 1);
+    if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
+  }
+}
+
+__device__ void mover_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
+  int64_t idle_t0 = 0;
+  for (;;) {
+    if (threadIdx.x == 0) sm.flag = (int32_t)ld_acq_gpu32(&P.sh->exit_flag);
+    __syncthreads();
+    if (sm.flag) break;
+    if (claim_tile(P, sm)) {
+      run_claimed(P, sm, buf);
+      idle_t0 = 0;
+    } else if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)now_ns();
+      if (idle_t0 == 0) idle_t0 = t;
+      // the control CTA always raises exit_flag before leaving; this bound only
+      // guards against a control CTA that never got scheduled
+      const uint64_t hb = ld_rlx_sys(&P.wctl->heartbeat);
+      if (t - idle_t0 > 4 * P.watchdog_ns && (int64_t)(t - (int64_t)hb) > 4 * P.watchdog_ns) {
+        set_error(P, -1, kErrTimeout);
+        sm.flag = 1;
+      }
+      __nanosleep(t - idle_t0 > 100000 ? 4000 : 500);
+    }
+    __syncthreads();
+    if (sm.flag) break;
+  }
+}
+
+extern __shared__ __align__(128) uint8_t g_dyn_smem[];
+
+__global__ void __launch_bounds__(512, 1) engine_kernel(EngineParams P) {
+  CtaShared& sm = *reinterpret_cast<CtaShared*>(g_dyn_smem);
+  uint8_t* buf = g_dyn_smem + ((sizeof(CtaShared) + 1023) & ~(size_t)1023);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTmaStages; ++s) mbar_init(&sm.bar[s], 1);
+    sm.phase = 0;
+    fence_proxy_async();
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Shared* sh = P.sh;
+    sh->exit_flag = 0;
+    // tasks left from a previous launch were all finished (quiescent exit) or
+    // abandoned by a watchdog failure; start claiming from the oldest live one
+    sh->task_head = sh->task_retire;
+    atomicAdd((unsigned long long*)&P.wctl->counters[0], 1ull);
+    __threadfence();
+  }
+  grid_barrier(P, gridDim.x);
+  if (blockIdx.x == 0) control_loop(P, sm, buf);
+  else mover_loop(P, sm, buf);
+}
+
+}  // namespace
+}  // namespace mpxi
+
+extern "C" int mpxi_engine_smem_bytes(void) {
+  return (int)(((sizeof(mpxi::CtaShared) + 1023) & ~(size_t)1023) +
+               (size_t)mpxi::kTmaStages * mpxi::kTmaChunk);
+}
+
+extern "C" int mpxi_engine_launch(const mpxi::EngineParams* p, int nctas, int nthreads,
+                                  void* cuda_stream, int cooperative) {
+  static bool attr_set = false;
+  const int smem = mpxi_engine_smem_bytes();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(mpxi::engine_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return (int)e;
+    attr_set = true;
+  }
+  mpxi::EngineParams params = *p;
+  void* args[] = {&params};
+  cudaError_t e;
+  if (cooperative)
+    e = cudaLaunchCooperativeKernel((const void*)mpxi::engine_kernel, dim3(nctas), dim3(nthreads),
+                                    args, (size_t)smem, (cudaStream_t)cuda_stream);
+  else
+    e = cudaLaunchKernel((const void*)mpxi::engine_kernel, dim3(nctas), dim3(nthreads), args,
+                         (size_t)smem, (cudaStream_t)cuda_stream);
+  return (int)e;
+}
+
+extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads) {
+  int n = 0;
+  if (cudaFuncSetAttribute(mpxi::engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           mpxi_engine_smem_bytes()) != cudaSuccess)
+    return 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mpxi::engine_kernel, nthreads,
+                                                (size_t)mpxi_engine_smem_bytes());
+  return n;
+}

@@ -1,0 +1,935 @@
+// Host runtime of libmpx: worlds, streams (endpoints), stream communicators,
+// datatypes, the lock-free enqueue path and the engine's life cycle.
+//
+// Enqueue path (§3.4; §5.2 names the better design: a progress agent plus
+// triggers enqueued in the GPU stream):
+//   1. validate the call,
+//   2. write a 64-byte descriptor into the stream's submission ring (pinned
+//      host memory) and publish the ring tail with a release store -- no lock,
+//      the stream is a serial context (§3.1),
+//   3. put a stream-ordered doorbell (cuStreamWriteValue64) on the user's
+//      CUDA stream, telling the engine that earlier work on the stream is done
+//      and the buffer may be read or written,
+//   4. for calls that block in stream order (send, recv, wait, waitall,
+//      allreduce) put cuStreamWaitValue64(done >= seq) on the stream: work
+//      enqueued afterwards starts once the engine has completed the call,
+//   5. make sure the engine kernel is running (persistent mode).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/mpx.h"
+#include "mpx_internal.h"
+#include "mpx_plain.h"
+
+using namespace mpxi;
+
+extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads);
+
+// Stream memory operations come from the driver; they are looked up through
+// the runtime so the library loads (and its symbols can be inspected) on a
+// machine without a driver.
+namespace {
+typedef CUresult (*PfnMemop64)(CUstream, CUdeviceptr, cuuint64_t, unsigned int);
+PfnMemop64 g_write64 = nullptr;
+PfnMemop64 g_wait64 = nullptr;
+std::once_flag g_memops_once;
+
+bool memops_ready() {
+  std::call_once(g_memops_once, [] {
+    void* fp = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue64", &fp, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_write64 = (PfnMemop64)fp;
+    fp = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuStreamWaitValue64", &fp, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      g_wait64 = (PfnMemop64)fp;
+  });
+  return g_write64 && g_wait64;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// datatypes (process-wide, append-only table; reads need no lock)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TypeRec {
+  int32_t alive;
+  int32_t base;
+  int32_t vcount, blocklen, stride;
+};
+
+constexpr int kMaxTypes = 1 << 16;
+constexpr int kFirstDerived = 16;
+TypeRec g_types[kMaxTypes];
+std::mutex g_types_mu;
+int g_types_next = kFirstDerived;
+std::vector<int> g_types_free;
+
+struct TypeInit {
+  TypeInit() {
+    for (int b = 0; b <= MPX_DOUBLE; ++b) g_types[b] = TypeRec{1, b, 1, 1, 1};
+  }
+} g_type_init;
+
+const TypeRec* type_get(mpx_datatype_t t) {
+  if (t < 0 || t >= kMaxTypes) return nullptr;
+  const TypeRec* r = &g_types[t];
+  if (!__atomic_load_n(&r->alive, __ATOMIC_ACQUIRE)) return nullptr;
+  return r;
+}
+
+int64_t now_ms() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (int64_t)ts.tv_sec * 1000 + ts.tv_nsec / 1000000;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int log2i(int64_t v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct mpx_world_s;
+
+struct mpx_stream_s {
+  mpx_world_s* w;
+  int id;
+  int rank;
+  cudaStream_t cs;
+  unsigned flags;
+  uint64_t next_seq;  // next sequence number to publish
+  uint64_t wl_next;   // next waitlist index
+  int ncomms;         // communicators using this stream
+};
+
+struct CommShared {
+  std::atomic<int> handles;
+  int id;
+  int reduce_mode;
+};
+
+struct mpx_comm_s {
+  mpx_world_s* w;
+  CommShared* shared;
+  int rank;
+  int size;
+  mpx_stream_s* stream;
+};
+
+struct mpx_world_s {
+  int widx;
+  int nranks;
+  mpx_world_config_t cfg;
+  int device;
+  int nsm;
+  int slots_log2, wl_log2, qcap_log2, tq_log2, sr_log2, iw;
+  // pinned host memory
+  Desc* rings;
+  int64_t* waitlists;
+  StreamCtl* sctl;
+  WorldCtl* wctl;
+  // device memory (one block; see layout in world_create)
+  void* dev_block;
+  size_t dev_bytes;
+  EngineParams params;
+  cudaStream_t engine_stream;
+  int engine_ctas, engine_threads;
+  std::mutex mu;                    // stream/comm creation
+  std::vector<mpx_stream_s*> streams;
+  std::vector<uint64_t> slot_seq;   // per endpoint: last sequence number used
+  int comms_used;
+  int live_comm_handles;
+  plain::PlainWorld* plain;
+};
+
+// Requests name (world index, endpoint, sequence number):
+// bits 56..62 world, 40..55 endpoint, 0..39 sequence number.
+namespace {
+constexpr int kMaxWorlds = 128;
+mpx_world_s* g_world_table[kMaxWorlds];
+std::mutex g_worlds_mu;
+}  // namespace
+
+static mpx_request_t make_request(mpx_stream_s* s, uint64_t seq);
+
+// ---------------------------------------------------------------------------
+// configuration
+// ---------------------------------------------------------------------------
+static int64_t env_i64(const char* name, int64_t dflt) {
+  const char* v = getenv(name);
+  if (!v || !*v) return dflt;
+  return strtoll(v, nullptr, 0);
+}
+
+extern "C" int mpx_world_config_init(mpx_world_config_t* c) {
+  if (!c) return MPX_ERR_ARG;
+  memset(c, 0, sizeof(*c));
+  c->engine_mode = (int32_t)env_i64("MPX_ENGINE_MODE", MPX_ENGINE_PERSISTENT);
+  c->max_streams = (int32_t)env_i64("MPX_MAX_STREAMS", 64);
+  c->ring_slots = (int32_t)env_i64("MPX_RING_SLOTS", 4096);
+  c->max_comms = (int32_t)env_i64("MPX_MAX_COMMS", 8);
+  c->queue_slots = (int32_t)env_i64("MPX_QUEUE_SLOTS", 4096);
+  c->task_slots = (int32_t)env_i64("MPX_TASK_SLOTS", 16384);
+  c->engine_ctas = (int32_t)env_i64("MPX_ENGINE_CTAS", 0);
+  c->engine_threads = (int32_t)env_i64("MPX_ENGINE_THREADS", 256);
+  c->tile_bytes = (int32_t)env_i64("MPX_TILE_BYTES", 65536);
+  c->bulk_min_bytes = (int32_t)env_i64("MPX_BULK_MIN_BYTES", 32768);
+  c->reduce_mode = (int32_t)env_i64("MPX_REDUCE_MODE", MPX_REDUCE_FIXED);
+  c->staging_bytes = env_i64("MPX_STAGING_BYTES", 256ll << 20);
+  c->budget_bytes = env_i64("MPX_BUDGET_BYTES", 0);
+  c->watchdog_ns = env_i64("MPX_WATCHDOG_NS", 10ll * 1000 * 1000 * 1000);
+  c->idle_exit_ns = env_i64("MPX_IDLE_EXIT_NS", 100ll * 1000 * 1000);
+  c->stage_delay_ns = env_i64("MPX_STAGE_DELAY_NS", 20000);
+  return MPX_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// world
+// ---------------------------------------------------------------------------
+static mpx_request_t make_request(mpx_stream_s* s, uint64_t seq) {
+  return (mpx_request_t)(((uint64_t)s->w->widx << 56) | ((uint64_t)s->id << 40) | seq);
+}
+
+static void world_release(mpx_world_s* w) {
+  if (!w) return;
+  if (w->widx >= 0) {
+    std::lock_guard<std::mutex> g(g_worlds_mu);
+    g_world_table[w->widx] = nullptr;
+  }
+  if (w->plain) plain::destroy(w->plain);
+  if (w->engine_stream) cudaStreamDestroy(w->engine_stream);
+  if (w->dev_block) cudaFree(w->dev_block);
+  if (w->rings) cudaFreeHost(w->rings);
+  if (w->waitlists) cudaFreeHost(w->waitlists);
+  if (w->sctl) cudaFreeHost(w->sctl);
+  if (w->wctl) cudaFreeHost(w->wctl);
+  delete w;
+}
+
+extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mpx_world_t* out) {
+  if (!out || nranks < 1 || nranks > 4096) return MPX_ERR_ARG;
+  *out = nullptr;
+  mpx_world_config_t cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else mpx_world_config_init(&cfg);
+  if (cfg.max_streams < 1 || cfg.max_streams > 1024) return MPX_ERR_ARG;
+  if (!is_pow2(cfg.ring_slots) || cfg.ring_slots < 16) return MPX_ERR_ARG;
+  if (!is_pow2(cfg.queue_slots) || cfg.queue_slots < 32) return MPX_ERR_ARG;
+  if (!is_pow2(cfg.task_slots) || cfg.task_slots < 64) return MPX_ERR_ARG;
+  if (cfg.max_comms < 1 || cfg.max_comms > 65535) return MPX_ERR_ARG;
+  if (cfg.tile_bytes < 256 || (cfg.tile_bytes & 15)) return MPX_ERR_ARG;
+  if (cfg.engine_threads < 64 || cfg.engine_threads > 512 || (cfg.engine_threads & 31))
+    return MPX_ERR_ARG;
+  if (cfg.engine_mode < MPX_ENGINE_PERSISTENT || cfg.engine_mode > MPX_ENGINE_PLAIN) return MPX_ERR_ARG;
+  if (cfg.staging_bytes < 4096) return MPX_ERR_ARG;
+
+  mpx_world_s* w = new (std::nothrow) mpx_world_s();
+  if (!w) return MPX_ERR_NO_MEM;
+  w->widx = -1;
+  {
+    std::lock_guard<std::mutex> g(g_worlds_mu);
+    for (int i = 0; i < kMaxWorlds; ++i)
+      if (!g_world_table[i]) { g_world_table[i] = w; w->widx = i; break; }
+  }
+  if (w->widx < 0) { delete w; return MPX_ERR_NO_MEM; }
+  w->nranks = nranks;
+  w->cfg = cfg;
+  w->plain = nullptr;
+  w->comms_used = 0;
+  w->live_comm_handles = 0;
+  if (cudaGetDevice(&w->device) != cudaSuccess) { world_release(w); return MPX_ERR_CUDA; }
+  cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, w->device);
+  // make sure the runtime's primary context exists, and the driver's stream
+  // memory operations are available
+  cudaFree(0);
+  if (cfg.engine_mode != MPX_ENGINE_PLAIN && !memops_ready()) { world_release(w); return MPX_ERR_CUDA; }
+  const int S = cfg.max_streams;
+  w->slots_log2 = log2i(cfg.ring_slots);
+  w->wl_log2 = log2i((int64_t)cfg.ring_slots * 4);
+  w->qcap_log2 = log2i(cfg.queue_slots);
+  w->tq_log2 = log2i(cfg.task_slots);
+  w->sr_log2 = 16;
+  w->iw = 32;
+  const size_t slots = (size_t)1 << w->slots_log2;
+  const size_t ndom = (size_t)cfg.max_comms * nranks;
+
+  // pinned host memory: rings, waitlists, control lines
+  if (cudaHostAlloc((void**)&w->rings, (size_t)S * slots * sizeof(Desc), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&w->waitlists, ((size_t)S << w->wl_log2) * sizeof(int64_t), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&w->sctl, (size_t)S * sizeof(StreamCtl), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&w->wctl, sizeof(WorldCtl), cudaHostAllocMapped) != cudaSuccess) {
+    world_release(w);
+    return MPX_ERR_NO_MEM;
+  }
+  memset(w->sctl, 0, (size_t)S * sizeof(StreamCtl));
+  memset(w->wctl, 0, sizeof(WorldCtl));
+  w->slot_seq.assign(S, 0);
+  w->streams.assign(S, nullptr);
+
+  if (cfg.engine_mode == MPX_ENGINE_PLAIN) {
+    w->plain = plain::create(nranks, cfg.max_streams, cfg.staging_bytes);
+    if (!w->plain) { world_release(w); return MPX_ERR_NO_MEM; }
+    *out = w;
+    return MPX_SUCCESS;
+  }
+
+  // device memory, carved from one allocation
+  struct Part { size_t bytes; void** dst; };
+  EngineParams& P = w->params;
+  memset(&P, 0, sizeof(P));
+  const size_t iwn = (size_t)cfg.max_comms * w->iw;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t o = (off + 255) & ~(size_t)255;
+    off = o + bytes;
+    return o;
+  };
+  const size_t o_door = carve(S * 8), o_done = carve(S * 8);
+  const size_t o_ops = carve((size_t)S * slots * sizeof(DOp));
+  const size_t o_ss = carve(S * sizeof(SState));
+  const size_t o_post = carve((size_t)S * slots * 8);
+  const size_t o_pq = carve((ndom << w->qcap_log2) * sizeof(QEntry));
+  const size_t o_uq = carve((ndom << w->qcap_log2) * sizeof(QEntry));
+  const size_t o_pqh = carve(ndom * sizeof(QHead)), o_uqh = carve(ndom * sizeof(QHead));
+  const size_t o_tasks = carve(((size_t)1 << w->tq_log2) * sizeof(Task));
+  const size_t o_sh = carve(sizeof(Shared));
+  const size_t o_srec = carve(((size_t)1 << w->sr_log2) * sizeof(StageRec));
+  const size_t o_inst = carve(iwn * sizeof(InstSlot));
+  const size_t o_irefs = carve(iwn * nranks * 8);
+  const size_t o_ninst = carve((size_t)cfg.max_comms * nranks * 8);
+  const size_t o_rptr = carve(iwn * 2 * nranks * 8);
+  const size_t o_stage = carve((size_t)cfg.staging_bytes);
+  w->dev_bytes = off;
+  if (cfg.budget_bytes > 0 && (int64_t)off > cfg.budget_bytes) { world_release(w); return MPX_ERR_NO_MEM; }
+  if (cudaMalloc(&w->dev_block, off) != cudaSuccess) { world_release(w); return MPX_ERR_NO_MEM; }
+  uint8_t* base = (uint8_t*)w->dev_block;
+  // zero everything except the staging arena
+  if (cudaMemset(base, 0, o_stage) != cudaSuccess) { world_release(w); return MPX_ERR_CUDA; }
+  std::vector<SState> ss(S);
+  for (auto& x : ss) {
+    memset(&x, 0, sizeof(x));
+    x.cursor = 1;
+    x.pc = 1;
+    x.sched = 1;
+  }
+  if (cudaMemcpy(base + o_ss, ss.data(), S * sizeof(SState), cudaMemcpyHostToDevice) != cudaSuccess) {
+    world_release(w);
+    return MPX_ERR_CUDA;
+  }
+
+  P.nranks = nranks;
+  P.max_streams = S;
+  P.slots_log2 = w->slots_log2;
+  P.max_comms = cfg.max_comms;
+  P.qcap_log2 = w->qcap_log2;
+  P.tq_log2 = w->tq_log2;
+  P.iw = w->iw;
+  P.mode = 0;
+  P.wl_log2 = w->wl_log2;
+  P.sr_log2 = w->sr_log2;
+  P.ctl_ctas = 1;
+  P.watchdog_ns = cfg.watchdog_ns;
+  P.idle_ns = cfg.idle_exit_ns;
+  P.stage_delay_ns = cfg.stage_delay_ns;
+  P.tile_bytes = cfg.tile_bytes;
+  P.bulk_min = cfg.bulk_min_bytes;
+  P.stage_bytes = cfg.staging_bytes;
+  void* dp;
+  cudaHostGetDevicePointer(&dp, w->rings, 0); P.rings = (const Desc*)dp;
+  cudaHostGetDevicePointer(&dp, w->waitlists, 0); P.waitlists = (const int64_t*)dp;
+  cudaHostGetDevicePointer(&dp, w->sctl, 0); P.sctl = (StreamCtl*)dp;
+  cudaHostGetDevicePointer(&dp, w->wctl, 0); P.wctl = (WorldCtl*)dp;
+  P.doorbell = (uint64_t*)(base + o_door);
+  P.done = (uint64_t*)(base + o_done);
+  P.ops = (DOp*)(base + o_ops);
+  P.ss = (SState*)(base + o_ss);
+  P.postbuf = (uint64_t*)(base + o_post);
+  P.pq = (QEntry*)(base + o_pq);
+  P.uq = (QEntry*)(base + o_uq);
+  P.pqh = (QHead*)(base + o_pqh);
+  P.uqh = (QHead*)(base + o_uqh);
+  P.tasks = (Task*)(base + o_tasks);
+  P.sh = (Shared*)(base + o_sh);
+  P.srec = (StageRec*)(base + o_srec);
+  P.inst = (InstSlot*)(base + o_inst);
+  P.inst_refs = (uint64_t*)(base + o_irefs);
+  P.next_inst = (int64_t*)(base + o_ninst);
+  P.reduce_ptrs = (uint64_t*)(base + o_rptr);
+  P.stage = base + o_stage;
+
+  if (cudaStreamCreateWithFlags(&w->engine_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    world_release(w);
+    return MPX_ERR_CUDA;
+  }
+  w->engine_threads = cfg.engine_threads;
+  int per_sm = mpxi_engine_max_ctas_per_sm(cfg.engine_threads);
+  if (per_sm < 1) { world_release(w); return MPX_ERR_CUDA; }
+  int ctas = cfg.engine_ctas > 0 ? cfg.engine_ctas : w->nsm;
+  ctas = std::min(ctas, per_sm * w->nsm);
+  w->engine_ctas = std::max(1, ctas);
+  *out = w;
+  return MPX_SUCCESS;
+}
+
+static int launch_engine(mpx_world_s* w, cudaStream_t s, int mode) {
+  EngineParams P = w->params;
+  P.mode = mode;
+  if (mode == 1) P.idle_ns = std::min<int64_t>(w->cfg.idle_exit_ns, 200000);
+  int e = mpxi_engine_launch(&P, w->engine_ctas, w->engine_threads, (void*)s, 1);
+  return e == 0 ? MPX_SUCCESS : MPX_ERR_CUDA;
+}
+
+// Persistent mode: launch the engine if it is not running (see the exit
+// protocol in the engine: it re-checks the rings after announcing EXITING).
+static int ensure_engine(mpx_world_s* w) {
+  if (w->cfg.engine_mode != MPX_ENGINE_PERSISTENT) return MPX_SUCCESS;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  const int64_t t0 = now_ms();
+  for (;;) {
+    int st = __atomic_load_n(&w->wctl->state, __ATOMIC_ACQUIRE);
+    if (st == ENG_RUNNING) return MPX_SUCCESS;
+    if (st == ENG_STOPPED) {
+      int expected = ENG_STOPPED;
+      if (__atomic_compare_exchange_n(&w->wctl->state, &expected, ENG_RUNNING, false,
+                                      __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
+        int rc = launch_engine(w, w->engine_stream, 0);
+        if (rc != MPX_SUCCESS) __atomic_store_n(&w->wctl->state, ENG_STOPPED, __ATOMIC_RELEASE);
+        return rc;
+      }
+      continue;
+    }
+    if (now_ms() - t0 > 5000) return MPX_ERR_STATE;
+    std::this_thread::yield();
+  }
+}
+
+extern "C" int mpx_world_start(mpx_world_t w) {
+  if (!w) return MPX_ERR_ARG;
+  if (w->cfg.engine_mode != MPX_ENGINE_PERSISTENT) return MPX_ERR_STATE;
+  return ensure_engine(w);
+}
+
+extern "C" int mpx_world_stop(mpx_world_t w, int timeout_ms) {
+  if (!w) return MPX_ERR_ARG;
+  if (w->cfg.engine_mode != MPX_ENGINE_PERSISTENT) return MPX_SUCCESS;
+  __atomic_store_n(&w->wctl->stop, 1, __ATOMIC_RELEASE);
+  const int64_t t0 = now_ms();
+  int rc = MPX_SUCCESS;
+  while (__atomic_load_n(&w->wctl->state, __ATOMIC_ACQUIRE) != ENG_STOPPED) {
+    if (now_ms() - t0 > timeout_ms) { rc = MPX_ERR_TIMEOUT; break; }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (rc == MPX_SUCCESS && cudaStreamSynchronize(w->engine_stream) != cudaSuccess) rc = MPX_ERR_CUDA;
+  __atomic_store_n(&w->wctl->stop, 0, __ATOMIC_RELEASE);
+  return rc;
+}
+
+extern "C" int mpx_world_progress(mpx_world_t w, mpx_cuda_stream_t stream) {
+  if (!w) return MPX_ERR_ARG;
+  if (w->cfg.engine_mode == MPX_ENGINE_PLAIN) return plain::progress(w->plain);
+  if (w->cfg.engine_mode != MPX_ENGINE_DRAIN) return MPX_ERR_STATE;
+  return launch_engine(w, (cudaStream_t)stream, 1);
+}
+
+// Failure recovery: mark the world failed (a running engine then releases
+// every waiter with MPX_ERR_TIMEOUT and moves no more data) and write every
+// completion word from the host, so no CUDA stream stays blocked on one.
+extern "C" int mpx_world_abort(mpx_world_t w) {
+  if (!w) return MPX_ERR_ARG;
+  if (w->plain) return MPX_SUCCESS;
+  __atomic_store_n(&w->wctl->error, MPX_ERR_TIMEOUT, __ATOMIC_RELEASE);
+  __atomic_store_n(&w->wctl->failed, 1, __ATOMIC_RELEASE);
+  const int S = w->cfg.max_streams;
+  uint64_t* hv = nullptr;
+  if (cudaHostAlloc((void**)&hv, (size_t)S * 8, cudaHostAllocDefault) != cudaSuccess) return MPX_ERR_NO_MEM;
+  for (int g = 0; g < S; ++g) hv[g] = __atomic_load_n(&w->sctl[g].tail, __ATOMIC_ACQUIRE);
+  cudaStream_t s;
+  int rc = MPX_SUCCESS;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFreeHost(hv);
+    return MPX_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(w->params.done, hv, (size_t)S * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = MPX_ERR_CUDA;
+  cudaStreamDestroy(s);
+  cudaFreeHost(hv);
+  return rc;
+}
+
+extern "C" int mpx_world_get_error(mpx_world_t w, int* err) {
+  if (!w || !err) return MPX_ERR_ARG;
+  if (w->plain) { *err = plain::error(w->plain); return MPX_SUCCESS; }
+  *err = __atomic_load_n(&w->wctl->error, __ATOMIC_ACQUIRE);
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_world_get_counters(mpx_world_t w, int64_t* outv, int n) {
+  if (!w || !outv || n < 0) return MPX_ERR_ARG;
+  for (int i = 0; i < n && i < 8; ++i)
+    outv[i] = w->plain ? plain::counter(w->plain, i)
+                       : (int64_t)__atomic_load_n(&w->wctl->counters[i], __ATOMIC_ACQUIRE);
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_world_free(mpx_world_t* pw) {
+  if (!pw || !*pw) return MPX_ERR_ARG;
+  mpx_world_s* w = *pw;
+  {
+    std::lock_guard<std::mutex> g(w->mu);
+    for (auto* s : w->streams)
+      if (s) return MPX_ERR_PENDING;
+    if (w->live_comm_handles) return MPX_ERR_PENDING;
+  }
+  if (w->cfg.engine_mode == MPX_ENGINE_PERSISTENT) {
+    if (mpx_world_stop(w, 10000) != MPX_SUCCESS) return MPX_ERR_TIMEOUT;
+  }
+  if (w->engine_stream) cudaStreamSynchronize(w->engine_stream);
+  world_release(w);
+  *pw = nullptr;
+  return MPX_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// streams
+// ---------------------------------------------------------------------------
+extern "C" int mpx_stream_create(mpx_world_t w, int rank, mpx_cuda_stream_t cs, unsigned flags,
+                                 mpx_stream_t* out) {
+  if (!w || !out) return MPX_ERR_ARG;
+  if (rank < 0 || rank >= w->nranks) return MPX_ERR_RANK;
+  if (flags & ~(unsigned)MPX_STREAM_EXCLUSIVE) return MPX_ERR_ARG;
+  std::lock_guard<std::mutex> g(w->mu);
+  int id = -1;
+  for (int i = 0; i < w->cfg.max_streams; ++i)
+    if (!w->streams[i]) { id = i; break; }
+  if (id < 0) return MPX_ERR_NO_ENDPOINT;
+  mpx_stream_s* s = new (std::nothrow) mpx_stream_s();
+  if (!s) return MPX_ERR_NO_MEM;
+  s->w = w;
+  s->id = id;
+  s->rank = rank;
+  s->cs = (cudaStream_t)cs;
+  s->flags = flags;
+  s->ncomms = 0;
+  if (w->plain) {
+    if (plain::stream_create(w->plain, id, rank, (cudaStream_t)cs) != MPX_SUCCESS) { delete s; return MPX_ERR_NO_MEM; }
+  } else {
+    StreamCtl* c = &w->sctl[id];
+    // sequence numbers continue across incarnations of an endpoint so the
+    // doorbell and completion words stay monotone
+    s->next_seq = __atomic_load_n(&c->tail, __ATOMIC_ACQUIRE) + 1;
+    s->wl_next = __atomic_load_n(&c->wl_retired, __ATOMIC_ACQUIRE);
+    c->error = 0;
+    c->rank = rank;
+    __atomic_store_n(&c->flags, SF_ACTIVE | ((flags & MPX_STREAM_EXCLUSIVE) ? SF_EXCLUSIVE : 0),
+                     __ATOMIC_RELEASE);
+  }
+  w->streams[id] = s;
+  *out = s;
+  return MPX_SUCCESS;
+}
+
+static int64_t stream_pending(mpx_stream_s* s) {
+  if (s->w->plain) return plain::stream_pending(s->w->plain, s->id);
+  StreamCtl* c = &s->w->sctl[s->id];
+  return (int64_t)(__atomic_load_n(&c->tail, __ATOMIC_ACQUIRE) - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE));
+}
+
+extern "C" int mpx_stream_free(mpx_stream_t* ps) {
+  if (!ps || !*ps) return MPX_ERR_ARG;
+  mpx_stream_s* s = *ps;
+  mpx_world_s* w = s->w;
+  std::lock_guard<std::mutex> g(w->mu);
+  if (s->ncomms > 0) return MPX_ERR_PENDING;
+  if (stream_pending(s) != 0) return MPX_ERR_PENDING;
+  if (w->plain) plain::stream_free(w->plain, s->id);
+  else __atomic_store_n(&w->sctl[s->id].flags, 0, __ATOMIC_RELEASE);
+  w->streams[s->id] = nullptr;
+  delete s;
+  *ps = nullptr;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_stream_get_id(mpx_stream_t s, int* id) {
+  if (!s || !id) return MPX_ERR_ARG;
+  *id = s->id;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_stream_get_error(mpx_stream_t s, int* err) {
+  if (!s || !err) return MPX_ERR_ARG;
+  if (s->w->plain) { *err = plain::stream_error(s->w->plain, s->id); return MPX_SUCCESS; }
+  *err = __atomic_load_n(&s->w->sctl[s->id].error, __ATOMIC_ACQUIRE);
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_stream_pending(mpx_stream_t s, int64_t* pending) {
+  if (!s || !pending) return MPX_ERR_ARG;
+  *pending = stream_pending(s);
+  return MPX_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// communicators
+// ---------------------------------------------------------------------------
+extern "C" int mpx_stream_comm_create(mpx_world_t w, int nranks, const mpx_stream_t streams[],
+                                      mpx_comm_t comms_out[]) {
+  if (!w || !streams || !comms_out) return MPX_ERR_ARG;
+  if (nranks != w->nranks) return MPX_ERR_ARG;
+  for (int r = 0; r < nranks; ++r) {
+    if (!streams[r]) return MPX_ERR_COMM;  // MPIX_STREAM_NULL members are not supported
+    if (streams[r]->w != w || streams[r]->rank != r) return MPX_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> g(w->mu);
+  if (w->comms_used >= w->cfg.max_comms) return MPX_ERR_NO_MEM;
+  CommShared* sh = new (std::nothrow) CommShared();
+  if (!sh) return MPX_ERR_NO_MEM;
+  sh->id = w->comms_used++;
+  sh->reduce_mode = w->cfg.reduce_mode;
+  sh->handles.store(nranks);
+  std::vector<mpx_comm_s*> made;
+  for (int r = 0; r < nranks; ++r) {
+    mpx_comm_s* c = new (std::nothrow) mpx_comm_s();
+    if (!c) {
+      for (auto* m : made) delete m;
+      delete sh;
+      return MPX_ERR_NO_MEM;
+    }
+    c->w = w;
+    c->shared = sh;
+    c->rank = r;
+    c->size = nranks;
+    c->stream = streams[r];
+    made.push_back(c);
+  }
+  if (w->plain) plain::comm_create(w->plain, sh->id);
+  for (int r = 0; r < nranks; ++r) {
+    streams[r]->ncomms++;
+    comms_out[r] = made[r];
+  }
+  w->live_comm_handles += nranks;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_comm_free(mpx_comm_t* pc) {
+  if (!pc || !*pc) return MPX_ERR_ARG;
+  mpx_comm_s* c = *pc;
+  mpx_world_s* w = c->w;
+  std::lock_guard<std::mutex> g(w->mu);
+  c->stream->ncomms--;
+  w->live_comm_handles--;
+  if (c->shared->handles.fetch_sub(1) == 1) delete c->shared;
+  delete c;
+  *pc = nullptr;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_comm_rank(mpx_comm_t c, int* rank) {
+  if (!c || !rank) return MPX_ERR_ARG;
+  *rank = c->rank;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_comm_size(mpx_comm_t c, int* size) {
+  if (!c || !size) return MPX_ERR_ARG;
+  *size = c->size;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_comm_set_reduce_mode(mpx_comm_t c, int mode) {
+  if (!c || (mode != MPX_REDUCE_FIXED && mode != MPX_REDUCE_TREE)) return MPX_ERR_ARG;
+  c->shared->reduce_mode = mode;
+  return MPX_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// datatypes
+// ---------------------------------------------------------------------------
+extern "C" int mpx_type_vector(int count, int blocklength, int stride, mpx_datatype_t oldtype,
+                               mpx_datatype_t* newtype) {
+  if (!newtype || count < 1 || blocklength < 1 || stride < blocklength) return MPX_ERR_ARG;
+  if (oldtype < 0 || oldtype > MPX_DOUBLE) return MPX_ERR_TYPE;
+  std::lock_guard<std::mutex> g(g_types_mu);
+  int id;
+  if (!g_types_free.empty()) {
+    id = g_types_free.back();
+    g_types_free.pop_back();
+  } else {
+    if (g_types_next >= kMaxTypes) return MPX_ERR_NO_MEM;
+    id = g_types_next++;
+  }
+  g_types[id].base = oldtype;
+  g_types[id].vcount = count;
+  g_types[id].blocklen = blocklength;
+  g_types[id].stride = stride;
+  __atomic_store_n(&g_types[id].alive, 1, __ATOMIC_RELEASE);
+  *newtype = id;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_type_free(mpx_datatype_t* t) {
+  if (!t) return MPX_ERR_ARG;
+  if (*t < kFirstDerived || *t >= kMaxTypes) return MPX_ERR_TYPE;
+  std::lock_guard<std::mutex> g(g_types_mu);
+  if (!g_types[*t].alive) return MPX_ERR_TYPE;
+  __atomic_store_n(&g_types[*t].alive, 0, __ATOMIC_RELEASE);
+  g_types_free.push_back(*t);
+  *t = -1;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_type_size(mpx_datatype_t t, int64_t* size) {
+  const TypeRec* r = type_get(t);
+  if (!r || !size) return r ? MPX_ERR_ARG : MPX_ERR_TYPE;
+  *size = base_size((uint32_t)r->base) * r->vcount * r->blocklen;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_type_extent(mpx_datatype_t t, int64_t* extent) {
+  const TypeRec* r = type_get(t);
+  if (!r || !extent) return r ? MPX_ERR_ARG : MPX_ERR_TYPE;
+  *extent = base_size((uint32_t)r->base) * ((int64_t)(r->vcount - 1) * r->stride + r->blocklen);
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_get_count(const mpx_status_t* st, mpx_datatype_t t, int64_t* count) {
+  if (!st || !count) return MPX_ERR_ARG;
+  int64_t sz;
+  int rc = mpx_type_size(t, &sz);
+  if (rc) return rc;
+  *count = (sz > 0 && st->bytes % sz == 0) ? st->bytes / sz : MPX_UNDEFINED;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+// enqueue
+// ---------------------------------------------------------------------------
+static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out) {
+  mpx_world_s* w = s->w;
+  StreamCtl* c = &w->sctl[s->id];
+  if (__atomic_load_n(&w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
+  const uint64_t seq = s->next_seq;
+  const uint64_t slots = 1ull << w->slots_log2;
+  if (seq - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE) > slots) {
+    if (w->cfg.engine_mode != MPX_ENGINE_PERSISTENT) return MPX_ERR_AGAIN;
+    int rc = ensure_engine(w);
+    if (rc) return rc;
+    const int64_t t0 = now_ms();
+    while (seq - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE) > slots) {
+      if (now_ms() - t0 > 1000) return MPX_ERR_AGAIN;
+      if (__atomic_load_n(&w->wctl->state, __ATOMIC_ACQUIRE) != ENG_RUNNING) ensure_engine(w);
+      std::this_thread::yield();
+    }
+  }
+  Desc* slot = &w->rings[((size_t)s->id << w->slots_log2) + ((seq - 1) & (slots - 1))];
+  memcpy(slot, &d, sizeof(Desc));
+  __atomic_store_n(&c->tail, seq, __ATOMIC_RELEASE);
+  s->next_seq = seq + 1;
+  if (seq_out) *seq_out = seq;  // the operation exists from here on
+  CUstream cs = (CUstream)s->cs;
+  if (!(s->flags & MPX_STREAM_EXCLUSIVE)) {
+    CUdeviceptr db = (CUdeviceptr)(w->params.doorbell + s->id);
+    if (g_write64(cs, db, seq, 0) != CUDA_SUCCESS) return MPX_ERR_CUDA;
+  }
+  if (blocking) {
+    CUdeviceptr dn = (CUdeviceptr)(w->params.done + s->id);
+    if (g_wait64(cs, dn, seq, CU_STREAM_WAIT_VALUE_GEQ) != CUDA_SUCCESS) return MPX_ERR_CUDA;
+  }
+  return ensure_engine(w);
+}
+
+static int fill_p2p(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt,
+                    int peer, int tag, mpx_comm_s* c, bool is_recv) {
+  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (count < 0) return MPX_ERR_ARG;
+  const TypeRec* t = type_get(dt);
+  if (!t) return MPX_ERR_TYPE;
+  if (is_recv) {
+    if (peer != MPX_ANY_SOURCE && (peer < 0 || peer >= c->size)) return MPX_ERR_RANK;
+    if (tag != MPX_ANY_TAG && (tag < 0 || tag > MPX_TAG_UB)) return MPX_ERR_TAG;
+  } else {
+    if (peer < 0 || peer >= c->size) return MPX_ERR_RANK;
+    if (tag < 0 || tag > MPX_TAG_UB) return MPX_ERR_TAG;
+  }
+  if (count > 0 && !buf) return MPX_ERR_ARG;
+  memset(&d, 0, sizeof(d));
+  d.kw = make_kw(kind, (uint32_t)t->base, 0);
+  d.comm = (uint16_t)c->shared->id;
+  d.rank = (uint16_t)c->rank;
+  d.peer = peer;
+  d.tag = tag;
+  d.buf = (uint64_t)buf;
+  d.count = count;
+  d.vcount = t->vcount;
+  d.blocklen = t->blocklen;
+  d.stride = t->stride;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_send_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
+                                int tag, mpx_comm_t c) {
+  if (c && c->w->plain) return plain::p2p(c->w->plain, K_SEND, buf, count, dt, dest, tag, c->shared->id, c->rank, c->stream->id, nullptr, nullptr);
+  Desc d;
+  int rc = fill_p2p(d, K_SEND, buf, count, dt, dest, tag, c, false);
+  if (rc) return rc;
+  return publish(c->stream, d, true, nullptr);
+}
+
+extern "C" int mpx_recv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source, int tag,
+                                mpx_comm_t c, mpx_status_t* status) {
+  if (c && c->w->plain) return plain::p2p(c->w->plain, K_RECV, buf, count, dt, source, tag, c->shared->id, c->rank, c->stream->id, status, nullptr);
+  Desc d;
+  int rc = fill_p2p(d, K_RECV, buf, count, dt, source, tag, c, true);
+  if (rc) return rc;
+  d.status = (uint64_t)status;
+  return publish(c->stream, d, true, nullptr);
+}
+
+extern "C" int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
+                                 int tag, mpx_comm_t c, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  if (c && c->w->plain) return plain::p2p(c->w->plain, K_ISEND, buf, count, dt, dest, tag, c->shared->id, c->rank, c->stream->id, nullptr, req);
+  Desc d;
+  int rc = fill_p2p(d, K_ISEND, buf, count, dt, dest, tag, c, false);
+  if (rc) return rc;
+  uint64_t seq = 0;
+  rc = publish(c->stream, d, false, &seq);
+  if (seq) *req = make_request(c->stream, seq);
+  return rc;
+}
+
+extern "C" int mpx_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source, int tag,
+                                 mpx_comm_t c, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  if (c && c->w->plain) return plain::p2p(c->w->plain, K_IRECV, buf, count, dt, source, tag, c->shared->id, c->rank, c->stream->id, nullptr, req);
+  Desc d;
+  int rc = fill_p2p(d, K_IRECV, buf, count, dt, source, tag, c, true);
+  if (rc) return rc;
+  uint64_t seq = 0;
+  rc = publish(c->stream, d, false, &seq);
+  if (seq) *req = make_request(c->stream, seq);
+  return rc;
+}
+
+static mpx_stream_s* request_stream(mpx_request_t r) {
+  if (r < 0) return nullptr;
+  const int widx = (int)(((uint64_t)r >> 56) & 0x7f);
+  const int id = (int)(((uint64_t)r >> 40) & 0xffff);
+  mpx_world_s* w = g_world_table[widx];
+  if (!w || id >= w->cfg.max_streams) return nullptr;
+  return w->streams[id];
+}
+
+static int wait_common(int n, mpx_request_t* reqs, mpx_status_t* statuses, bool single) {
+  mpx_world_s* w = nullptr;
+  mpx_stream_s* s = nullptr;
+  int live = 0;
+  for (int i = 0; i < n; ++i) {
+    if (reqs[i] == MPX_REQUEST_NULL) continue;
+    if (reqs[i] < 0) return MPX_ERR_REQUEST;
+    mpx_stream_s* si = request_stream(reqs[i]);
+    if (!si) return MPX_ERR_REQUEST;
+    w = si->w;
+    if (s && si != s) return MPX_ERR_STREAM;  // §3.4: one local stream per waitall
+    s = si;
+    const uint64_t seq = (uint64_t)reqs[i] & ((1ull << 40) - 1);
+    if (seq == 0 || seq >= s->next_seq) return MPX_ERR_REQUEST;
+    ++live;
+  }
+  (void)live;
+  if (!s) return MPX_SUCCESS;  // every request is null: nothing to wait for
+  if (w->plain) {
+    int rc = plain::wait(w->plain, s->id, n, reqs, statuses);
+    if (rc == MPX_SUCCESS)
+      for (int i = 0; i < n; ++i) reqs[i] = MPX_REQUEST_NULL;
+    return rc;
+  }
+  Desc d;
+  memset(&d, 0, sizeof(d));
+  d.status = (uint64_t)statuses;
+  if (single) {
+    d.kw = make_kw(K_WAIT, 0, 0);
+    d.aux = (uint64_t)reqs[0] & ((1ull << 40) - 1);
+  } else {
+    const uint64_t wl_slots = 1ull << w->wl_log2;
+    StreamCtl* c = &w->sctl[s->id];
+    if (s->wl_next + (uint64_t)n - __atomic_load_n(&c->wl_retired, __ATOMIC_ACQUIRE) > wl_slots)
+      return MPX_ERR_AGAIN;
+    // statuses are positional: a null request stays in the list as seq 0,
+    // which the engine treats as complete with an empty status
+    int64_t* wl = w->waitlists + ((size_t)s->id << w->wl_log2);
+    uint64_t k = s->wl_next;
+    for (int i = 0; i < n; ++i) {
+      wl[k & (wl_slots - 1)] =
+          reqs[i] == MPX_REQUEST_NULL ? 0 : (int64_t)((uint64_t)reqs[i] & ((1ull << 40) - 1));
+      ++k;
+    }
+    d.kw = make_kw(K_WAITALL, 0, 0);
+    d.aux = s->wl_next;
+    d.n32 = n;
+    s->wl_next = k;
+  }
+  int rc = publish(s, d, true, nullptr);
+  if (rc == MPX_SUCCESS)
+    for (int i = 0; i < n; ++i) reqs[i] = MPX_REQUEST_NULL;
+  return rc;
+}
+
+extern "C" int mpx_wait_enqueue(mpx_request_t* req, mpx_status_t* status) {
+  if (!req) return MPX_ERR_ARG;
+  return wait_common(1, req, status, true);
+}
+
+extern "C" int mpx_waitall_enqueue(int n, mpx_request_t reqs[], mpx_status_t statuses[]) {
+  if (n < 0 || (n > 0 && !reqs)) return MPX_ERR_ARG;
+  return wait_common(n, reqs, statuses, false);
+}
+
+extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                     mpx_datatype_t dt, int op, mpx_comm_t c) {
+  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (op != MPX_SUM) return MPX_ERR_ARG;
+  if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
+  if (count < 0 || (count > 0 && !recvbuf)) return MPX_ERR_ARG;
+  if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;
+  if (count > 0 && !sendbuf) return MPX_ERR_ARG;
+  if (c->w->plain)
+    return plain::allreduce(c->w->plain, sendbuf, recvbuf, count, dt, c->shared->reduce_mode,
+                            c->shared->id, c->rank, c->stream->id);
+  Desc d;
+  memset(&d, 0, sizeof(d));
+  d.kw = make_kw(K_ALLREDUCE, (uint32_t)dt, (uint32_t)c->shared->reduce_mode);
+  d.comm = (uint16_t)c->shared->id;
+  d.rank = (uint16_t)c->rank;
+  d.buf = (uint64_t)sendbuf;
+  d.aux = (uint64_t)recvbuf;
+  d.count = count;
+  d.vcount = 1;
+  d.blocklen = 1;
+  d.stride = 1;
+  return publish(c->stream, d, true, nullptr);
+}
+

@@ -1,0 +1,239 @@
+// Internal layout shared by the host runtime and the device engine of libmpx.
+// Nothing here is part of the public ABI (include/mpx.h).
+#pragma once
+#include <stdint.h>
+
+namespace mpxi {
+
+// ---------------------------------------------------------------------------
+// operation descriptor: one 64-byte record per enqueued call, written by the
+// host into the stream's submission ring (pinned host memory) and copied by
+// the engine into its device-resident operation table.
+// ---------------------------------------------------------------------------
+enum OpKind : uint32_t {
+  K_SEND = 0, K_RECV = 1, K_ISEND = 2, K_IRECV = 3, K_WAIT = 4, K_WAITALL = 5, K_ALLREDUCE = 6
+};
+
+// kind word: bits 0-7 kind, 8-11 base type (MPX_BYTE..MPX_DOUBLE),
+// 12-13 reduce mode
+__host__ __device__ inline uint32_t kw_kind(uint32_t kw) { return kw & 0xffu; }
+__host__ __device__ inline uint32_t kw_base(uint32_t kw) { return (kw >> 8) & 0xfu; }
+__host__ __device__ inline uint32_t kw_mode(uint32_t kw) { return (kw >> 12) & 0x3u; }
+__host__ __device__ inline uint32_t make_kw(uint32_t kind, uint32_t base, uint32_t mode) {
+  return kind | (base << 8) | (mode << 12);
+}
+__host__ __device__ inline int64_t base_size(uint32_t base) {
+  return base == 0 ? 1 : (base == 1 ? 4 : (base == 2 ? 8 : (base == 3 ? 4 : 8)));
+}
+
+struct alignas(64) Desc {
+  uint32_t kw;        // kind word
+  uint16_t comm;      // communicator slot
+  uint16_t rank;      // issuing stream's rank in the communicator
+  int32_t peer;       // dest (send) / source or ANY_SOURCE (recv)
+  int32_t tag;        // tag / ANY_TAG
+  uint64_t buf;       // send or receive buffer; allreduce send buffer
+  int64_t count;      // datatype instances; allreduce elements
+  int32_t vcount;     // vector layout of one instance, in base elements
+  int32_t blocklen;   // (1, 1, 1 for a predefined type)
+  int32_t stride;
+  int32_t n32;        // waitall: number of requests
+  uint64_t aux;       // allreduce: receive buffer; wait: request seq; waitall: waitlist index
+  uint64_t status;    // mpx_status_t* (device-accessible) or 0
+};
+static_assert(sizeof(Desc) == 64, "descriptor is 64 bytes");
+
+// ---------------------------------------------------------------------------
+// host <-> engine control words (pinned host memory, one cache line each)
+// ---------------------------------------------------------------------------
+struct alignas(128) StreamCtl {
+  uint64_t tail;        // H->D  last published sequence number
+  uint64_t wl_tail;     // H->D  waitlist entries published
+  uint64_t retired;     // D->H  every op with seq <= retired is finished
+  uint64_t wl_retired;  // D->H  waitlist entries no longer read
+  uint64_t done;        // D->H  mirror of the completion word
+  int32_t error;        // D->H  first asynchronous error
+  int32_t flags;        // H->D  bit0 active, bit1 exclusive
+  int32_t rank;         // H->D  world rank of the stream
+  int32_t pad[5];
+};
+static_assert(sizeof(StreamCtl) == 128, "stream control line");
+
+enum { SF_ACTIVE = 1, SF_EXCLUSIVE = 2 };
+enum { ENG_STOPPED = 0, ENG_RUNNING = 1, ENG_EXITING = 2 };
+
+struct alignas(128) WorldCtl {
+  int32_t state;      // ENG_*
+  int32_t stop;       // H->D exit when idle
+  int32_t error;      // D->H first world error
+  int32_t failed;     // D->H watchdog fired: operations are released without data
+  uint64_t counters[8];
+  uint64_t heartbeat;  // D->H globaltimer of the last engine tick
+  int32_t pad[8];
+};
+
+// ---------------------------------------------------------------------------
+// device-side state
+// ---------------------------------------------------------------------------
+// physical flags of an operation
+enum : int32_t {
+  PF_MATCHED = 1,     // logical partner known
+  PF_SCHED = 2,       // a data task has been created
+  PF_STAGED = 4,      // send payload is in the staging arena
+  PF_DELIVERED = 8,   // payload is in the receive buffer (send or recv side)
+  PF_COMPLETE = 16,   // completion visible to the stream (send: staged or delivered)
+  PF_WAITED = 32,     // a completed wait covered this request
+  PF_STAGING = 64     // staging task in flight
+};
+
+struct alignas(64) DOp {
+  Desc d;             // copy of the descriptor
+  uint64_t partner;   // ref (stream << 40 | seq) of the matched partner
+  int64_t bytes;      // recv: bytes delivered; send: packed bytes
+  uint64_t stage;     // staging arena offset + 1 when staged
+  int32_t lstate;     // 0 new, 1 posted, 2 logically complete
+  int32_t lround;     // round of logical completion
+  int32_t pflags;     // PF_*
+  int32_t err;        // status error
+  int32_t msrc;       // recv: matched source rank
+  int32_t mtag;       // recv: matched tag
+  uint32_t wscan;     // waitall: logical scan position
+  uint32_t pscan;     // waitall: physical scan position
+  int64_t t_ingest;   // globaltimer at ingest
+};
+static_assert(sizeof(DOp) == 128, "device op record");
+
+struct SState {
+  uint64_t ingested;   // last seq copied from the ring
+  uint64_t cursor;     // next seq the logical advance looks at
+  uint64_t pc;         // next seq the physical completion scan looks at
+  uint64_t retire;     // last retired seq
+  uint64_t sched;      // next seq the scheduler looks at
+  uint64_t done;       // last completion word value written
+  uint64_t reached;    // stream has executed up to this seq (doorbell)
+  uint64_t wl_retired; // waitlist entries finished
+  int64_t stall_t0;    // globaltimer when the current physical stall began (0: none)
+  int32_t flags;       // copy of StreamCtl.flags
+  int32_t rank;
+  int32_t nposts;      // posts of the current round
+  int32_t pad;
+};
+
+struct QEntry {
+  uint64_t ref;   // 0 = tombstone
+  int32_t src;    // send: sender rank; recv: source or ANY_SOURCE
+  int32_t tag;    // send: tag; recv: tag or ANY_TAG
+};
+
+struct QHead {
+  uint32_t head, tail;
+};
+
+struct Layout {
+  uint64_t base;     // address of instance 0
+  int64_t seg;       // contiguous bytes per segment (whole message when contiguous)
+  int64_t stride;    // bytes between segment starts within an instance
+  int64_t per;       // segments per instance
+  int64_t extent;    // bytes between instance starts
+};
+
+enum TaskType : uint32_t { T_COPY = 1, T_REDUCE = 2 };
+enum TaskAction : uint32_t { A_DELIVER = 1, A_STAGE = 2, A_DELIVER_STAGED = 3, A_REDUCE = 4 };
+
+struct alignas(128) Task {
+  uint64_t claim;       // (task id << 32) | next unclaimed tile
+  uint32_t tiles_done;  // tiles finished
+  uint32_t ntiles;
+  uint32_t type;        // TaskType
+  uint32_t action;      // TaskAction
+  int64_t bytes;        // COPY: packed bytes; REDUCE: elements
+  int64_t tile;         // COPY: packed bytes per tile; REDUCE: elements per tile
+  Layout src, dst;      // COPY
+  uint64_t ref_s, ref_r;  // COPY: send / recv ops; REDUCE: instance slot
+  uint32_t nr, dtype, mode, unit;   // unit: bytes moved per access (16/8/4/2/1)
+  uint64_t ptrs;        // REDUCE: device array of nr inputs then nr outputs
+  int64_t chunk;        // COPY: bytes contiguous on both sides (kContig = whole tile)
+};
+static_assert(sizeof(Task) <= 256, "task record");
+
+struct InstSlot {
+  uint64_t k1;      // instance number + 1, 0 = free
+  int32_t arrived;  // arrivals so far
+  int32_t state;    // 0 collecting, 1 logically complete, 2 task created
+  int32_t err;
+  int32_t pad;
+};
+
+struct StageRec {
+  uint64_t off;     // arena offset
+  uint64_t size;    // bytes reserved (0 = free slot)
+  int32_t freed;
+  int32_t pad;
+};
+
+struct alignas(128) Shared {
+  // task ring
+  uint64_t task_head;    // lowest task id that may have unclaimed tiles (movers)
+  uint64_t task_alloc;   // next task id to allocate (control)
+  uint64_t task_retire;  // tasks below this are finished and processed
+  uint64_t pad0[13];
+  // control
+  uint64_t round;
+  int64_t last_progress;
+  int32_t exit_flag;     // control -> movers: leave now
+  int32_t epoch;         // launch epoch
+  int32_t ctl_error;
+  int32_t pad1;
+  // staging ring allocator (control-owned)
+  uint64_t st_head, st_tail;     // arena byte offsets (monotone)
+  uint64_t sr_head, sr_tail;     // StageRec ring indices
+  uint64_t pad2[8];
+  // grid barrier for the control group
+  uint32_t bar_count, bar_gen;
+};
+
+// Kernel argument: pointers into world-owned memory plus configuration.
+struct EngineParams {
+  int32_t nranks, max_streams, slots_log2, max_comms;
+  int32_t qcap_log2, tq_log2, iw, mode;   // mode: 0 persistent, 1 drain
+  int32_t wl_log2, sr_log2, ctl_ctas, pad;
+  int64_t watchdog_ns, idle_ns, stage_delay_ns;
+  int64_t tile_bytes, bulk_min;
+  int64_t stage_bytes;
+  const Desc* rings;          // [max_streams << slots_log2]   pinned
+  const int64_t* waitlists;   // [max_streams << wl_log2]      pinned
+  StreamCtl* sctl;            // [max_streams]                 pinned
+  WorldCtl* wctl;             //                                pinned
+  uint64_t* doorbell;         // [max_streams] device (written by stream memops)
+  uint64_t* done;             // [max_streams] device (waited on by stream memops)
+  DOp* ops;                   // [max_streams << slots_log2]
+  SState* ss;                 // [max_streams]
+  uint64_t* postbuf;          // [max_streams << slots_log2] this round's posts
+  QEntry* pq;                 // posted receives [ndomains << qcap_log2]
+  QEntry* uq;                 // unexpected sends
+  QHead* pqh;                 // [ndomains]
+  QHead* uqh;
+  Task* tasks;                // [1 << tq_log2]
+  Shared* sh;
+  uint8_t* stage;             // staging arena
+  StageRec* srec;             // [1 << sr_log2]
+  InstSlot* inst;             // [max_comms * iw]
+  uint64_t* inst_refs;        // [max_comms * iw * nranks]
+  int64_t* next_inst;         // [max_comms * nranks]
+  uint64_t* reduce_ptrs;      // [max_comms * iw * 2 * nranks]
+};
+
+constexpr int64_t kContig = (int64_t)1 << 62;
+
+__host__ __device__ inline uint64_t make_ref(int g, uint64_t seq) {
+  return ((uint64_t)g << 40) | seq;
+}
+__host__ __device__ inline int ref_stream(uint64_t ref) { return (int)(ref >> 40); }
+__host__ __device__ inline uint64_t ref_seq(uint64_t ref) { return ref & ((1ull << 40) - 1); }
+
+}  // namespace mpxi
+
+// engine launch entry (mpx_engine.cu)
+extern "C" int mpxi_engine_launch(const mpxi::EngineParams* p, int nctas, int nthreads,
+                                  void* cuda_stream, int cooperative);
+extern "C" int mpxi_engine_smem_bytes(void);

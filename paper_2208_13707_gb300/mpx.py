@@ -1,0 +1,285 @@
+"""ctypes binding of libmpx.so (include/mpx.h): same names, argument
+marshalling only.  Every call that returns an error code raises MpxError with
+that code (`.code`); `lib` gives the raw functions.  Raises at import time
+when the library has not been built: there is no fallback path."""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmpx.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmpx.so is not built ({LIB_PATH}); run paper_2208_13707_gb300.build.build()")
+
+lib = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
+
+# --- constants (include/mpx.h) ---
+ANY_SOURCE, ANY_TAG, TAG_UB, UNDEFINED = -2, -1, (1 << 30) - 1, -32766
+BYTE = UINT8 = 0
+INT32, INT64, FLOAT, DOUBLE = 1, 2, 3, 4
+SUM = 0
+REDUCE_FIXED, REDUCE_TREE = 0, 1
+STREAM_DEFAULT, STREAM_EXCLUSIVE = 0, 1
+ENGINE_PERSISTENT, ENGINE_DRAIN, ENGINE_PLAIN = 0, 1, 2
+REQUEST_NULL = -1
+IN_PLACE = 1
+ERRORS = {0: "SUCCESS", 1: "ERR_ARG", 2: "ERR_RANK", 3: "ERR_TAG", 4: "ERR_TYPE", 5: "ERR_COMM",
+          6: "ERR_NO_ENDPOINT", 7: "ERR_AGAIN", 8: "ERR_STREAM", 9: "ERR_PENDING", 10: "ERR_CUDA",
+          11: "ERR_REQUEST", 12: "ERR_NO_MEM", 13: "ERR_STATE", 14: "ERR_INTERN",
+          15: "ERR_TRUNCATE", 16: "ERR_TIMEOUT", 17: "ERR_UNSUPPORTED"}
+globals().update({"ERR_" + v[4:] if v.startswith("ERR_") else v: k for k, v in ERRORS.items()})
+
+
+class MpxError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        super().__init__(f"{where}: MPX_{ERRORS.get(code, code)}")
+        self.code = code
+
+
+class WorldConfig(ctypes.Structure):
+    _fields_ = [("engine_mode", ctypes.c_int32), ("max_streams", ctypes.c_int32),
+                ("ring_slots", ctypes.c_int32), ("max_comms", ctypes.c_int32),
+                ("queue_slots", ctypes.c_int32), ("task_slots", ctypes.c_int32),
+                ("engine_ctas", ctypes.c_int32), ("engine_threads", ctypes.c_int32),
+                ("tile_bytes", ctypes.c_int32), ("bulk_min_bytes", ctypes.c_int32),
+                ("reduce_mode", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("staging_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("watchdog_ns", ctypes.c_int64), ("idle_exit_ns", ctypes.c_int64),
+                ("stage_delay_ns", ctypes.c_int64)]
+
+
+class Status(ctypes.Structure):
+    _fields_ = [("source", ctypes.c_int32), ("tag", ctypes.c_int32), ("error", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("bytes", ctypes.c_int64)]
+
+
+_vp, _i32, _i64, _u32, _f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
+_P = ctypes.POINTER
+_SIGS = {
+    "mpx_world_config_init": [_P(WorldConfig)],
+    "mpx_world_create": [ctypes.c_int, _P(WorldConfig), _P(_vp)],
+    "mpx_world_free": [_P(_vp)],
+    "mpx_world_start": [_vp],
+    "mpx_world_stop": [_vp, ctypes.c_int],
+    "mpx_world_progress": [_vp, _vp],
+    "mpx_world_abort": [_vp],
+    "mpx_world_get_error": [_vp, _P(ctypes.c_int)],
+    "mpx_world_get_counters": [_vp, _P(_i64), ctypes.c_int],
+    "mpx_stream_create": [_vp, ctypes.c_int, _vp, ctypes.c_uint, _P(_vp)],
+    "mpx_stream_free": [_P(_vp)],
+    "mpx_stream_get_id": [_vp, _P(ctypes.c_int)],
+    "mpx_stream_get_error": [_vp, _P(ctypes.c_int)],
+    "mpx_stream_pending": [_vp, _P(_i64)],
+    "mpx_stream_comm_create": [_vp, ctypes.c_int, _P(_vp), _P(_vp)],
+    "mpx_comm_free": [_P(_vp)],
+    "mpx_comm_rank": [_vp, _P(ctypes.c_int)],
+    "mpx_comm_size": [_vp, _P(ctypes.c_int)],
+    "mpx_comm_set_reduce_mode": [_vp, ctypes.c_int],
+    "mpx_type_vector": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32, _P(_i32)],
+    "mpx_type_free": [_P(_i32)],
+    "mpx_type_size": [_i32, _P(_i64)],
+    "mpx_type_extent": [_i32, _P(_i64)],
+    "mpx_send_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp],
+    "mpx_recv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _vp],
+    "mpx_isend_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_irecv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_wait_enqueue": [_P(_i64), _vp],
+    "mpx_waitall_enqueue": [ctypes.c_int, _P(_i64), _vp],
+    "mpx_allreduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp],
+    "mpx_get_count": [_P(Status), _i32, _P(_i64)],
+    "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
+    "mpx_version": [],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+
+
+def _chk(rc: int, where: str):
+    if rc != 0:
+        raise MpxError(rc, where)
+
+
+# --- world ---
+def mpx_world_config_init() -> WorldConfig:
+    c = WorldConfig()
+    _chk(lib.mpx_world_config_init(ctypes.byref(c)), "mpx_world_config_init")
+    return c
+
+
+def mpx_world_create(nranks: int, cfg: Optional[WorldConfig] = None) -> int:
+    w = _vp()
+    _chk(lib.mpx_world_create(nranks, ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(w)),
+         "mpx_world_create")
+    return w.value
+
+
+def mpx_world_free(world: int) -> None:
+    w = _vp(world)
+    _chk(lib.mpx_world_free(ctypes.byref(w)), "mpx_world_free")
+
+
+def mpx_world_start(world: int) -> None:
+    _chk(lib.mpx_world_start(world), "mpx_world_start")
+
+
+def mpx_world_stop(world: int, timeout_ms: int = 10000) -> None:
+    _chk(lib.mpx_world_stop(world, timeout_ms), "mpx_world_stop")
+
+
+def mpx_world_progress(world: int, stream: int) -> None:
+    _chk(lib.mpx_world_progress(world, stream), "mpx_world_progress")
+
+
+def mpx_world_abort(world: int) -> None:
+    _chk(lib.mpx_world_abort(world), "mpx_world_abort")
+
+
+def mpx_world_get_error(world: int) -> int:
+    e = ctypes.c_int()
+    _chk(lib.mpx_world_get_error(world, ctypes.byref(e)), "mpx_world_get_error")
+    return e.value
+
+
+def mpx_world_get_counters(world: int) -> list:
+    a = (_i64 * 8)()
+    _chk(lib.mpx_world_get_counters(world, a, 8), "mpx_world_get_counters")
+    return list(a)
+
+
+# --- streams and communicators ---
+def mpx_stream_create(world: int, rank: int, cuda_stream: int, flags: int = 0) -> int:
+    s = _vp()
+    _chk(lib.mpx_stream_create(world, rank, cuda_stream, flags, ctypes.byref(s)), "mpx_stream_create")
+    return s.value
+
+
+def mpx_stream_free(stream: int) -> None:
+    s = _vp(stream)
+    _chk(lib.mpx_stream_free(ctypes.byref(s)), "mpx_stream_free")
+
+
+def mpx_stream_get_id(stream: int) -> int:
+    i = ctypes.c_int()
+    _chk(lib.mpx_stream_get_id(stream, ctypes.byref(i)), "mpx_stream_get_id")
+    return i.value
+
+
+def mpx_stream_get_error(stream: int) -> int:
+    e = ctypes.c_int()
+    _chk(lib.mpx_stream_get_error(stream, ctypes.byref(e)), "mpx_stream_get_error")
+    return e.value
+
+
+def mpx_stream_pending(stream: int) -> int:
+    n = _i64()
+    _chk(lib.mpx_stream_pending(stream, ctypes.byref(n)), "mpx_stream_pending")
+    return n.value
+
+
+def mpx_stream_comm_create(world: int, streams: Sequence[int]) -> list:
+    n = len(streams)
+    arr = (_vp * n)(*streams)
+    out = (_vp * n)()
+    _chk(lib.mpx_stream_comm_create(world, n, arr, out), "mpx_stream_comm_create")
+    return [out[i] for i in range(n)]
+
+
+def mpx_comm_free(comm: int) -> None:
+    c = _vp(comm)
+    _chk(lib.mpx_comm_free(ctypes.byref(c)), "mpx_comm_free")
+
+
+def mpx_comm_rank(comm: int) -> int:
+    r = ctypes.c_int()
+    _chk(lib.mpx_comm_rank(comm, ctypes.byref(r)), "mpx_comm_rank")
+    return r.value
+
+
+def mpx_comm_size(comm: int) -> int:
+    r = ctypes.c_int()
+    _chk(lib.mpx_comm_size(comm, ctypes.byref(r)), "mpx_comm_size")
+    return r.value
+
+
+def mpx_comm_set_reduce_mode(comm: int, mode: int) -> None:
+    _chk(lib.mpx_comm_set_reduce_mode(comm, mode), "mpx_comm_set_reduce_mode")
+
+
+# --- datatypes ---
+def mpx_type_vector(count: int, blocklength: int, stride: int, oldtype: int) -> int:
+    t = _i32()
+    _chk(lib.mpx_type_vector(count, blocklength, stride, oldtype, ctypes.byref(t)), "mpx_type_vector")
+    return t.value
+
+
+def mpx_type_free(t: int) -> None:
+    x = _i32(t)
+    _chk(lib.mpx_type_free(ctypes.byref(x)), "mpx_type_free")
+
+
+def mpx_type_size(t: int) -> int:
+    x = _i64()
+    _chk(lib.mpx_type_size(t, ctypes.byref(x)), "mpx_type_size")
+    return x.value
+
+
+def mpx_type_extent(t: int) -> int:
+    x = _i64()
+    _chk(lib.mpx_type_extent(t, ctypes.byref(x)), "mpx_type_extent")
+    return x.value
+
+
+# --- enqueue (buffers and statuses are device addresses as ints) ---
+def mpx_send_enqueue(buf: int, count: int, datatype: int, dest: int, tag: int, comm: int) -> None:
+    _chk(lib.mpx_send_enqueue(buf, count, datatype, dest, tag, comm), "mpx_send_enqueue")
+
+
+def mpx_recv_enqueue(buf: int, count: int, datatype: int, source: int, tag: int, comm: int,
+                     status: int = 0) -> None:
+    _chk(lib.mpx_recv_enqueue(buf, count, datatype, source, tag, comm, status or None), "mpx_recv_enqueue")
+
+
+def mpx_isend_enqueue(buf: int, count: int, datatype: int, dest: int, tag: int, comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_isend_enqueue(buf, count, datatype, dest, tag, comm, ctypes.byref(r)), "mpx_isend_enqueue")
+    return r.value
+
+
+def mpx_irecv_enqueue(buf: int, count: int, datatype: int, source: int, tag: int, comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_irecv_enqueue(buf, count, datatype, source, tag, comm, ctypes.byref(r)), "mpx_irecv_enqueue")
+    return r.value
+
+
+def mpx_wait_enqueue(request: int, status: int = 0) -> None:
+    r = _i64(request)
+    _chk(lib.mpx_wait_enqueue(ctypes.byref(r), status or None), "mpx_wait_enqueue")
+
+
+def mpx_waitall_enqueue(requests: Sequence[int], statuses: int = 0) -> None:
+    n = len(requests)
+    arr = (_i64 * max(1, n))(*requests)
+    _chk(lib.mpx_waitall_enqueue(n, arr, statuses or None), "mpx_waitall_enqueue")
+
+
+def mpx_allreduce_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, comm: int) -> None:
+    _chk(lib.mpx_allreduce_enqueue(sendbuf, recvbuf, count, datatype, op, comm), "mpx_allreduce_enqueue")
+
+
+def mpx_get_count(status: Status, datatype: int) -> int:
+    c = _i64()
+    _chk(lib.mpx_get_count(ctypes.byref(status), datatype, ctypes.byref(c)), "mpx_get_count")
+    return c.value
+
+
+def mpx_saxpy_enqueue(n: int, a: float, x: int, y: int, stream: int) -> None:
+    _chk(lib.mpx_saxpy_enqueue(n, a, x, y, stream), "mpx_saxpy_enqueue")
+
+
+def mpx_version() -> int:
+    return lib.mpx_version()

@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, byte
+for byte on payloads and field by field on statuses."""
+import numpy as np
+import pytest
+
+import oracle
+from traffic import gen
+from traffic.program import (ANY_SOURCE, ANY_TAG, ERR_TRUNCATE, MODE_FIXED, MODE_TREE, T_BYTE,
+                             T_DOUBLE, T_FLOAT, T_INT32, T_INT64, ProgramBuilder)
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from traffic import gpu
+    return gpu
+
+
+def _compare(p, mode="persistent", exclusive=False, status=True, cfg_over=None, timeout_s=120):
+    gpu = _gpu()
+    ref = oracle.run(p)
+    assert ref.error == 0, "oracle rejected the program"
+    assert not ref.deadlock
+    out = gpu.run(p, mode=mode, exclusive=exclusive, cfg_over=cfg_over, timeout_s=timeout_s)
+    assert out.finished, "GPU run did not finish before the deadline"
+    assert out.world_error == 0, f"world error {out.world_error}"
+    for k, (a, b) in enumerate(zip(out.buffers, ref.buffers)):
+        if not np.array_equal(a, b):
+            diff = np.nonzero(a != b)[0]
+            raise AssertionError(f"buffer {k}: {len(diff)} bytes differ, first at {diff[:8]}")
+    if status and p.nstatus:
+        assert np.array_equal(out.status, ref.status), "statuses differ"
+    return out, ref
+
+
+def test_listing4_gives_four():
+    p = gen.listing4(1 << 20)
+    out, _ = _compare(p)
+    assert np.all(out.buffers[p.meta["dy"]].view(np.float32) == 4.0)
+
+
+def test_listing3_four_stream_comms():
+    _compare(gen.listing3(4, 100))
+
+
+@pytest.mark.parametrize("exclusive", [False, True])
+def test_tiny_pairs_blocking_sends_and_permuted_recvs(exclusive):
+    _compare(gen.tiny_pairs(nmsg=1000), exclusive=exclusive)
+
+
+@pytest.mark.parametrize("mode", ["persistent", "drain"])
+def test_ring_exchange_small(mode):
+    p = gen.ring_exchange(nranks=8, n=1 << 12, steps=4, min_bytes=256, max_bytes=256 << 10)
+    _compare(p, mode=mode)
+
+
+def test_ring_exchange_tiles_and_ragged_tail():
+    # messages up to 3 MB: many tiles per message, TMA bulk and strided paths
+    p = gen.ring_exchange(nranks=4, n=1 << 16, steps=3, min_bytes=100_000, max_bytes=3 << 20)
+    _compare(p, cfg_over={"tile_bytes": 65536})
+
+
+@pytest.mark.parametrize("mode", [MODE_FIXED, MODE_TREE])
+def test_allreduce_matches_oracle(mode):
+    dts = (T_INT64, T_FLOAT, T_INT32, T_BYTE, T_DOUBLE) if mode == MODE_FIXED else (T_FLOAT,)
+    p = gen.allreduce_suite(nranks=16, sizes=(1, 7, 1024, 65537), dtypes=dts, modes=(mode,))
+    gpu = _gpu()
+    ref = oracle.run(p)
+    out = gpu.run(p, timeout_s=120)
+    assert out.finished and out.world_error == 0
+    for inst in p.meta["instances"]:
+        for r in range(p.nranks):
+            b = inst["recv"][r]
+            if mode == MODE_FIXED:
+                assert np.array_equal(out.buffers[b], ref.buffers[b])
+            else:
+                xs = [p.buf_init[inst["send"][k]].view(np.float32) for k in range(p.nranks)]
+                s64, a64 = oracle.sum_f32_ref(xs)
+                y = out.buffers[b].view(np.float32).astype(np.float64)
+                assert np.all(np.abs(y - s64) <= 1e-6 * a64 + 1e-30)
+
+
+def test_allreduce_in_place_tree():
+    p = gen.allreduce_suite(nranks=16, sizes=(4099,), dtypes=(T_FLOAT,), modes=(MODE_TREE,), in_place=True)
+    gpu = _gpu()
+    out = gpu.run(p, timeout_s=120)
+    assert out.finished and out.world_error == 0
+    inst = p.meta["instances"][0]
+    xs = [p.buf_init[inst["recv"][k]].view(np.float32) for k in range(p.nranks)]
+    s64, a64 = oracle.sum_f32_ref(xs)
+    for r in range(p.nranks):
+        y = out.buffers[inst["recv"][r]].view(np.float32).astype(np.float64)
+        assert np.all(np.abs(y - s64) <= 1e-6 * a64 + 1e-30)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_wildcard_programs_drain_exact(seed):
+    p = gen.random_small(seed, nranks=3, nmsg=6)
+    ref = oracle.run(p)
+    if ref.deadlock:
+        pytest.skip("program deadlocks by construction")
+    _compare(p, mode="drain")
+
+
+def test_halo_exchange_small():
+    _compare(gen.halo3d(sub=16, steps=2))
+
+
+def test_batching_wildcards_drain_exact():
+    fix = lambda prog: [int(j) for j in oracle.run(prog).stuck_op if j >= 0] if oracle.run(prog).deadlock else None
+    p = gen.batching(nranks=8, streams_per_rank=2, nmsg=3000, max_bytes=64 << 10, fixup=fix)
+    _compare(p, mode="drain")
+
+
+def test_truncation_and_any_tag_status():
+    b = ProgramBuilder(2)
+    g0, g1 = b.stream(0), b.stream(1)
+    c = b.comm([g0, g1])
+    src = b.buffer(np.arange(1, 161, dtype=np.uint8))
+    dst = b.buffer(np.full(256, 0xEE, np.uint8))
+    st = b.status_slots(2)
+    b.send(g0, c, src, 0, 40, T_INT32, 1, 5)
+    b.send(g0, c, src, 0, 3, T_INT32, 1, 9)
+    b.recv(g1, c, dst, 4, 6, T_INT32, 0, 5, st)
+    b.recv(g1, c, dst, 64, 10, T_INT32, ANY_SOURCE, ANY_TAG, st + 1)
+    p = b.build()
+    out, ref = _compare(p)
+    assert out.status[0]["error"] == ERR_TRUNCATE and out.status[1]["tag"] == 9
+
+
+def test_zero_count_messages():
+    b = ProgramBuilder(2)
+    g0, g1 = b.stream(0), b.stream(1)
+    c = b.comm([g0, g1])
+    x = b.buffer(64)
+    st = b.status_slots(1)
+    b.send(g0, c, x, 0, 0, T_FLOAT, 1, 1)
+    b.recv(g1, c, x, 0, 0, T_FLOAT, 0, 1, st)
+    h = b.isend(g1, c, x, 0, 0, T_BYTE, 0, 2)
+    b.wait(g1, h)
+    b.recv(g0, c, x, 32, 4, T_BYTE, 1, 2)
+    _compare(b.build())

@@ -1,0 +1,188 @@
+"""Run a traffic program on the GPU through libmpx's C ABI.
+
+Device memory and CUDA streams come from PyTorch; every operation goes
+through the library (`paper_2208_13707_gb300.mpx`), and the user compute op
+(axpy) through the library's exported Listing 4 kernel.  Nothing here
+computes a result: it allocates, enqueues in the program's issue order,
+waits with a host-side deadline, and reads buffers and statuses back.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from .program import (ALLREDUCE, AXPY, IN_PLACE, IRECV, ISEND, RECV, SEND, STATUS_DTYPE, WAIT,
+                      WAITALL, Program)
+
+
+@dataclass
+class GpuOutcome:
+    buffers: List[np.ndarray]
+    status: np.ndarray
+    stream_errors: List[int]
+    world_error: int
+    counters: List[int]
+    finished: bool
+    seconds: float
+    extra: dict = field(default_factory=dict)
+
+
+def _pow2_at_least(n: int, lo: int) -> int:
+    v = lo
+    while v < n:
+        v *= 2
+    return v
+
+
+def make_config(prog: Program, mode: int, **over):
+    from paper_2208_13707_gb300 import mpx
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mode
+    cfg.max_streams = max(cfg.max_streams, prog.nstreams)
+    per_stream = int(np.max(np.diff(prog.stream_op_lo))) if prog.nstreams else 1
+    cfg.ring_slots = _pow2_at_least(per_stream + 1, 256)
+    cfg.max_comms = max(1, prog.ncomms)
+    cfg.queue_slots = _pow2_at_least(per_stream + 1, 256)
+    cfg.watchdog_ns = int(5e9)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclusive: bool = False,
+        cfg_over: Optional[dict] = None, buffers: Optional[list] = None, keep_world: bool = False,
+        drain_passes: int = 10000) -> GpuOutcome:
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    dev = torch.device("cuda")
+    m = {"persistent": mpx.ENGINE_PERSISTENT, "drain": mpx.ENGINE_DRAIN, "plain": mpx.ENGINE_PLAIN}[mode]
+    cfg = make_config(prog, m, **(cfg_over or {}))
+    init = buffers if buffers is not None else prog.buf_init
+    dbufs = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) if b.size else
+             torch.empty(16, dtype=torch.uint8, device=dev) for b in init]
+    st = torch.zeros(max(1, prog.nstatus) * STATUS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    ptr = [b.data_ptr() for b in dbufs]
+    st_ptr = st.data_ptr()
+
+    def sptr(slot):
+        return 0 if slot < 0 else st_ptr + STATUS_DTYPE.itemsize * int(slot)
+
+    world = mpx.mpx_world_create(prog.nranks, cfg)
+    cstreams = [torch.cuda.Stream(device=dev) for _ in range(prog.nstreams)]
+    flags = mpx.STREAM_EXCLUSIVE if exclusive else mpx.STREAM_DEFAULT
+    ms = []
+    for g in range(prog.nstreams):
+        ms.append(mpx.mpx_stream_create(world, int(prog.stream_rank[g]), cstreams[g].cuda_stream, flags))
+        assert mpx.mpx_stream_get_id(ms[g]) == g
+    comms = [mpx.mpx_stream_comm_create(world, [ms[int(g)] for g in prog.comm_stream[c]])
+             for c in range(prog.ncomms)]
+    tmap = {}
+    for t in range(len(prog.types)):
+        r = prog.types[t]
+        tmap[t] = t if t < 5 else mpx.mpx_type_vector(int(r["vcount"]), int(r["blocklen"]),
+                                                      int(r["stride"]), int(r["base"]))
+    rank_in = {}
+    for c in range(prog.ncomms):
+        for r, g in enumerate(prog.comm_stream[c]):
+            rank_in[(c, int(g))] = r
+    engine_stream = torch.cuda.Stream(device=dev)
+    req: Dict[int, int] = {}
+    ops = prog.ops
+
+    def retry(fn):
+        for _ in range(100000):
+            try:
+                return fn()
+            except mpx.MpxError as e:
+                if e.code != mpx.ERR_AGAIN:
+                    raise
+                if m == mpx.ENGINE_DRAIN:
+                    mpx.mpx_world_progress(world, engine_stream.cuda_stream)
+                    engine_stream.synchronize()
+                else:
+                    time.sleep(1e-4)
+        raise RuntimeError("submission ring stayed full")
+
+    t0 = time.perf_counter()
+    for j in prog.issue_order:
+        o = ops[int(j)]
+        k, g = int(o["kind"]), int(o["stream"])
+        c = int(o["comm"])
+        comm = comms[c][rank_in[(c, g)]] if c >= 0 else None
+        b = int(o["buf"])
+        p = ptr[b] + int(o["off"]) if b >= 0 else 0
+        cnt, ty, peer, tag = int(o["count"]), tmap.get(int(o["type"]), 0), int(o["peer"]), int(o["tag"])
+        if k == SEND:
+            retry(lambda: mpx.mpx_send_enqueue(p, cnt, ty, peer, tag, comm))
+        elif k == RECV:
+            retry(lambda: mpx.mpx_recv_enqueue(p, cnt, ty, peer, tag, comm, sptr(int(o["status"]))))
+        elif k == ISEND:
+            req[int(j)] = retry(lambda: mpx.mpx_isend_enqueue(p, cnt, ty, peer, tag, comm))
+        elif k == IRECV:
+            req[int(j)] = retry(lambda: mpx.mpx_irecv_enqueue(p, cnt, ty, peer, tag, comm))
+        elif k in (WAIT, WAITALL):
+            lo, n = int(o["req_lo"]), int(o["req_n"])
+            hs = [req[int(q)] for q in prog.reqlist[lo: lo + n]]
+            if k == WAIT:
+                retry(lambda: mpx.mpx_wait_enqueue(hs[0], sptr(int(o["status"]))))
+            else:
+                retry(lambda: mpx.mpx_waitall_enqueue(hs, sptr(int(o["status"]))))
+        elif k == ALLREDUCE:
+            rb = ptr[int(o["buf2"])] + int(o["off2"])
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            retry(lambda: mpx.mpx_allreduce_enqueue(sb, rb, cnt, ty, mpx.SUM, comm))
+        elif k == AXPY:
+            yb = ptr[int(o["buf2"])] + int(o["off2"])
+            mpx.mpx_saxpy_enqueue(cnt, float(o["alpha"]), p, yb, cstreams[g].cuda_stream)
+        else:
+            raise ValueError(k)
+    t_issue = time.perf_counter() - t0
+
+    deadline = time.perf_counter() + timeout_s
+    finished = False
+    passes = 0
+    if m == mpx.ENGINE_DRAIN:
+        while time.perf_counter() < deadline and passes < drain_passes:
+            mpx.mpx_world_progress(world, engine_stream.cuda_stream)
+            engine_stream.synchronize()
+            passes += 1
+            if all(mpx.mpx_stream_pending(s) == 0 for s in ms):
+                break
+    while time.perf_counter() < deadline:
+        if all(s.query() for s in cstreams):
+            finished = True
+            break
+        time.sleep(1e-4)
+    seconds = time.perf_counter() - t0
+    if not finished:
+        # release every waiter so the streams drain, then give them a moment
+        mpx.mpx_world_abort(world)
+        t1 = time.perf_counter()
+        while time.perf_counter() - t1 < 10 and not all(s.query() for s in cstreams):
+            time.sleep(1e-3)
+    if finished:
+        torch.cuda.synchronize()
+    out_bufs = [b.cpu().numpy()[: init[i].size].copy() for i, b in enumerate(dbufs)] if finished else []
+    status = np.frombuffer(st.cpu().numpy().tobytes(), STATUS_DTYPE)[: prog.nstatus].copy() if finished else None
+    serr = [mpx.mpx_stream_get_error(s) for s in ms]
+    werr = mpx.mpx_world_get_error(world)
+    counters = mpx.mpx_world_get_counters(world)
+    extra = {"issue_seconds": t_issue, "drain_passes": passes}
+    if finished and not keep_world:
+        for c in range(prog.ncomms):
+            for h in comms[c]:
+                mpx.mpx_comm_free(h)
+        for t, v in tmap.items():
+            if t >= 5:
+                mpx.mpx_type_free(v)
+        for s in ms:
+            mpx.mpx_stream_free(s)
+        mpx.mpx_world_free(world)
+    elif keep_world:
+        extra.update(world=world, streams=ms, comms=comms, cstreams=cstreams, dbufs=dbufs)
+    return GpuOutcome(buffers=out_bufs, status=status, stream_errors=serr, world_error=werr,
+                      counters=counters, finished=finished, seconds=seconds, extra=extra)
