@@ -37,6 +37,14 @@
  *     different threads concurrently.
  *   - Nothing here allocates per message.  Library memory is allocated at
  *     mpx_world_create and mpx_stream_create.
+ *   - Blocking calls put cuStreamWaitValue64 on the caller's stream.  An
+ *     unsatisfied wait stalls the hardware queue the stream is mapped to, and
+ *     so every stream sharing it; CUDA maps streams onto
+ *     CUDA_DEVICE_MAX_CONNECTIONS queues.  Loading the library sets that
+ *     variable to 32 unless it is already set (it only takes effect if CUDA
+ *     is not initialised yet).  Keep the non-exclusive streams of a world
+ *     within that many queues; exclusive streams carry no doorbell and are
+ *     not limited.
  */
 #ifndef MPX_H
 #define MPX_H
@@ -186,6 +194,10 @@ int mpx_world_progress(mpx_world_t world, mpx_cuda_stream_t stream);
  * enqueue calls return MPX_ERR_STATE.  Use it when a deadline passes. */
 int mpx_world_abort(mpx_world_t world);
 
+/* Diagnostic: print the engine's per-stream cursors and task-ring state to
+ * stderr (bounded wait; safe while the engine runs). */
+int mpx_world_debug_dump(mpx_world_t world);
+
 /* Sticky first asynchronous error of the world (MPX_SUCCESS if none). */
 int mpx_world_get_error(mpx_world_t world, int* first_error);
 
@@ -286,6 +298,11 @@ int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* 
  * enqueued communication: y[i] = a*x[i] + y[i] (fused multiply-add, one
  * rounding) for i < n, launched on `stream`.  Not an MPI call. */
 int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y, mpx_cuda_stream_t stream);
+
+/* Convenience: create / destroy a non-blocking CUDA stream (each call makes a
+ * new stream).  Not an MPI call. */
+int mpx_cuda_stream_create(mpx_cuda_stream_t* stream);
+int mpx_cuda_stream_destroy(mpx_cuda_stream_t stream);
 
 /* Library version (major*100+minor). */
 int mpx_version(void);

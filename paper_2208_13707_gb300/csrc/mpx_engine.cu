@@ -369,13 +369,15 @@ __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint6
   for (uint32_t j = 0; j < nch; ++j) {
     const uint32_t s = j % kTmaStages;
     const uint32_t par = (phase >> s) & 1u;
-    uint32_t spins = 0;
     bool landed = true;
-    while (!mbar_try_wait(&sm.bar[s], par)) {
-      if (++spins > (1u << 22)) {  // a bulk load that never lands: report and give up
-        set_error(P, -1, kErrIntern);
-        landed = false;
-        break;
+    if (!mbar_try_wait(&sm.bar[s], par)) {
+      const uint64_t t0 = now_ns();
+      while (!mbar_try_wait(&sm.bar[s], par)) {
+        if (now_ns() - t0 > 50000000ull) {  // a bulk load that never lands: report and give up
+          set_error(P, -1, kErrIntern);
+          landed = false;
+          break;
+        }
       }
     }
     if (!landed) {
@@ -611,7 +613,7 @@ __device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
       if (i >= a) break;
       Task* T = &P.tasks[i & mask];
       const uint64_t c = ld_acq_gpu(&T->claim);
-      if ((uint32_t)(c >> 32) != (uint32_t)i) break;  // not published yet
+      if ((uint32_t)(c >> 32) != (uint32_t)(i + 1)) break;  // not published yet
       const uint32_t k = (uint32_t)c;
       const uint32_t nt = *(volatile uint32_t*)&T->ntiles;
       if (k >= nt) {
@@ -863,16 +865,14 @@ struct Ctl {
       }
       head += (uint32_t)__popc(r);
     }
-    if (lane == 0) h.head = head;
+    h.head = head;  // every lane keeps the same copy of the queue bounds
     __syncwarp();
   }
 
   __device__ bool q_push(QEntry* q, QHead& h, uint32_t qmask, QEntry e) {
     if ((h.tail - h.head) > qmask) return false;
-    if ((threadIdx.x & 31) == 0) {
-      q[h.tail & qmask] = e;
-      h.tail = h.tail + 1;
-    }
+    if ((threadIdx.x & 31) == 0) q[h.tail & qmask] = e;
+    h.tail = h.tail + 1;  // all lanes: loop bounds in q_find must stay warp-uniform
     __syncwarp();
     return true;
   }
@@ -1000,10 +1000,12 @@ struct Ctl {
     id = a;
     return &P.tasks[id & (cap - 1)];
   }
+  // The claim word carries id+1 in its high half, so a zeroed or recycled
+  // slot never looks published for this id.
   __device__ void task_publish(Task* T, uint64_t id) {
     T->tiles_done = 0;
     __threadfence();
-    st_rel_gpu(&T->claim, (id << 32));
+    st_rel_gpu(&T->claim, ((id + 1) << 32));
   }
 
   __device__ void fill_copy(Task* T, const Layout& src, const Layout& dst, int64_t bytes) {
@@ -1443,7 +1445,7 @@ struct Ctl {
     for (uint64_t id = r0 + threadIdx.x; id < a; id += blockDim.x) {
       Task* T = &P.tasks[id & mask];
       if (T->type == 0) continue;  // already processed
-      if ((uint32_t)(ld_acq_gpu(&T->claim) >> 32) != (uint32_t)id) continue;
+      if ((uint32_t)(ld_acq_gpu(&T->claim) >> 32) != (uint32_t)(id + 1)) continue;
       if (ld_acq_gpu32(&T->tiles_done) < T->ntiles) continue;
       if (T->type == T_COPY) {
         DOp* s = op_ref(P, T->ref_s);
@@ -1508,6 +1510,14 @@ __device__ void release_all(const EngineParams& P, int err) {
   }
 }
 
+// A failed world moves no more data: drop every task that was not finished.
+__device__ void abandon_tasks(const EngineParams& P) {
+  Shared* sh = P.sh;
+  const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+  st_rel_gpu(&sh->task_head, a);
+  sh->task_retire = a;
+}
+
 __device__ void grid_barrier(const EngineParams& P, int nctas) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1561,7 +1571,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     if (ing) sm.any = 1;
     __syncthreads();
     if (failed_at_start || ld_vol32(&P.wctl->failed)) {
-      if (tid == 0) sm.pending = 0;
+      if (tid == 0) {
+        sm.pending = 0;
+        abandon_tasks(P);
+      }
       release_all(P, kErrTimeout);
       __syncthreads();
     } else {
@@ -1603,7 +1616,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         uint64_t r0 = sh->task_retire;
         const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
         while (r0 < a && P.tasks[r0 & mask].type == 0 &&
-               (uint32_t)(P.tasks[r0 & mask].claim >> 32) == (uint32_t)r0)
+               (uint32_t)(P.tasks[r0 & mask].claim >> 32) == (uint32_t)(r0 + 1))
           ++r0;
         sh->task_retire = r0;
         C.stage_reclaim();
@@ -1670,6 +1683,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     __syncthreads();
     if (sm.flag == 1) break;
     if (sm.flag == 2) {
+      if (tid == 0) abandon_tasks(P);
       release_all(P, kErrTimeout);
       __syncthreads();
       continue;
@@ -1769,6 +1783,14 @@ extern "C" int mpxi_engine_launch(const mpxi::EngineParams* p, int nctas, int nt
     e = cudaLaunchKernel((const void*)mpxi::engine_kernel, dim3(nctas), dim3(nthreads), args,
                          (size_t)smem, (cudaStream_t)cuda_stream);
   return (int)e;
+}
+
+// Load the engine's module now: a module loaded lazily at its first launch
+// may wait for running kernels to finish, which a resident engine never does
+// while it has work.
+extern "C" int mpxi_engine_preload(void) {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, mpxi::engine_kernel) == cudaSuccess ? 0 : 1;
 }
 
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads) {

@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 #include <time.h>
@@ -35,6 +36,36 @@
 using namespace mpxi;
 
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads);
+extern "C" int mpxi_engine_preload(void);
+extern "C" int mpxi_saxpy_preload(void);
+
+// A cuStreamWaitValue64 that is not yet satisfied stalls the hardware queue
+// its CUDA stream is mapped to, and every other stream sharing that queue.
+// CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS queues (default 8), so
+// a doorbell of one virtual rank could sit behind another rank's blocked
+// wait.  Ask for the maximum (32) when the library is loaded before CUDA is
+// initialised; an explicit user setting is kept.
+__attribute__((constructor)) static void mpxi_default_connections() {
+  setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0);
+}
+
+// MPX_DEBUG=1 traces host-side steps to stderr.
+static bool debug_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MPX_DEBUG");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+#define MPX_TRACE(...)                    \
+  do {                                    \
+    if (debug_on()) {                     \
+      fprintf(stderr, "[mpx] " __VA_ARGS__); \
+      fprintf(stderr, "\n");              \
+      fflush(stderr);                     \
+    }                                     \
+  } while (0)
 
 // Stream memory operations come from the driver; they are looked up through
 // the runtime so the library loads (and its symbols can be inspected) on a
@@ -262,8 +293,14 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, w->device);
   // make sure the runtime's primary context exists, and the driver's stream
   // memory operations are available
+  MPX_TRACE("world_create: nranks=%d mode=%d", nranks, cfg.engine_mode);
   cudaFree(0);
+  MPX_TRACE("world_create: context ready");
   if (cfg.engine_mode != MPX_ENGINE_PLAIN && !memops_ready()) { world_release(w); return MPX_ERR_CUDA; }
+  // load every kernel of the library before any engine runs (lazy loading of
+  // a module can wait for running kernels, and a resident engine is one)
+  if (mpxi_engine_preload() || mpxi_saxpy_preload()) { world_release(w); return MPX_ERR_CUDA; }
+  MPX_TRACE("world_create: memops and kernels loaded");
   const int S = cfg.max_streams;
   w->slots_log2 = log2i(cfg.ring_slots);
   w->wl_log2 = log2i((int64_t)cfg.ring_slots * 4);
@@ -322,6 +359,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
   w->dev_bytes = off;
   if (cfg.budget_bytes > 0 && (int64_t)off > cfg.budget_bytes) { world_release(w); return MPX_ERR_NO_MEM; }
+  MPX_TRACE("world_create: device block %zu bytes", off);
   if (cudaMalloc(&w->dev_block, off) != cudaSuccess) { world_release(w); return MPX_ERR_NO_MEM; }
   uint8_t* base = (uint8_t*)w->dev_block;
   // zero everything except the staging arena
@@ -388,6 +426,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   int ctas = cfg.engine_ctas > 0 ? cfg.engine_ctas : w->nsm;
   ctas = std::min(ctas, per_sm * w->nsm);
   w->engine_ctas = std::max(1, ctas);
+  MPX_TRACE("world_create: done, engine %d x %d (per_sm %d)", w->engine_ctas, w->engine_threads, per_sm);
   *out = w;
   return MPX_SUCCESS;
 }
@@ -396,7 +435,9 @@ static int launch_engine(mpx_world_s* w, cudaStream_t s, int mode) {
   EngineParams P = w->params;
   P.mode = mode;
   if (mode == 1) P.idle_ns = std::min<int64_t>(w->cfg.idle_exit_ns, 200000);
+  MPX_TRACE("launch_engine: mode %d", mode);
   int e = mpxi_engine_launch(&P, w->engine_ctas, w->engine_threads, (void*)s, 1);
+  MPX_TRACE("launch_engine: rc %d", e);
   return e == 0 ? MPX_SUCCESS : MPX_ERR_CUDA;
 }
 
@@ -440,7 +481,14 @@ extern "C" int mpx_world_stop(mpx_world_t w, int timeout_ms) {
     if (now_ms() - t0 > timeout_ms) { rc = MPX_ERR_TIMEOUT; break; }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-  if (rc == MPX_SUCCESS && cudaStreamSynchronize(w->engine_stream) != cudaSuccess) rc = MPX_ERR_CUDA;
+  // the kernel has announced its exit; wait (bounded) until it has left the GPU
+  while (rc == MPX_SUCCESS) {
+    cudaError_t q = cudaStreamQuery(w->engine_stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) { rc = MPX_ERR_CUDA; break; }
+    if (now_ms() - t0 > timeout_ms) { rc = MPX_ERR_TIMEOUT; break; }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
   __atomic_store_n(&w->wctl->stop, 0, __ATOMIC_RELEASE);
   return rc;
 }
@@ -478,6 +526,47 @@ extern "C" int mpx_world_abort(mpx_world_t w) {
   return rc;
 }
 
+// Diagnostic: print the engine's per-stream cursors and task-ring state to
+// stderr.  Reads device memory through a private non-blocking stream with a
+// bounded wait, so it is safe while the engine runs.
+extern "C" int mpx_world_debug_dump(mpx_world_t w) {
+  if (!w || w->plain) return MPX_ERR_ARG;
+  const int S = w->cfg.max_streams;
+  std::vector<SState> ss(S);
+  Shared sh;
+  std::vector<uint64_t> door(S), done(S);
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MPX_ERR_CUDA;
+  cudaMemcpyAsync(ss.data(), w->params.ss, S * sizeof(SState), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&sh, w->params.sh, sizeof(Shared), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(door.data(), w->params.doorbell, S * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(done.data(), w->params.done, S * 8, cudaMemcpyDeviceToHost, st);
+  const int64_t t0 = now_ms();
+  while (cudaStreamQuery(st) == cudaErrorNotReady && now_ms() - t0 < 2000)
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  const bool ok = cudaStreamQuery(st) == cudaSuccess;
+  cudaStreamDestroy(st);
+  if (!ok) return MPX_ERR_TIMEOUT;
+  fprintf(stderr, "[mpx dump] state %d failed %d error %d tasks head %llu alloc %llu retire %llu round %llu\n",
+          w->wctl->state, w->wctl->failed, w->wctl->error, (unsigned long long)sh.task_head,
+          (unsigned long long)sh.task_alloc, (unsigned long long)sh.task_retire,
+          (unsigned long long)sh.round);
+  for (int g = 0; g < S; ++g) {
+    const StreamCtl& c = w->sctl[g];
+    if (!c.flags && !c.tail) continue;
+    const SState& x = ss[g];
+    fprintf(stderr,
+            "[mpx dump] g%d tail %llu retired %llu | ing %llu cur %llu pc %llu ret %llu sched %llu done %llu "
+            "reached %llu door %llu dn %llu stall %lld flags %d err %d\n",
+            g, (unsigned long long)c.tail, (unsigned long long)c.retired, (unsigned long long)x.ingested,
+            (unsigned long long)x.cursor, (unsigned long long)x.pc, (unsigned long long)x.retire,
+            (unsigned long long)x.sched, (unsigned long long)x.done, (unsigned long long)x.reached,
+            (unsigned long long)door[g], (unsigned long long)done[g], (long long)x.stall_t0, x.flags, c.error);
+  }
+  fflush(stderr);
+  return MPX_SUCCESS;
+}
+
 extern "C" int mpx_world_get_error(mpx_world_t w, int* err) {
   if (!w || !err) return MPX_ERR_ARG;
   if (w->plain) { *err = plain::error(w->plain); return MPX_SUCCESS; }
@@ -505,7 +594,18 @@ extern "C" int mpx_world_free(mpx_world_t* pw) {
   if (w->cfg.engine_mode == MPX_ENGINE_PERSISTENT) {
     if (mpx_world_stop(w, 10000) != MPX_SUCCESS) return MPX_ERR_TIMEOUT;
   }
-  if (w->engine_stream) cudaStreamSynchronize(w->engine_stream);
+  // every wait here is bounded: a kernel that does not finish leaves the
+  // world allocated and reports MPX_ERR_TIMEOUT
+  if (w->engine_stream) {
+    const int64_t t0 = now_ms();
+    for (;;) {
+      cudaError_t q = cudaStreamQuery(w->engine_stream);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return MPX_ERR_CUDA;
+      if (now_ms() - t0 > 10000) return MPX_ERR_TIMEOUT;
+      std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+  }
   world_release(w);
   *pw = nullptr;
   return MPX_SUCCESS;
@@ -724,6 +824,18 @@ extern "C" int mpx_get_count(const mpx_status_t* st, mpx_datatype_t t, int64_t* 
 
 extern "C" int mpx_version(void) { return 100; }
 
+extern "C" int mpx_cuda_stream_create(mpx_cuda_stream_t* stream) {
+  if (!stream) return MPX_ERR_ARG;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return MPX_ERR_CUDA;
+  *stream = (mpx_cuda_stream_t)s;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_cuda_stream_destroy(mpx_cuda_stream_t stream) {
+  return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? MPX_SUCCESS : MPX_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // enqueue
 // ---------------------------------------------------------------------------
@@ -744,11 +856,17 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out) {
       std::this_thread::yield();
     }
   }
+  MPX_TRACE("publish: stream %d seq %llu kind %u blocking %d", s->id, (unsigned long long)seq,
+            kw_kind(d.kw), (int)blocking);
   Desc* slot = &w->rings[((size_t)s->id << w->slots_log2) + ((seq - 1) & (slots - 1))];
   memcpy(slot, &d, sizeof(Desc));
   __atomic_store_n(&c->tail, seq, __ATOMIC_RELEASE);
   s->next_seq = seq + 1;
   if (seq_out) *seq_out = seq;  // the operation exists from here on
+  // launch the engine (persistent mode) before this call's wait can stall a
+  // hardware queue the engine's stream might share
+  int erc = ensure_engine(w);
+  if (erc) return erc;
   CUstream cs = (CUstream)s->cs;
   if (!(s->flags & MPX_STREAM_EXCLUSIVE)) {
     CUdeviceptr db = (CUdeviceptr)(w->params.doorbell + s->id);
@@ -758,7 +876,8 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out) {
     CUdeviceptr dn = (CUdeviceptr)(w->params.done + s->id);
     if (g_wait64(cs, dn, seq, CU_STREAM_WAIT_VALUE_GEQ) != CUDA_SUCCESS) return MPX_ERR_CUDA;
   }
-  return ensure_engine(w);
+  MPX_TRACE("publish: memops queued");
+  return MPX_SUCCESS;
 }
 
 static int fill_p2p(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt,

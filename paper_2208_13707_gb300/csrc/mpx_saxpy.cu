@@ -32,6 +32,11 @@ __global__ void saxpy_kernel(int64_t n, float a, const float* __restrict__ x, fl
 
 }  // namespace
 
+extern "C" int mpxi_saxpy_preload(void) {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, saxpy_kernel) == cudaSuccess ? 0 : 1;
+}
+
 extern "C" int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y,
                                  mpx_cuda_stream_t stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return MPX_ERR_ARG;

@@ -11,6 +11,9 @@ from typing import Optional, Sequence
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmpx.so")
 
+# see include/mpx.h: unsatisfied stream waits stall their hardware queue
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libmpx.so is not built ({LIB_PATH}); run paper_2208_13707_gb300.build.build()")
 
@@ -66,6 +69,7 @@ _SIGS = {
     "mpx_world_stop": [_vp, ctypes.c_int],
     "mpx_world_progress": [_vp, _vp],
     "mpx_world_abort": [_vp],
+    "mpx_world_debug_dump": [_vp],
     "mpx_world_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_world_get_counters": [_vp, _P(_i64), ctypes.c_int],
     "mpx_stream_create": [_vp, ctypes.c_int, _vp, ctypes.c_uint, _P(_vp)],
@@ -92,6 +96,8 @@ _SIGS = {
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_version": [],
+    "mpx_cuda_stream_create": [_P(_vp)],
+    "mpx_cuda_stream_destroy": [_vp],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(lib, _name)
@@ -137,6 +143,10 @@ def mpx_world_progress(world: int, stream: int) -> None:
 
 def mpx_world_abort(world: int) -> None:
     _chk(lib.mpx_world_abort(world), "mpx_world_abort")
+
+
+def mpx_world_debug_dump(world: int) -> None:
+    lib.mpx_world_debug_dump(world)
 
 
 def mpx_world_get_error(world: int) -> int:
@@ -279,6 +289,16 @@ def mpx_get_count(status: Status, datatype: int) -> int:
 
 def mpx_saxpy_enqueue(n: int, a: float, x: int, y: int, stream: int) -> None:
     _chk(lib.mpx_saxpy_enqueue(n, a, x, y, stream), "mpx_saxpy_enqueue")
+
+
+def mpx_cuda_stream_create() -> int:
+    s = _vp()
+    _chk(lib.mpx_cuda_stream_create(ctypes.byref(s)), "mpx_cuda_stream_create")
+    return s.value
+
+
+def mpx_cuda_stream_destroy(stream: int) -> None:
+    _chk(lib.mpx_cuda_stream_destroy(stream), "mpx_cuda_stream_destroy")
 
 
 def mpx_version() -> int:

@@ -19,14 +19,15 @@ def _gpu():
     return gpu
 
 
-def _compare(p, mode="persistent", exclusive=False, status=True, cfg_over=None, timeout_s=120):
+def _compare(p, mode="persistent", exclusive=False, status=True, cfg_over=None, timeout_s=45,
+             world_error=0):
     gpu = _gpu()
     ref = oracle.run(p)
     assert ref.error == 0, "oracle rejected the program"
     assert not ref.deadlock
     out = gpu.run(p, mode=mode, exclusive=exclusive, cfg_over=cfg_over, timeout_s=timeout_s)
     assert out.finished, "GPU run did not finish before the deadline"
-    assert out.world_error == 0, f"world error {out.world_error}"
+    assert out.world_error == world_error, f"world error {out.world_error}"
     for k, (a, b) in enumerate(zip(out.buffers, ref.buffers)):
         if not np.array_equal(a, b):
             diff = np.nonzero(a != b)[0]
@@ -69,7 +70,7 @@ def test_allreduce_matches_oracle(mode):
     p = gen.allreduce_suite(nranks=16, sizes=(1, 7, 1024, 65537), dtypes=dts, modes=(mode,))
     gpu = _gpu()
     ref = oracle.run(p)
-    out = gpu.run(p, timeout_s=120)
+    out = gpu.run(p, timeout_s=45)
     assert out.finished and out.world_error == 0
     for inst in p.meta["instances"]:
         for r in range(p.nranks):
@@ -86,7 +87,7 @@ def test_allreduce_matches_oracle(mode):
 def test_allreduce_in_place_tree():
     p = gen.allreduce_suite(nranks=16, sizes=(4099,), dtypes=(T_FLOAT,), modes=(MODE_TREE,), in_place=True)
     gpu = _gpu()
-    out = gpu.run(p, timeout_s=120)
+    out = gpu.run(p, timeout_s=45)
     assert out.finished and out.world_error == 0
     inst = p.meta["instances"][0]
     xs = [p.buf_init[inst["recv"][k]].view(np.float32) for k in range(p.nranks)]
@@ -127,7 +128,7 @@ def test_truncation_and_any_tag_status():
     b.recv(g1, c, dst, 4, 6, T_INT32, 0, 5, st)
     b.recv(g1, c, dst, 64, 10, T_INT32, ANY_SOURCE, ANY_TAG, st + 1)
     p = b.build()
-    out, ref = _compare(p)
+    out, ref = _compare(p, world_error=ERR_TRUNCATE)   # truncation is a sticky async error
     assert out.status[0]["error"] == ERR_TRUNCATE and out.status[1]["tag"] == 9
 
 

@@ -64,7 +64,7 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
     dbufs = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) if b.size else
              torch.empty(16, dtype=torch.uint8, device=dev) for b in init]
     st = torch.zeros(max(1, prog.nstatus) * STATUS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
+    torch.cuda.current_stream(dev).synchronize()
     ptr = [b.data_ptr() for b in dbufs]
     st_ptr = st.data_ptr()
 
@@ -72,7 +72,9 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
         return 0 if slot < 0 else st_ptr + STATUS_DTYPE.itemsize * int(slot)
 
     world = mpx.mpx_world_create(prog.nranks, cfg)
-    cstreams = [torch.cuda.Stream(device=dev) for _ in range(prog.nstreams)]
+    # distinct non-blocking streams (torch.cuda.Stream() hands out a fixed pool)
+    raw_streams = [mpx.mpx_cuda_stream_create() for _ in range(prog.nstreams + 1)]
+    cstreams = [torch.cuda.ExternalStream(h, device=dev) for h in raw_streams[:-1]]
     flags = mpx.STREAM_EXCLUSIVE if exclusive else mpx.STREAM_DEFAULT
     ms = []
     for g in range(prog.nstreams):
@@ -89,7 +91,7 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
     for c in range(prog.ncomms):
         for r, g in enumerate(prog.comm_stream[c]):
             rank_in[(c, int(g))] = r
-    engine_stream = torch.cuda.Stream(device=dev)
+    engine_stream = torch.cuda.ExternalStream(raw_streams[-1], device=dev)
     req: Dict[int, int] = {}
     ops = prog.ops
 
@@ -102,7 +104,9 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
                     raise
                 if m == mpx.ENGINE_DRAIN:
                     mpx.mpx_world_progress(world, engine_stream.cuda_stream)
-                    engine_stream.synchronize()
+                    t_dl = time.perf_counter() + timeout_s
+                    while not engine_stream.query() and time.perf_counter() < t_dl:
+                        time.sleep(5e-5)
                 else:
                     time.sleep(1e-4)
         raise RuntimeError("submission ring stayed full")
@@ -148,9 +152,17 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
     if m == mpx.ENGINE_DRAIN:
         while time.perf_counter() < deadline and passes < drain_passes:
             mpx.mpx_world_progress(world, engine_stream.cuda_stream)
-            engine_stream.synchronize()
+            while not engine_stream.query() and time.perf_counter() < deadline:
+                time.sleep(5e-5)
             passes += 1
             if all(mpx.mpx_stream_pending(s) == 0 for s in ms):
+                break
+            if passes % 200 == 0 and all(s.query() for s in cstreams):
+                # the streams are idle yet operations stay pending: report
+                import sys
+                print(f"[gpu.run] drain: streams idle, pending "
+                      f"{[mpx.mpx_stream_pending(s) for s in ms]}", file=sys.stderr, flush=True)
+                mpx.mpx_world_debug_dump(world)
                 break
     while time.perf_counter() < deadline:
         if all(s.query() for s in cstreams):
@@ -158,14 +170,18 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             break
         time.sleep(1e-4)
     seconds = time.perf_counter() - t0
+    if not finished or (m == mpx.ENGINE_DRAIN and passes >= drain_passes):
+        import sys
+        print(f"[gpu.run] deadline: finished={finished} passes={passes} counters="
+              f"{mpx.mpx_world_get_counters(world)}", file=sys.stderr, flush=True)
+        if m != mpx.ENGINE_PLAIN:
+            mpx.mpx_world_debug_dump(world)
     if not finished:
         # release every waiter so the streams drain, then give them a moment
         mpx.mpx_world_abort(world)
         t1 = time.perf_counter()
         while time.perf_counter() - t1 < 10 and not all(s.query() for s in cstreams):
             time.sleep(1e-3)
-    if finished:
-        torch.cuda.synchronize()
     out_bufs = [b.cpu().numpy()[: init[i].size].copy() for i, b in enumerate(dbufs)] if finished else []
     status = np.frombuffer(st.cpu().numpy().tobytes(), STATUS_DTYPE)[: prog.nstatus].copy() if finished else None
     serr = [mpx.mpx_stream_get_error(s) for s in ms]
@@ -180,8 +196,19 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             if t >= 5:
                 mpx.mpx_type_free(v)
         for s in ms:
-            mpx.mpx_stream_free(s)
+            for _ in range(2000):
+                try:
+                    mpx.mpx_stream_free(s)
+                    break
+                except mpx.MpxError as e:
+                    if e.code != mpx.ERR_PENDING:
+                        raise
+                    time.sleep(5e-4)
+            else:
+                raise RuntimeError("stream still has pending operations")
         mpx.mpx_world_free(world)
+        for h in raw_streams:
+            mpx.mpx_cuda_stream_destroy(h)
     elif keep_world:
         extra.update(world=world, streams=ms, comms=comms, cstreams=cstreams, dbufs=dbufs)
     return GpuOutcome(buffers=out_bufs, status=status, stream_errors=serr, world_error=werr,
