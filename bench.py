@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark: ring exchange among 8 virtual ranks on one GB300, every step an
+fp32 axpy (n = 2^24) interleaved with isend/irecv to both neighbours and a
+waitall, all enqueued on the ranks' CUDA streams through libmpx.
+
+Messages are fp32, log-uniform 4 KB .. 64 MB; half are MPI_Type_vector
+(blocklen 64, stride 128) on the send side, receive layouts are the same
+vector or contiguous.  One step = 8 axpys + 16 messages + 8 waitalls; each
+step's communication completes in one engine pass (mpx_world_progress) that
+is enqueued after the step's axpys.  Timing uses CUDA events on the streams
+that run the work; inputs are larger than L2 (each step touches > 1.5 GB).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the world
+(the path has no cross-GPU exchange step): weak scaling, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "enqueued msgs/s, payload HBM GB/s (% of peak), p50/p99 enqueue-to-done µs"
+SEED = 0x220813707 + 1
+RANKS, N_AXPY = 8, 1 << 24
+MIN_BYTES, MAX_BYTES = 4096, 64 << 20
+BLOCKLEN, STRIDE = 64, 128
+ALPHA = 0.5
+WORKLOAD = ("ring exchange: 8 virtual ranks x 1 stream, fp32 axpy n=2^24 per rank per step, "
+            "isend/irecv to both neighbours + waitall, fp32 messages log-uniform 4KB-64MB, "
+            "half MPI_Type_vector(blocklen 64, stride 128)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ring_message(step, rank, direction):
+    from traffic.gen import _ring_message
+    return _ring_message(SEED, step, rank, direction, MIN_BYTES, MAX_BYTES)
+
+
+class ClockSampler:
+    """nvidia-smi samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+class RingBench:
+    def __init__(self, ranks=RANKS, n=N_AXPY, max_bytes=MAX_BYTES, tile_bytes=None, engine_ctas=0,
+                 bulk_min=None):
+        import torch
+        from paper_2208_13707_gb300 import mpx
+        self.torch, self.mpx = torch, mpx
+        self.dev = torch.device("cuda")
+        self.R, self.n = ranks, n
+        self.max_bytes = max_bytes
+        arena = max(2 * max_bytes, 4 * n) + 4096
+        self.arena = arena
+        g = torch.Generator(device=self.dev)
+        g.manual_seed(SEED)
+        f32 = torch.float32
+        self.S = [torch.randn(arena // 4, generator=g, device=self.dev, dtype=f32) for _ in range(ranks)]
+        self.RL = [torch.randn(arena // 4, generator=g, device=self.dev, dtype=f32) for _ in range(ranks)]
+        self.RR = [torch.zeros(arena // 4, device=self.dev, dtype=f32) for _ in range(ranks)]
+        torch.cuda.synchronize()
+        cfg = mpx.mpx_world_config_init()
+        cfg.engine_mode = mpx.ENGINE_DRAIN
+        cfg.max_streams = max(16, ranks)
+        cfg.ring_slots = 4096
+        cfg.max_comms = 2
+        cfg.queue_slots = 1024
+        cfg.engine_ctas = engine_ctas
+        if tile_bytes:
+            cfg.tile_bytes = tile_bytes
+        if bulk_min is not None:
+            cfg.bulk_min_bytes = bulk_min
+        self.world = mpx.mpx_world_create(ranks, cfg)
+        self.raw = [mpx.mpx_cuda_stream_create() for _ in range(ranks + 1)]
+        self.cs = [torch.cuda.ExternalStream(h, device=self.dev) for h in self.raw[:ranks]]
+        self.es = torch.cuda.ExternalStream(self.raw[-1], device=self.dev)
+        self.ms = [mpx.mpx_stream_create(self.world, r, self.raw[r]) for r in range(ranks)]
+        self.comm = mpx.mpx_stream_comm_create(self.world, self.ms)
+        self.vtypes = {}
+        self.launches = 0
+
+    def vtype(self, nb):
+        if nb not in self.vtypes:
+            self.vtypes[nb] = self.mpx.mpx_type_vector(nb, BLOCKLEN, STRIDE, self.mpx.FLOAT)
+        return self.vtypes[nb]
+
+    def layout(self, nbytes, lay, send):
+        vec = lay in ((1, 2) if send else (1, 3))
+        if vec:
+            return 1, self.vtype(nbytes // (4 * BLOCKLEN))
+        return nbytes // 4, self.mpx.FLOAT
+
+    def step_plan(self, step):
+        """Per rank: (sends [(count, type, dest, tag)], recvs [(count, type, src, tag, buf)]), bytes."""
+        R = self.R
+        plan, total = [], 0
+        for r in range(R):
+            sends, recvs = [], []
+            for d, dest in ((0, (r + 1) % R), (1, (r - 1) % R)):
+                nb, lay = ring_message(step, r, d)
+                sends.append(self.layout(nb, lay, True) + (dest, d))
+                total += nb
+            for d, src, buf in ((0, (r - 1) % R, self.RL[r]), (1, (r + 1) % R, self.RR[r])):
+                nb, lay = ring_message(step, src, d)
+                recvs.append(self.layout(nb, lay, False) + (src, d, buf))
+            plan.append((sends, recvs))
+        return plan, total
+
+    def enqueue_step(self, step, ev_reach=None, ev_done=None, ev_pass=None, h2d=None, d2h=None):
+        """Enqueue one step.  Returns the number of our kernel launches."""
+        mpx, torch = self.mpx, self.torch
+        plan, _ = self.step_plan(step)
+        axpy_ev = []
+        launches = 0
+        for r in range(self.R):
+            cs = self.cs[r]
+            if h2d is not None:
+                h2d(r, cs)
+            mpx.mpx_saxpy_enqueue(self.n, ALPHA, self.RL[r].data_ptr(), self.S[r].data_ptr(), cs.cuda_stream)
+            launches += 1
+            e = torch.cuda.Event()
+            e.record(cs)
+            axpy_ev.append(e)
+            if ev_reach is not None:
+                ev_reach[r].record(cs)
+            sends, recvs = plan[r]
+            reqs = []
+            for cnt, ty, dest, tag in sends:
+                reqs.append(mpx.mpx_isend_enqueue(self.S[r].data_ptr(), cnt, ty, dest, tag, self.comm[r]))
+            for cnt, ty, src, tag, buf in recvs:
+                reqs.append(mpx.mpx_irecv_enqueue(buf.data_ptr(), cnt, ty, src, tag, self.comm[r]))
+            mpx.mpx_waitall_enqueue(reqs)
+            if ev_done is not None:
+                ev_done[r].record(cs)
+            if d2h is not None:
+                d2h(r, cs)
+        for e in axpy_ev:
+            self.es.wait_event(e)
+        if ev_pass is not None:
+            ev_pass[0].record(self.es)
+        mpx.mpx_world_progress(self.world, self.es.cuda_stream)
+        launches += 1
+        if ev_pass is not None:
+            ev_pass[1].record(self.es)
+        return launches
+
+    def sync_all(self, timeout=120.0):
+        t0 = time.perf_counter()
+        streams = self.cs + [self.es]
+        while not all(s.query() for s in streams):
+            if time.perf_counter() - t0 > timeout:
+                self.mpx.mpx_world_debug_dump(self.world)
+                self.mpx.mpx_world_abort(self.world)
+                raise RuntimeError("benchmark step did not complete before the deadline")
+            time.sleep(2e-5)
+
+    def run(self, warmup, steps):
+        torch = self.torch
+        for s in range(warmup):
+            self.enqueue_step(s)
+        self.sync_all()
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        start, end = ev(), ev()
+        reach = [[ev() for _ in range(self.R)] for _ in range(steps)]
+        done = [[ev() for _ in range(self.R)] for _ in range(steps)]
+        passes = [[ev(), ev()] for _ in range(steps)]
+        payload = 0
+        # the timed region starts when every stream has passed `start`
+        start.record(self.es)
+        for s in self.cs:
+            s.wait_event(start)
+        launches = 0
+        t_host0 = time.perf_counter()
+        for k in range(steps):
+            step = warmup + k
+            payload += self.step_plan(step)[1]
+            launches += self.enqueue_step(step, reach[k], done[k], passes[k])
+        t_issue = time.perf_counter() - t_host0
+        for s in self.cs:
+            self.es.wait_stream(s)
+        end.record(self.es)
+        self.sync_all()
+        total_ms = start.elapsed_time(end)
+        pass_ms = [a.elapsed_time(b) for a, b in passes]
+        lat_us = [reach[k][r].elapsed_time(done[k][r]) * 1e3 for k in range(steps) for r in range(self.R)]
+        err = self.mpx.mpx_world_get_error(self.world)
+        if err:
+            raise RuntimeError(f"world error {err}")
+        return dict(total_ms=total_ms, pass_ms=pass_ms, lat_us=lat_us, payload=payload,
+                    launches=launches, issue_s=t_issue)
+
+    def run_e2e(self, warmup, steps):
+        """Same steps, with every step's send payload copied in from pinned host
+        memory and every received payload read back, inside the timed region."""
+        torch = self.torch
+        plan_bytes = []
+        pinned_in = [torch.empty(self.arena // 4, dtype=torch.float32, pin_memory=True) for _ in range(self.R)]
+        pinned_l = [torch.empty(self.arena // 4, dtype=torch.float32, pin_memory=True) for _ in range(self.R)]
+        pinned_r = [torch.empty(self.arena // 4, dtype=torch.float32, pin_memory=True) for _ in range(self.R)]
+        for r in range(self.R):
+            pinned_in[r].copy_(self.S[r].cpu())
+        counters = {"h2d": 0, "d2h": 0}
+
+        def make_h2d(step):
+            plan, _ = self.step_plan(step)
+
+            def h2d(r, cs):
+                span = 0
+                for cnt, ty, dest, tag in plan[r][0]:
+                    span = max(span, cnt * 4 if ty == self.mpx.FLOAT else
+                               (self.mpx.mpx_type_extent(ty) + 3) // 4 * 4)
+                with torch.cuda.stream(cs):
+                    self.S[r][: span // 4].copy_(pinned_in[r][: span // 4], non_blocking=True)
+                counters["h2d"] += span
+
+            def d2h(r, cs):
+                for cnt, ty, src, tag, buf in plan[r][1]:
+                    span = cnt * 4 if ty == self.mpx.FLOAT else (self.mpx.mpx_type_extent(ty) + 3) // 4 * 4
+                    dst = pinned_l[r] if buf is self.RL[r] else pinned_r[r]
+                    with torch.cuda.stream(cs):
+                        dst[: span // 4].copy_(buf[: span // 4], non_blocking=True)
+                    counters["d2h"] += span
+            return h2d, d2h
+
+        for s in range(warmup):
+            h, d = make_h2d(s)
+            self.enqueue_step(s, h2d=h, d2h=d)
+        self.sync_all()
+        counters["h2d"] = counters["d2h"] = 0
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        start, end = ev(), ev()
+        start.record(self.es)
+        for s in self.cs:
+            s.wait_event(start)
+        msgs = 0
+        for k in range(steps):
+            h, d = make_h2d(warmup + k)
+            self.enqueue_step(warmup + k, h2d=h, d2h=d)
+            msgs += 2 * self.R
+        for s in self.cs:
+            self.es.wait_stream(s)
+        end.record(self.es)
+        self.sync_all()
+        ms = start.elapsed_time(end)
+        return dict(value=msgs / (ms / 1e3), ms=ms, h2d=counters["h2d"] // steps, d2h=counters["d2h"] // steps)
+
+    def close(self):
+        mpx = self.mpx
+        for c in self.comm:
+            mpx.mpx_comm_free(c)
+        for t in self.vtypes.values():
+            mpx.mpx_type_free(t)
+        for s in self.ms:
+            for _ in range(2000):
+                try:
+                    mpx.mpx_stream_free(s)
+                    break
+                except mpx.MpxError:
+                    time.sleep(5e-4)
+        mpx.mpx_world_free(self.world)
+        for h in self.raw:
+            mpx.mpx_cuda_stream_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host: CPU baseline and the reference arm
+# ---------------------------------------------------------------------------
+def oracle_sample(steps=1, first_step=0):
+    """Time the CPU oracle on `steps` full-size ring steps (same sizes, same
+    axpy length).  Returns (msgs/s, seconds, messages)."""
+    import oracle
+    from traffic import gen
+    p = gen.ring_exchange(nranks=RANKS, n=N_AXPY, steps=steps, min_bytes=MIN_BYTES, max_bytes=MAX_BYTES,
+                          alpha=ALPHA, seed=SEED)
+    bufs = p.fresh_buffers()
+    t0 = time.perf_counter()
+    o = oracle.run(p, bufs)
+    dt = time.perf_counter() - t0
+    assert o.error == 0 and not o.deadlock
+    msgs = 2 * RANKS * steps
+    return msgs / dt, dt, msgs
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 2))
+    value, dt, msgs = oracle_sample(steps)
+    sample = f"{steps} full-size ring step(s): {msgs} messages, 8 axpys of 2^24 each, single thread"
+    line = {"metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ranks": RANKS, "n": N_AXPY},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "msgs/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "msgs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-bytes", type=int, default=0)
+    ap.add_argument("--engine-ctas", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world_size = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    if args.impl == "reference":
+        reference_arm(args, rank, world_size)
+        return
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    if dist is not None:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    b = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas)
+    sampler = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    res = b.run(args.warmup, args.steps)
+    clocks = sampler.stop()
+    total_s = res["total_ms"] / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    msgs_rank = 2 * b.R * args.steps
+    value = msgs_rank * world_size / total_s
+    payload_gbs = 2 * res["payload"] * world_size / total_s / 1e9
+    peak, peak_kind = peaks()
+    pass_s = sum(res["pass_ms"]) / 1e3
+    achieved = 2 * res["payload"] / pass_s / 1e9
+    lat = np.array(res["lat_us"])
+    e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
+    b.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, msgs = oracle_sample(1)
+        cpu = {"value": v, "unit": "msgs/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 full-size ring step ({msgs} messages + 8 axpys of 2^24), {dt:.1f} s single-threaded"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": world_size,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "ranks": b.R, "n": b.n, "messages_per_step": 2 * b.R,
+                           "engine": "drain pass per step (mpx_world_progress after the step's axpys)",
+                           "l2": "inputs larger than L2 (>1.5 GB touched per step)",
+                           "parallelism": f"replicas x{world_size}"},
+                "payload_gbs": payload_gbs, "payload_frac_of_peak": payload_gbs / peak,
+                "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": "engine_kernel (drain pass)", "peak_source": peak_kind,
+                             "avg_pass_us": 1e3 * float(np.mean(res["pass_ms"]))},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e["value"], "unit": "msgs/s", "h2d_bytes_per_step": e2e["h2d"],
+                        "d2h_bytes_per_step": e2e["d2h"]},
+                "gpu_launches": res["launches"], "clocks": clocks,
+                "host_issue_s": res["issue_s"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -180,10 +180,11 @@ int mpx_world_start(mpx_world_t world);
  * most timeout_ms) until it has exited.  MPX_ERR_TIMEOUT if it did not. */
 int mpx_world_stop(mpx_world_t world, int timeout_ms);
 
-/* DRAIN mode: enqueue one engine pass on `stream` (stream-ordered, may be
- * captured in a CUDA graph).  The pass ingests every operation published
- * so far, moves every payload whose both ends are ready, and returns when
- * nothing more can complete without new operations.  A pass must not
+/* DRAIN mode: enqueue one engine pass on `stream` (stream-ordered).  The pass
+ * ingests the operations published before this call (for worlds of at most
+ * 256 streams; larger worlds ingest everything visible when the pass runs),
+ * moves every payload whose both ends are ready, and returns once all of
+ * them are finished or nothing has progressed for 200 us.  A pass must not
  * overlap another engine pass of the same world (enqueue them on one
  * stream).  PLAIN mode: run host progress until nothing more can complete. */
 int mpx_world_progress(mpx_world_t world, mpx_cuda_stream_t stream);

@@ -667,6 +667,7 @@ struct Ctl {
       S.rank = ((volatile int32_t*)&P.sctl[g].rank)[0];
       uint64_t tail = 0;
       if (flags & SF_ACTIVE) tail = ld_acq_sys(&P.sctl[g].tail);
+      if (g < P.nlimit && tail > P.limit[g]) tail = P.limit[g];
       sm.cnt[g] = (flags & SF_ACTIVE) && tail > S.ingested ? (int32_t)(tail - S.ingested) : 0;
     }
     __syncthreads();

@@ -434,7 +434,15 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
 static int launch_engine(mpx_world_s* w, cudaStream_t s, int mode) {
   EngineParams P = w->params;
   P.mode = mode;
-  if (mode == 1) P.idle_ns = std::min<int64_t>(w->cfg.idle_exit_ns, 200000);
+  P.nlimit = 0;
+  if (mode == 1) {
+    P.idle_ns = std::min<int64_t>(w->cfg.idle_exit_ns, 200000);
+    // a pass drains what was published before it was enqueued
+    if (w->cfg.max_streams <= kMaxDrainLimits) {
+      P.nlimit = w->cfg.max_streams;
+      for (int g = 0; g < P.nlimit; ++g) P.limit[g] = __atomic_load_n(&w->sctl[g].tail, __ATOMIC_ACQUIRE);
+    }
+  }
   MPX_TRACE("launch_engine: mode %d", mode);
   int e = mpxi_engine_launch(&P, w->engine_ctas, w->engine_threads, (void*)s, 1);
   MPX_TRACE("launch_engine: rc %d", e);

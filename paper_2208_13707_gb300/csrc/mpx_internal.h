@@ -192,6 +192,8 @@ struct alignas(128) Shared {
   uint32_t bar_count, bar_gen;
 };
 
+constexpr int kMaxDrainLimits = 256;
+
 // Kernel argument: pointers into world-owned memory plus configuration.
 struct EngineParams {
   int32_t nranks, max_streams, slots_log2, max_comms;
@@ -221,6 +223,10 @@ struct EngineParams {
   uint64_t* inst_refs;        // [max_comms * iw * nranks]
   int64_t* next_inst;         // [max_comms * nranks]
   uint64_t* reduce_ptrs;      // [max_comms * iw * 2 * nranks]
+  // drain pass: ingest stream g only up to limit[g] (the operations published
+  // when the pass was enqueued); nlimit = 0 means no limit
+  int32_t nlimit, pad2;
+  uint64_t limit[kMaxDrainLimits];
 };
 
 constexpr int64_t kContig = (int64_t)1 << 62;
