@@ -150,6 +150,7 @@ class RingBench:
         self.comm = mpx.mpx_stream_comm_create(self.world, self.ms)
         self.vtypes = {}
         self.launches = 0
+        self.plans = {}
 
     def vtype(self, nb):
         if nb not in self.vtypes:
@@ -162,8 +163,15 @@ class RingBench:
             return 1, self.vtype(nbytes // (4 * BLOCKLEN))
         return nbytes // 4, self.mpx.FLOAT
 
+    def prepare(self, steps):
+        """Work out every step's message sizes and datatypes before timing."""
+        for s in range(steps):
+            self.step_plan(s)
+
     def step_plan(self, step):
         """Per rank: (sends [(count, type, dest, tag)], recvs [(count, type, src, tag, buf)]), bytes."""
+        if step in self.plans:
+            return self.plans[step]
         R = self.R
         plan, total = [], 0
         for r in range(R):
@@ -176,6 +184,7 @@ class RingBench:
                 nb, lay = ring_message(step, src, d)
                 recvs.append(self.layout(nb, lay, False) + (src, d, buf))
             plan.append((sends, recvs))
+        self.plans[step] = (plan, total)
         return plan, total
 
     def enqueue_step(self, step, ev_reach=None, ev_done=None, ev_pass=None, h2d=None, d2h=None):
@@ -228,6 +237,7 @@ class RingBench:
 
     def run(self, warmup, steps):
         torch = self.torch
+        self.prepare(warmup + steps)
         for s in range(warmup):
             self.enqueue_step(s)
         self.sync_all()
@@ -294,6 +304,7 @@ class RingBench:
                     counters["d2h"] += span
             return h2d, d2h
 
+        self.prepare(warmup + steps)
         for s in range(warmup):
             h, d = make_h2d(s)
             self.enqueue_step(s, h2d=h, d2h=d)

@@ -315,38 +315,73 @@ __device__ __forceinline__ void copy_unit(uint64_t d, uint64_t s) {
   else st1((void*)d, ld_cg1((const void*)s));
 }
 
-// Strided gather/scatter: chunks of C bytes are contiguous on both sides.
 template <int U>
-__device__ void chunked_copy(const Task& T, int64_t p0, int64_t p1) {
-  const int64_t C = T.chunk;
-  const int64_t upc = C / U;
-  int L = 32;
-  if (upc < 32) {
-    L = 1;
-    while (L * 2 <= upc) L *= 2;
-  }
-  const int cpw = 32 / L;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int sub = lane / L, ul = lane % L;
-  const int64_t nch = (p1 - p0 + C - 1) / C;
-  const int64_t D = (int64_t)nwarps * cpw;
-  int64_t c = (int64_t)warp * cpw + sub;
-  if (c >= nch) return;
-  SideIter si, di;
-  si.init(T.src, p0 + c * C, D * C);
-  di.init(T.dst, p0 + c * C, D * C);
-  for (; c < nch; c += D) {
-    const int64_t p = p0 + c * C;
-    const int64_t n = (p1 - p) < C ? (p1 - p) : C;
-    const uint64_t s = si.addr(), d = di.addr();
-    const int64_t full = n / U;
-#pragma unroll 4
-    for (int64_t u = ul; u < full; u += L) copy_unit<U>(d + u * U, s + u * U);
-    if (U > 1 && ul == 0) {
-      for (int64_t q = full * U; q < n; ++q) copy_unit<1>(d + q, s + q);
+struct UnitT;
+template <> struct UnitT<16> { typedef uint4 T; };
+template <> struct UnitT<8> { typedef uint2 T; };
+template <> struct UnitT<4> { typedef uint32_t T; };
+template <> struct UnitT<2> { typedef uint16_t T; };
+template <> struct UnitT<1> { typedef uint8_t T; };
+
+template <int U>
+__device__ __forceinline__ typename UnitT<U>::T ld_unit(uint64_t a) {
+  if constexpr (U == 16) return ld_cg16((const void*)a);
+  else if constexpr (U == 8) return ld_cg8((const void*)a);
+  else if constexpr (U == 4) return ld_cg4((const void*)a);
+  else if constexpr (U == 2) return ld_cg2((const void*)a);
+  else return ld_cg1((const void*)a);
+}
+template <int U>
+__device__ __forceinline__ void st_unit(uint64_t a, typename UnitT<U>::T v) {
+  if constexpr (U == 16) st16((void*)a, v);
+  else if constexpr (U == 8) st8((void*)a, v);
+  else if constexpr (U == 4) st4((void*)a, v);
+  else if constexpr (U == 2) st2((void*)a, v);
+  else st1((void*)a, v);
+}
+
+// Strided gather/scatter (MPI_Type_vector on either side): the packed
+// stream is cut into U-byte units that are contiguous and aligned on both
+// sides; thread t moves units t, t+nt, ... and keeps kBatch independent loads
+// in flight before storing them.
+template <int U>
+__device__ void strided_copy(const Task& T, int64_t p0, int64_t p1) {
+  constexpr int kBatch = U >= 8 ? 8 : 16;
+  typedef typename UnitT<U>::T V;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t nunits = (p1 - p0) / U;
+  if (tid < nunits) {
+    SideIter si, di;
+    si.init(T.src, p0 + (int64_t)tid * U, (int64_t)nt * U);
+    di.init(T.dst, p0 + (int64_t)tid * U, (int64_t)nt * U);
+    int64_t u = tid;
+    for (; u + (int64_t)(kBatch - 1) * nt < nunits; u += (int64_t)kBatch * nt) {
+      uint64_t sa[kBatch], da[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        sa[k] = si.addr();
+        da[k] = di.addr();
+        si.step();
+        di.step();
+      }
+      V v[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) v[k] = ld_unit<U>(sa[k]);
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) st_unit<U>(da[k], v[k]);
     }
-    si.step();
-    di.step();
+    for (; u < nunits; u += nt) {
+      st_unit<U>(di.addr(), ld_unit<U>(si.addr()));
+      si.step();
+      di.step();
+    }
+  }
+  // bytes past the last whole unit (only at the end of a message)
+  for (int64_t q = p0 + nunits * U + tid; q < p1; q += nt) {
+    SideIter si, di;
+    si.init(T.src, q, 1);
+    di.init(T.dst, q, 1);
+    st1((void*)di.addr(), ld_cg1((const void*)si.addr()));
   }
 }
 
@@ -415,15 +450,12 @@ __device__ void contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t 
     const uint64_t s = src + head, d = dst + head;
     const int64_t nv = (n - head) >> 4;
     int64_t i = tid;
-    for (; i + 3 * nt < nv; i += 4 * nt) {
-      uint4 a = ld_cg16((const void*)(s + 16 * i));
-      uint4 b = ld_cg16((const void*)(s + 16 * (i + nt)));
-      uint4 c = ld_cg16((const void*)(s + 16 * (i + 2 * nt)));
-      uint4 e = ld_cg16((const void*)(s + 16 * (i + 3 * nt)));
-      st16((void*)(d + 16 * i), a);
-      st16((void*)(d + 16 * (i + nt)), b);
-      st16((void*)(d + 16 * (i + 2 * nt)), c);
-      st16((void*)(d + 16 * (i + 3 * nt)), e);
+    for (; i + 7 * nt < nv; i += 8 * nt) {
+      uint4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = ld_cg16((const void*)(s + 16 * (i + k * nt)));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) st16((void*)(d + 16 * (i + k * nt)), v[k]);
     }
     for (; i < nv; i += nt) st16((void*)(d + 16 * i), ld_cg16((const void*)(s + 16 * i)));
     const int64_t tail0 = head + (nv << 4);
@@ -452,11 +484,11 @@ __device__ void copy_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k
     return;
   }
   switch (T.unit) {
-    case 16: chunked_copy<16>(T, p0, p1); break;
-    case 8: chunked_copy<8>(T, p0, p1); break;
-    case 4: chunked_copy<4>(T, p0, p1); break;
-    case 2: chunked_copy<2>(T, p0, p1); break;
-    default: chunked_copy<1>(T, p0, p1); break;
+    case 16: strided_copy<16>(T, p0, p1); break;
+    case 8: strided_copy<8>(T, p0, p1); break;
+    case 4: strided_copy<4>(T, p0, p1); break;
+    case 2: strided_copy<2>(T, p0, p1); break;
+    default: strided_copy<1>(T, p0, p1); break;
   }
 }
 
@@ -1031,7 +1063,10 @@ struct Ctl {
       while (U > 1 && bad(U)) U >>= 1;
     }
     T->unit = U;
-    int64_t tile = P.tile_bytes;
+    // about two tiles per engine CTA, never below tile_bytes or above 1 MiB
+    int64_t tile = (bytes + 2 * P.nctas - 1) / (2 * P.nctas);
+    tile = tile < P.tile_bytes ? P.tile_bytes : (tile > (1 << 20) ? (1 << 20) : tile);
+    tile = (tile + 255) & ~(int64_t)255;
     if (C != kContig) tile = C >= tile ? C : (tile / C) * C;
     T->tile = tile;
     T->ntiles = (uint32_t)((bytes + tile - 1) / tile);

@@ -426,6 +426,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   int ctas = cfg.engine_ctas > 0 ? cfg.engine_ctas : w->nsm;
   ctas = std::min(ctas, per_sm * w->nsm);
   w->engine_ctas = std::max(1, ctas);
+  P.nctas = w->engine_ctas;
   MPX_TRACE("world_create: done, engine %d x %d (per_sm %d)", w->engine_ctas, w->engine_threads, per_sm);
   *out = w;
   return MPX_SUCCESS;

@@ -198,7 +198,7 @@ constexpr int kMaxDrainLimits = 256;
 struct EngineParams {
   int32_t nranks, max_streams, slots_log2, max_comms;
   int32_t qcap_log2, tq_log2, iw, mode;   // mode: 0 persistent, 1 drain
-  int32_t wl_log2, sr_log2, ctl_ctas, pad;
+  int32_t wl_log2, sr_log2, ctl_ctas, nctas;
   int64_t watchdog_ns, idle_ns, stage_delay_ns;
   int64_t tile_bytes, bulk_min;
   int64_t stage_bytes;

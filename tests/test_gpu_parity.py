@@ -20,11 +20,13 @@ def _gpu():
 
 
 def _compare(p, mode="persistent", exclusive=False, status=True, cfg_over=None, timeout_s=45,
-             world_error=0):
+             world_error=None):
     gpu = _gpu()
     ref = oracle.run(p)
     assert ref.error == 0, "oracle rejected the program"
     assert not ref.deadlock
+    if world_error is None:  # the first asynchronous error the oracle's statuses imply
+        world_error = ERR_TRUNCATE if p.nstatus and np.any(ref.status["error"] == ERR_TRUNCATE) else 0
     out = gpu.run(p, mode=mode, exclusive=exclusive, cfg_over=cfg_over, timeout_s=timeout_s)
     assert out.finished, "GPU run did not finish before the deadline"
     assert out.world_error == world_error, f"world error {out.world_error}"
