@@ -199,9 +199,6 @@ class RingBench:
                 h2d(r, cs)
             mpx.mpx_saxpy_enqueue(self.n, ALPHA, self.RL[r].data_ptr(), self.S[r].data_ptr(), cs.cuda_stream)
             launches += 1
-            e = torch.cuda.Event()
-            e.record(cs)
-            axpy_ev.append(e)
             if ev_reach is not None:
                 ev_reach[r].record(cs)
             sends, recvs = plan[r]
@@ -210,6 +207,11 @@ class RingBench:
                 reqs.append(mpx.mpx_isend_enqueue(self.S[r].data_ptr(), cnt, ty, dest, tag, self.comm[r]))
             for cnt, ty, src, tag, buf in recvs:
                 reqs.append(mpx.mpx_irecv_enqueue(buf.data_ptr(), cnt, ty, src, tag, self.comm[r]))
+            # the pass starts once every rank has run its axpy and rung the
+            # doorbells of its isends/irecvs (before the waitall it releases)
+            e = torch.cuda.Event()
+            e.record(cs)
+            axpy_ev.append(e)
             mpx.mpx_waitall_enqueue(reqs)
             if ev_done is not None:
                 ev_done[r].record(cs)

@@ -1592,6 +1592,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   int64_t last_prog = (int64_t)now_ns();
   int64_t idle_since = last_prog;
   uint64_t ticks = 0;
+  // phase timing (thread 0): first task seen, last time tasks drained
+  const int64_t t_launch = last_prog;
+  const uint64_t alloc0 = *(volatile uint64_t*)&sh->task_alloc;
+  int64_t t_first_task = 0, t_tasks_done = 0;
   const bool failed_at_start = ld_acq_sys32(&P.wctl->failed) != 0;
   for (;;) {
     ++ticks;
@@ -1683,6 +1687,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
       const uint64_t rt = sh->task_retire;
       const bool tasks_live = rt != a;
+      if (a != alloc0 && t_first_task == 0) t_first_task = now;
+      if (a != alloc0 && !tasks_live) t_tasks_done = now;
       const bool pending = tasks_live || sm.pending != 0;
       const bool new_in_ring = false;  // rings were drained at the start of this tick
       if (pending || new_in_ring || any) idle_since = now;
@@ -1734,6 +1740,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   }
   // let the movers go; tasks in flight were finished before deciding to exit
   if (tid == 0) {
+    const int64_t t_exit = (int64_t)now_ns();
+    if (t_first_task) {
+      const int64_t td = t_tasks_done ? t_tasks_done : t_exit;
+      atomicAdd((unsigned long long*)&P.wctl->phase[0], (unsigned long long)(t_first_task - t_launch));
+      atomicAdd((unsigned long long*)&P.wctl->phase[1], (unsigned long long)(td - t_first_task));
+      atomicAdd((unsigned long long*)&P.wctl->phase[2], (unsigned long long)(t_exit - td));
+    }
+    atomicAdd((unsigned long long*)&P.wctl->phase[3], (unsigned long long)ticks);
     st_rel_gpu32(&sh->exit_flag, 1);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }

@@ -69,6 +69,9 @@ struct alignas(128) WorldCtl {
   int32_t failed;     // D->H watchdog fired: operations are released without data
   uint64_t counters[8];
   uint64_t heartbeat;  // D->H globaltimer of the last engine tick
+  // D->H phase times summed over launches (ns): start->first task,
+  // first task->all tasks done, last task->exit; [3] ticks
+  uint64_t phase[4];
   int32_t pad[8];
 };
 
