@@ -227,6 +227,33 @@ class RingBench:
             ev_pass[1].record(self.es)
         return launches
 
+    def run_profile_safe(self, warmup, steps):
+        """The same steps ordered for a profiler that serialises kernel
+        launches: each rank's axpy and its isends/irecvs (doorbells only),
+        then the engine pass.  No operation blocks a stream, so no launch
+        ever waits behind a stream wait that a later pass would release.
+        Requests are left unwaited; the world is not freed."""
+        mpx = self.mpx
+        self.prepare(warmup + steps)
+        for step in range(warmup + steps):
+            plan, _ = self.step_plan(step)
+            evs = []
+            for r in range(self.R):
+                cs = self.cs[r]
+                mpx.mpx_saxpy_enqueue(self.n, ALPHA, self.RL[r].data_ptr(), self.S[r].data_ptr(), cs.cuda_stream)
+                sends, recvs = plan[r]
+                for cnt, ty, dest, tag in sends:
+                    mpx.mpx_isend_enqueue(self.S[r].data_ptr(), cnt, ty, dest, tag, self.comm[r])
+                for cnt, ty, src, tag, buf in recvs:
+                    mpx.mpx_irecv_enqueue(buf.data_ptr(), cnt, ty, src, tag, self.comm[r])
+                e = self.torch.cuda.Event()
+                e.record(cs)
+                evs.append(e)
+            for e in evs:
+                self.es.wait_event(e)
+            mpx.mpx_world_progress(self.world, self.es.cuda_stream)
+            self.sync_all()
+
     def sync_all(self, timeout=120.0):
         t0 = time.perf_counter()
         streams = self.cs + [self.es]
@@ -392,6 +419,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-bytes", type=int, default=0)
     ap.add_argument("--engine-ctas", type=int, default=0)
+    ap.add_argument("--profile-safe", action="store_true",
+                    help="run the steps in an order that a kernel-serialising profiler can replay "
+                         "(no stream waits); prints no benchmark line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -411,6 +441,12 @@ def main():
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     b = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas)
+    if args.profile_safe:
+        b.run_profile_safe(args.warmup, args.steps)
+        print(json.dumps({"profile_safe": True, "steps": args.steps, "warmup": args.warmup,
+                          "counters": b.mpx.mpx_world_get_counters(b.world)}), flush=True)
+        sys.stdout.flush()
+        os._exit(0)
     sampler = ClockSampler(local_rank)
     if dist is not None:
         dist.barrier()
@@ -430,6 +466,7 @@ def main():
     pass_s = sum(res["pass_ms"]) / 1e3
     achieved = 2 * res["payload"] / pass_s / 1e9
     lat = np.array(res["lat_us"])
+    ctr = b.mpx.mpx_world_get_counters(b.world)
     e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
     b.close()
     cpu = None
@@ -456,6 +493,11 @@ def main():
                 "e2e": {"value": e2e["value"], "unit": "msgs/s", "h2d_bytes_per_step": e2e["h2d"],
                         "d2h_bytes_per_step": e2e["d2h"]},
                 "gpu_launches": res["launches"], "clocks": clocks,
+                "engine_phase_us_per_launch": {
+                    "launch_to_first_task": ctr[8] / max(1, ctr[0]) / 1e3,
+                    "first_task_to_tasks_done": ctr[9] / max(1, ctr[0]) / 1e3,
+                    "tasks_done_to_exit": ctr[10] / max(1, ctr[0]) / 1e3,
+                    "ticks": ctr[11] / max(1, ctr[0])},
                 "host_issue_s": res["issue_s"]}
         print(json.dumps(line), flush=True)
     if dist is not None:
