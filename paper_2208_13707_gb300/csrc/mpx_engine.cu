@@ -38,7 +38,8 @@ constexpr int kErrTruncate = 15;
 constexpr int kErrTimeout = 16;
 constexpr int kMaxRoundsPerTick = 64;
 constexpr int kMaxStagePerTick = 128;
-constexpr int kTmaStages = 4;
+constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipeline
+constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
 constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
 
@@ -185,9 +186,6 @@ __device__ __forceinline__ void tma_store_1d(void* gdst, const void* ssrc, uint3
                : "memory");
 }
 __device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void tma_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
 __device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -202,6 +200,8 @@ struct CtaShared {
   int32_t flag;           // broadcast scalar
   int64_t claim_task;     // task id claimed by this CTA (-1: none)
   uint32_t claim_tile;
+  int64_t cached_slot;    // task slot whose record is in `task`
+  uint32_t cached_idp;
   int32_t any;            // control: something happened
   int32_t nstage;         // control: staging candidates
   int32_t ntask_full;     // control: task ring full this tick
@@ -387,20 +387,23 @@ __device__ void strided_copy(const Task& T, int64_t p0, int64_t p1) {
 
 __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t src,
                                 int64_t n, const EngineParams& P) {
-  // one thread drives the bulk copies: loads into kTmaStages smem buffers,
-  // stores back out, keeping up to kTmaStages-1 loads in flight
+  // One thread drives the bulk copies through kTmaStages shared-memory
+  // stages: up to kTmaLead loads and kTmaStages-kTmaLead stores in flight.
   if (threadIdx.x != 0) return;
   const uint32_t nch = (uint32_t)((n + kTmaChunk - 1) / kTmaChunk);
   uint32_t phase = sm.phase;
+  auto bytes_of = [&](uint32_t j) {
+    const int64_t off = (int64_t)j * kTmaChunk;
+    return (uint32_t)((n - off) < (int64_t)kTmaChunk ? (n - off) : kTmaChunk);
+  };
   auto issue = [&](uint32_t j) {
     const uint32_t s = j % kTmaStages;
-    const uint64_t off = (uint64_t)j * kTmaChunk;
-    const uint32_t bytes = (uint32_t)((n - (int64_t)off) < (int64_t)kTmaChunk ? (n - off) : kTmaChunk);
+    const uint32_t bytes = bytes_of(j);
     mbar_expect_tx(&sm.bar[s], bytes);
-    tma_load_1d(buf + (size_t)s * kTmaChunk, (const void*)(src + off), bytes, &sm.bar[s]);
+    tma_load_1d(buf + (size_t)s * kTmaChunk, (const void*)(src + (uint64_t)j * kTmaChunk), bytes, &sm.bar[s]);
   };
   uint32_t issued = 0;
-  while (issued < nch && issued < (uint32_t)kTmaStages) issue(issued++);
+  while (issued < nch && issued < (uint32_t)kTmaLead) issue(issued++);
   for (uint32_t j = 0; j < nch; ++j) {
     const uint32_t s = j % kTmaStages;
     const uint32_t par = (phase >> s) & 1u;
@@ -420,12 +423,13 @@ __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint6
       return;
     }
     phase ^= (1u << s);
-    const uint64_t off = (uint64_t)j * kTmaChunk;
-    const uint32_t bytes = (uint32_t)((n - (int64_t)off) < (int64_t)kTmaChunk ? (n - off) : kTmaChunk);
-    tma_store_1d((void*)(dst + off), buf + (size_t)s * kTmaChunk, bytes);
+    tma_store_1d((void*)(dst + (uint64_t)j * kTmaChunk), buf + (size_t)s * kTmaChunk, bytes_of(j));
     tma_commit();
     if (issued < nch) {
-      tma_wait_read_all();  // stage s is free again once the store has read it
+      // stage issued%kTmaStages was last read by store issued-kTmaStages, which
+      // is older than the kTmaStages-kTmaLead most recent stores
+      if (issued >= (uint32_t)kTmaStages)
+        asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kTmaStages - kTmaLead) : "memory");
       issue(issued++);
     }
   }
@@ -632,34 +636,37 @@ __device__ void reduce_tile(const Task& T, uint32_t k) {
   }
 }
 
-// Claim one tile: thread 0 walks the task ring from task_head.
-// Returns false when there is no claimable tile right now.
+// Claim one tile: thread 0 fetch-and-adds the claim word of the task at
+// task_head.  The returned word alone says which tile of which published task
+// was won (a tile index below the task's tile count), so no claim is ever
+// retried or lost; the task record is copied to shared memory when it
+// changes.  Returns false when there is no claimable tile right now.
 __device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
   if (threadIdx.x == 0) {
     sm.claim_task = -1;
     Shared* sh = P.sh;
     const uint64_t mask = (1ull << P.tq_log2) - 1;
-    for (int tries = 0; tries < 64; ++tries) {
+    for (int tries = 0; tries < 8; ++tries) {
       const uint64_t i = ld_acq_gpu(&sh->task_head);
       const uint64_t a = ld_acq_gpu(&sh->task_alloc);
       if (i >= a) break;
       Task* T = &P.tasks[i & mask];
-      const uint64_t c = ld_acq_gpu(&T->claim);
-      if ((uint32_t)(c >> 32) != (uint32_t)(i + 1)) break;  // not published yet
-      const uint32_t k = (uint32_t)c;
-      const uint32_t nt = *(volatile uint32_t*)&T->ntiles;
-      if (k >= nt) {
-        atomicCAS((unsigned long long*)&sh->task_head, (unsigned long long)i,
-                  (unsigned long long)(i + 1));
-        continue;
-      }
-      if (atomicCAS((unsigned long long*)&T->claim, (unsigned long long)c,
-                    (unsigned long long)(c + 1)) == c) {
-        sm.claim_task = (int64_t)i;
+      if (claim_idp(ld_acq_gpu(&T->claim)) == 0) break;  // not published yet
+      const uint64_t c = atomicAdd((unsigned long long*)&T->claim, 1ull);
+      const uint32_t idp = claim_idp(c), k = claim_next(c), nt = claim_ntiles(c);
+      if (idp != 0 && k < nt) {
+        sm.claim_task = (int64_t)(i & mask);
         sm.claim_tile = k;
-        sm.task = *T;
+        if (sm.cached_slot != (int64_t)(i & mask) || sm.cached_idp != idp) {
+          __threadfence();
+          sm.task = *T;
+          sm.cached_slot = (int64_t)(i & mask);
+          sm.cached_idp = idp;
+        }
         break;
       }
+      if (idp == id_tag(i))  // task i has handed out all its tiles: move on
+        atomicCAS((unsigned long long*)&sh->task_head, (unsigned long long)i, (unsigned long long)(i + 1));
     }
   }
   __syncthreads();
@@ -673,8 +680,7 @@ __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) 
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    const uint64_t mask = (1ull << P.tq_log2) - 1;
-    atomicAdd(&P.tasks[(uint64_t)sm.claim_task & mask].tiles_done, 1u);
+    atomicAdd(&P.tasks[(uint64_t)sm.claim_task].tiles_done, 1u);
   }
 }
 
@@ -694,11 +700,13 @@ struct Ctl {
   __device__ bool ingest() {
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
       SState& S = P.ss[g];
-      const int32_t flags = ld_acq_sys32(&P.sctl[g].flags);
+      const uint4 line = ld_vol16(&P.sctl[g].tail);  // tail, flags, rank
+      asm volatile("fence.acq_rel.sys;" ::: "memory");
+      const int32_t flags = (int32_t)line.z;
       S.flags = flags;
-      S.rank = ((volatile int32_t*)&P.sctl[g].rank)[0];
+      S.rank = (int32_t)line.w;
       uint64_t tail = 0;
-      if (flags & SF_ACTIVE) tail = ld_acq_sys(&P.sctl[g].tail);
+      if (flags & SF_ACTIVE) tail = ((uint64_t)line.y << 32) | line.x;
       if (g < P.nlimit && tail > P.limit[g]) tail = P.limit[g];
       sm.cnt[g] = (flags & SF_ACTIVE) && tail > S.ingested ? (int32_t)(tail - S.ingested) : 0;
     }
@@ -1038,7 +1046,7 @@ struct Ctl {
   __device__ void task_publish(Task* T, uint64_t id) {
     T->tiles_done = 0;
     __threadfence();
-    st_rel_gpu(&T->claim, ((id + 1) << 32));
+    st_rel_gpu(&T->claim, claim_word(id, T->ntiles));
   }
 
   __device__ void fill_copy(Task* T, const Layout& src, const Layout& dst, int64_t bytes) {
@@ -1481,7 +1489,7 @@ struct Ctl {
     for (uint64_t id = r0 + threadIdx.x; id < a; id += blockDim.x) {
       Task* T = &P.tasks[id & mask];
       if (T->type == 0) continue;  // already processed
-      if ((uint32_t)(ld_acq_gpu(&T->claim) >> 32) != (uint32_t)(id + 1)) continue;
+      if (claim_idp(ld_acq_gpu(&T->claim)) != id_tag(id)) continue;
       if (ld_acq_gpu32(&T->tiles_done) < T->ntiles) continue;
       if (T->type == T_COPY) {
         DOp* s = op_ref(P, T->ref_s);
@@ -1655,8 +1663,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         const uint64_t mask = (1ull << P.tq_log2) - 1;
         uint64_t r0 = sh->task_retire;
         const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
-        while (r0 < a && P.tasks[r0 & mask].type == 0 &&
-               (uint32_t)(P.tasks[r0 & mask].claim >> 32) == (uint32_t)(r0 + 1))
+        // a slot is reused only after the movers' head has passed its task
+        const uint64_t head = ld_acq_gpu(&sh->task_head);
+        while (r0 < a && r0 < head && P.tasks[r0 & mask].type == 0 &&
+               claim_idp(P.tasks[r0 & mask].claim) == id_tag(r0))
           ++r0;
         sh->task_retire = r0;
         C.stage_reclaim();
@@ -1787,6 +1797,8 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(EngineParams P) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTmaStages; ++s) mbar_init(&sm.bar[s], 1);
     sm.phase = 0;
+    sm.cached_slot = -1;
+    sm.cached_idp = 0;
     fence_proxy_async();
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }

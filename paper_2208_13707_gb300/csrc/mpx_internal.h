@@ -48,14 +48,14 @@ static_assert(sizeof(Desc) == 64, "descriptor is 64 bytes");
 // ---------------------------------------------------------------------------
 struct alignas(128) StreamCtl {
   uint64_t tail;        // H->D  last published sequence number
+  int32_t flags;        // H->D  bit0 active, bit1 exclusive  (tail, flags, rank: one 16-byte load)
+  int32_t rank;         // H->D  world rank of the stream
   uint64_t wl_tail;     // H->D  waitlist entries published
   uint64_t retired;     // D->H  every op with seq <= retired is finished
   uint64_t wl_retired;  // D->H  waitlist entries no longer read
   uint64_t done;        // D->H  mirror of the completion word
   int32_t error;        // D->H  first asynchronous error
-  int32_t flags;        // H->D  bit0 active, bit1 exclusive
-  int32_t rank;         // H->D  world rank of the stream
-  int32_t pad[5];
+  int32_t pad[13];
 };
 static_assert(sizeof(StreamCtl) == 128, "stream control line");
 
@@ -143,8 +143,18 @@ struct Layout {
 enum TaskType : uint32_t { T_COPY = 1, T_REDUCE = 2 };
 enum TaskAction : uint32_t { A_DELIVER = 1, A_STAGE = 2, A_DELIVER_STAGED = 3, A_REDUCE = 4 };
 
+// Task claim word: bits 40..63 (id+1) mod 2^24 (0: never published),
+// 20..39 number of tiles, 0..19 next unclaimed tile (fetch-and-add).
+__host__ __device__ inline uint64_t claim_word(uint64_t id, uint32_t ntiles) {
+  return (((id + 1) & 0xFFFFFFull) << 40) | ((uint64_t)(ntiles & 0xFFFFF) << 20);
+}
+__host__ __device__ inline uint32_t claim_idp(uint64_t c) { return (uint32_t)(c >> 40); }
+__host__ __device__ inline uint32_t claim_ntiles(uint64_t c) { return (uint32_t)((c >> 20) & 0xFFFFF); }
+__host__ __device__ inline uint32_t claim_next(uint64_t c) { return (uint32_t)(c & 0xFFFFF); }
+__host__ __device__ inline uint32_t id_tag(uint64_t id) { return (uint32_t)((id + 1) & 0xFFFFFF); }
+
 struct alignas(128) Task {
-  uint64_t claim;       // (task id << 32) | next unclaimed tile
+  uint64_t claim;       // claim_word(id, ntiles) + tiles handed out
   uint32_t tiles_done;  // tiles finished
   uint32_t ntiles;
   uint32_t type;        // TaskType
