@@ -206,6 +206,9 @@ struct CtaShared {
   int32_t nstage;         // control: staging candidates
   int32_t ntask_full;     // control: task ring full this tick
   int32_t pending;        // control: some stream has unretired operations
+  int32_t failed;         // control: cached copy of the world's failed word
+  int32_t dirty;          // control: logical rounds needed
+  int32_t tasks_live;     // control: tasks in flight at the last decision
   uint64_t stage_ref[kMaxStagePerTick];
   int32_t cnt[kMaxStreamsPerCta];
   Task task;              // claimed task (copy)
@@ -701,12 +704,13 @@ struct Ctl {
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
       SState& S = P.ss[g];
       const uint4 line = ld_vol16(&P.sctl[g].tail);  // tail, flags, rank
-      asm volatile("fence.acq_rel.sys;" ::: "memory");
       const int32_t flags = (int32_t)line.z;
       S.flags = flags;
       S.rank = (int32_t)line.w;
       uint64_t tail = 0;
       if (flags & SF_ACTIVE) tail = ((uint64_t)line.y << 32) | line.x;
+      // descriptors published before this tail are read after this fence
+      if (tail > S.ingested) asm volatile("fence.acq_rel.sys;" ::: "memory");
       if (g < P.nlimit && tail > P.limit[g]) tail = P.limit[g];
       sm.cnt[g] = (flags & SF_ACTIVE) && tail > S.ingested ? (int32_t)(tail - S.ingested) : 0;
     }
@@ -1282,7 +1286,10 @@ struct Ctl {
     S.pc = pc;
     if (newdone != S.done) {
       S.done = newdone;
-      fence_sc_sys();
+      // payloads were made visible at gpu scope by the movers (fence, then the
+      // tiles_done count this thread acquired); order them before the word the
+      // stream's cuStreamWaitValue64 polls
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
       st_rlx_sys(&P.done[g], newdone);
       st_rlx_sys(&P.sctl[g].done, newdone);
       prog = true;
@@ -1443,6 +1450,7 @@ struct Ctl {
         __threadfence();
         atomicExch((unsigned long long*)&s->k1, 0ull);
         sm.any = 1;
+        sm.dirty = 1;
         continue;
       }
       uint64_t* ptrs = P.reduce_ptrs + (size_t)i * 2 * P.nranks;
@@ -1513,6 +1521,7 @@ struct Ctl {
         s->arrived = 0;
         __threadfence();
         atomicExch((unsigned long long*)&s->k1, 0ull);
+        sm.dirty = 1;  // a stream may wait for this instance slot
         atomicAdd((unsigned long long*)&P.wctl->counters[3],
                   (unsigned long long)(T->bytes * base_size(T->dtype) * P.nranks));
       }
@@ -1604,28 +1613,41 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   const int64_t t_launch = last_prog;
   const uint64_t alloc0 = *(volatile uint64_t*)&sh->task_alloc;
   int64_t t_first_task = 0, t_tasks_done = 0;
-  const bool failed_at_start = ld_acq_sys32(&P.wctl->failed) != 0;
+  // the host-written `failed` word is polled every few ticks (it only changes
+  // on a watchdog or mpx_world_abort); logical rounds run only after new
+  // descriptors arrived (physical events never change matching)
+  if (tid == 0) {
+    sm.failed = ld_acq_sys32(&P.wctl->failed);
+    sm.dirty = 1;
+  }
   for (;;) {
     ++ticks;
     const int64_t now = (int64_t)now_ns();
     if (tid == 0) {
       sm.any = 0;
       sm.ntask_full = 0;
-      st_rlx_sys(&P.wctl->heartbeat, (uint64_t)now);
+      if ((ticks & 15) == 0) {
+        st_rlx_sys(&P.wctl->heartbeat, (uint64_t)now);
+        sm.failed = ld_vol32(&P.wctl->failed);
+      }
     }
     __syncthreads();
     // 1. ingest
     const bool ing = C.ingest();
-    if (ing) sm.any = 1;
+    if (ing) {
+      sm.any = 1;
+      sm.dirty = 1;
+    }
     __syncthreads();
-    if (failed_at_start || ld_vol32(&P.wctl->failed)) {
+    if (sm.failed) {
       if (tid == 0) {
         sm.pending = 0;
         abandon_tasks(P);
       }
       release_all(P, kErrTimeout);
       __syncthreads();
-    } else {
+    } else if (sm.dirty) {
+      if (tid == 0) sm.dirty = 0;
       // 2. logical rounds
       for (int r = 0; r < kMaxRoundsPerTick; ++r) {
         if (tid == 0) sm.flag = 0;
@@ -1655,7 +1677,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         C.round += 1;
         __syncthreads();
         if (!moved) break;
+        if (r == kMaxRoundsPerTick - 1 && tid == 0) sm.dirty = 1;  // more rounds next tick
       }
+    }
+    if (!sm.failed) {
       // 3. finished tasks, then per-stream completion and retirement
       C.complete_tasks();
       __syncthreads();
@@ -1702,11 +1727,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       const bool pending = tasks_live || sm.pending != 0;
       const bool new_in_ring = false;  // rings were drained at the start of this tick
       if (pending || new_in_ring || any) idle_since = now;
-      if (ld_vol32(&P.wctl->failed) && !tasks_live && !new_in_ring) decision = 1;
+      if (!any && !tasks_live) sm.failed = ld_vol32(&P.wctl->failed);
+      if (sm.failed && !tasks_live && !new_in_ring) decision = 1;
       if (!decision && pending && !any && now - last_prog > P.watchdog_ns) {
         // nothing moved for too long: fail the pending work and release waiters
         atomicCAS(&P.wctl->error, 0, kErrTimeout);
         st_rel_sys32(&P.wctl->failed, 1);
+        sm.failed = 1;
         decision = 2;
       }
       if (!decision) {
@@ -1730,7 +1757,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         }
       }
       sm.flag = decision;
-      atomicAdd((unsigned long long*)&P.wctl->counters[1], 1ull);
+      sm.tasks_live = tasks_live;
     }
     __syncthreads();
     if (sm.flag == 1) break;
@@ -1743,8 +1770,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     // 5. help with data movement, or back off when there is nothing to do
     if (claim_tile(P, sm)) {
       run_claimed(P, sm, buf);
-    } else if (!sm.any) {
-      if (tid == 0) __nanosleep(2000);
+    } else if (!sm.any && !sm.tasks_live) {
+      if (tid == 0) __nanosleep(1000);
     }
     __syncthreads();
   }
@@ -1758,6 +1785,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       atomicAdd((unsigned long long*)&P.wctl->phase[2], (unsigned long long)(t_exit - td));
     }
     atomicAdd((unsigned long long*)&P.wctl->phase[3], (unsigned long long)ticks);
+    atomicAdd((unsigned long long*)&P.wctl->counters[1], (unsigned long long)ticks);
     st_rel_gpu32(&sh->exit_flag, 1);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }
