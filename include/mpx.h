@@ -206,7 +206,10 @@ int mpx_world_get_error(mpx_world_t world, int* first_error);
  * [3] payload bytes moved, [4] tasks, [5] staged sends, [6] rounds,
  * [7] allreduce instances; summed over launches, in ns: [8] launch to first
  * data task, [9] first task to all tasks done, [10] last task to exit;
- * [11] control ticks.  n is the array length (<= 12 filled). */
+ * [11] control ticks; control-tick time by phase in ns: [12] ingest,
+ * [13] logical rounds, [14] finished tasks, [15] per-stream completion,
+ * [16] scheduling, [17] decisions, [18] the control CTA's own data movement.
+ * n is the array length (<= 19 filled). */
 int mpx_world_get_counters(mpx_world_t world, int64_t* out, int n);
 
 /* MPIX_Stream_create (§3.1) for virtual rank `rank`, backed by a CUDA

@@ -42,6 +42,7 @@ constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipelin
 constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
 constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
+constexpr int kSmemStreams = 128;  // worlds up to this many streams keep per-stream state in shared memory
 
 // ------------------------------------------------------------------------
 // memory-model helpers
@@ -211,6 +212,11 @@ struct CtaShared {
   int32_t tasks_live;     // control: tasks in flight at the last decision
   uint64_t stage_ref[kMaxStagePerTick];
   int32_t cnt[kMaxStreamsPerCta];
+  int32_t arrivals;       // control: allreduce arrivals this round
+  int32_t limits_reached; // control: a drain pass has ingested up to all its limits
+  uint64_t t_retire, t_alloc;
+  int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
+  SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
 };
 
@@ -694,24 +700,28 @@ struct Ctl {
   const EngineParams& P;
   CtaShared& sm;
   int64_t round;
-  __device__ Ctl(const EngineParams& p, CtaShared& s) : P(p), sm(s), round(0) {}
+  SState* ss;  // per-stream state: shared memory for small worlds, else global
+  __device__ Ctl(const EngineParams& p, CtaShared& s)
+      : P(p), sm(s), round(0), ss(p.max_streams <= kSmemStreams ? s.ss_cache : p.ss) {}
 
   __device__ uint64_t slots_mask() const { return (1ull << P.slots_log2) - 1; }
 
   // --- 1. ingest: every thread polls one ring tail, then a warp per stream
   // with new entries copies the descriptors ---
   __device__ bool ingest() {
+    // a drain pass with limits has nothing more to poll once it reached them
+    if (P.nlimit > 0 && sm.limits_reached) return false;
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
-      SState& S = P.ss[g];
+      SState& S = ss[g];
       const uint4 line = ld_vol16(&P.sctl[g].tail);  // tail, flags, rank
       const int32_t flags = (int32_t)line.z;
       S.flags = flags;
       S.rank = (int32_t)line.w;
       uint64_t tail = 0;
       if (flags & SF_ACTIVE) tail = ((uint64_t)line.y << 32) | line.x;
+      if (g < P.nlimit && tail > P.limit[g]) tail = P.limit[g];
       // descriptors published before this tail are read after this fence
       if (tail > S.ingested) asm volatile("fence.acq_rel.sys;" ::: "memory");
-      if (g < P.nlimit && tail > P.limit[g]) tail = P.limit[g];
       sm.cnt[g] = (flags & SF_ACTIVE) && tail > S.ingested ? (int32_t)(tail - S.ingested) : 0;
     }
     __syncthreads();
@@ -719,7 +729,7 @@ struct Ctl {
     bool any = false;
     for (int g = warp; g < P.max_streams; g += nw) {
       if (sm.cnt[g] == 0) continue;
-      SState& S = P.ss[g];
+      SState& S = ss[g];
       const uint64_t ing = S.ingested;
       const uint64_t tail = ing + (uint64_t)sm.cnt[g];
       any = true;
@@ -752,6 +762,13 @@ struct Ctl {
       __syncwarp();
       if (lane == 0) S.ingested = tail;
     }
+    __syncthreads();
+    if (P.nlimit > 0) {
+      if (threadIdx.x == 0) sm.limits_reached = 1;
+      __syncthreads();
+      for (int g = threadIdx.x; g < P.nlimit; g += blockDim.x)
+        if ((ss[g].flags & SF_ACTIVE) && ss[g].ingested < P.limit[g]) sm.limits_reached = 0;
+    }
     return any;
   }
 
@@ -774,7 +791,7 @@ struct Ctl {
   }
 
   __device__ bool advance_stream(int g) {
-    SState& S = P.ss[g];
+    SState& S = ss[g];
     int n = 0;
     bool arrived = false;
     uint64_t cur = S.cursor;
@@ -844,6 +861,7 @@ struct Ctl {
           if (arrive(g, o, cur)) {
             o->lstate = 1;
             arrived = true;
+            sm.arrivals = 1;
           }
           break;
         }
@@ -1020,6 +1038,7 @@ struct Ctl {
         o->err = err;
       }
       s->state = 1;
+      atomicAdd(&sm.ready_insts, 1);
       sm.any = 1;
     }
   }
@@ -1264,7 +1283,7 @@ struct Ctl {
   }
 
   __device__ bool stream_physical(int g, int64_t now) {
-    SState& S = P.ss[g];
+    SState& S = ss[g];
     if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return false;
     bool prog = false;
     // completion word: blocking ops complete in order
@@ -1298,7 +1317,8 @@ struct Ctl {
     if (S.flags & SF_EXCLUSIVE) {
       S.reached = pc <= S.ingested ? pc : S.ingested;
     } else {
-      uint64_t db = ld_rlx_sys(&P.doorbell[g]);
+      uint64_t db;
+      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
       S.reached = db;
     }
     // stall clock: the stream sits at blocking op pc
@@ -1321,7 +1341,7 @@ struct Ctl {
       S.retire = rt;
       S.wl_retired = wlr;
       st_rlx_sys(&P.sctl[g].wl_retired, wlr);
-      st_rel_sys(&P.sctl[g].retired, rt);
+      st_rlx_sys(&P.sctl[g].retired, rt);  // descriptors were consumed at ingest, long before
       prog = true;
     }
     return prog;
@@ -1329,7 +1349,7 @@ struct Ctl {
 
   // --- 3b. per stream: schedule deliveries and stage stalled sends ---
   __device__ void stream_schedule(int g, int64_t now) {
-    SState& S = P.ss[g];
+    SState& S = ss[g];
     if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return;
     const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
     uint64_t sc = S.sched > S.retire ? S.sched : S.retire + 1;
@@ -1349,7 +1369,7 @@ struct Ctl {
             if (sf & PF_STAGED) {
               settled = create_deliver(sref, make_ref(g, seq), true);
             } else if (!(sf & PF_SCHED)) {
-              const SState& SS = P.ss[ref_stream(sref)];
+              const SState& SS = ss[ref_stream(sref)];
               if (*(volatile uint64_t*)&SS.reached >= ref_seq(sref)) {
                 const int32_t old = atomicOr(&s->pflags, PF_SCHED);
                 if (!(old & PF_SCHED)) {
@@ -1430,6 +1450,7 @@ struct Ctl {
 
   // --- 3c. allreduce instances whose ranks have all reached them ---
   __device__ void schedule_reduce() {
+    if (sm.ready_insts == 0) return;
     const int nslots = P.max_comms * P.iw;
     for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
       InstSlot* s = &P.inst[i];
@@ -1438,7 +1459,7 @@ struct Ctl {
       bool ready = true;
       for (int r = 0; r < P.nranks && ready; ++r) {
         const uint64_t ref = refs[r];
-        if (*(volatile uint64_t*)&P.ss[ref_stream(ref)].reached < ref_seq(ref)) ready = false;
+        if (*(volatile uint64_t*)&ss[ref_stream(ref)].reached < ref_seq(ref)) ready = false;
       }
       if (!ready) continue;
       const DOp* o0 = op_ref(P, refs[0]);
@@ -1449,6 +1470,7 @@ struct Ctl {
         s->arrived = 0;
         __threadfence();
         atomicExch((unsigned long long*)&s->k1, 0ull);
+        atomicSub(&sm.ready_insts, 1);
         sm.any = 1;
         sm.dirty = 1;
         continue;
@@ -1482,6 +1504,7 @@ struct Ctl {
       T->ref_r = 0;
       T->chunk = 0;
       s->state = 2;
+      atomicSub(&sm.ready_insts, 1);
       task_publish(T, id);
       atomicAdd((unsigned long long*)&P.wctl->counters[7], 1ull);
       sm.any = 1;
@@ -1489,11 +1512,8 @@ struct Ctl {
   }
 
   // --- 4. finished tasks (thread per task in flight) ---
-  __device__ void complete_tasks() {
-    Shared* sh = P.sh;
+  __device__ void complete_tasks(uint64_t r0, uint64_t a) {
     const uint64_t mask = (1ull << P.tq_log2) - 1;
-    const uint64_t r0 = *(volatile uint64_t*)&sh->task_retire;
-    const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
     for (uint64_t id = r0 + threadIdx.x; id < a; id += blockDim.x) {
       Task* T = &P.tasks[id & mask];
       if (T->type == 0) continue;  // already processed
@@ -1533,9 +1553,9 @@ struct Ctl {
 };
 
 // Release every stream's waiters without moving data (watchdog / failed world).
-__device__ void release_all(const EngineParams& P, int err) {
+__device__ void release_all(const EngineParams& P, SState* ss, int err) {
   for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
-    SState& S = P.ss[g];
+    SState& S = ss[g];
     if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) continue;
     for (uint64_t seq = S.retire + 1; seq <= S.ingested; ++seq) {
       DOp* o = op_at(P, g, seq);
@@ -1600,6 +1620,17 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   Ctl C(P, sm);
   Shared* sh = P.sh;
   const int tid = threadIdx.x;
+  if (C.ss != P.ss) {
+    for (int g = tid; g < P.max_streams; g += blockDim.x) C.ss[g] = P.ss[g];
+  }
+  if (tid == 0) {
+    sm.limits_reached = 0;
+    sm.arrivals = 0;
+    sm.ready_insts = 0;
+    for (int i = 0; i < P.max_comms * P.iw; ++i)
+      if (P.inst[i].k1 != 0 && P.inst[i].state == 1) ++sm.ready_insts;
+  }
+  __syncthreads();
   if (tid == 0) {
     C.round = (int64_t)sh->round;
     sm.nstage = 0;
@@ -1613,6 +1644,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   const int64_t t_launch = last_prog;
   const uint64_t alloc0 = *(volatile uint64_t*)&sh->task_alloc;
   int64_t t_first_task = 0, t_tasks_done = 0;
+  uint64_t tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // the host-written `failed` word is polled every few ticks (it only changes
   // on a watchdog or mpx_world_abort); logical rounds run only after new
   // descriptors arrived (physical events never change matching)
@@ -1632,6 +1664,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     }
     __syncthreads();
+    uint64_t tp = tid == 0 ? now_ns() : 0;
+    auto lap = [&](int k) {
+      if (tid == 0) {
+        const uint64_t t = now_ns();
+        tacc[k] += t - tp;
+        tp = t;
+      }
+    };
     // 1. ingest
     const bool ing = C.ingest();
     if (ing) {
@@ -1639,12 +1679,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       sm.dirty = 1;
     }
     __syncthreads();
+    lap(0);
     if (sm.failed) {
       if (tid == 0) {
         sm.pending = 0;
         abandon_tasks(P);
       }
-      release_all(P, kErrTimeout);
+      release_all(P, C.ss, kErrTimeout);
       __syncthreads();
     } else if (sm.dirty) {
       if (tid == 0) sm.dirty = 0;
@@ -1655,7 +1696,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         __syncthreads();
         int local_any = 0;
         for (int g = tid; g < P.max_streams; g += blockDim.x) {
-          SState& S = P.ss[g];
+          SState& S = C.ss[g];
           if (!(S.flags & SF_ACTIVE) && S.cursor > S.ingested) continue;
           if (C.advance_stream(g)) local_any = 1;
         }
@@ -1668,9 +1709,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
           for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
           __syncthreads();
         }
-        C.collectives();
+        if (sm.arrivals) C.collectives();
         __syncthreads();
         if (tid == 0) {
+          sm.arrivals = 0;
           sh->round = (uint64_t)(C.round + 1);
           if (moved) atomicAdd((unsigned long long*)&P.wctl->counters[6], 1ull);
         }
@@ -1680,9 +1722,16 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (r == kMaxRoundsPerTick - 1 && tid == 0) sm.dirty = 1;  // more rounds next tick
       }
     }
+    lap(1);
     if (!sm.failed) {
       // 3. finished tasks, then per-stream completion and retirement
-      C.complete_tasks();
+      if (tid == 0) {
+        sm.t_retire = sh->task_retire;
+        sm.t_alloc = *(volatile uint64_t*)&sh->task_alloc;
+      }
+      __syncthreads();
+      const uint64_t t_r0 = sm.t_retire, t_a = sm.t_alloc;
+      if (t_r0 != t_a) C.complete_tasks(t_r0, t_a);
       __syncthreads();
       if (tid == 0) {
         const uint64_t mask = (1ull << P.tq_log2) - 1;
@@ -1697,22 +1746,25 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         C.stage_reclaim();
       }
       __syncthreads();
+      lap(2);
       int phys = 0, pend = 0;
       if (tid == 0) sm.pending = 0;
       __syncthreads();
       for (int g = tid; g < P.max_streams; g += blockDim.x) {
         if (C.stream_physical(g, now)) phys = 1;
-        const SState& S = P.ss[g];
+        const SState& S = C.ss[g];
         if (S.retire < S.ingested) pend = 1;
       }
       if (phys) atomicOr(&sm.any, 1);
       if (pend) atomicOr(&sm.pending, 1);
       __syncthreads();
+      lap(3);
       for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
       __syncthreads();
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
       __syncthreads();
+      lap(4);
     }
     // 4. bookkeeping and exit decisions (thread 0)
     if (tid == 0) {
@@ -1748,8 +1800,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
             fence_sc_sys();
             bool fresh = false;
             for (int g = 0; g < P.max_streams; ++g) {
-              if (!(P.ss[g].flags & SF_ACTIVE) && !(ld_acq_sys32(&P.sctl[g].flags) & SF_ACTIVE)) continue;
-              if (ld_acq_sys(&P.sctl[g].tail) > P.ss[g].ingested) fresh = true;
+              if (!(C.ss[g].flags & SF_ACTIVE) && !(ld_acq_sys32(&P.sctl[g].flags) & SF_ACTIVE)) continue;
+              if (ld_acq_sys(&P.sctl[g].tail) > C.ss[g].ingested) fresh = true;
             }
             if (fresh) st_rel_sys32(&P.wctl->state, ENG_RUNNING);
             else decision = 1;
@@ -1760,10 +1812,11 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       sm.tasks_live = tasks_live;
     }
     __syncthreads();
+    lap(5);
     if (sm.flag == 1) break;
     if (sm.flag == 2) {
       if (tid == 0) abandon_tasks(P);
-      release_all(P, kErrTimeout);
+      release_all(P, C.ss, kErrTimeout);
       __syncthreads();
       continue;
     }
@@ -1774,7 +1827,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if (tid == 0) __nanosleep(1000);
     }
     __syncthreads();
+    lap(6);
   }
+  if (C.ss != P.ss) {
+    for (int g = tid; g < P.max_streams; g += blockDim.x) P.ss[g] = C.ss[g];
+    __threadfence();
+  }
+  __syncthreads();
   // let the movers go; tasks in flight were finished before deciding to exit
   if (tid == 0) {
     const int64_t t_exit = (int64_t)now_ns();
@@ -1786,6 +1845,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     }
     atomicAdd((unsigned long long*)&P.wctl->phase[3], (unsigned long long)ticks);
     atomicAdd((unsigned long long*)&P.wctl->counters[1], (unsigned long long)ticks);
+    for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->tick_ns[k], (unsigned long long)tacc[k]);
     st_rel_gpu32(&sh->exit_flag, 1);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }

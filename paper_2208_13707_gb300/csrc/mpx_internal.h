@@ -72,6 +72,9 @@ struct alignas(128) WorldCtl {
   // D->H phase times summed over launches (ns): start->first task,
   // first task->all tasks done, last task->exit; [3] ticks
   uint64_t phase[4];
+  // D->H control-tick time by phase, summed (ns): ingest, rounds, finished
+  // tasks, per-stream completion, scheduling, decision, own data movement
+  uint64_t tick_ns[8];
   int32_t pad[8];
 };
 
