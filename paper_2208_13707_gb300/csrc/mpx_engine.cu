@@ -214,6 +214,7 @@ struct CtaShared {
   int32_t cnt[kMaxStreamsPerCta];
   int32_t arrivals;       // control: allreduce arrivals this round
   int32_t limits_reached; // control: a drain pass has ingested up to all its limits
+  int32_t left;           // control: some stream still has ingested operations ahead of its cursor
   uint64_t t_retire, t_alloc;
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
@@ -758,6 +759,16 @@ struct Ctl {
         o->wscan = 0;
         o->pscan = 0;
         o->t_ingest = (int64_t)t0;
+        if (kw_kind(o->d.kw) == K_WAITALL) {
+          // request lists are read many times: keep a device copy
+          const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+          const int64_t* hw = P.waitlists + ((size_t)g << P.wl_log2);
+          int64_t* dw = P.wl_dev + ((size_t)g << P.wl_log2);
+          for (int32_t k = 0; k < o->d.n32; ++k) {
+            const uint64_t idx = (o->d.aux + (uint64_t)k) & wl_mask;
+            dw[idx] = *(const volatile int64_t*)&hw[idx];
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) S.ingested = tail;
@@ -840,7 +851,7 @@ struct Ctl {
       }
       if (k == K_WAITALL) {
         const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-        const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+        const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
         uint32_t w = o->wscan;
         while (w < (uint32_t)o->d.n32) {
           const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
@@ -1191,6 +1202,7 @@ struct Ctl {
   }
   __device__ void stage_reclaim() {
     Shared* sh = P.sh;
+    if (sh->sr_tail == sh->sr_head) return;
     const uint64_t srmask = (1ull << P.sr_log2) - 1;
     while (sh->sr_tail != sh->sr_head) {
       StageRec& rec = P.srec[sh->sr_tail & srmask];
@@ -1224,7 +1236,7 @@ struct Ctl {
     }
     if (k == K_WAITALL) {
       const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-      const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+      const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
       uint32_t w = o->pscan;
       while (w < (uint32_t)o->d.n32) {
         const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
@@ -1251,7 +1263,7 @@ struct Ctl {
       }
     } else if (k == K_WAITALL) {
       const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-      const int64_t* wl = P.waitlists + ((size_t)g << P.wl_log2);
+      const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
       for (uint32_t w = 0; w < (uint32_t)o->d.n32; ++w) {
         const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
         if (rs == 0) {
@@ -1627,9 +1639,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     sm.limits_reached = 0;
     sm.arrivals = 0;
     sm.ready_insts = 0;
-    for (int i = 0; i < P.max_comms * P.iw; ++i)
-      if (P.inst[i].k1 != 0 && P.inst[i].state == 1) ++sm.ready_insts;
   }
+  __syncthreads();
+  for (int i = tid; i < P.max_comms * P.iw; i += blockDim.x)
+    if (P.inst[i].k1 != 0 && P.inst[i].state == 1) atomicAdd(&sm.ready_insts, 1);
   __syncthreads();
   if (tid == 0) {
     C.round = (int64_t)sh->round;
@@ -1694,13 +1707,17 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (tid == 0) sm.flag = 0;
         for (int g = tid; g < P.max_streams; g += blockDim.x) sm.cnt[g] = 0;
         __syncthreads();
-        int local_any = 0;
+        int local_any = 0, local_left = 0;
         for (int g = tid; g < P.max_streams; g += blockDim.x) {
           SState& S = C.ss[g];
           if (!(S.flags & SF_ACTIVE) && S.cursor > S.ingested) continue;
           if (C.advance_stream(g)) local_any = 1;
+          if (S.cursor <= S.ingested) local_left = 1;
         }
+        if (tid == 0) sm.left = 0;
+        __syncthreads();
         if (local_any) atomicOr(&sm.flag, 1);
+        if (local_left) atomicOr(&sm.left, 1);
         __syncthreads();
         const bool moved = sm.flag != 0;
         if (moved) {
@@ -1719,6 +1736,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         C.round += 1;
         __syncthreads();
         if (!moved) break;
+        // every stream consumed what it has: another round cannot move
+        // unless this round completed something a stream is blocked on
+        if (!sm.left) break;
         if (r == kMaxRoundsPerTick - 1 && tid == 0) sm.dirty = 1;  // more rounds next tick
       }
     }
@@ -1820,8 +1840,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       __syncthreads();
       continue;
     }
-    // 5. help with data movement, or back off when there is nothing to do
-    if (claim_tile(P, sm)) {
+    // 5. move data only when no mover CTA exists (a tile would stall the
+    // control loop); back off when there is nothing to do
+    if (gridDim.x == 1 && claim_tile(P, sm)) {
       run_claimed(P, sm, buf);
     } else if (!sm.any && !sm.tasks_live) {
       if (tid == 0) __nanosleep(1000);

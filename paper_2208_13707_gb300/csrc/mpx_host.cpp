@@ -356,6 +356,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_irefs = carve(iwn * nranks * 8);
   const size_t o_ninst = carve((size_t)cfg.max_comms * nranks * 8);
   const size_t o_rptr = carve(iwn * 2 * nranks * 8);
+  const size_t o_wl = carve(((size_t)S << w->wl_log2) * sizeof(int64_t));
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
   w->dev_bytes = off;
   if (cfg.budget_bytes > 0 && (int64_t)off > cfg.budget_bytes) { world_release(w); return MPX_ERR_NO_MEM; }
@@ -415,6 +416,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.next_inst = (int64_t*)(base + o_ninst);
   P.reduce_ptrs = (uint64_t*)(base + o_rptr);
   P.stage = base + o_stage;
+  P.wl_dev = (int64_t*)(base + o_wl);
 
   if (cudaStreamCreateWithFlags(&w->engine_stream, cudaStreamNonBlocking) != cudaSuccess) {
     world_release(w);

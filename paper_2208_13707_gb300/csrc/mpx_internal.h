@@ -220,6 +220,7 @@ struct EngineParams {
   int64_t stage_bytes;
   const Desc* rings;          // [max_streams << slots_log2]   pinned
   const int64_t* waitlists;   // [max_streams << wl_log2]      pinned
+  int64_t* wl_dev;            // [max_streams << wl_log2]      device copy of waitall lists
   StreamCtl* sctl;            // [max_streams]                 pinned
   WorldCtl* wctl;             //                                pinned
   uint64_t* doorbell;         // [max_streams] device (written by stream memops)
