@@ -305,6 +305,31 @@ int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* 
  * rounding) for i < n, launched on `stream`.  Not an MPI call. */
 int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y, mpx_cuda_stream_t stream);
 
+/* Staged point-to-point copy that allocates nothing.  The paper has no
+ * counterpart; it is for callers that cannot call cudaMalloc: code that runs
+ * while a stream is being captured into a CUDA graph (an allocation there is
+ * not recorded, and cudaMalloc/cudaFree may synchronize the device), code on
+ * latency-critical paths that must not risk an implicit device-wide
+ * synchronization, and processes whose device memory is entirely carved up
+ * in advance.  In stream order on `stream`, the message described by
+ * (sendbuf, sendcount, sendtype) is packed into a staging area and unpacked
+ * into (recvbuf, recvcount, recvtype); like a matched send/receive it
+ * delivers min(message, receive capacity) bytes, and *bytes_delivered (host
+ * memory, may be NULL) is set to that number before the call returns.
+ * The staging area is a 16 MiB array in the library's device memory (a
+ * file-scope __device__ array that every GPU which loads the library holds
+ * until the process exits); the call returns MPX_ERR_NO_MEM when more than
+ * 16 MiB would be delivered, and allocates nothing itself.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array, so calls that overlap on the GPU (on
+ * different streams, or on devices sharing nothing but this process)
+ * race: order them in one stream.  Errors: MPX_ERR_TYPE, MPX_ERR_ARG,
+ * MPX_ERR_NO_MEM, MPX_ERR_CUDA. */
+int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, mpx_datatype_t sendtype,
+                        void* recvbuf, int64_t recvcount, mpx_datatype_t recvtype,
+                        mpx_cuda_stream_t stream, int64_t* bytes_delivered);
+
 /* Convenience: create / destroy a non-blocking CUDA stream (each call makes a
  * new stream).  Not an MPI call. */
 int mpx_cuda_stream_create(mpx_cuda_stream_t* stream);

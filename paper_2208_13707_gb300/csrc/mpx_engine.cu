@@ -22,6 +22,7 @@
 // watchdog fails pending work with MPX_ERR_TIMEOUT instead of hanging.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "mpx_internal.h"
 
@@ -447,16 +448,11 @@ __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint6
   sm.phase = phase;
 }
 
-__device__ void contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t src, int64_t n,
-                            const EngineParams& P) {
+// Contiguous copy by the whole CTA with 16-byte accesses where the two
+// addresses agree modulo 16 (8 loads in flight per thread), else 4 or 1 bytes.
+__device__ void contig_copy_simd(uint64_t dst, uint64_t src, int64_t n) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (n <= 0) return;
-  if (((src | dst) & 15) == 0 && P.bulk_min > 0 && n >= P.bulk_min) {
-    const int64_t n16 = n & ~(int64_t)15;
-    tma_contig_copy(sm, buf, dst, src, n16, P);
-    for (int64_t q = n16 + tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
-    return;
-  }
   if (((src ^ dst) & 15) == 0) {
     int64_t head = (int64_t)((16 - (src & 15)) & 15);
     if (head > n) head = n;
@@ -486,6 +482,19 @@ __device__ void contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t 
     return;
   }
   for (int64_t q = tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+}
+
+__device__ void contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint64_t src, int64_t n,
+                            const EngineParams& P) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (n <= 0) return;
+  if (((src | dst) & 15) == 0 && P.bulk_min > 0 && n >= P.bulk_min) {
+    const int64_t n16 = n & ~(int64_t)15;
+    tma_contig_copy(sm, buf, dst, src, n16, P);
+    for (int64_t q = n16 + tid; q < n; q += nt) copy_unit<1>(dst + q, src + q);
+    return;
+  }
+  contig_copy_simd(dst, src, n);
 }
 
 __device__ void copy_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
@@ -1926,6 +1935,26 @@ __global__ void __launch_bounds__(512, 1) engine_kernel(EngineParams P) {
   else mover_loop(P, sm, buf);
 }
 
+// A standalone copy of one packed stream between two layouts, tile by
+// tile over the grid (no TMA, no shared memory).
+__global__ void __launch_bounds__(256) static_copy_kernel(Task T) {
+  for (uint32_t k = blockIdx.x; k < T.ntiles; k += gridDim.x) {
+    const int64_t p0 = (int64_t)k * T.tile;
+    const int64_t p1 = (p0 + T.tile) < T.bytes ? (p0 + T.tile) : T.bytes;
+    if (T.chunk == kContig) {
+      contig_copy_simd(T.dst.base + p0, T.src.base + p0, p1 - p0);
+      continue;
+    }
+    switch (T.unit) {
+      case 16: strided_copy<16>(T, p0, p1); break;
+      case 8: strided_copy<8>(T, p0, p1); break;
+      case 4: strided_copy<4>(T, p0, p1); break;
+      case 2: strided_copy<2>(T, p0, p1); break;
+      default: strided_copy<1>(T, p0, p1); break;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace mpxi
 
@@ -1972,4 +2001,132 @@ extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mpxi::engine_kernel, nthreads,
                                                 (size_t)mpxi_engine_smem_bytes());
   return n;
+}
+
+// ---------------------------------------------------------------------------
+// Staged point-to-point copy that allocates nothing (see include/mpx.h,
+// mpx_sendrecv_static).  The staging area is a file-scope device array; host
+// code only ever sees its address through cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+extern "C" int mpxi_type_desc(int32_t type, int32_t* base, int32_t* vcount, int32_t* blocklen,
+                              int32_t* stride);
+
+namespace {
+
+constexpr int64_t kStaticStageBytes = 16ll << 20;  // 16 MiB per device, held until exit
+constexpr int kStaticMaxDevices = 64;
+static __device__ __align__(256) uint8_t g_static_stage[kStaticStageBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices];
+int g_static_nsm[kStaticMaxDevices];
+
+int64_t host_gcd(int64_t a, int64_t b) {
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// The layout of `count` instances of a datatype at `base` (the engine's rules).
+mpxi::Layout host_layout(uint64_t base, int32_t elem, int32_t vcount, int32_t blocklen, int32_t stride) {
+  mpxi::Layout L;
+  const int64_t seg = (int64_t)blocklen * elem, st = (int64_t)stride * elem, per = vcount;
+  const int64_t extent = (per - 1) * st + seg;
+  L.base = base;
+  if ((per == 1 && extent == seg) || (st == seg && extent == per * seg)) {
+    L.seg = mpxi::kContig;
+    L.stride = 0;
+    L.per = 1;
+    L.extent = 0;
+  } else {
+    L.seg = seg;
+    L.stride = st;
+    L.per = per;
+    L.extent = extent;
+  }
+  return L;
+}
+
+mpxi::Task host_copy_task(const mpxi::Layout& src, const mpxi::Layout& dst, int64_t bytes) {
+  mpxi::Task T;
+  memset(&T, 0, sizeof(T));
+  T.type = mpxi::T_COPY;
+  T.src = src;
+  T.dst = dst;
+  T.bytes = bytes;
+  int64_t C;
+  if (src.seg == mpxi::kContig && dst.seg == mpxi::kContig) C = mpxi::kContig;
+  else if (src.seg == mpxi::kContig) C = dst.seg;
+  else if (dst.seg == mpxi::kContig) C = src.seg;
+  else C = host_gcd(src.seg, dst.seg);
+  T.chunk = C;
+  uint32_t U = 16;
+  if (C != mpxi::kContig) {
+    auto bad = [&](int64_t u) {
+      if ((C % u) || ((int64_t)src.base % u) || ((int64_t)dst.base % u)) return true;
+      if (src.seg != mpxi::kContig && ((src.stride % u) || (src.extent % u))) return true;
+      if (dst.seg != mpxi::kContig && ((dst.stride % u) || (dst.extent % u))) return true;
+      return false;
+    };
+    while (U > 1 && bad(U)) U >>= 1;
+  }
+  T.unit = U;
+  int64_t tile = 65536;
+  if (C != mpxi::kContig) tile = C >= tile ? C : (tile / C) * C;
+  T.tile = tile;
+  T.ntiles = (uint32_t)((bytes + tile - 1) / tile);
+  return T;
+}
+
+}  // namespace
+
+extern "C" int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, int32_t sendtype,
+                                   void* recvbuf, int64_t recvcount, int32_t recvtype,
+                                   void* stream, int64_t* bytes_delivered) {
+  int32_t sb, sv, sbl, sst, rb, rv, rbl, rst;
+  if (mpxi_type_desc(sendtype, &sb, &sv, &sbl, &sst) || mpxi_type_desc(recvtype, &rb, &rv, &rbl, &rst))
+    return 4;  // MPX_ERR_TYPE
+  if (sendcount < 0 || recvcount < 0) return 1;  // MPX_ERR_ARG
+  const int64_t se = mpxi::base_size((uint32_t)sb), re = mpxi::base_size((uint32_t)rb);
+  const int64_t sbytes = sendcount * sv * sbl * se;
+  const int64_t cap = recvcount * rv * rbl * re;
+  const int64_t n = sbytes < cap ? sbytes : cap;  // MPI truncation: the receive capacity
+  if (n > kStaticStageBytes) return 12;           // MPX_ERR_NO_MEM: beyond the static staging area
+  if ((sbytes > 0 && !sendbuf) || (n > 0 && !recvbuf)) return 1;
+  if (bytes_delivered) *bytes_delivered = n;
+  if (n == 0) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return 10;  // MPX_ERR_CUDA
+  void* stage = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_addr[dev]) {
+      // the array's host-side name is not a device address: ask the runtime
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_stage) != cudaSuccess || !p) return 10;
+      int nsm = 0;
+      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 10;
+      g_static_nsm[dev] = nsm;
+      g_static_addr[dev] = p;
+    }
+    stage = g_static_addr[dev];
+  }
+  const mpxi::Layout lsend = host_layout((uint64_t)sendbuf, (int32_t)se, sv, sbl, sst);
+  const mpxi::Layout lrecv = host_layout((uint64_t)recvbuf, (int32_t)re, rv, rbl, rst);
+  const mpxi::Layout lstage = host_layout((uint64_t)stage, 1, 1, 1, 1);
+  const mpxi::Task pack = host_copy_task(lsend, lstage, n);
+  const mpxi::Task unpack = host_copy_task(lstage, lrecv, n);
+  const int cap_ctas = 2 * g_static_nsm[dev];
+  const unsigned g1 = (unsigned)(pack.ntiles < (uint32_t)cap_ctas ? pack.ntiles : cap_ctas);
+  const unsigned g2 = (unsigned)(unpack.ntiles < (uint32_t)cap_ctas ? unpack.ntiles : cap_ctas);
+  mpxi::static_copy_kernel<<<g1, 256, 0, (cudaStream_t)stream>>>(pack);
+  if (cudaGetLastError() != cudaSuccess) return 10;
+  mpxi::static_copy_kernel<<<g2, 256, 0, (cudaStream_t)stream>>>(unpack);
+  if (cudaGetLastError() != cudaSuccess) return 10;
+  return 0;
 }

@@ -827,6 +827,18 @@ extern "C" int mpx_type_extent(mpx_datatype_t t, int64_t* extent) {
   return MPX_SUCCESS;
 }
 
+// Layout parameters of a datatype, for library code outside this file.
+extern "C" int mpxi_type_desc(int32_t t, int32_t* base, int32_t* vcount, int32_t* blocklen,
+                              int32_t* stride) {
+  const TypeRec* r = type_get(t);
+  if (!r) return MPX_ERR_TYPE;
+  *base = r->base;
+  *vcount = r->vcount;
+  *blocklen = r->blocklen;
+  *stride = r->stride;
+  return MPX_SUCCESS;
+}
+
 extern "C" int mpx_get_count(const mpx_status_t* st, mpx_datatype_t t, int64_t* count) {
   if (!st || !count) return MPX_ERR_ARG;
   int64_t sz;

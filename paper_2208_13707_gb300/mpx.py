@@ -95,6 +95,7 @@ _SIGS = {
     "mpx_allreduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp],
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
+    "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
     "mpx_version": [],
     "mpx_cuda_stream_create": [_P(_vp)],
     "mpx_cuda_stream_destroy": [_vp],
@@ -299,6 +300,15 @@ def mpx_cuda_stream_create() -> int:
 
 def mpx_cuda_stream_destroy(stream: int) -> None:
     _chk(lib.mpx_cuda_stream_destroy(stream), "mpx_cuda_stream_destroy")
+
+
+def mpx_sendrecv_static(sendbuf: int, sendcount: int, sendtype: int, recvbuf: int, recvcount: int,
+                        recvtype: int, stream: int) -> int:
+    """Returns the number of bytes delivered."""
+    n = _i64()
+    _chk(lib.mpx_sendrecv_static(sendbuf, sendcount, sendtype, recvbuf, recvcount, recvtype, stream,
+                                 ctypes.byref(n)), "mpx_sendrecv_static")
+    return n.value
 
 
 def mpx_version() -> int:
