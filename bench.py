@@ -115,7 +115,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 class RingBench:
     def __init__(self, ranks=RANKS, n=N_AXPY, max_bytes=MAX_BYTES, tile_bytes=None, engine_ctas=0,
-                 bulk_min=None):
+                 bulk_min=None, persistent=False):
         import torch
         from paper_2208_13707_gb300 import mpx
         self.torch, self.mpx = torch, mpx
@@ -131,8 +131,9 @@ class RingBench:
         self.RL = [torch.randn(arena // 4, generator=g, device=self.dev, dtype=f32) for _ in range(ranks)]
         self.RR = [torch.zeros(arena // 4, device=self.dev, dtype=f32) for _ in range(ranks)]
         torch.cuda.synchronize()
+        self.persistent = persistent
         cfg = mpx.mpx_world_config_init()
-        cfg.engine_mode = mpx.ENGINE_DRAIN
+        cfg.engine_mode = mpx.ENGINE_PERSISTENT if persistent else mpx.ENGINE_DRAIN
         cfg.max_streams = max(16, ranks)
         cfg.ring_slots = 4096
         cfg.max_comms = 2
@@ -217,6 +218,8 @@ class RingBench:
                 ev_done[r].record(cs)
             if d2h is not None:
                 d2h(r, cs)
+        if self.persistent:
+            return launches  # the resident engine picks the step up by itself
         for e in axpy_ev:
             self.es.wait_event(e)
         if ev_pass is not None:
@@ -292,7 +295,7 @@ class RingBench:
         end.record(self.es)
         self.sync_all()
         total_ms = start.elapsed_time(end)
-        pass_ms = [a.elapsed_time(b) for a, b in passes]
+        pass_ms = [] if self.persistent else [a.elapsed_time(b) for a, b in passes]
         lat_us = [reach[k][r].elapsed_time(done[k][r]) * 1e3 for k in range(steps) for r in range(self.R)]
         err = self.mpx.mpx_world_get_error(self.world)
         if err:
@@ -469,6 +472,16 @@ def main():
     ctr = b.mpx.mpx_world_get_counters(b.world)
     e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
     b.close()
+    # the same steps with the resident engine (no launch per step)
+    pb = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas, persistent=True)
+    pres = pb.run(args.warmup, args.steps)
+    pb.mpx.mpx_world_stop(pb.world, 10000)
+    pb.close()
+    plat = np.array(pres["lat_us"])
+    persistent = {"value": 2 * pb.R * args.steps / (pres["total_ms"] / 1e3), "unit": "msgs/s",
+                  "ms_per_step": pres["total_ms"] / args.steps,
+                  "payload_gbs": 2 * pres["payload"] / (pres["total_ms"] / 1e3) / 1e9,
+                  "p50_us": float(np.percentile(plat, 50)), "p99_us": float(np.percentile(plat, 99))}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -492,6 +505,7 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e["value"], "unit": "msgs/s", "h2d_bytes_per_step": e2e["h2d"],
                         "d2h_bytes_per_step": e2e["d2h"]},
+                "persistent_engine": persistent,
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {
                     "launch_to_first_task": ctr[8] / max(1, ctr[0]) / 1e3,

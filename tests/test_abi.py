@@ -1,0 +1,94 @@
+"""The C ABI: libmpx.so loads on a machine without a GPU driver and exports
+every function include/mpx.h declares; calls that need a GPU fail with an
+error code instead of crashing."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mpx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\bint\s+(mpx_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = os.path.join(ROOT, "paper_2208_13707_gb300", "_lib", "libmpx.so")
+    if not os.path.exists(path):
+        from paper_2208_13707_gb300 import build
+        build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_paper_calls():
+    names = _declared()
+    for n in ["mpx_stream_create", "mpx_stream_free", "mpx_stream_comm_create", "mpx_send_enqueue",
+              "mpx_recv_enqueue", "mpx_isend_enqueue", "mpx_irecv_enqueue", "mpx_wait_enqueue",
+              "mpx_waitall_enqueue", "mpx_allreduce_enqueue", "mpx_type_vector"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_exposes_the_same_names():
+    from paper_2208_13707_gb300 import mpx
+    missing = [n for n in _declared() if not hasattr(mpx, n)]
+    assert missing == []
+
+
+def test_datatype_calls_work_without_a_gpu():
+    from paper_2208_13707_gb300 import mpx
+    t = mpx.mpx_type_vector(4, 2, 3, mpx.FLOAT)
+    assert mpx.mpx_type_size(t) == 4 * 2 * 4
+    assert mpx.mpx_type_extent(t) == ((4 - 1) * 3 + 2) * 4
+    st = mpx.Status(source=1, tag=2, error=0, pad=0, bytes=20)
+    assert mpx.mpx_get_count(st, mpx.INT32) == 5
+    assert mpx.mpx_get_count(st, mpx.INT64) == mpx.UNDEFINED
+    mpx.mpx_type_free(t)
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_type_vector(0, 1, 1, mpx.FLOAT)
+    assert e.value.code == mpx.ERR_ARG
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_type_vector(2, 3, 2, mpx.FLOAT)        # stride < blocklength
+    assert e.value.code == mpx.ERR_ARG
+
+
+def test_world_create_reports_missing_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2208_13707_gb300 import mpx
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_world_create(2)
+    assert e.value.code == mpx.ERR_CUDA
+
+
+def test_config_defaults_and_validation():
+    from paper_2208_13707_gb300 import mpx
+    c = mpx.mpx_world_config_init()
+    assert c.ring_slots & (c.ring_slots - 1) == 0
+    assert c.engine_threads % 32 == 0 and c.engine_threads <= 512
+    assert c.watchdog_ns > 0 and c.staging_bytes > 0
+    bad = mpx.mpx_world_config_init()
+    bad.ring_slots = 1000                                # not a power of two
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_world_create(2, bad)
+    assert e.value.code == mpx.ERR_ARG
+
+
+def test_sendrecv_static_rejects_bad_arguments_before_touching_the_gpu():
+    from paper_2208_13707_gb300 import mpx
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_sendrecv_static(0, 1, 999, 0, 1, mpx.FLOAT, 0)
+    assert e.value.code == mpx.ERR_TYPE
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_sendrecv_static(16, 5 << 20, mpx.FLOAT, 32, 5 << 20, mpx.FLOAT, 0)
+    assert e.value.code == mpx.ERR_NO_MEM
