@@ -412,6 +412,63 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
+    """One message per engine pass, per layout and size: the movers' bandwidth
+    with the pass's fixed cost included.  Prints one JSON line per case."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    dev = torch.device("cuda")
+    maxb = max(sizes_mb) << 20
+    src = torch.randn(2 * maxb // 4 + 1024, device=dev)
+    dst = torch.zeros(2 * maxb // 4 + 1024, device=dev)
+    torch.cuda.synchronize()
+    peak, _ = peaks()
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mpx.ENGINE_DRAIN
+    cfg.max_streams = 4
+    w = mpx.mpx_world_create(2, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(3)]
+    cs = [torch.cuda.ExternalStream(h) for h in raw[:2]]
+    es = torch.cuda.ExternalStream(raw[2])
+    ms = [mpx.mpx_stream_create(w, r, raw[r]) for r in range(2)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    for lay in ("contig->contig", "vector->vector", "vector->contig", "contig->vector"):
+        for mb in sizes_mb:
+            nbytes = mb << 20
+            vt = mpx.mpx_type_vector(nbytes // 256, BLOCKLEN, STRIDE, mpx.FLOAT) if "vector" in lay else None
+            s_cnt, s_ty = (1, vt) if lay.startswith("vector") else (nbytes // 4, mpx.FLOAT)
+            r_cnt, r_ty = (1, vt) if lay.endswith("vector") else (nbytes // 4, mpx.FLOAT)
+            ts = []
+            for _ in range(reps):
+                a = mpx.mpx_isend_enqueue(src.data_ptr(), s_cnt, s_ty, 1, 0, comm[0])
+                b = mpx.mpx_irecv_enqueue(dst.data_ptr(), r_cnt, r_ty, 0, 0, comm[1])
+                for s in cs:
+                    es.wait_stream(s)  # after the doorbells, before the waits
+                mpx.mpx_waitall_enqueue([a])
+                mpx.mpx_waitall_enqueue([b])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(es)
+                mpx.mpx_world_progress(w, es.cuda_stream)
+                e1.record(es)
+                t0 = time.perf_counter()
+                while not all(s.query() for s in cs + [es]):
+                    if time.perf_counter() - t0 > 30:
+                        raise RuntimeError("copy sweep pass did not finish")
+                    time.sleep(1e-4)
+                ts.append(e0.elapsed_time(e1))
+            if vt is not None:
+                mpx.mpx_type_free(vt)
+            t = float(np.median(ts[1:]))
+            gbs = 2 * nbytes / (t / 1e3) / 1e9
+            print(json.dumps({"copy_sweep": lay, "MiB": mb, "pass_us": round(t * 1e3, 1),
+                              "GBps": round(gbs, 1), "frac_of_peak": round(gbs / peak, 3)}), flush=True)
+    for c in comm:
+        mpx.mpx_comm_free(c)
+    for s in ms:
+        mpx.mpx_stream_free(s)
+    mpx.mpx_world_free(w)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,6 +479,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-bytes", type=int, default=0)
     ap.add_argument("--engine-ctas", type=int, default=0)
+    ap.add_argument("--copy-sweep", action="store_true",
+                    help="single-message engine passes per layout and size (diagnostic lines, no benchmark line)")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -441,6 +500,9 @@ def main():
 
     import torch
     torch.cuda.set_device(local_rank)
+    if args.copy_sweep:
+        copy_sweep()
+        return
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     b = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas)
