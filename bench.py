@@ -115,7 +115,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 class RingBench:
     def __init__(self, ranks=RANKS, n=N_AXPY, max_bytes=MAX_BYTES, tile_bytes=None, engine_ctas=0,
-                 bulk_min=None, persistent=False):
+                 bulk_min=None, persistent=False, plain=False):
         import torch
         from paper_2208_13707_gb300 import mpx
         self.torch, self.mpx = torch, mpx
@@ -132,8 +132,10 @@ class RingBench:
         self.RR = [torch.zeros(arena // 4, device=self.dev, dtype=f32) for _ in range(ranks)]
         torch.cuda.synchronize()
         self.persistent = persistent
+        self.plain = plain
         cfg = mpx.mpx_world_config_init()
-        cfg.engine_mode = mpx.ENGINE_PERSISTENT if persistent else mpx.ENGINE_DRAIN
+        cfg.engine_mode = (mpx.ENGINE_PLAIN if plain else
+                           mpx.ENGINE_PERSISTENT if persistent else mpx.ENGINE_DRAIN)
         cfg.max_streams = max(16, ranks)
         cfg.ring_slots = 4096
         cfg.max_comms = 2
@@ -256,6 +258,38 @@ class RingBench:
                 self.es.wait_event(e)
             mpx.mpx_world_progress(self.world, self.es.cuda_stream)
             self.sync_all()
+
+    def run_plain(self, warmup, steps):
+        """The same steps through the plain path: receives pre-posted, then
+        sends, then waits; every call synchronizes its stream on the host and
+        every match is one copy the host waits for."""
+        mpx, torch = self.mpx, self.torch
+        self.prepare(warmup + steps)
+
+        def one(step):
+            plan, _ = self.step_plan(step)
+            for r in range(self.R):
+                mpx.mpx_saxpy_enqueue(self.n, ALPHA, self.RL[r].data_ptr(), self.S[r].data_ptr(),
+                                      self.cs[r].cuda_stream)
+            reqs = [[] for _ in range(self.R)]
+            for r in range(self.R):
+                for cnt, ty, src, tag, buf in plan[r][1]:
+                    reqs[r].append(mpx.mpx_irecv_enqueue(buf.data_ptr(), cnt, ty, src, tag, self.comm[r]))
+            for r in range(self.R):
+                for cnt, ty, dest, tag in plan[r][0]:
+                    reqs[r].append(mpx.mpx_isend_enqueue(self.S[r].data_ptr(), cnt, ty, dest, tag, self.comm[r]))
+            for r in range(self.R):
+                mpx.mpx_waitall_enqueue(reqs[r])
+
+        for s in range(warmup):
+            one(s)
+        self.sync_all()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            one(warmup + k)
+        self.sync_all()
+        total = time.perf_counter() - t0
+        return dict(total_ms=total * 1e3)
 
     def sync_all(self, timeout=120.0):
         t0 = time.perf_counter()
@@ -534,6 +568,13 @@ def main():
     ctr = b.mpx.mpx_world_get_counters(b.world)
     e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
     b.close()
+    # the same steps through the plain path (host timed: it synchronizes per call)
+    qb = RingBench(tile_bytes=args.tile_bytes or None, plain=True)
+    qres = qb.run_plain(args.warmup, min(args.steps, 50))
+    qb.close()
+    plain = {"value": 2 * qb.R * min(args.steps, 50) / (qres["total_ms"] / 1e3), "unit": "msgs/s",
+             "ms_per_step": qres["total_ms"] / min(args.steps, 50), "steps": min(args.steps, 50),
+             "timing": "host clock (the plain path synchronizes the host on every call)"}
     # the same steps with the resident engine (no launch per step)
     pb = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas, persistent=True)
     pres = pb.run(args.warmup, args.steps)
@@ -568,6 +609,8 @@ def main():
                 "e2e": {"value": e2e["value"], "unit": "msgs/s", "h2d_bytes_per_step": e2e["h2d"],
                         "d2h_bytes_per_step": e2e["d2h"]},
                 "persistent_engine": persistent,
+                "plain_path": plain,
+                "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {
                     "launch_to_first_task": ctr[8] / max(1, ctr[0]) / 1e3,

@@ -2085,6 +2085,29 @@ mpxi::Task host_copy_task(const mpxi::Layout& src, const mpxi::Layout& dst, int6
 
 }  // namespace
 
+// Launch the packed-stream copy of `n` bytes between two typed layouts on
+// `stream` (the plain path uses it: one kernel per operation).
+extern "C" int mpxi_copy_typed(const void* src, int64_t scount, int32_t stype, void* dst,
+                               int64_t dcount, int32_t dtype, int64_t n, void* stream) {
+  (void)scount;
+  (void)dcount;
+  int32_t sb, sv, sbl, sst, rb, rv, rbl, rst;
+  if (mpxi_type_desc(stype, &sb, &sv, &sbl, &sst) || mpxi_type_desc(dtype, &rb, &rv, &rbl, &rst)) return 4;
+  if (n <= 0) return 0;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 10;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 10;
+  const mpxi::Layout ls = host_layout((uint64_t)src, (int32_t)mpxi::base_size((uint32_t)sb), sv, sbl, sst);
+  const mpxi::Layout ld = host_layout((uint64_t)dst, (int32_t)mpxi::base_size((uint32_t)rb), rv, rbl, rst);
+  if (ls.seg == mpxi::kContig && ld.seg == mpxi::kContig) {
+    return cudaMemcpyAsync(dst, src, (size_t)n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) == cudaSuccess ? 0 : 10;
+  }
+  const mpxi::Task T = host_copy_task(ls, ld, n);
+  const unsigned grid = (unsigned)(T.ntiles < (uint32_t)(2 * nsm) ? T.ntiles : (uint32_t)(2 * nsm));
+  mpxi::static_copy_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(T);
+  return cudaGetLastError() == cudaSuccess ? 0 : 10;
+}
+
 extern "C" int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, int32_t sendtype,
                                    void* recvbuf, int64_t recvcount, int32_t recvtype,
                                    void* stream, int64_t* bytes_delivered) {

@@ -327,6 +327,8 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   if (cfg.engine_mode == MPX_ENGINE_PLAIN) {
     w->plain = plain::create(nranks, cfg.max_streams, cfg.staging_bytes);
     if (!w->plain) { world_release(w); return MPX_ERR_NO_MEM; }
+    plain::set_world_index(w->plain, w->widx);
+    if (mpxi_saxpy_preload()) { world_release(w); return MPX_ERR_CUDA; }
     *out = w;
     return MPX_SUCCESS;
   }

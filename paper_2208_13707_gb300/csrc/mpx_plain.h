@@ -13,6 +13,7 @@ struct PlainWorld;
 
 PlainWorld* create(int nranks, int max_streams, int64_t staging_bytes);
 void destroy(PlainWorld* pw);
+void set_world_index(PlainWorld* pw, int widx);
 int progress(PlainWorld* pw);
 int error(PlainWorld* pw);
 int64_t counter(PlainWorld* pw, int i);

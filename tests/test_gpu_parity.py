@@ -155,3 +155,17 @@ def test_zero_count_messages():
     b.wait(g1, h)
     b.recv(g0, c, x, 32, 4, T_BYTE, 1, 2)
     _compare(b.build())
+
+
+# ---------------------------------------------------------------------------
+# the plain path (host matching, one copy per operation) on wildcard-free
+# traffic, where the outcome is unique
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["tiny", "ring", "halo", "allreduce"])
+def test_plain_path_matches_oracle(name):
+    p = {"tiny": lambda: gen.tiny_pairs(nmsg=300),
+         "ring": lambda: gen.ring_exchange(nranks=8, n=1 << 12, steps=3, min_bytes=256, max_bytes=256 << 10),
+         "halo": lambda: gen.halo3d(sub=16, steps=2),
+         "allreduce": lambda: gen.allreduce_suite(nranks=8, sizes=(1, 1000), dtypes=(T_INT64, T_FLOAT),
+                                                  modes=(MODE_FIXED,))}[name]()
+    _compare(p, mode="plain")

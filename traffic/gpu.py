@@ -111,8 +111,7 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
                     time.sleep(1e-4)
         raise RuntimeError("submission ring stayed full")
 
-    t0 = time.perf_counter()
-    for j in prog.issue_order:
+    def issue(j):
         o = ops[int(j)]
         k, g = int(o["kind"]), int(o["stream"])
         c = int(o["comm"])
@@ -144,6 +143,34 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             mpx.mpx_saxpy_enqueue(cnt, float(o["alpha"]), p, yb, cstreams[g].cuda_stream)
         else:
             raise ValueError(k)
+
+    t0 = time.perf_counter()
+    if m != mpx.ENGINE_PLAIN:
+        for j in prog.issue_order:
+            issue(j)
+    else:
+        # the plain path completes calls on the host; a blocking call that
+        # cannot complete yet answers MPX_ERR_AGAIN: move on to other streams
+        retry = lambda fn: fn()
+        lo = prog.stream_op_lo
+        cur = [int(lo[g]) for g in range(prog.nstreams)]
+        idle_since = time.perf_counter()
+        while any(cur[g] < int(lo[g + 1]) for g in range(prog.nstreams)):
+            moved = False
+            for g in range(prog.nstreams):
+                while cur[g] < int(lo[g + 1]):
+                    try:
+                        issue(cur[g])
+                    except mpx.MpxError as e:
+                        if e.code != mpx.ERR_AGAIN:
+                            raise
+                        break
+                    cur[g] += 1
+                    moved = True
+            if moved:
+                idle_since = time.perf_counter()
+            elif time.perf_counter() - idle_since > timeout_s:
+                raise RuntimeError("plain path made no progress (deadlocked program?)")
     t_issue = time.perf_counter() - t0
 
     deadline = time.perf_counter() + timeout_s
