@@ -1003,7 +1003,8 @@ static int wait_common(int n, mpx_request_t* reqs, mpx_status_t* statuses, bool 
     if (s && si != s) return MPX_ERR_STREAM;  // §3.4: one local stream per waitall
     s = si;
     const uint64_t seq = (uint64_t)reqs[i] & ((1ull << 40) - 1);
-    if (seq == 0 || seq >= s->next_seq) return MPX_ERR_REQUEST;
+    // the plain path numbers its own operations and validates them itself
+    if (!w->plain && (seq == 0 || seq >= s->next_seq)) return MPX_ERR_REQUEST;
     ++live;
   }
   (void)live;
