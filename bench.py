@@ -446,6 +446,60 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
+    """Small-message batching: 64 ranks x 4 MPIX streams (four stream comms),
+    `nmsg` messages per step with uniform sources, destinations and tags,
+    log-uniform 8 B - 64 KB sizes, mixed uint8/int32/fp32, 5% ANY_TAG and 2%
+    ANY_SOURCE receives (ANY_SOURCE receives also ANY_TAG).  Every step is one
+    mpx_enqueue_batch call: each stream's isends/irecvs, its waitall and a
+    one-element allreduce on its comm that separates the steps; steps are
+    enqueued back to back and the host waits once at the end.  The plain path
+    runs the same step through the same call (host matching, one copy per
+    message, a host synchronization per waitall).  Wall-clock timing."""
+    import torch
+    from traffic import gen, gpu
+    prog = gen.batching(nranks=64, streams_per_rank=4, nmsg=nmsg, max_bytes=64 << 10,
+                        laminar=True, seed=gen.SEED_BASE + 2)
+    payload = int(prog.meta["payload_bytes"])
+    out = {"messages_per_step": nmsg, "sizes": "log-uniform 8 B - 64 KB",
+           "payload_bytes_per_step": payload}
+    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=120,
+                        cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+    try:
+        for _ in range(warmup):
+            r.enqueue()
+        assert r.finish(), "warm-up steps did not finish"
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r.enqueue()
+        t_enq = time.perf_counter() - t0
+        ok = r.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = r.errors()
+        assert ok and werr == 0 and not any(serr), "batched steps failed"
+        ctr = r.mpx.mpx_world_get_counters(r.world)
+    finally:
+        r.close()
+    out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
+                     "ms_per_step": 1e3 * dt / steps, "host_enqueue_ms_per_step": 1e3 * t_enq / steps,
+                     "payload_gbs": 2 * payload * steps / dt / 1e9,
+                     "rounds": int(ctr[6]), "ticks": int(ctr[1])}
+    q = gpu.BatchRunner(prog, mode="plain", timeout_s=300)
+    try:
+        q.step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(plain_steps):
+            assert q.step(), "plain step did not finish"
+        dt = time.perf_counter() - t0
+    finally:
+        q.close()
+    out["plain"] = {"value": nmsg * plain_steps / dt, "unit": "msgs/s", "steps": plain_steps,
+                    "ms_per_step": 1e3 * dt / plain_steps}
+    out["speedup_vs_plain"] = out["engine"]["value"] / out["plain"]["value"]
+    return out
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -515,6 +569,11 @@ def main():
     ap.add_argument("--engine-ctas", type=int, default=0)
     ap.add_argument("--copy-sweep", action="store_true",
                     help="single-message engine passes per layout and size (diagnostic lines, no benchmark line)")
+    ap.add_argument("--batch-msgs", type=int, default=65536,
+                    help="messages per step of the small-message batching measurement (0 = skip it)")
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batching-only", action="store_true",
+                    help="print only the small-message batching measurement")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -536,6 +595,10 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.copy_sweep:
         copy_sweep()
+        return
+    if args.batching_only:
+        print(json.dumps({"batching_small": batching_small(args.batch_steps, args.warmup,
+                                                           args.batch_msgs)}), flush=True)
         return
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
@@ -585,6 +648,7 @@ def main():
                   "ms_per_step": pres["total_ms"] / args.steps,
                   "payload_gbs": 2 * pres["payload"] / (pres["total_ms"] / 1e3) / 1e9,
                   "p50_us": float(np.percentile(plat, 50)), "p99_us": float(np.percentile(plat, 99))}
+    batching = batching_small(args.batch_steps, args.warmup, args.batch_msgs) if args.batch_msgs else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -610,6 +674,7 @@ def main():
                         "d2h_bytes_per_step": e2e["d2h"]},
                 "persistent_engine": persistent,
                 "plain_path": plain,
+                "batching_small": batching,
                 "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {

@@ -297,6 +297,43 @@ int mpx_waitall_enqueue(int n, mpx_request_t requests[], mpx_status_t statuses[]
 int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                           mpx_datatype_t datatype, int op, mpx_comm_t comm);
 
+/* One operation of mpx_enqueue_batch.  Fields a kind does not use are ignored. */
+enum {
+  MPX_OP_SEND = 0,      /* mpx_send_enqueue(buf, count, datatype, peer, tag, comm) */
+  MPX_OP_RECV = 1,      /* mpx_recv_enqueue(buf, count, datatype, peer, tag, comm, status) */
+  MPX_OP_ISEND = 2,     /* mpx_isend_enqueue(buf, count, datatype, peer, tag, comm, requests) */
+  MPX_OP_IRECV = 3,     /* mpx_irecv_enqueue(buf, count, datatype, peer, tag, comm, requests) */
+  MPX_OP_WAIT = 4,      /* mpx_wait_enqueue(requests, status) */
+  MPX_OP_WAITALL = 5,   /* mpx_waitall_enqueue(count, requests, status) */
+  MPX_OP_ALLREDUCE = 6  /* mpx_allreduce_enqueue(buf, recvbuf, count, datatype, op, comm) */
+};
+
+typedef struct {
+  int32_t kind;             /* MPX_OP_* */
+  mpx_datatype_t datatype;
+  int32_t peer;             /* destination (send kinds) or source (receive kinds) */
+  int32_t tag;
+  int64_t count;            /* elements; for MPX_OP_WAITALL the number of requests */
+  const void* buf;          /* message buffer; allreduce send buffer (or MPX_IN_PLACE) */
+  void* recvbuf;            /* allreduce receive buffer */
+  mpx_comm_t comm;
+  mpx_request_t* requests;  /* isend/irecv: receives the request; wait/waitall: the request(s) */
+  mpx_status_t* status;     /* recv/wait: one status; waitall: `count` statuses; may be NULL */
+  int32_t op;               /* allreduce: MPX_SUM */
+  int32_t pad;
+} mpx_op_t;                 /* 72 bytes */
+
+/* Batch submission: enqueue ops[0..n) in array order, each exactly as its
+ * single call would (same validation, same semantics, same stream order),
+ * and stop at the first one that fails.  *done (may be NULL) receives the
+ * number of operations enqueued; the return value is the failing
+ * operation's error, else MPX_SUCCESS.  Nothing is enqueued on a CUDA stream
+ * by anyone else during the call, so consecutive non-blocking operations of
+ * one non-exclusive stream share one stream-order doorbell (the last one's);
+ * doorbells still owed when the batch stops are written before it returns.
+ * The host cost per operation is that of filling one descriptor. */
+int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done);
+
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);
 

@@ -43,7 +43,9 @@ constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipelin
 constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
 constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
-constexpr int kSmemStreams = 128;  // worlds up to this many streams keep per-stream state in shared memory
+constexpr int kSmemStreams = 128;
+constexpr int kMaxCtaThreads = 512;  // engine block size bound (launch bounds)
+constexpr int kSortMinPosts = 128;   // rounds with more posts match from domain-sorted lists  // worlds up to this many streams keep per-stream state in shared memory
 
 // ------------------------------------------------------------------------
 // memory-model helpers
@@ -216,6 +218,7 @@ struct CtaShared {
   int32_t arrivals;       // control: allreduce arrivals this round
   int32_t limits_reached; // control: a drain pass has ingested up to all its limits
   int32_t left;           // control: some stream still has ingested operations ahead of its cursor
+  int32_t nposts_round;   // control: posts of the current round
   uint64_t t_retire, t_alloc;
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
@@ -903,6 +906,12 @@ struct Ctl {
     S.cursor = cur;
     S.nposts = n;
     sm.cnt[g] = n;
+    if (P.cnt2 && n) {
+      const int nd = P.max_comms * P.nranks;
+      int32_t* row = P.cnt2 + (size_t)g * nd;
+      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] += 1;
+      atomicAdd(&sm.nposts_round, n);
+    }
     if (moved) sm.any = 1;
     return moved;
   }
@@ -978,29 +987,10 @@ struct Ctl {
     atomicOr(&s->pflags, PF_MATCHED);
   }
 
-  __device__ void match_domain(uint32_t d) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t qmask = (1u << P.qcap_log2) - 1;
-    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
-    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
-    QHead ph = P.pqh[d], uh = P.uqh[d];
-    for (int g = 0; g < P.max_streams; ++g) {
-      const int n = sm.cnt[g];
-      if (n == 0) continue;
-      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
-      for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        uint64_t pv = 0;
-        bool mine = false;
-        if (i < n) {
-          pv = posts[i];
-          mine = (uint32_t)(pv >> 40) == d;
-        }
-        unsigned b = __ballot_sync(FULL, mine);
-        while (b) {
-          const int src_lane = __ffs(b) - 1;
-          b &= b - 1;
-          const uint64_t seq = __shfl_sync(FULL, pv, src_lane) & ((1ull << 40) - 1);
+  // One post of domain d, in key order (warp-cooperative).
+  __device__ void match_post(int g, uint64_t seq, QEntry* pq, QEntry* uq, QHead& ph, QHead& uh,
+                             uint32_t qmask) {
+          const int lane = threadIdx.x & 31;
           const DOp* o = op_at(P, g, seq);
           const uint32_t kind = kw_kind(o->d.kw);
           const uint64_t ref = make_ref(g, seq);
@@ -1026,12 +1016,140 @@ struct Ctl {
             }
           }
           __syncwarp();
+  }
+
+  // Domain d's posts found by scanning every stream's post list (small rounds).
+  __device__ void match_domain(uint32_t d) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t qmask = (1u << P.qcap_log2) - 1;
+    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
+    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
+    QHead ph = P.pqh[d], uh = P.uqh[d];
+    for (int g = 0; g < P.max_streams; ++g) {
+      const int n = sm.cnt[g];
+      if (n == 0) continue;
+      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        uint64_t pv = 0;
+        bool mine = false;
+        if (i < n) {
+          pv = posts[i];
+          mine = (uint32_t)(pv >> 40) == d;
+        }
+        unsigned b = __ballot_sync(FULL, mine);
+        while (b) {
+          const int src_lane = __ffs(b) - 1;
+          b &= b - 1;
+          const uint64_t seq = __shfl_sync(FULL, pv, src_lane) & ((1ull << 40) - 1);
+          match_post(g, seq, pq, uq, ph, uh, qmask);
         }
       }
     }
     if (lane == 0) {
       P.pqh[d] = ph;
       P.uqh[d] = uh;
+    }
+  }
+
+  // Domain d's posts from its sorted list (large rounds): the stable counting
+  // sort below leaves them in key order (stream id, then sequence number).
+  __device__ void match_domain_sorted(uint32_t d) {
+    const int lane = threadIdx.x & 31;
+    const int32_t n = P.dtot[d];
+    if (n == 0) return;
+    const uint32_t qmask = (1u << P.qcap_log2) - 1;
+    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
+    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
+    QHead ph = P.pqh[d], uh = P.uqh[d];
+    const uint64_t* list = P.dlist + P.dbase[d];
+    for (int base = 0; base < n; base += 32) {
+      const uint64_t pv = base + lane < n ? list[base + lane] : 0;
+      const int m = (n - base) < 32 ? (n - base) : 32;
+      for (int k = 0; k < m; ++k) {
+        const uint64_t v = __shfl_sync(FULL, pv, k);
+        match_post(ref_stream(v), ref_seq(v), pq, uq, ph, uh, qmask);
+      }
+    }
+    if (lane == 0) {
+      P.pqh[d] = ph;
+      P.uqh[d] = uh;
+    }
+  }
+
+  // Stable counting sort of this round's posts by domain (counts per
+  // (stream, domain) were taken while posting).
+  __device__ void sort_posts() {
+    __shared__ int64_t part[kMaxCtaThreads];
+    const int nd = P.max_comms * P.nranks;
+    const int nt = blockDim.x, t = threadIdx.x;
+    // each thread owns a contiguous chunk of domains: per domain, the
+    // exclusive prefix over streams (in place) and the domain's total
+    const int chunk = (nd + nt - 1) / nt;
+    const int d0 = t * chunk < nd ? t * chunk : nd;
+    const int d1 = d0 + chunk < nd ? d0 + chunk : nd;
+    int64_t mine = 0;
+    for (int d = d0; d < d1; ++d) {
+      int32_t off = 0;
+      for (int g = 0; g < P.max_streams; ++g) {
+        if (sm.cnt[g] == 0) continue;
+        int32_t* c = &P.cnt2[(size_t)g * nd + d];
+        const int32_t v = *c;
+        if (v) {
+          *c = off;
+          off += v;
+        }
+      }
+      P.dtot[d] = off;
+      mine += off;
+    }
+    part[t] = mine;
+    __syncthreads();
+    if (t < 32) {  // exclusive scan of the chunk sums by warp 0
+      const int per = (nt + 31) / 32;
+      int64_t s = 0;
+      for (int k = 0; k < per && t * per + k < nt; ++k) s += part[t * per + k];
+      int64_t x = s;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, x, o);
+        if (t >= o) x += y;
+      }
+      int64_t b = x - s;
+      for (int k = 0; k < per && t * per + k < nt; ++k) {
+        const int64_t v = part[t * per + k];
+        part[t * per + k] = b;
+        b += v;
+      }
+    }
+    __syncthreads();
+    int64_t b = part[t];
+    for (int d = d0; d < d1; ++d) {
+      P.dbase[d] = b;
+      b += P.dtot[d];
+    }
+    __syncthreads();
+    // scatter each stream's posts in program order
+    for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
+      const int n = sm.cnt[g];
+      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      int32_t* row = P.cnt2 + (size_t)g * nd;
+      for (int i = 0; i < n; ++i) {
+        const uint64_t pv = posts[i];
+        const uint32_t d = (uint32_t)(pv >> 40);
+        const int32_t k = row[d]++;
+        P.dlist[P.dbase[d] + k] = make_ref(g, pv & ((1ull << 40) - 1));
+      }
+    }
+  }
+
+  // zero the (stream, domain) counts this round used
+  __device__ void clear_counts() {
+    const int nd = P.max_comms * P.nranks;
+    for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
+      const int n = sm.cnt[g];
+      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      int32_t* row = P.cnt2 + (size_t)g * nd;
+      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] = 0;
     }
   }
 
@@ -1646,6 +1764,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   }
   if (tid == 0) {
     sm.limits_reached = 0;
+    sm.nposts_round = 0;
     sm.arrivals = 0;
     sm.ready_insts = 0;
   }
@@ -1732,9 +1851,22 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (moved) {
           const int warp = tid >> 5, nw = blockDim.x >> 5;
           const uint32_t nd = (uint32_t)(P.max_comms * P.nranks);
-          for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
+          if (P.cnt2 && sm.nposts_round >= kSortMinPosts) {
+            C.sort_posts();
+            __syncthreads();
+            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain_sorted(d);
+            __syncthreads();
+            C.clear_counts();
+          } else {
+            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
+            if (P.cnt2 && sm.nposts_round > 0) {
+              __syncthreads();
+              C.clear_counts();
+            }
+          }
           __syncthreads();
         }
+        if (tid == 0) sm.nposts_round = 0;
         if (sm.arrivals) C.collectives();
         __syncthreads();
         if (tid == 0) {
@@ -1909,7 +2041,7 @@ __device__ void mover_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
 
 extern __shared__ __align__(128) uint8_t g_dyn_smem[];
 
-__global__ void __launch_bounds__(512, 1) engine_kernel(EngineParams P) {
+__global__ void __launch_bounds__(kMaxCtaThreads, 1) engine_kernel(EngineParams P) {
   CtaShared& sm = *reinterpret_cast<CtaShared*>(g_dyn_smem);
   uint8_t* buf = g_dyn_smem + ((sizeof(CtaShared) + 1023) & ~(size_t)1023);
   if (threadIdx.x == 0) {

@@ -151,6 +151,7 @@ struct mpx_stream_s {
   unsigned flags;
   uint64_t next_seq;  // next sequence number to publish
   uint64_t wl_next;   // next waitlist index
+  uint64_t db_owed;   // a batch published ops up to here without their doorbell (0 = none)
   int ncomms;         // communicators using this stream
 };
 
@@ -359,6 +360,13 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_ninst = carve((size_t)cfg.max_comms * nranks * 8);
   const size_t o_rptr = carve(iwn * 2 * nranks * 8);
   const size_t o_wl = carve(((size_t)S << w->wl_log2) * sizeof(int64_t));
+  // counting-sort scratch for large rounds (skipped for very large worlds,
+  // which then match by scanning)
+  const bool sort_ok = (size_t)S * ndom <= ((size_t)16 << 20);
+  const size_t o_cnt2 = sort_ok ? carve((size_t)S * ndom * 4) : 0;
+  const size_t o_dtot = sort_ok ? carve(ndom * 4) : 0;
+  const size_t o_dbase = sort_ok ? carve(ndom * 8) : 0;
+  const size_t o_dlist = sort_ok ? carve((size_t)S * slots * 8) : 0;
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
   w->dev_bytes = off;
   if (cfg.budget_bytes > 0 && (int64_t)off > cfg.budget_bytes) { world_release(w); return MPX_ERR_NO_MEM; }
@@ -419,6 +427,10 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.reduce_ptrs = (uint64_t*)(base + o_rptr);
   P.stage = base + o_stage;
   P.wl_dev = (int64_t*)(base + o_wl);
+  P.cnt2 = sort_ok ? (int32_t*)(base + o_cnt2) : nullptr;
+  P.dtot = sort_ok ? (int32_t*)(base + o_dtot) : nullptr;
+  P.dbase = sort_ok ? (int64_t*)(base + o_dbase) : nullptr;
+  P.dlist = sort_ok ? (uint64_t*)(base + o_dlist) : nullptr;
 
   if (cudaStreamCreateWithFlags(&w->engine_stream, cudaStreamNonBlocking) != cudaSuccess) {
     world_release(w);
@@ -649,7 +661,7 @@ extern "C" int mpx_stream_create(mpx_world_t w, int rank, mpx_cuda_stream_t cs, 
   s->flags = flags;
   s->ncomms = 0;
   if (w->plain) {
-    if (plain::stream_create(w->plain, id, rank, (cudaStream_t)cs) != MPX_SUCCESS) { delete s; return MPX_ERR_NO_MEM; }
+    if (plain::stream_create(w->plain, id, rank, (cudaStream_t)cs, (flags & MPX_STREAM_EXCLUSIVE) != 0) != MPX_SUCCESS) { delete s; return MPX_ERR_NO_MEM; }
   } else {
     StreamCtl* c = &w->sctl[id];
     // sequence numbers continue across incarnations of an endpoint so the
@@ -867,7 +879,17 @@ extern "C" int mpx_cuda_stream_destroy(mpx_cuda_stream_t stream) {
 // ---------------------------------------------------------------------------
 // enqueue
 // ---------------------------------------------------------------------------
-static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out) {
+static int write_doorbell(mpx_stream_s* s, uint64_t seq) {
+  CUdeviceptr db = (CUdeviceptr)(s->w->params.doorbell + s->id);
+  s->db_owed = 0;
+  return g_write64((CUstream)s->cs, db, seq, 0) == CUDA_SUCCESS ? MPX_SUCCESS : MPX_ERR_CUDA;
+}
+
+// defer_db: a batch will publish the next op on this stream right after this
+// one, with nothing enqueued on the CUDA stream in between; that op's doorbell
+// (or the batch's final flush) also announces this one.
+static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
+                   bool defer_db = false) {
   mpx_world_s* w = s->w;
   StreamCtl* c = &w->sctl[s->id];
   if (__atomic_load_n(&w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
@@ -897,8 +919,11 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out) {
   if (erc) return erc;
   CUstream cs = (CUstream)s->cs;
   if (!(s->flags & MPX_STREAM_EXCLUSIVE)) {
-    CUdeviceptr db = (CUdeviceptr)(w->params.doorbell + s->id);
-    if (g_write64(cs, db, seq, 0) != CUDA_SUCCESS) return MPX_ERR_CUDA;
+    if (defer_db && !blocking) {
+      s->db_owed = seq;
+    } else if (write_doorbell(s, seq) != MPX_SUCCESS) {
+      return MPX_ERR_CUDA;
+    }
   }
   if (blocking) {
     CUdeviceptr dn = (CUdeviceptr)(w->params.done + s->id);
@@ -955,30 +980,29 @@ extern "C" int mpx_recv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int
   return publish(c->stream, d, true, nullptr);
 }
 
-extern "C" int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
-                                 int tag, mpx_comm_t c, mpx_request_t* req) {
+static int nb_p2p(uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt, int peer,
+                  int tag, mpx_comm_t c, mpx_request_t* req, bool defer_db) {
   if (!req) return MPX_ERR_ARG;
-  if (c && c->w->plain) return plain::p2p(c->w->plain, K_ISEND, buf, count, dt, dest, tag, c->shared->id, c->rank, c->stream->id, nullptr, req);
+  if (c && c->w->plain)
+    return plain::p2p(c->w->plain, kind, buf, count, dt, peer, tag, c->shared->id, c->rank,
+                      c->stream->id, nullptr, req);
   Desc d;
-  int rc = fill_p2p(d, K_ISEND, buf, count, dt, dest, tag, c, false);
+  int rc = fill_p2p(d, kind, buf, count, dt, peer, tag, c, kind == K_IRECV);
   if (rc) return rc;
   uint64_t seq = 0;
-  rc = publish(c->stream, d, false, &seq);
+  rc = publish(c->stream, d, false, &seq, defer_db);
   if (seq) *req = make_request(c->stream, seq);
   return rc;
 }
 
+extern "C" int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
+                                 int tag, mpx_comm_t c, mpx_request_t* req) {
+  return nb_p2p(K_ISEND, buf, count, dt, dest, tag, c, req, false);
+}
+
 extern "C" int mpx_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source, int tag,
                                  mpx_comm_t c, mpx_request_t* req) {
-  if (!req) return MPX_ERR_ARG;
-  if (c && c->w->plain) return plain::p2p(c->w->plain, K_IRECV, buf, count, dt, source, tag, c->shared->id, c->rank, c->stream->id, nullptr, req);
-  Desc d;
-  int rc = fill_p2p(d, K_IRECV, buf, count, dt, source, tag, c, true);
-  if (rc) return rc;
-  uint64_t seq = 0;
-  rc = publish(c->stream, d, false, &seq);
-  if (seq) *req = make_request(c->stream, seq);
-  return rc;
+  return nb_p2p(K_IRECV, buf, count, dt, source, tag, c, req, false);
 }
 
 static mpx_stream_s* request_stream(mpx_request_t r) {
@@ -1081,3 +1105,88 @@ extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t
   return publish(c->stream, d, true, nullptr);
 }
 
+
+// ---------------------------------------------------------------------------
+// batch submission
+// ---------------------------------------------------------------------------
+static mpx_stream_s* batch_op_stream(const mpx_op_t& o) {
+  switch (o.kind) {
+    case MPX_OP_SEND: case MPX_OP_RECV: case MPX_OP_ISEND: case MPX_OP_IRECV:
+    case MPX_OP_ALLREDUCE:
+      return o.comm ? o.comm->stream : nullptr;
+    case MPX_OP_WAIT: case MPX_OP_WAITALL:
+      if (!o.requests) return nullptr;
+      for (int64_t i = 0; i < (o.kind == MPX_OP_WAIT ? 1 : o.count); ++i)
+        if (o.requests[i] != MPX_REQUEST_NULL) return request_stream(o.requests[i]);
+      return nullptr;
+    default:
+      return nullptr;
+  }
+}
+
+extern "C" int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done) {
+  if (done) *done = 0;
+  if (n < 0 || (n > 0 && !ops)) return MPX_ERR_ARG;
+  // streams owing a doorbell (a stream owes one at most, for its last deferred op)
+  mpx_stream_s* owed[64];
+  int nowed = 0;
+  auto flush = [&](mpx_stream_s* only) -> int {
+    int rc = MPX_SUCCESS;
+    for (int k = 0; k < nowed;) {
+      mpx_stream_s* st = owed[k];
+      if (only && st != only) { ++k; continue; }
+      if (st->db_owed && write_doorbell(st, st->db_owed) != MPX_SUCCESS) rc = MPX_ERR_CUDA;
+      owed[k] = owed[--nowed];
+    }
+    return rc;
+  };
+  int rc = MPX_SUCCESS, i = 0;
+  for (; i < n; ++i) {
+    const mpx_op_t& o = ops[i];
+    mpx_stream_s* st = batch_op_stream(o);
+    const bool nb = o.kind == MPX_OP_ISEND || o.kind == MPX_OP_IRECV;
+    // defer this op's doorbell only when the next op goes to the same stream
+    bool defer = false;
+    if (nb && st && !st->w->plain && !(st->flags & MPX_STREAM_EXCLUSIVE) && i + 1 < n &&
+        batch_op_stream(ops[i + 1]) == st) {
+      defer = nowed < 64 || st->db_owed;
+    }
+    switch (o.kind) {
+      case MPX_OP_SEND:
+        rc = mpx_send_enqueue(o.buf, o.count, o.datatype, o.peer, o.tag, o.comm);
+        break;
+      case MPX_OP_RECV:
+        rc = mpx_recv_enqueue((void*)o.buf, o.count, o.datatype, o.peer, o.tag, o.comm, o.status);
+        break;
+      case MPX_OP_ISEND:
+        rc = nb_p2p(K_ISEND, o.buf, o.count, o.datatype, o.peer, o.tag, o.comm, o.requests, defer);
+        break;
+      case MPX_OP_IRECV:
+        rc = nb_p2p(K_IRECV, o.buf, o.count, o.datatype, o.peer, o.tag, o.comm, o.requests, defer);
+        break;
+      case MPX_OP_WAIT:
+        rc = mpx_wait_enqueue(o.requests, o.status);
+        break;
+      case MPX_OP_WAITALL:
+        rc = o.count > INT32_MAX ? MPX_ERR_ARG
+                                 : mpx_waitall_enqueue((int)o.count, o.requests, o.status);
+        break;
+      case MPX_OP_ALLREDUCE:
+        rc = mpx_allreduce_enqueue(o.buf, o.recvbuf, o.count, o.datatype, o.op, o.comm);
+        break;
+      default:
+        rc = MPX_ERR_ARG;
+    }
+    if (rc != MPX_SUCCESS) break;
+    if (st && st->db_owed) {
+      bool listed = false;
+      for (int k = 0; k < nowed; ++k) listed |= owed[k] == st;
+      if (!listed) owed[nowed++] = st;
+    } else if (st) {
+      flush(st);  // the op's own doorbell covered what the stream owed
+    }
+  }
+  const int frc = flush(nullptr);
+  if (done) *done = i;
+  return rc != MPX_SUCCESS ? rc : frc;
+}

@@ -221,6 +221,10 @@ struct EngineParams {
   const Desc* rings;          // [max_streams << slots_log2]   pinned
   const int64_t* waitlists;   // [max_streams << wl_log2]      pinned
   int64_t* wl_dev;            // [max_streams << wl_log2]      device copy of waitall lists
+  int32_t* cnt2;              // [max_streams * ndomains] posts per (stream, domain), or null
+  int32_t* dtot;              // [ndomains] posts per domain this round
+  int64_t* dbase;             // [ndomains] start of each domain's list
+  uint64_t* dlist;            // [max_streams << slots_log2] this round's posts sorted by domain
   StreamCtl* sctl;            // [max_streams]                 pinned
   WorldCtl* wctl;             //                                pinned
   uint64_t* doorbell;         // [max_streams] device (written by stream memops)

@@ -1,12 +1,13 @@
 // Plain path of libmpx (MPX_ENGINE_PLAIN): the baseline the device engine is
 // measured against.  It does what a GPU-aware MPI does without stream
-// integration (§2.4): every call first synchronizes the caller's CUDA stream
-// (the full CPU/GPU synchronization the paper names as the penalty), matching
+// integration (§2.4): a call on a non-exclusive stream first synchronizes the
+// caller's CUDA stream (the full CPU/GPU synchronization the paper names as
+// the penalty; an exclusive stream promises its buffers are ready), matching
 // runs on the host under one world-wide lock, each match moves its payload
-// with one cudaMemcpyAsync or one copy kernel, and the host waits for that
-// copy before the operation counts as complete.  Blocking calls that cannot
-// complete yet return MPX_ERR_AGAIN (a progress loop retries them); nothing
-// is left queued on the GPU.
+// with one cudaMemcpyAsync or one copy kernel on the world's copy stream, and
+// every blocking call (recv, send, wait, waitall, allreduce) synchronizes the
+// host with that copy stream before it returns.  Blocking calls that cannot
+// complete yet return MPX_ERR_AGAIN (a progress loop retries them).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -124,6 +125,7 @@ struct Req {
 
 struct Stream {
   bool alive = false;
+  bool exclusive = false;
   int rank = 0;
   cudaStream_t cs = nullptr;
   uint64_t next_seq = 1;
@@ -190,9 +192,9 @@ mpx_status_t make_status(int src, int tag, int err, int64_t bytes) {
 int deliver(PlainWorld* pw, const Msg& m, const Recv& r, mpx_status_t* out) {
   const int64_t cap = r.count * type_bytes(r.type);
   const int64_t n = m.bytes < cap ? m.bytes : cap;
+  // the copy is stream-ordered on the copy stream; a later staging copy into
+  // the same arena space queues behind it
   int rc = mpxi_copy_typed(m.buf, m.count, m.type, r.buf, r.count, r.type, n, pw->copy_stream);
-  if (rc) return rc;
-  rc = sync_stream(pw->copy_stream);
   if (rc) return rc;
   if (m.stage_off >= 0 && --pw->staged_live == 0) pw->stage_head = 0;
   *out = make_status(m.src, m.tag, m.bytes > cap ? MPX_ERR_TRUNCATE : 0, n);
@@ -206,9 +208,11 @@ int deliver(PlainWorld* pw, const Msg& m, const Recv& r, mpx_status_t* out) {
   return MPX_SUCCESS;
 }
 
-int write_status(mpx_status_t* dst, const mpx_status_t& st) {
-  if (!dst) return MPX_SUCCESS;
-  return cudaMemcpy(dst, &st, sizeof(st), cudaMemcpyDefault) == cudaSuccess ? MPX_SUCCESS : MPX_ERR_CUDA;
+int write_statuses(mpx_status_t* dst, const mpx_status_t* st, int n) {
+  if (!dst || n <= 0) return MPX_SUCCESS;
+  return cudaMemcpy(dst, st, sizeof(*st) * (size_t)n, cudaMemcpyDefault) == cudaSuccess
+             ? MPX_SUCCESS
+             : MPX_ERR_CUDA;
 }
 
 }  // namespace
@@ -243,12 +247,13 @@ int error(PlainWorld* pw) { return pw->error; }
 
 int64_t counter(PlainWorld* pw, int i) { return (i >= 0 && i < 19) ? pw->counters[i] : 0; }
 
-int stream_create(PlainWorld* pw, int id, int rank, cudaStream_t cs) {
+int stream_create(PlainWorld* pw, int id, int rank, cudaStream_t cs, bool exclusive) {
   std::lock_guard<std::mutex> g(pw->mu);
   Stream& s = pw->streams[id];
   const uint64_t keep = s.next_seq;
   s = Stream();
   s.alive = true;
+  s.exclusive = exclusive;
   s.rank = rank;
   s.cs = cs;
   s.next_seq = keep;
@@ -289,7 +294,7 @@ int p2p(PlainWorld* pw, uint32_t kind, const void* buf, int64_t count, mpx_datat
   std::lock_guard<std::mutex> g(pw->mu);
   Stream& S = pw->streams[sid];
   // the buffer is ready only once the work enqueued before the call is done
-  int rc = sync_stream(S.cs);
+  int rc = S.exclusive ? MPX_SUCCESS : sync_stream(S.cs);
   if (rc) return rc;
   if (is_send) {
     Msg m{sid, S.next_seq, rank, tag, buf, count, dt, count * tb, -1};
@@ -318,8 +323,6 @@ int p2p(PlainWorld* pw, uint32_t kind, const void* buf, int64_t count, mpx_datat
       uint8_t* dst = pw->stage + pw->stage_head;
       rc = mpxi_copy_typed(buf, count, dt, dst, m.bytes, MPX_BYTE, m.bytes, pw->copy_stream);
       if (rc) return rc;
-      rc = sync_stream(pw->copy_stream);
-      if (rc) return rc;
       m.buf = dst;
       m.count = m.bytes;
       m.type = MPX_BYTE;
@@ -329,6 +332,10 @@ int p2p(PlainWorld* pw, uint32_t kind, const void* buf, int64_t count, mpx_datat
       pw->counters[5] += 1;
     }
     if (!matched) pw->unexpected[{comm, peer}].push_back(m);
+    if (kind == mpxi::K_SEND) {  // blocking: the buffer is reusable on return
+      rc = sync_stream(pw->copy_stream);
+      if (rc) return rc;
+    }
     const uint64_t seq = S.next_seq++;
     if (kind == mpxi::K_ISEND && req) {
       Req r0{true, false, make_status(MPX_ANY_SOURCE, MPX_ANY_TAG, 0, 0)};
@@ -353,7 +360,9 @@ int p2p(PlainWorld* pw, uint32_t kind, const void* buf, int64_t count, mpx_datat
       *req = (mpx_request_t)(((uint64_t)pw->widx << 56) | ((uint64_t)sid << 40) | seq);
       return MPX_SUCCESS;
     }
-    return write_status(status, st);
+    rc = sync_stream(pw->copy_stream);  // blocking receive: data in place on return
+    if (rc) return rc;
+    return write_statuses(status, &st, 1);
   }
   if (kind == mpxi::K_RECV) return MPX_ERR_AGAIN;  // nothing to receive yet: retry
   const uint64_t seq = S.next_seq++;
@@ -374,6 +383,10 @@ int wait(PlainWorld* pw, int sid, int n, const mpx_request_t* reqs, mpx_status_t
     if (it == S.reqs.end()) return MPX_ERR_REQUEST;
     if (!it->second.complete) return MPX_ERR_AGAIN;
   }
+  // one host synchronization per wait: every copy of these requests is done
+  int rc = sync_stream(pw->copy_stream);
+  if (rc) return rc;
+  std::vector<mpx_status_t> sts((size_t)n);
   for (int i = 0; i < n; ++i) {
     mpx_status_t st = make_status(MPX_ANY_SOURCE, MPX_ANY_TAG, 0, 0);
     if (reqs[i] != MPX_REQUEST_NULL) {
@@ -382,12 +395,9 @@ int wait(PlainWorld* pw, int sid, int n, const mpx_request_t* reqs, mpx_status_t
       st = it->second.st;
       S.reqs.erase(it);
     }
-    if (statuses) {
-      int rc = write_status(statuses + i, st);
-      if (rc) return rc;
-    }
+    sts[(size_t)i] = st;
   }
-  return MPX_SUCCESS;
+  return write_statuses(statuses, sts.data(), n);
 }
 
 int allreduce(PlainWorld* pw, const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t dt,

@@ -1,5 +1,5 @@
 // Plain path of libmpx: host matching, one cudaMemcpyAsync or one kernel per
-// operation, a host synchronization at every completion.  It is the
+// operation, a host synchronization at every blocking call and wait.  It is the
 // baseline the device engine is measured against (MPX_ENGINE_PLAIN).
 #pragma once
 #include <cuda_runtime.h>
@@ -17,7 +17,7 @@ void set_world_index(PlainWorld* pw, int widx);
 int progress(PlainWorld* pw);
 int error(PlainWorld* pw);
 int64_t counter(PlainWorld* pw, int i);
-int stream_create(PlainWorld* pw, int id, int rank, cudaStream_t cs);
+int stream_create(PlainWorld* pw, int id, int rank, cudaStream_t cs, bool exclusive);
 void stream_free(PlainWorld* pw, int id);
 int64_t stream_pending(PlainWorld* pw, int id);
 int stream_error(PlainWorld* pw, int id);

@@ -54,6 +54,17 @@ class WorldConfig(ctypes.Structure):
                 ("stage_delay_ns", ctypes.c_int64)]
 
 
+OP_SEND, OP_RECV, OP_ISEND, OP_IRECV, OP_WAIT, OP_WAITALL, OP_ALLREDUCE = range(7)
+
+
+def op_dtype():
+    """numpy layout of mpx_op_t (72 bytes), for building batches as arrays."""
+    import numpy as np
+    return np.dtype([("kind", "<i4"), ("datatype", "<i4"), ("peer", "<i4"), ("tag", "<i4"),
+                     ("count", "<i8"), ("buf", "<u8"), ("recvbuf", "<u8"), ("comm", "<u8"),
+                     ("requests", "<u8"), ("status", "<u8"), ("op", "<i4"), ("pad", "<i4")])
+
+
 class Status(ctypes.Structure):
     _fields_ = [("source", ctypes.c_int32), ("tag", ctypes.c_int32), ("error", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("bytes", ctypes.c_int64)]
@@ -96,6 +107,7 @@ _SIGS = {
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
+    "mpx_enqueue_batch": [ctypes.c_int, _vp, _P(ctypes.c_int)],
     "mpx_version": [],
     "mpx_cuda_stream_create": [_P(_vp)],
     "mpx_cuda_stream_destroy": [_vp],
@@ -313,3 +325,19 @@ def mpx_sendrecv_static(sendbuf: int, sendcount: int, sendtype: int, recvbuf: in
 
 def mpx_version() -> int:
     return lib.mpx_version()
+
+
+def mpx_enqueue_batch(ops, n: Optional[int] = None) -> int:
+    """`ops`: a C-contiguous numpy array of op_dtype() (or anything exposing
+    the buffer protocol with that layout).  Returns the number enqueued;
+    raises MpxError (with `.done`) if an operation failed."""
+    import numpy as np
+    a = np.ascontiguousarray(ops)
+    cnt = len(a) if n is None else int(n)
+    done = ctypes.c_int(0)
+    rc = lib.mpx_enqueue_batch(cnt, a.ctypes.data, ctypes.byref(done))
+    if rc != 0:
+        e = MpxError(rc, "mpx_enqueue_batch")
+        e.done = done.value
+        raise e
+    return done.value

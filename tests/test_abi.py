@@ -92,3 +92,42 @@ def test_sendrecv_static_rejects_bad_arguments_before_touching_the_gpu():
     with pytest.raises(mpx.MpxError) as e:
         mpx.mpx_sendrecv_static(16, 5 << 20, mpx.FLOAT, 32, 5 << 20, mpx.FLOAT, 0)
     assert e.value.code == mpx.ERR_NO_MEM
+
+
+def test_op_struct_layout_matches_the_binding(tmp_path):
+    """mpx_op_t as the C compiler lays it out equals the binding's numpy layout."""
+    from paper_2208_13707_gb300 import mpx
+    dt = mpx.op_dtype()
+    fields = list(dt.names)
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpx.h"\nint main(void){\n'
+                   '  printf("%zu", sizeof(mpx_op_t));\n' +
+                   "".join(f'  printf(" %zu", offsetof(mpx_op_t, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == dt.itemsize
+    assert out[1:] == [dt.fields[f][1] for f in fields]
+
+
+def test_enqueue_batch_stops_at_the_first_invalid_op():
+    """Validation happens before anything is published: an op without a
+    communicator fails with MPX_ERR_COMM and nothing counts as enqueued."""
+    import numpy as np
+    from paper_2208_13707_gb300 import mpx
+    ops = np.zeros(3, mpx.op_dtype())
+    ops["kind"] = mpx.OP_SEND
+    ops["count"] = 1
+    ops["buf"] = 64
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_enqueue_batch(ops)
+    assert e.value.code == mpx.ERR_COMM and e.value.done == 0
+    ops["kind"] = 99
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_enqueue_batch(ops)
+    assert e.value.code == mpx.ERR_ARG and e.value.done == 0
+    assert mpx.mpx_enqueue_batch(ops[:0]) == 0

@@ -482,3 +482,17 @@ def test_planted_mistake_is_caught(k, tmp_path, monkeypatch):
         assert caught, f"mutant {k} survived"
     finally:
         sys.modules["oracle"] = saved
+
+
+@pytest.mark.parametrize("k", range(12))
+def test_laminar_batching_programs_complete_without_truncation(k):
+    """The batching generator's laminar option (ANY_SOURCE receives are also
+    ANY_TAG; receives posted most specific first; capacities the largest
+    admissible message) yields programs every receive of which completes
+    untruncated.  Checked here through the oracle at high wildcard rates."""
+    from traffic import gen
+    p = gen.batching(nranks=4, streams_per_rank=2, nmsg=60, max_bytes=256, ntags=3,
+                     p_any_tag=0.3, p_any_source=0.3, laminar=True, seed=gen.SEED_BASE + 1000 + k)
+    o = oracle.run(p)
+    assert o.error == 0 and not o.deadlock
+    assert np.all(o.status["error"] == 0)

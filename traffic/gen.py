@@ -288,7 +288,7 @@ def batching(nranks: int = 64, streams_per_rank: int = 4, nmsg: int = 1_000_000,
              p_any_tag: float = 0.05, p_any_source: float = 0.02,
              seed: int = SEED_BASE + 2,
              fixup: Optional[Callable[[Program], Optional[np.ndarray]]] = None,
-             max_fixups: int = 8) -> Program:
+             max_fixups: int = 8, laminar: bool = False) -> Program:
     """R ranks x S streams; stream comm c holds every rank's c-th stream.  Each
     message has a uniform source stream, a uniform destination rank (same comm
     index), a uniform tag and log-uniform bytes; its dtype is uniform over
@@ -300,7 +300,14 @@ def batching(nranks: int = 64, streams_per_rank: int = 4, nmsg: int = 1_000_000,
 
     `fixup`, when given, receives the program and returns the receive op
     indices that can never match (or None); those receives are widened to
-    (ANY_SOURCE, ANY_TAG) and the program is rebuilt, up to `max_fixups` times."""
+    (ANY_SOURCE, ANY_TAG) and the program is rebuilt, up to `max_fixups` times.
+
+    `laminar` makes every program complete without that check: an ANY_SOURCE
+    receive is also ANY_TAG, so a domain's receive patterns are exact (s, t),
+    (s, ANY_TAG) or (ANY_SOURCE, ANY_TAG) and any two are nested or disjoint.
+    Posted most specific first, greedy matching in post-key order then never
+    strands a receive.  Every receive gets the largest capacity among the
+    messages its pattern admits, so none truncates either."""
     rng = Rng(seed, 50)
     ns = nranks * streams_per_rank
     src_stream = rng.integers(0, ns - 1, nmsg)
@@ -316,10 +323,12 @@ def batching(nranks: int = 64, streams_per_rank: int = 4, nmsg: int = 1_000_000,
     send_key = rng.u64(nmsg)
     recv_key = rng.u64(nmsg)
     widened = np.zeros(nmsg, bool)
+    if laminar:
+        wild_tag = wild_tag | wild_src
     for attempt in range(max_fixups + 1):
         prog = _batching_build(nranks, streams_per_rank, src_stream, dst_rank, tags,
                                counts, dts, esz, wild_tag | widened, wild_src | widened,
-                               send_key, recv_key, seed)
+                               send_key, recv_key, seed, laminar)
         if fixup is None:
             break
         bad = fixup(prog)
@@ -335,7 +344,7 @@ def batching(nranks: int = 64, streams_per_rank: int = 4, nmsg: int = 1_000_000,
 
 
 def _batching_build(nranks, spr, src_stream, dst_rank, tags, counts, dts, esz,
-                    wild_tag, wild_src, send_key, recv_key, seed) -> Program:
+                    wild_tag, wild_src, send_key, recv_key, seed, laminar=False) -> Program:
     nmsg = len(src_stream)
     ns = nranks * spr
     b = ProgramBuilder(nranks, "batching")
@@ -355,6 +364,22 @@ def _batching_build(nranks, spr, src_stream, dst_rank, tags, counts, dts, esz,
     np.maximum.at(maxdom, dom, nbytes)
     wild = wild_tag | wild_src
     cap[wild] = maxdom[dom[wild]]
+    if laminar:
+        # (s, ANY_TAG): largest message from s in the domain; exact (s, t):
+        # largest (s, t) message, since a wildcard may take an earlier one
+        src_rank_ = src_stream // spr
+        key_s = dom * nranks + src_rank_
+        max_s = np.zeros(spr * nranks * nranks, np.int64)
+        np.maximum.at(max_s, key_s, nbytes)
+        key_st = key_s * (int(tags.max()) + 1) + tags
+        uniq, inv = np.unique(key_st, return_inverse=True)
+        max_st = np.zeros(len(uniq), np.int64)
+        np.maximum.at(max_st, inv, nbytes)
+        only_tag = wild_tag & ~wild_src
+        cap = max_st[inv].copy()
+        cap[only_tag] = max_s[key_s[only_tag]]
+        cap[wild_src] = maxdom[dom[wild_src]]
+        cap = (np.maximum(cap, esz) + esz - 1) // esz * esz
     # per-stream send arenas (payload) and receive arenas (capacity)
     send_off = np.zeros(nmsg, np.int64)
     recv_off = np.zeros(nmsg, np.int64)

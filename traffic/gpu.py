@@ -240,3 +240,196 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
         extra.update(world=world, streams=ms, comms=comms, cstreams=cstreams, dbufs=dbufs)
     return GpuOutcome(buffers=out_bufs, status=status, stream_errors=serr, world_error=werr,
                       counters=counters, finished=finished, seconds=seconds, extra=extra)
+
+
+class BatchRunner:
+    """A closed program in which every stream's only blocking operation is its
+    last one (a waitall over all of the stream's requests), run repeatedly
+    through mpx_enqueue_batch: one call enqueues every stream's non-blocking
+    operations, then every stream's waitall.  Holds the world, streams,
+    buffers and the prebuilt operation array between steps."""
+
+    def __init__(self, prog: Program, mode: str = "persistent", exclusive: bool = True,
+                 cfg_over: Optional[dict] = None, timeout_s: float = 60.0,
+                 epoch_barrier: bool = False):
+        """epoch_barrier: end every stream's step with a one-element in-place
+        allreduce on the stream's comm, so that steps enqueued back to back
+        stay separate epochs (a stream's next step posts nothing before every
+        member of its comm has finished this one).  Not for the plain path,
+        whose blocking allreduce cannot wait inside one batch call."""
+        import torch
+        from paper_2208_13707_gb300 import mpx
+        self.mpx, self.torch, self.prog, self.timeout_s = mpx, torch, prog, timeout_s
+        dev = torch.device("cuda")
+        self.mode = {"persistent": mpx.ENGINE_PERSISTENT, "drain": mpx.ENGINE_DRAIN,
+                     "plain": mpx.ENGINE_PLAIN}[mode]
+        over = {"task_slots": 1 << 16}
+        over.update(cfg_over or {})
+        cfg = make_config(prog, self.mode, **over)
+        self.dbufs = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) if b.size else
+                      torch.empty(16, dtype=torch.uint8, device=dev) for b in prog.buf_init]
+        self.st = torch.zeros(max(1, prog.nstatus) * STATUS_DTYPE.itemsize, dtype=torch.uint8,
+                              device=dev)
+        torch.cuda.current_stream(dev).synchronize()
+        self.world = mpx.mpx_world_create(prog.nranks, cfg)
+        self.raw = [mpx.mpx_cuda_stream_create() for _ in range(prog.nstreams + 1)]
+        self.cstreams = [torch.cuda.ExternalStream(h, device=dev) for h in self.raw[:-1]]
+        self.engine_stream = torch.cuda.ExternalStream(self.raw[-1], device=dev)
+        flags = mpx.STREAM_EXCLUSIVE if exclusive else mpx.STREAM_DEFAULT
+        self.ms = [mpx.mpx_stream_create(self.world, int(prog.stream_rank[g]),
+                                         self.cstreams[g].cuda_stream, flags)
+                   for g in range(prog.nstreams)]
+        self.comms = [mpx.mpx_stream_comm_create(self.world, [self.ms[int(g)] for g in prog.comm_stream[c]])
+                      for c in range(prog.ncomms)]
+        self.epoch_barrier = epoch_barrier
+        if epoch_barrier:
+            assert self.mode != mpx.ENGINE_PLAIN
+            self.bar = torch.zeros(prog.nstreams * 4, dtype=torch.int32, device=dev)
+            torch.cuda.synchronize()
+        self.ops = self._build_ops()
+        self.messages = int((np.isin(prog.ops["kind"], [SEND, ISEND])).sum())
+
+    def _build_ops(self):
+        mpx, prog = self.mpx, self.prog
+        ops = prog.ops
+        nops = len(ops)
+        self.reqs = np.full(nops, -1, np.int64)
+        req_base = self.reqs.ctypes.data
+        ptr = np.array([b.data_ptr() for b in self.dbufs], np.uint64)
+        st_ptr = self.st.data_ptr()
+        rank_in = {}
+        for c in range(prog.ncomms):
+            for r, g in enumerate(prog.comm_stream[c]):
+                rank_in[(c, int(g))] = r
+        comm_h = np.array([self.comms[int(o["comm"])][rank_in[(int(o["comm"]), int(o["stream"]))]]
+                           if o["comm"] >= 0 else 0 for o in ops], np.uint64)
+        out = np.zeros(nops, mpx.op_dtype())
+        kind = ops["kind"].astype(np.int64)
+        lo = prog.stream_op_lo
+        assert (ops["type"] < 5).all(), "basic datatypes only"
+        nb_idx, wait_idx = [], []
+        for g in range(prog.nstreams):
+            a, b = int(lo[g]), int(lo[g + 1])
+            if b == a:
+                continue
+            assert kind[b - 1] == WAITALL and np.isin(kind[a:b - 1], [ISEND, IRECV]).all(), \
+                "each stream must be non-blocking operations followed by one waitall"
+            q = prog.reqlist[int(ops[b - 1]["req_lo"]): int(ops[b - 1]["req_lo"]) + int(ops[b - 1]["req_n"])]
+            assert np.array_equal(q, np.arange(a, b - 1)), "the waitall must cover the stream's requests in order"
+            nb_idx.extend(range(a, b - 1))
+            wait_idx.append(b - 1)
+        order = np.array(nb_idx + wait_idx, np.int64)
+        o = ops[order]
+        k = kind[order]
+        rec = out[: len(order)]
+        rec["kind"] = np.where(k == ISEND, mpx.OP_ISEND, np.where(k == IRECV, mpx.OP_IRECV, mpx.OP_WAITALL))
+        rec["datatype"] = o["type"]
+        rec["peer"] = o["peer"]
+        rec["tag"] = o["tag"]
+        bufp = np.where(o["buf"] >= 0, ptr[np.maximum(o["buf"], 0)] + o["off"].astype(np.uint64), 0)
+        rec["buf"] = np.where(k == WAITALL, 0, bufp)
+        rec["comm"] = comm_h[order]
+        isw = k == WAITALL
+        rec["count"] = np.where(isw, o["req_n"], o["count"])
+        first_req = np.where(isw, order - o["req_n"], order)
+        rec["requests"] = req_base + 8 * first_req.astype(np.uint64)
+        rec["status"] = np.where(isw & (o["status"] >= 0),
+                                 st_ptr + STATUS_DTYPE.itemsize * np.maximum(o["status"], 0).astype(np.uint64), 0)
+        out = out[: len(order)].copy()
+        if self.epoch_barrier:
+            bar = np.zeros(prog.nstreams, mpx.op_dtype())
+            bar["kind"] = mpx.OP_ALLREDUCE
+            bar["datatype"] = mpx.INT32
+            bar["count"] = 1
+            bar["op"] = mpx.SUM
+            bar["buf"] = mpx.IN_PLACE
+            bar["recvbuf"] = self.bar.data_ptr() + 16 * np.arange(prog.nstreams, dtype=np.uint64)
+            stream_comm = {}
+            for c in range(prog.ncomms):
+                for r, g in enumerate(prog.comm_stream[c]):
+                    stream_comm.setdefault(int(g), self.comms[c][r])
+            bar["comm"] = [stream_comm[g] for g in range(prog.nstreams)]
+            out = np.concatenate([out, bar])
+        return out
+
+    def enqueue(self):
+        """Enqueue one step (returns once every operation is enqueued)."""
+        mpx = self.mpx
+        done = 0
+        n = len(self.ops)
+        t_dl = time.perf_counter() + self.timeout_s
+        while done < n:
+            try:
+                done += mpx.mpx_enqueue_batch(self.ops[done:])
+            except mpx.MpxError as e:
+                if e.code != mpx.ERR_AGAIN:
+                    raise
+                done += e.done
+                if time.perf_counter() > t_dl:
+                    raise RuntimeError("batch enqueue made no progress")
+                if self.mode == mpx.ENGINE_DRAIN:
+                    self.progress_once()
+                else:
+                    time.sleep(1e-5)
+
+    def progress_once(self):
+        self.mpx.mpx_world_progress(self.world, self.engine_stream.cuda_stream)
+
+    def finish(self) -> bool:
+        """Drive (drain mode) and wait until every stream is idle."""
+        mpx = self.mpx
+        t_dl = time.perf_counter() + self.timeout_s
+        if self.mode == mpx.ENGINE_DRAIN:
+            while time.perf_counter() < t_dl:
+                self.progress_once()
+                self.engine_stream.synchronize()
+                if all(mpx.mpx_stream_pending(s) == 0 for s in self.ms):
+                    break
+        while time.perf_counter() < t_dl:
+            if all(s.query() for s in self.cstreams):
+                return True
+            time.sleep(2e-5)
+        return False
+
+    def step(self) -> bool:
+        self.enqueue()
+        return self.finish()
+
+    def results(self):
+        bufs = [b.cpu().numpy()[: self.prog.buf_init[i].size].copy() for i, b in enumerate(self.dbufs)]
+        status = np.frombuffer(self.st.cpu().numpy().tobytes(), STATUS_DTYPE)[: self.prog.nstatus].copy()
+        return bufs, status
+
+    def reset_buffers(self):
+        for b, init in zip(self.dbufs, self.prog.buf_init):
+            if init.size:
+                b.copy_(self.torch.from_numpy(np.ascontiguousarray(init)).to(b.device))
+        self.st.zero_()
+        self.torch.cuda.synchronize()
+
+    def errors(self):
+        mpx = self.mpx
+        return [mpx.mpx_stream_get_error(s) for s in self.ms], mpx.mpx_world_get_error(self.world)
+
+    def close(self):
+        mpx = self.mpx
+        if not self.finish():
+            mpx.mpx_world_abort(self.world)
+            t1 = time.perf_counter()
+            while time.perf_counter() - t1 < 10 and not all(s.query() for s in self.cstreams):
+                time.sleep(1e-3)
+        for cl in self.comms:
+            for h in cl:
+                mpx.mpx_comm_free(h)
+        for s in self.ms:
+            for _ in range(2000):
+                try:
+                    mpx.mpx_stream_free(s)
+                    break
+                except mpx.MpxError as e:
+                    if e.code != mpx.ERR_PENDING:
+                        raise
+                    time.sleep(5e-4)
+        mpx.mpx_world_free(self.world)
+        for h in self.raw:
+            mpx.mpx_cuda_stream_destroy(h)
