@@ -469,6 +469,8 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
         for _ in range(warmup):
             r.enqueue()
         assert r.finish(), "warm-up steps did not finish"
+        r.mpx.mpx_world_stop(r.world, 10000)
+        ctr0 = r.mpx.mpx_world_get_counters(r.world)
         t0 = time.perf_counter()
         for _ in range(steps):
             r.enqueue()
@@ -477,13 +479,17 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
         dt = time.perf_counter() - t0
         serr, werr = r.errors()
         assert ok and werr == 0 and not any(serr), "batched steps failed"
-        ctr = r.mpx.mpx_world_get_counters(r.world)
+        r.mpx.mpx_world_stop(r.world, 10000)  # phase times are summed when the engine exits
+        ctr = [a - b for a, b in zip(r.mpx.mpx_world_get_counters(r.world), ctr0)]
     finally:
         r.close()
     out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
                      "ms_per_step": 1e3 * dt / steps, "host_enqueue_ms_per_step": 1e3 * t_enq / steps,
                      "payload_gbs": 2 * payload * steps / dt / 1e9,
-                     "rounds": int(ctr[6]), "ticks": int(ctr[1])}
+                     "rounds": int(ctr[6]), "ticks": int(ctr[1]),
+                     "control_ms_by_phase": {k: ctr[12 + i] / 1e6 for i, k in enumerate(
+                         ["ingest", "rounds", "finished_tasks", "completion", "scheduling",
+                          "decisions", "own_moves"])}}
     q = gpu.BatchRunner(prog, mode="plain", timeout_s=300)
     try:
         q.step()

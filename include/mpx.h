@@ -42,9 +42,11 @@
  *     so every stream sharing it; CUDA maps streams onto
  *     CUDA_DEVICE_MAX_CONNECTIONS queues.  Loading the library sets that
  *     variable to 32 unless it is already set (it only takes effect if CUDA
- *     is not initialised yet).  Keep the non-exclusive streams of a world
- *     within that many queues; exclusive streams carry no doorbell and are
- *     not limited.
+ *     is not initialised yet).  In PERSISTENT mode the engine is resident
+ *     before any wait is enqueued, so the number of streams is not limited
+ *     by this.  In DRAIN mode the pass that would satisfy a wait is itself
+ *     launched on a stream: keep the streams that can sit at a blocking call
+ *     at the same time, plus the pass's stream, within that many queues.
  */
 #ifndef MPX_H
 #define MPX_H

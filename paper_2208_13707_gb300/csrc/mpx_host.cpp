@@ -151,7 +151,8 @@ struct mpx_stream_s {
   unsigned flags;
   uint64_t next_seq;  // next sequence number to publish
   uint64_t wl_next;   // next waitlist index
-  uint64_t db_owed;   // a batch published ops up to here without their doorbell (0 = none)
+  uint64_t owed;      // a batch wrote descriptors up to here without releasing the tail
+                      // and ringing the doorbell (0 = none)
   int ncomms;         // communicators using this stream
 };
 
@@ -879,25 +880,42 @@ extern "C" int mpx_cuda_stream_destroy(mpx_cuda_stream_t stream) {
 // ---------------------------------------------------------------------------
 // enqueue
 // ---------------------------------------------------------------------------
-static int write_doorbell(mpx_stream_s* s, uint64_t seq) {
-  CUdeviceptr db = (CUdeviceptr)(s->w->params.doorbell + s->id);
-  s->db_owed = 0;
-  return g_write64((CUstream)s->cs, db, seq, 0) == CUDA_SUCCESS ? MPX_SUCCESS : MPX_ERR_CUDA;
+// Make descriptors up to `seq` visible to the engine (release the ring tail),
+// have the engine running, and ring the stream-order doorbell.
+static int announce(mpx_stream_s* s, uint64_t seq) {
+  mpx_world_s* w = s->w;
+  s->owed = 0;
+  __atomic_store_n(&w->sctl[s->id].tail, seq, __ATOMIC_RELEASE);
+  // launch the engine (persistent mode) before a later wait can stall a
+  // hardware queue the engine's stream might share
+  int erc = ensure_engine(w);
+  if (erc) return erc;
+  if (!(s->flags & MPX_STREAM_EXCLUSIVE)) {
+    CUdeviceptr db = (CUdeviceptr)(w->params.doorbell + s->id);
+    if (g_write64((CUstream)s->cs, db, seq, 0) != CUDA_SUCCESS) return MPX_ERR_CUDA;
+  }
+  return MPX_SUCCESS;
 }
 
-// defer_db: a batch will publish the next op on this stream right after this
-// one, with nothing enqueued on the CUDA stream in between; that op's doorbell
-// (or the batch's final flush) also announces this one.
+static int flush_owed(mpx_stream_s* s) { return s->owed ? announce(s, s->owed) : MPX_SUCCESS; }
+
+// defer: a batch will publish the next op on this stream right after this
+// one, with nothing enqueued on the CUDA stream in between; the descriptor is
+// written but the tail release and the doorbell are left to that op (or to
+// the batch's flush), so a run of operations costs one of each.
 static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
-                   bool defer_db = false) {
+                   bool defer = false) {
   mpx_world_s* w = s->w;
   StreamCtl* c = &w->sctl[s->id];
   if (__atomic_load_n(&w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
   const uint64_t seq = s->next_seq;
   const uint64_t slots = 1ull << w->slots_log2;
   if (seq - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE) > slots) {
+    // the engine can only retire what it can see
+    int rc = flush_owed(s);
+    if (rc) return rc;
     if (w->cfg.engine_mode != MPX_ENGINE_PERSISTENT) return MPX_ERR_AGAIN;
-    int rc = ensure_engine(w);
+    rc = ensure_engine(w);
     if (rc) return rc;
     const int64_t t0 = now_ms();
     while (seq - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE) > slots) {
@@ -910,24 +928,17 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
             kw_kind(d.kw), (int)blocking);
   Desc* slot = &w->rings[((size_t)s->id << w->slots_log2) + ((seq - 1) & (slots - 1))];
   memcpy(slot, &d, sizeof(Desc));
-  __atomic_store_n(&c->tail, seq, __ATOMIC_RELEASE);
   s->next_seq = seq + 1;
   if (seq_out) *seq_out = seq;  // the operation exists from here on
-  // launch the engine (persistent mode) before this call's wait can stall a
-  // hardware queue the engine's stream might share
-  int erc = ensure_engine(w);
-  if (erc) return erc;
-  CUstream cs = (CUstream)s->cs;
-  if (!(s->flags & MPX_STREAM_EXCLUSIVE)) {
-    if (defer_db && !blocking) {
-      s->db_owed = seq;
-    } else if (write_doorbell(s, seq) != MPX_SUCCESS) {
-      return MPX_ERR_CUDA;
-    }
+  if (defer && !blocking) {
+    s->owed = seq;
+    return MPX_SUCCESS;
   }
+  int rc = announce(s, seq);
+  if (rc) return rc;
   if (blocking) {
     CUdeviceptr dn = (CUdeviceptr)(w->params.done + s->id);
-    if (g_wait64(cs, dn, seq, CU_STREAM_WAIT_VALUE_GEQ) != CUDA_SUCCESS) return MPX_ERR_CUDA;
+    if (g_wait64((CUstream)s->cs, dn, seq, CU_STREAM_WAIT_VALUE_GEQ) != CUDA_SUCCESS) return MPX_ERR_CUDA;
   }
   MPX_TRACE("publish: memops queued");
   return MPX_SUCCESS;
@@ -1127,30 +1138,15 @@ static mpx_stream_s* batch_op_stream(const mpx_op_t& o) {
 extern "C" int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done) {
   if (done) *done = 0;
   if (n < 0 || (n > 0 && !ops)) return MPX_ERR_ARG;
-  // streams owing a doorbell (a stream owes one at most, for its last deferred op)
-  mpx_stream_s* owed[64];
-  int nowed = 0;
-  auto flush = [&](mpx_stream_s* only) -> int {
-    int rc = MPX_SUCCESS;
-    for (int k = 0; k < nowed;) {
-      mpx_stream_s* st = owed[k];
-      if (only && st != only) { ++k; continue; }
-      if (st->db_owed && write_doorbell(st, st->db_owed) != MPX_SUCCESS) rc = MPX_ERR_CUDA;
-      owed[k] = owed[--nowed];
-    }
-    return rc;
-  };
+  // At most one stream owes an announcement at a time: a run is deferred
+  // only while the next op goes to the same stream.
+  mpx_stream_s* owing = nullptr;
   int rc = MPX_SUCCESS, i = 0;
+  mpx_stream_s* st = n > 0 ? batch_op_stream(ops[0]) : nullptr;
   for (; i < n; ++i) {
     const mpx_op_t& o = ops[i];
-    mpx_stream_s* st = batch_op_stream(o);
-    const bool nb = o.kind == MPX_OP_ISEND || o.kind == MPX_OP_IRECV;
-    // defer this op's doorbell only when the next op goes to the same stream
-    bool defer = false;
-    if (nb && st && !st->w->plain && !(st->flags & MPX_STREAM_EXCLUSIVE) && i + 1 < n &&
-        batch_op_stream(ops[i + 1]) == st) {
-      defer = nowed < 64 || st->db_owed;
-    }
+    mpx_stream_s* next = i + 1 < n ? batch_op_stream(ops[i + 1]) : nullptr;
+    const bool defer = st && next == st && !st->w->plain;
     switch (o.kind) {
       case MPX_OP_SEND:
         rc = mpx_send_enqueue(o.buf, o.count, o.datatype, o.peer, o.tag, o.comm);
@@ -1178,15 +1174,22 @@ extern "C" int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done) {
         rc = MPX_ERR_ARG;
     }
     if (rc != MPX_SUCCESS) break;
-    if (st && st->db_owed) {
-      bool listed = false;
-      for (int k = 0; k < nowed; ++k) listed |= owed[k] == st;
-      if (!listed) owed[nowed++] = st;
-    } else if (st) {
-      flush(st);  // the op's own doorbell covered what the stream owed
+    owing = st && st->owed ? st : nullptr;
+    if (owing && next != st) {  // the run ends here
+      rc = flush_owed(owing);
+      owing = nullptr;
+      if (rc != MPX_SUCCESS) {
+        ++i;
+        break;
+      }
     }
+    st = next;
   }
-  const int frc = flush(nullptr);
+  // an op that failed validation leaves its predecessor's run unannounced
+  if (owing) {
+    const int frc = flush_owed(owing);
+    if (rc == MPX_SUCCESS) rc = frc;
+  }
   if (done) *done = i;
-  return rc != MPX_SUCCESS ? rc : frc;
+  return rc;
 }

@@ -382,13 +382,19 @@ class BatchRunner:
         if self.mode == mpx.ENGINE_DRAIN:
             while time.perf_counter() < t_dl:
                 self.progress_once()
-                self.engine_stream.synchronize()
+                while not self.engine_stream.query() and time.perf_counter() < t_dl:
+                    time.sleep(2e-5)
                 if all(mpx.mpx_stream_pending(s) == 0 for s in self.ms):
                     break
         while time.perf_counter() < t_dl:
             if all(s.query() for s in self.cstreams):
                 return True
             time.sleep(2e-5)
+        import sys
+        print(f"[BatchRunner] deadline: counters={mpx.mpx_world_get_counters(self.world)}",
+              file=sys.stderr, flush=True)
+        if self.mode != mpx.ENGINE_PLAIN:
+            mpx.mpx_world_debug_dump(self.world)
         return False
 
     def step(self) -> bool:
