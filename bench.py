@@ -506,6 +506,106 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
     return out
 
 
+def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26), R=16, iters=None):
+    """Enqueued SUM allreduce among R ranks (one stream each, persistent
+    engine): per size, dtype (int64, fp32) and order (fixed, tree), `iters`
+    instances back to back after warm-up.  Algorithmic bytes per instance:
+    2*R*n*elem (R inputs read, R outputs written).  Inputs are filled on the
+    device (int64 round(N(0,1)*2^40), fp32 N(0,1)); wall-clock timing over
+    the instances, inputs far larger than L2 at the large sizes."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    dev = torch.device("cuda")
+    cfg = mpx.mpx_world_config_init()
+    cfg.max_streams = R
+    world = mpx.mpx_world_create(R, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(R)]
+    cs = [torch.cuda.ExternalStream(h, device=dev) for h in raw]
+    ms = [mpx.mpx_stream_create(world, r, raw[r], mpx.STREAM_EXCLUSIVE) for r in range(R)]
+    comm = mpx.mpx_stream_comm_create(world, ms)
+    gen_ = torch.Generator(device=dev)
+    gen_.manual_seed(0x220813707 + 3)
+    out = []
+    nmax = 1 << max(log2_sizes)
+    xs = torch.empty((R, nmax), dtype=torch.int64, device=dev)
+    ys = torch.empty((R, nmax), dtype=torch.int64, device=dev)
+    try:
+        for dt_name, dt, esz in (("int64", mpx.INT64, 8), ("f32", mpx.FLOAT, 4)):
+            modes = [("fixed", mpx.REDUCE_FIXED)] + ([("tree", mpx.REDUCE_TREE)] if dt == mpx.FLOAT else [])
+            for mode_name, mode in modes:
+                mpx.mpx_comm_set_reduce_mode(comm[0], mode)
+                for lg in log2_sizes:
+                    n = 1 << lg
+                    if dt == mpx.INT64:
+                        x = xs[:, :n]
+                        x.copy_(torch.round(torch.randn((R, n), device=dev, generator=gen_) * 2.0 ** 40).to(torch.int64))
+                        y = ys[:, :n]
+                    else:
+                        x = xs.view(torch.float32)[:, :n]
+                        x.normal_(generator=gen_)
+                        y = ys.view(torch.float32)[:, :n]
+                    torch.cuda.synchronize()
+                    k = iters or max(4, min(200, (1 << 30) // (2 * R * n * esz)))
+
+                    def run(m):
+                        for _ in range(m):
+                            for r in range(R):
+                                mpx.mpx_allreduce_enqueue(x[r].data_ptr(), y[r].data_ptr(), n, dt, mpx.SUM, comm[r])
+                        for c in cs:
+                            c.synchronize()
+                    run(3)
+                    t0 = time.perf_counter()
+                    run(k)
+                    dt_s = (time.perf_counter() - t0) / k
+                    gbs = 2 * R * n * esz / dt_s / 1e9
+                    out.append({"n": n, "dtype": dt_name, "mode": mode_name, "instances": k,
+                                "us_per_instance": 1e6 * dt_s, "gbs": gbs})
+        mpx.mpx_world_stop(world, 10000)
+    finally:
+        for h in comm:
+            mpx.mpx_comm_free(h)
+        for s_ in ms:
+            mpx.mpx_stream_free(s_)
+        mpx.mpx_world_free(world)
+        for h in raw:
+            mpx.mpx_cuda_stream_destroy(h)
+        del xs, ys
+        torch.cuda.empty_cache()
+    return out
+
+
+def halo_bench(steps=100, warmup=5, sub=256):
+    """3-D 7-point halo exchange, (2*sub)^3 fp32 in 8 subdomains (2x2x2,
+    periodic): per step each rank isends its 6 faces (x faces as
+    vector(sub*sub,1,sub), y faces vector(sub,sub,sub*sub), z faces
+    contiguous) and irecvs 6 ghosts, then one waitall; steps enqueued back to
+    back through mpx_enqueue_batch, one host wait at the end."""
+    import torch
+    from traffic import gen, gpu
+    prog = gen.halo3d(sub=sub, steps=1, init=False)
+    r = gpu.BatchRunner(prog, mode="persistent", exclusive=True, timeout_s=120)
+    try:
+        for k in prog.meta["U"]:
+            r.dbufs[k].view(torch.float32).normal_()
+        torch.cuda.synchronize()
+        for _ in range(warmup):
+            r.enqueue()
+        assert r.finish()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r.enqueue()
+        ok = r.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = r.errors()
+        assert ok and werr == 0 and not any(serr), "halo steps failed"
+    finally:
+        r.close()
+    face_bytes = int(prog.meta["payload_bytes"])
+    return {"grid": f"{2 * sub}^3 fp32, 8 subdomains", "steps": steps, "us_per_step": 1e6 * dt / steps,
+            "messages_per_step": int(prog.meta["messages"]),
+            "face_gbs": 2 * face_bytes * steps / dt / 1e9, "timing": "wall clock, steps back to back"}
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -580,6 +680,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--batching-only", action="store_true",
                     help="print only the small-message batching measurement")
+    ap.add_argument("--allreduce-only", action="store_true",
+                    help="print only the allreduce bandwidth sweep and the halo exchange")
+    ap.add_argument("--no-c4", action="store_true", help="skip the allreduce sweep and the halo exchange")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -601,6 +704,14 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.copy_sweep:
         copy_sweep()
+        return
+    if args.allreduce_only:
+        pk, pkind = peaks()
+        ar = allreduce_bw()
+        for e in ar:
+            e["frac_of_peak"] = e["gbs"] / pk
+        print(json.dumps({"allreduce": ar, "halo": halo_bench(), "peak_gbs": pk, "peak_source": pkind}),
+              flush=True)
         return
     if args.batching_only:
         print(json.dumps({"batching_small": batching_small(args.batch_steps, args.warmup,
@@ -655,6 +766,13 @@ def main():
                   "payload_gbs": 2 * pres["payload"] / (pres["total_ms"] / 1e3) / 1e9,
                   "p50_us": float(np.percentile(plat, 50)), "p99_us": float(np.percentile(plat, 99))}
     batching = batching_small(args.batch_steps, args.warmup, args.batch_msgs) if args.batch_msgs else None
+    c4 = None
+    if not args.no_c4:
+        pk, _ = peaks()
+        ar = allreduce_bw()
+        for e in ar:
+            e["frac_of_peak"] = e["gbs"] / pk
+        c4 = {"allreduce": ar, "halo": halo_bench()}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -681,6 +799,7 @@ def main():
                 "persistent_engine": persistent,
                 "plain_path": plain,
                 "batching_small": batching,
+                "allreduce_and_halo": c4,
                 "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {

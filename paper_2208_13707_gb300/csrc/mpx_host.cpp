@@ -151,6 +151,7 @@ struct mpx_stream_s {
   unsigned flags;
   uint64_t next_seq;  // next sequence number to publish
   uint64_t wl_next;   // next waitlist index
+  uint64_t retired_seen;  // last value read of the engine's retirement word
   uint64_t owed;      // a batch wrote descriptors up to here without releasing the tail
                       // and ringing the doorbell (0 = none)
   int ncomms;         // communicators using this stream
@@ -910,7 +911,9 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
   if (__atomic_load_n(&w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
   const uint64_t seq = s->next_seq;
   const uint64_t slots = 1ull << w->slots_log2;
-  if (seq - __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE) > slots) {
+  // read the engine-written retirement word only when the cached one says full
+  if (seq - s->retired_seen > slots) s->retired_seen = __atomic_load_n(&c->retired, __ATOMIC_ACQUIRE);
+  if (seq - s->retired_seen > slots) {
     // the engine can only retire what it can see
     int rc = flush_owed(s);
     if (rc) return rc;

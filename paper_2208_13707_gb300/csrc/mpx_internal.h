@@ -1,6 +1,7 @@
 // Internal layout shared by the host runtime and the device engine of libmpx.
 // Nothing here is part of the public ABI (include/mpx.h).
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 namespace mpxi {
@@ -46,18 +47,24 @@ static_assert(sizeof(Desc) == 64, "descriptor is 64 bytes");
 // ---------------------------------------------------------------------------
 // host <-> engine control words (pinned host memory, one cache line each)
 // ---------------------------------------------------------------------------
+// Host-written and engine-written words sit on different 128-byte lines: the
+// host stores a tail per batch run while the engine polls it, and the engine
+// stores retirement while the host reads it; sharing a line would bounce it
+// across the chip-to-chip link on every access.
 struct alignas(128) StreamCtl {
   uint64_t tail;        // H->D  last published sequence number
   int32_t flags;        // H->D  bit0 active, bit1 exclusive  (tail, flags, rank: one 16-byte load)
   int32_t rank;         // H->D  world rank of the stream
   uint64_t wl_tail;     // H->D  waitlist entries published
+  int32_t pad0[26];
   uint64_t retired;     // D->H  every op with seq <= retired is finished
   uint64_t wl_retired;  // D->H  waitlist entries no longer read
   uint64_t done;        // D->H  mirror of the completion word
   int32_t error;        // D->H  first asynchronous error
-  int32_t pad[13];
+  int32_t pad1[25];
 };
-static_assert(sizeof(StreamCtl) == 128, "stream control line");
+static_assert(sizeof(StreamCtl) == 256, "stream control: two lines");
+static_assert(offsetof(StreamCtl, retired) == 128, "engine-written line");
 
 enum { SF_ACTIVE = 1, SF_EXCLUSIVE = 2 };
 enum { ENG_STOPPED = 0, ENG_RUNNING = 1, ENG_EXITING = 2 };
@@ -67,6 +74,7 @@ struct alignas(128) WorldCtl {
   int32_t stop;       // H->D exit when idle
   int32_t error;      // D->H first world error
   int32_t failed;     // D->H watchdog fired: operations are released without data
+  int32_t pad0[28];   // the engine updates the words below all the time
   uint64_t counters[8];
   uint64_t heartbeat;  // D->H globaltimer of the last engine tick
   // D->H phase times summed over launches (ns): start->first task,
@@ -77,6 +85,7 @@ struct alignas(128) WorldCtl {
   uint64_t tick_ns[8];
   int32_t pad[8];
 };
+static_assert(offsetof(WorldCtl, counters) == 128, "engine-updated words on their own lines");
 
 // ---------------------------------------------------------------------------
 // device-side state

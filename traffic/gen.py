@@ -229,13 +229,14 @@ def allreduce_suite(nranks: int = 16, sizes: Sequence[int] = (1024,),
 # ----------------------------------------------------------------------------
 # 3-D 7-point halo exchange on a periodic 2x2x2 decomposition
 # ----------------------------------------------------------------------------
-def halo3d(sub: int = 256, steps: int = 100, seed: int = SEED_BASE + 3) -> Program:
+def halo3d(sub: int = 256, steps: int = 100, seed: int = SEED_BASE + 3, init: bool = True) -> Program:
     """A (2*sub)^3 fp32 grid split into 8 subdomains of sub^3 ([z][y][x]), one
     rank and one stream each, periodic boundaries.  Per step each rank sends its
     6 boundary faces (x faces as vector(sub*sub, 1, sub), y faces as
     vector(sub, sub, sub*sub), z faces contiguous) to the neighbour across that
     face (tag = face id), receives 6 faces into 6 contiguous ghost buffers, and
-    waits for all 12 requests."""
+    waits for all 12 requests.  init=False leaves the subdomains zero (for
+    callers that fill them on the device)."""
     nr = 8
     b = ProgramBuilder(nr, "halo3d")
     gs = [b.stream(r) for r in range(nr)]
@@ -245,7 +246,8 @@ def halo3d(sub: int = 256, steps: int = 100, seed: int = SEED_BASE + 3) -> Progr
     ty = b.vector(sub, sub, plane, T_FLOAT)
     U, G = [], []
     for r in range(nr):
-        U.append(b.buffer(Rng(seed, 40, r).normal(sub ** 3).astype(np.float32)))
+        U.append(b.buffer(Rng(seed, 40, r).normal(sub ** 3).astype(np.float32) if init
+                          else 4 * sub ** 3))
         G.append([b.buffer(4 * plane) for _ in range(6)])
 
     def coords(r):

@@ -281,6 +281,10 @@ class BatchRunner:
                    for g in range(prog.nstreams)]
         self.comms = [mpx.mpx_stream_comm_create(self.world, [self.ms[int(g)] for g in prog.comm_stream[c]])
                       for c in range(prog.ncomms)]
+        self.tmap = np.array([t if t < 5 else mpx.mpx_type_vector(
+            int(prog.types[t]["vcount"]), int(prog.types[t]["blocklen"]),
+            int(prog.types[t]["stride"]), int(prog.types[t]["base"]))
+            for t in range(len(prog.types))], np.int32)
         self.epoch_barrier = epoch_barrier
         if epoch_barrier:
             assert self.mode != mpx.ENGINE_PLAIN
@@ -306,7 +310,6 @@ class BatchRunner:
         out = np.zeros(nops, mpx.op_dtype())
         kind = ops["kind"].astype(np.int64)
         lo = prog.stream_op_lo
-        assert (ops["type"] < 5).all(), "basic datatypes only"
         nb_idx, wait_idx = [], []
         for g in range(prog.nstreams):
             a, b = int(lo[g]), int(lo[g + 1])
@@ -323,7 +326,7 @@ class BatchRunner:
         k = kind[order]
         rec = out[: len(order)]
         rec["kind"] = np.where(k == ISEND, mpx.OP_ISEND, np.where(k == IRECV, mpx.OP_IRECV, mpx.OP_WAITALL))
-        rec["datatype"] = o["type"]
+        rec["datatype"] = self.tmap[o["type"]]
         rec["peer"] = o["peer"]
         rec["tag"] = o["tag"]
         bufp = np.where(o["buf"] >= 0, ptr[np.maximum(o["buf"], 0)] + o["off"].astype(np.uint64), 0)
@@ -439,3 +442,5 @@ class BatchRunner:
         mpx.mpx_world_free(self.world)
         for h in self.raw:
             mpx.mpx_cuda_stream_destroy(h)
+        for t in self.tmap[5:]:
+            mpx.mpx_type_free(int(t))
