@@ -591,6 +591,8 @@ def halo_bench(steps=100, warmup=5, sub=256):
         for _ in range(warmup):
             r.enqueue()
         assert r.finish()
+        r.mpx.mpx_world_stop(r.world, 10000)
+        ctr0 = r.mpx.mpx_world_get_counters(r.world)
         t0 = time.perf_counter()
         for _ in range(steps):
             r.enqueue()
@@ -598,12 +600,18 @@ def halo_bench(steps=100, warmup=5, sub=256):
         dt = time.perf_counter() - t0
         serr, werr = r.errors()
         assert ok and werr == 0 and not any(serr), "halo steps failed"
+        r.mpx.mpx_world_stop(r.world, 10000)
+        ctr = [a - b for a, b in zip(r.mpx.mpx_world_get_counters(r.world), ctr0)]
     finally:
         r.close()
     face_bytes = int(prog.meta["payload_bytes"])
     return {"grid": f"{2 * sub}^3 fp32, 8 subdomains", "steps": steps, "us_per_step": 1e6 * dt / steps,
             "messages_per_step": int(prog.meta["messages"]),
-            "face_gbs": 2 * face_bytes * steps / dt / 1e9, "timing": "wall clock, steps back to back"}
+            "face_gbs": 2 * face_bytes * steps / dt / 1e9, "timing": "wall clock, steps back to back",
+            "ticks_per_step": ctr[11] / steps, "rounds": int(ctr[6]),
+            "control_us_per_step_by_phase": {k: ctr[12 + i] / 1e3 / steps for i, k in enumerate(
+                ["ingest", "rounds", "finished_tasks", "completion", "scheduling", "decisions",
+                 "own_moves"])}}
 
 
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):

@@ -592,7 +592,100 @@ __device__ __forceinline__ V tree_sum(int nr, Load load, Add add) {
   return res;
 }
 
-__device__ void reduce_tile(const Task& T, uint32_t k) {
+// Bytes per rank of one bulk-reduction chunk: two stages of R input chunks
+// plus one result chunk each fit the pipeline's shared memory.
+__device__ __forceinline__ uint32_t bulk_reduce_chunk(int nr) {
+  const uint32_t c = (uint32_t)(kTmaStages * kTmaChunk) / (2u * (uint32_t)(nr + 1));
+  return c >= 4096 ? 4096 : (c & ~255u);
+}
+
+// Elements [v0, v1) of a tile (16-byte aligned buffers, v1 - v0 a multiple of
+// 16 bytes) reduced through shared memory: one thread bulk-loads the R input
+// chunks of a stage (one mbarrier per stage), every thread reduces 16-byte
+// columns across the R rows in shared memory into the stage's result chunk,
+// and one thread bulk-stores that chunk to all R outputs.  Two stages: the
+// loads of chunk j+1 and the stores of chunk j-1 are in flight while chunk j
+// is reduced.  Returns false (error recorded) if a load never landed.
+__device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* ptrs, int nr,
+                                 uint32_t dt, bool tree, int64_t boff0, int64_t nbytes,
+                                 const EngineParams& P) {
+  const uint32_t C = bulk_reduce_chunk(nr);
+  const uint32_t nch = (uint32_t)((nbytes + C - 1) / C);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t stage_bytes = (size_t)(nr + 1) * C;
+  auto cbytes = [&](uint32_t j) {
+    const int64_t rem = nbytes - (int64_t)j * C;
+    return (uint32_t)(rem < (int64_t)C ? rem : (int64_t)C);
+  };
+  auto issue_loads = [&](uint32_t j) {
+    const uint32_t s = j & 1u, b = cbytes(j);
+    uint8_t* in = buf + s * stage_bytes;
+    mbar_expect_tx(&sm.bar[s], b * (uint32_t)nr);
+    for (int r = 0; r < nr; ++r)
+      tma_load_1d(in + (size_t)r * C, (const void*)(ptrs[r] + boff0 + (int64_t)j * C), b, &sm.bar[s]);
+  };
+  uint32_t phase = sm.phase;
+  __syncthreads();  // every thread has read the phase bits before thread 0 moves on
+  if (tid == 0) {
+    issue_loads(0);
+    if (nch > 1) issue_loads(1);
+  }
+  bool ok = true;
+  for (uint32_t j = 0; j < nch; ++j) {
+    const uint32_t s = j & 1u, b = cbytes(j);
+    uint8_t* in = buf + s * stage_bytes;
+    uint8_t* res = in + (size_t)nr * C;
+    // the stores of chunk j-2 read this stage's result chunk
+    if (tid == 0 && j >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    const uint32_t par = (phase >> s) & 1u;
+    bool landed = mbar_try_wait(&sm.bar[s], par);
+    if (!landed) {
+      const uint64_t t0 = now_ns();
+      while (!(landed = mbar_try_wait(&sm.bar[s], par)) && now_ns() - t0 < 50000000ull) {
+      }
+    }
+    phase ^= (1u << s);
+    if (__syncthreads_or(!landed)) {
+      ok = false;
+      break;
+    }
+    const uint32_t ncol = b >> 4;
+    for (uint32_t v = tid; v < ncol; v += nt) {
+      uint4* col = reinterpret_cast<uint4*>(in) + v;
+      const size_t rs = C >> 4;  // row stride in uint4
+      uint4 acc;
+      if (tree) {
+        // pairwise by doubling strides, in place in this column
+        for (int st = 1; st < nr; st <<= 1)
+          for (int i = 0; i + st < nr; i += 2 * st)
+            col[(size_t)i * rs] = vadd(dt, col[(size_t)i * rs], col[(size_t)(i + st) * rs]);
+        acc = col[0];
+      } else {
+        acc = col[0];
+        for (int r = 1; r < nr; ++r) acc = vadd(dt, acc, col[(size_t)r * rs]);
+      }
+      reinterpret_cast<uint4*>(res)[v] = acc;
+    }
+    fence_proxy_async();  // result chunk written by this thread -> visible to the bulk stores
+    __syncthreads();
+    if (tid == 0) {
+      for (int r = 0; r < nr; ++r)
+        tma_store_1d((void*)(ptrs[nr + r] + boff0 + (int64_t)j * C), res, b);
+      tma_commit();
+      if (j + 2 < nch) issue_loads(j + 2);  // this stage's inputs were consumed above
+    }
+  }
+  if (tid == 0) {
+    tma_wait_all();
+    if (!ok) set_error(P, -1, kErrIntern);
+  }
+  if (tid == 0) sm.phase = phase;
+  __syncthreads();
+  return ok;
+}
+
+__device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
+                            const EngineParams& P) {
   const int64_t e0 = (int64_t)k * T.tile;
   const int64_t e1 = (e0 + T.tile) < T.bytes ? (e0 + T.tile) : T.bytes;
   if (e1 <= e0) return;
@@ -603,7 +696,13 @@ __device__ void reduce_tile(const Task& T, uint32_t k) {
   const bool tree = (T.mode == 1) && (dt == 3 || dt == 4);
   const int tid = threadIdx.x, nt = blockDim.x;
   int64_t vstart = e0, vend = e0;
-  if (T.unit == 16) {
+  if (T.unit == 16 && bulk_reduce_chunk(nr) >= 256) {
+    const int64_t per = 16 / es;
+    vend = e0 + ((e1 - e0) / per) * per;
+    if (vend > e0 && !reduce_span_bulk(sm, buf, ptrs, nr, dt, tree, e0 * es, (vend - e0) * es, P))
+      return;
+    vstart = vend;
+  } else if (T.unit == 16) {
     const int64_t per = 16 / es;
     vend = e0 + ((e1 - e0) / per) * per;
     const int64_t nv = (vend - e0) / per;
@@ -698,7 +797,7 @@ __device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
 __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
   const Task& T = sm.task;
   if (T.type == T_COPY) copy_tile(sm, buf, T, sm.claim_tile, P);
-  else if (T.type == T_REDUCE) reduce_tile(T, sm.claim_tile);
+  else if (T.type == T_REDUCE) reduce_tile(sm, buf, T, sm.claim_tile, P);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1630,8 +1729,12 @@ struct Ctl {
       T->type = T_REDUCE;
       T->action = A_REDUCE;
       T->bytes = n;
-      int64_t tile = P.tile_bytes / (es * (P.nranks < 8 ? 1 : P.nranks / 8));
-      tile = tile < 256 ? 256 : (tile & ~(int64_t)15);
+      // about four tiles per engine CTA, within [tile_bytes*8/R, 256 KiB] per rank
+      const int64_t tmin = P.tile_bytes / (es * (P.nranks < 8 ? 1 : P.nranks / 8));
+      const int64_t tmax = ((int64_t)256 << 10) / es;
+      int64_t tile = n / (4 * (int64_t)(P.nctas > 0 ? P.nctas : 1));
+      tile = tile < tmin ? tmin : (tile > tmax ? tmax : tile);
+      tile = tile < 256 ? 256 : (tile & ~(int64_t)255);
       T->tile = tile;
       T->ntiles = (uint32_t)((n + tile - 1) / tile);
       T->nr = (uint32_t)P.nranks;
