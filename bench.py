@@ -486,7 +486,7 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
     out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
                      "ms_per_step": 1e3 * dt / steps, "host_enqueue_ms_per_step": 1e3 * t_enq / steps,
                      "payload_gbs": 2 * payload * steps / dt / 1e9,
-                     "rounds": int(ctr[6]), "ticks": int(ctr[1]),
+                     "rounds": int(ctr[6]), "ticks": int(ctr[1]), "staged_sends": int(ctr[5]),
                      "control_ms_by_phase": {k: ctr[12 + i] / 1e6 for i, k in enumerate(
                          ["ingest", "rounds", "finished_tasks", "completion", "scheduling",
                           "decisions", "own_moves"])}}
@@ -608,7 +608,7 @@ def halo_bench(steps=100, warmup=5, sub=256):
     return {"grid": f"{2 * sub}^3 fp32, 8 subdomains", "steps": steps, "us_per_step": 1e6 * dt / steps,
             "messages_per_step": int(prog.meta["messages"]),
             "face_gbs": 2 * face_bytes * steps / dt / 1e9, "timing": "wall clock, steps back to back",
-            "ticks_per_step": ctr[11] / steps, "rounds": int(ctr[6]),
+            "ticks_per_step": ctr[11] / steps, "rounds": int(ctr[6]), "staged_sends": int(ctr[5]),
             "control_us_per_step_by_phase": {k: ctr[12 + i] / 1e3 / steps for i, k in enumerate(
                 ["ingest", "rounds", "finished_tasks", "completion", "scheduling", "decisions",
                  "own_moves"])}}

@@ -45,7 +45,8 @@ constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
 constexpr int kSmemStreams = 128;
 constexpr int kMaxCtaThreads = 512;  // engine block size bound (launch bounds)
-constexpr int kSortMinPosts = 128;   // rounds with more posts match from domain-sorted lists  // worlds up to this many streams keep per-stream state in shared memory
+constexpr int kSortMinPosts = 128;
+constexpr uint64_t kCqDone = ~0ull;  // completion-queue entry already processed   // rounds with more posts match from domain-sorted lists  // worlds up to this many streams keep per-stream state in shared memory
 
 // ------------------------------------------------------------------------
 // memory-model helpers
@@ -220,6 +221,9 @@ struct CtaShared {
   int32_t left;           // control: some stream still has ingested operations ahead of its cursor
   int32_t nposts_round;   // control: posts of the current round
   uint64_t t_retire, t_alloc;
+  uint64_t t_base;        // control: task_alloc at the start of the scheduling phase
+  uint32_t t_avail;       // control: free task slots then
+  uint32_t t_used;        // control: task ids handed out in this phase
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
@@ -801,7 +805,12 @@ __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) 
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(&P.tasks[(uint64_t)sm.claim_task].tiles_done, 1u);
+    const uint32_t done = atomicAdd(&P.tasks[(uint64_t)sm.claim_task].tiles_done, 1u) + 1u;
+    if (done == T.ntiles) {  // the task's last tile: hand the task to the control CTA
+      __threadfence();
+      const uint64_t pos = atomicAdd((unsigned long long*)&P.sh->cq_tail, 1ull);
+      st_rel_gpu(&P.cq[pos & ((1ull << P.tq_log2) - 1)], (uint64_t)sm.claim_task + 1);
+    }
   }
 }
 
@@ -1281,25 +1290,32 @@ struct Ctl {
   }
 
   // --- task creation ---
-  // Allocate a task id; fails when the ring is full.  task_retire only moves
-  // in a phase of its own, so a CAS on task_alloc suffices.
-  __device__ Task* task_new(uint64_t& id) {
+  // Tasks are created only in the scheduling phase.  Its first thread takes
+  // the ring's free space once (task_retire moves only in a phase of its own);
+  // creators then draw ids from a shared-memory counter, and the phase ends by
+  // advancing task_alloc over the ids handed out.  Every id handed out is
+  // published before that.
+  __device__ void task_phase_begin() {
     Shared* sh = P.sh;
     const uint64_t cap = 1ull << P.tq_log2;
+    const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
     const uint64_t r = *(volatile uint64_t*)&sh->task_retire;
-    uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
-    for (;;) {
-      if (a - r >= cap) {
-        sm.ntask_full = 1;
-        return nullptr;
-      }
-      const uint64_t old = atomicCAS((unsigned long long*)&sh->task_alloc, (unsigned long long)a,
-                                     (unsigned long long)(a + 1));
-      if (old == a) break;
-      a = old;
+    sm.t_base = a;
+    sm.t_avail = (uint32_t)(cap - (a - r));
+    sm.t_used = 0;
+  }
+  __device__ void task_phase_end() {
+    const uint32_t n = sm.t_used < sm.t_avail ? sm.t_used : sm.t_avail;
+    if (n) st_rel_gpu(&P.sh->task_alloc, sm.t_base + n);
+  }
+  __device__ Task* task_new(uint64_t& id) {
+    const uint32_t idx = atomicAdd(&sm.t_used, 1u);
+    if (idx >= sm.t_avail) {
+      sm.ntask_full = 1;
+      return nullptr;
     }
-    id = a;
-    return &P.tasks[id & (cap - 1)];
+    id = sm.t_base + idx;
+    return &P.tasks[id & ((1ull << P.tq_log2) - 1)];
   }
   // The claim word carries id+1 in its high half, so a zeroed or recycled
   // slot never looks published for this id.
@@ -1622,8 +1638,16 @@ struct Ctl {
         const int32_t f = o->pflags;
         if (!(f & (PF_SCHED | PF_COMPLETE))) {
           settled = false;
+          // a matched send whose receive has been reached is delivered by the
+          // receive's stream in this phase: staging it would only copy twice
+          bool partner_reached = false;
+          if (f & PF_MATCHED) {
+            const uint64_t rref = o->partner;
+            partner_reached = *(volatile uint64_t*)&ss[ref_stream(rref)].reached >= ref_seq(rref);
+          }
           // stage when the stream sits at a blocking op at or after this send
-          if (S.stall_t0 != 0 && now - S.stall_t0 >= P.stage_delay_ns && seq <= S.pc) {
+          if (!partner_reached && S.stall_t0 != 0 && now - S.stall_t0 >= P.stage_delay_ns &&
+              seq <= S.pc) {
             const int32_t old = atomicOr(&o->pflags, PF_SCHED);
             if (!(old & PF_SCHED)) {
               const int slot = atomicAdd(&sm.nstage, 1);
@@ -1753,14 +1777,20 @@ struct Ctl {
     }
   }
 
-  // --- 4. finished tasks (thread per task in flight) ---
-  __device__ void complete_tasks(uint64_t r0, uint64_t a) {
+  // --- 4. finished tasks (thread per completion-queue entry) ---
+  // Entries [h, t) were appended by the CTAs that finished those tasks; an
+  // entry still 0 is being written (its tail increment came first) and is
+  // left for the next tick.  Processed entries become kCqDone; the head then
+  // moves over them.
+  __device__ void complete_tasks(uint64_t h, uint64_t t) {
     const uint64_t mask = (1ull << P.tq_log2) - 1;
-    for (uint64_t id = r0 + threadIdx.x; id < a; id += blockDim.x) {
-      Task* T = &P.tasks[id & mask];
-      if (T->type == 0) continue;  // already processed
-      if (claim_idp(ld_acq_gpu(&T->claim)) != id_tag(id)) continue;
-      if (ld_acq_gpu32(&T->tiles_done) < T->ntiles) continue;
+    unsigned long long n_msg = 0, n_bytes = 0, n_tasks = 0;  // counters, added once per thread
+    for (uint64_t pos = h + threadIdx.x; pos < t; pos += blockDim.x) {
+      uint64_t* e = &P.cq[pos & mask];
+      const uint64_t v = ld_acq_gpu(e);
+      if (v == 0 || v == kCqDone) continue;
+      *e = kCqDone;
+      Task* T = &P.tasks[v - 1];
       if (T->type == T_COPY) {
         DOp* s = op_ref(P, T->ref_s);
         if (T->action == A_STAGE) {
@@ -1771,9 +1801,9 @@ struct Ctl {
           if (T->action == A_DELIVER_STAGED) stage_free(s);
           atomicOr(&r->pflags, PF_DELIVERED | PF_COMPLETE);
           atomicOr(&s->pflags, PF_DELIVERED | PF_COMPLETE);
-          atomicAdd((unsigned long long*)&P.wctl->counters[2], 1ull);
+          ++n_msg;
         }
-        atomicAdd((unsigned long long*)&P.wctl->counters[3], (unsigned long long)T->bytes);
+        n_bytes += (unsigned long long)T->bytes;
       } else if (T->type == T_REDUCE) {
         InstSlot* s = &P.inst[T->ref_s];
         const uint64_t* refs = P.inst_refs + (size_t)T->ref_s * P.nranks;
@@ -1784,12 +1814,16 @@ struct Ctl {
         __threadfence();
         atomicExch((unsigned long long*)&s->k1, 0ull);
         sm.dirty = 1;  // a stream may wait for this instance slot
-        atomicAdd((unsigned long long*)&P.wctl->counters[3],
-                  (unsigned long long)(T->bytes * base_size(T->dtype) * P.nranks));
+        n_bytes += (unsigned long long)(T->bytes * base_size(T->dtype) * P.nranks);
       }
-      atomicAdd((unsigned long long*)&P.wctl->counters[4], 1ull);
+      ++n_tasks;
       T->type = 0;
       sm.any = 1;
+    }
+    if (n_tasks) {
+      if (n_msg) atomicAdd((unsigned long long*)&P.wctl->counters[2], n_msg);
+      atomicAdd((unsigned long long*)&P.wctl->counters[3], n_bytes);
+      atomicAdd((unsigned long long*)&P.wctl->counters[4], n_tasks);
     }
   }
 };
@@ -1831,6 +1865,11 @@ __device__ void abandon_tasks(const EngineParams& P) {
   const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
   st_rel_gpu(&sh->task_head, a);
   sh->task_retire = a;
+  // forget queued completions of the abandoned tasks
+  const uint64_t mask = (1ull << P.tq_log2) - 1;
+  const uint64_t t = ld_acq_gpu(&sh->cq_tail);
+  for (uint64_t h = sh->cq_head; h < t; ++h) P.cq[h & mask] = 0;
+  sh->cq_head = t;
 }
 
 __device__ void grid_barrier(const EngineParams& P, int nctas) {
@@ -1990,15 +2029,18 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     if (!sm.failed) {
       // 3. finished tasks, then per-stream completion and retirement
       if (tid == 0) {
-        sm.t_retire = sh->task_retire;
-        sm.t_alloc = *(volatile uint64_t*)&sh->task_alloc;
+        sm.t_retire = sh->cq_head;
+        sm.t_alloc = ld_acq_gpu(&sh->cq_tail);
       }
       __syncthreads();
-      const uint64_t t_r0 = sm.t_retire, t_a = sm.t_alloc;
-      if (t_r0 != t_a) C.complete_tasks(t_r0, t_a);
+      const uint64_t cq_h = sm.t_retire, cq_t = sm.t_alloc;
+      if (cq_h != cq_t) C.complete_tasks(cq_h, cq_t);
       __syncthreads();
       if (tid == 0) {
         const uint64_t mask = (1ull << P.tq_log2) - 1;
+        uint64_t h = cq_h;
+        while (h < cq_t && P.cq[h & mask] == kCqDone) P.cq[h++ & mask] = 0;
+        sh->cq_head = h;
         uint64_t r0 = sh->task_retire;
         const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
         // a slot is reused only after the movers' head has passed its task
@@ -2023,11 +2065,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if (pend) atomicOr(&sm.pending, 1);
       __syncthreads();
       lap(3);
+      if (tid == 0) C.task_phase_begin();
+      __syncthreads();
       for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
       __syncthreads();
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
       __syncthreads();
+      if (tid == 0) C.task_phase_end();
       lap(4);
     }
     // 4. bookkeeping and exit decisions (thread 0)

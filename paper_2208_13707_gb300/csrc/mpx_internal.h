@@ -212,7 +212,13 @@ struct alignas(128) Shared {
   // staging ring allocator (control-owned)
   uint64_t st_head, st_tail;     // arena byte offsets (monotone)
   uint64_t sr_head, sr_tail;     // StageRec ring indices
-  uint64_t pad2[8];
+  uint64_t pad2[6];
+  // completion queue: the CTA that finishes a task's last tile appends the
+  // task's slot (movers: cq_tail); the control CTA consumes (cq_head)
+  uint64_t cq_head;
+  uint64_t pad3[15];
+  uint64_t cq_tail;
+  uint64_t pad4[15];
   // grid barrier for the control group
   uint32_t bar_count, bar_gen;
 };
@@ -230,6 +236,7 @@ struct EngineParams {
   const Desc* rings;          // [max_streams << slots_log2]   pinned
   const int64_t* waitlists;   // [max_streams << wl_log2]      pinned
   int64_t* wl_dev;            // [max_streams << wl_log2]      device copy of waitall lists
+  uint64_t* cq;               // [1 << tq_log2] completion queue entries (slot + 1; 0 empty)
   int32_t* cnt2;              // [max_streams * ndomains] posts per (stream, domain), or null
   int32_t* dtot;              // [ndomains] posts per domain this round
   int64_t* dbase;             // [ndomains] start of each domain's list
