@@ -224,6 +224,8 @@ struct CtaShared {
   uint64_t t_base;        // control: task_alloc at the start of the scheduling phase
   uint32_t t_avail;       // control: free task slots then
   uint32_t t_used;        // control: task ids handed out in this phase
+  int64_t last_prog;      // control: time of the last tick that changed anything
+  uint64_t scan_a, scan_b;  // control: parallel first-failure scans
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
@@ -798,6 +800,12 @@ __device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
   return sm.claim_task >= 0;
 }
 
+// The completion queue holds twice the task ring: every allocated task
+// appends one entry, and allocation keeps task_alloc - cq_head below it.
+__device__ __forceinline__ uint64_t cq_mask(const EngineParams& P) {
+  return (2ull << P.tq_log2) - 1;
+}
+
 __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
   const Task& T = sm.task;
   if (T.type == T_COPY) copy_tile(sm, buf, T, sm.claim_tile, P);
@@ -809,7 +817,7 @@ __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) 
     if (done == T.ntiles) {  // the task's last tile: hand the task to the control CTA
       __threadfence();
       const uint64_t pos = atomicAdd((unsigned long long*)&P.sh->cq_tail, 1ull);
-      st_rel_gpu(&P.cq[pos & ((1ull << P.tq_log2) - 1)], (uint64_t)sm.claim_task + 1);
+      st_rel_gpu(&P.cq[pos & cq_mask(P)], (uint64_t)sm.claim_task + 1);
     }
   }
 }
@@ -1301,7 +1309,9 @@ struct Ctl {
     const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
     const uint64_t r = *(volatile uint64_t*)&sh->task_retire;
     sm.t_base = a;
-    sm.t_avail = (uint32_t)(cap - (a - r));
+    const uint64_t free_tasks = cap - (a - r);
+    const uint64_t free_cq = 2 * cap - (a - *(volatile uint64_t*)&sh->cq_head);
+    sm.t_avail = (uint32_t)(free_tasks < free_cq ? free_tasks : free_cq);
     sm.t_used = 0;
   }
   __device__ void task_phase_end() {
@@ -1645,9 +1655,14 @@ struct Ctl {
             const uint64_t rref = o->partner;
             partner_reached = *(volatile uint64_t*)&ss[ref_stream(rref)].reached >= ref_seq(rref);
           }
-          // stage when the stream sits at a blocking op at or after this send
-          if (!partner_reached && S.stall_t0 != 0 && now - S.stall_t0 >= P.stage_delay_ns &&
-              seq <= S.pc) {
+          // stage when the stream sits at a blocking op at or after this send,
+          // and either the engine as a whole has stopped progressing (the
+          // stall may be a cycle only staging breaks) or the stall has lasted
+          // fifty delays (a bound while other traffic keeps the engine busy)
+          const int64_t stalled = now - S.stall_t0;
+          const bool quiet = now - sm.last_prog >= P.stage_delay_ns;
+          if (!partner_reached && S.stall_t0 != 0 && stalled >= P.stage_delay_ns &&
+              (quiet || stalled >= 50 * P.stage_delay_ns) && seq <= S.pc) {
             const int32_t old = atomicOr(&o->pflags, PF_SCHED);
             if (!(old & PF_SCHED)) {
               const int slot = atomicAdd(&sm.nstage, 1);
@@ -1783,7 +1798,7 @@ struct Ctl {
   // left for the next tick.  Processed entries become kCqDone; the head then
   // moves over them.
   __device__ void complete_tasks(uint64_t h, uint64_t t) {
-    const uint64_t mask = (1ull << P.tq_log2) - 1;
+    const uint64_t mask = cq_mask(P);
     unsigned long long n_msg = 0, n_bytes = 0, n_tasks = 0;  // counters, added once per thread
     for (uint64_t pos = h + threadIdx.x; pos < t; pos += blockDim.x) {
       uint64_t* e = &P.cq[pos & mask];
@@ -1866,7 +1881,7 @@ __device__ void abandon_tasks(const EngineParams& P) {
   st_rel_gpu(&sh->task_head, a);
   sh->task_retire = a;
   // forget queued completions of the abandoned tasks
-  const uint64_t mask = (1ull << P.tq_log2) - 1;
+  const uint64_t mask = cq_mask(P);
   const uint64_t t = ld_acq_gpu(&sh->cq_tail);
   for (uint64_t h = sh->cq_head; h < t; ++h) P.cq[h & mask] = 0;
   sh->cq_head = t;
@@ -1922,6 +1937,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   C.round = (int64_t)*(volatile uint64_t*)&sh->round;
   int64_t last_prog = (int64_t)now_ns();
   int64_t idle_since = last_prog;
+  if (tid == 0) sm.last_prog = last_prog;
   uint64_t ticks = 0;
   // phase timing (thread 0): first task seen, last time tasks drained
   const int64_t t_launch = last_prog;
@@ -2035,21 +2051,43 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       __syncthreads();
       const uint64_t cq_h = sm.t_retire, cq_t = sm.t_alloc;
       if (cq_h != cq_t) C.complete_tasks(cq_h, cq_t);
-      __syncthreads();
       if (tid == 0) {
-        const uint64_t mask = (1ull << P.tq_log2) - 1;
-        uint64_t h = cq_h;
-        while (h < cq_t && P.cq[h & mask] == kCqDone) P.cq[h++ & mask] = 0;
-        sh->cq_head = h;
-        uint64_t r0 = sh->task_retire;
+        sm.scan_a = cq_t;
+        const uint64_t r0 = sh->task_retire;
         const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
         // a slot is reused only after the movers' head has passed its task
         const uint64_t head = ld_acq_gpu(&sh->task_head);
-        while (r0 < a && r0 < head && P.tasks[r0 & mask].type == 0 &&
-               claim_idp(P.tasks[r0 & mask].claim) == id_tag(r0))
-          ++r0;
-        sh->task_retire = r0;
-        C.stage_reclaim();
+        uint64_t lim = a < head ? a : head;
+        if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
+        sm.t_retire = r0;
+        sm.scan_b = lim;
+      }
+      __syncthreads();
+      {
+        // parallel: the completion-queue head moves over processed entries,
+        // task_retire over processed tasks (a window of 8 per thread a tick)
+        const uint64_t mask = (1ull << P.tq_log2) - 1, qmask = cq_mask(P);
+        for (uint64_t pos = cq_h + tid; pos < cq_t; pos += blockDim.x)
+          if (P.cq[pos & qmask] != kCqDone) {
+            atomicMin((unsigned long long*)&sm.scan_a, (unsigned long long)pos);
+            break;
+          }
+        const uint64_t r0 = sm.t_retire, lim = sm.scan_b;
+        for (uint64_t id = r0 + tid; id < lim; id += blockDim.x) {
+          const Task& T = P.tasks[id & mask];
+          if (T.type != 0 || claim_idp(T.claim) != id_tag(id)) {
+            atomicMin((unsigned long long*)&sm.scan_b, (unsigned long long)id);
+            break;
+          }
+        }
+        __syncthreads();
+        const uint64_t newh = sm.scan_a;
+        for (uint64_t pos = cq_h + tid; pos < newh; pos += blockDim.x) P.cq[pos & qmask] = 0;
+        if (tid == 0) {
+          sh->cq_head = newh;
+          sh->task_retire = sm.scan_b;
+          C.stage_reclaim();
+        }
       }
       __syncthreads();
       lap(2);
@@ -2080,6 +2118,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       int decision = 0;  // 0 continue, 1 exit
       const bool any = sm.any != 0;
       if (any) last_prog = now;
+      sm.last_prog = last_prog;
       const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
       const uint64_t rt = sh->task_retire;
       const bool tasks_live = rt != a;

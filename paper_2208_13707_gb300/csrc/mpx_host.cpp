@@ -355,7 +355,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_uq = carve((ndom << w->qcap_log2) * sizeof(QEntry));
   const size_t o_pqh = carve(ndom * sizeof(QHead)), o_uqh = carve(ndom * sizeof(QHead));
   const size_t o_tasks = carve(((size_t)1 << w->tq_log2) * sizeof(Task));
-  const size_t o_cq = carve(((size_t)1 << w->tq_log2) * sizeof(uint64_t));
+  const size_t o_cq = carve(((size_t)2 << w->tq_log2) * sizeof(uint64_t));
   const size_t o_sh = carve(sizeof(Shared));
   const size_t o_srec = carve(((size_t)1 << w->sr_log2) * sizeof(StageRec));
   const size_t o_inst = carve(iwn * sizeof(InstSlot));

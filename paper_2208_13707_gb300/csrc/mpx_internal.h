@@ -236,7 +236,7 @@ struct EngineParams {
   const Desc* rings;          // [max_streams << slots_log2]   pinned
   const int64_t* waitlists;   // [max_streams << wl_log2]      pinned
   int64_t* wl_dev;            // [max_streams << wl_log2]      device copy of waitall lists
-  uint64_t* cq;               // [1 << tq_log2] completion queue entries (slot + 1; 0 empty)
+  uint64_t* cq;               // [2 << tq_log2] completion queue entries (slot + 1; 0 empty)
   int32_t* cnt2;              // [max_streams * ndomains] posts per (stream, domain), or null
   int32_t* dtot;              // [ndomains] posts per domain this round
   int64_t* dbase;             // [ndomains] start of each domain's list
