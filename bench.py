@@ -490,6 +490,26 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
                      "control_ms_by_phase": {k: ctr[12 + i] / 1e6 for i, k in enumerate(
                          ["ingest", "rounds", "finished_tasks", "completion", "scheduling",
                           "decisions", "own_moves"])}}
+    # the same step recorded once and replayed as a CUDA graph
+    gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120,
+                         cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+    try:
+        for _ in range(warmup):
+            gr.enqueue()
+        assert gr.finish(), "graph warm-up did not finish"
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            gr.enqueue()
+        t_enq = time.perf_counter() - t0
+        ok = gr.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = gr.errors()
+        assert ok and werr == 0 and not any(serr), "graph steps failed"
+    finally:
+        gr.close()
+    out["graph"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
+                    "ms_per_step": 1e3 * dt / steps, "host_launch_ms_per_step": 1e3 * t_enq / steps,
+                    "payload_gbs": 2 * payload * steps / dt / 1e9}
     q = gpu.BatchRunner(prog, mode="plain", timeout_s=300)
     try:
         q.step()
@@ -503,6 +523,7 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
     out["plain"] = {"value": nmsg * plain_steps / dt, "unit": "msgs/s", "steps": plain_steps,
                     "ms_per_step": 1e3 * dt / plain_steps}
     out["speedup_vs_plain"] = out["engine"]["value"] / out["plain"]["value"]
+    out["graph_speedup_vs_plain"] = out["graph"]["value"] / out["plain"]["value"]
     return out
 
 

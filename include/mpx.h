@@ -64,6 +64,7 @@ typedef struct CUstream_st* mpx_cuda_stream_t;
 typedef struct mpx_world_s* mpx_world_t;   /* R virtual ranks on this GPU (stands in for MPI_COMM_WORLD) */
 typedef struct mpx_stream_s* mpx_stream_t; /* MPIX_Stream */
 typedef struct mpx_comm_s* mpx_comm_t;     /* one rank's handle of a stream communicator */
+typedef struct mpx_step_s* mpx_step_t;     /* a recorded step replayed as one CUDA graph */
 typedef int64_t mpx_request_t;             /* opaque: (world << 56) | (stream << 40) | seq; MPX_REQUEST_NULL = -1 */
 typedef int32_t mpx_datatype_t;
 
@@ -335,6 +336,38 @@ typedef struct {
  * doorbells still owed when the batch stops are written before it returns.
  * The host cost per operation is that of filling one descriptor. */
 int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done);
+
+/* Recorded steps: the CUDA-graph form of batch submission, for a step that
+ * repeats (the same operations on the same buffers every iteration, like
+ * MPI persistent requests started together).  mpx_step_create validates
+ * ops[0..n) as mpx_enqueue_batch would and records them instead of
+ * enqueueing them; it then captures one CUDA graph with two nodes: a kernel
+ * that publishes the step's descriptors and waitall lists into the streams'
+ * submission rings from device memory (sequence numbers continue from the
+ * streams' own), and one engine pass that matches, moves and completes
+ * everything the step published.  mpx_step_launch replays that graph on
+ * `stream`: the host cost of a step is one cudaGraphLaunch, whatever its
+ * number of messages, and work enqueued on `stream` after the launch sees
+ * the step complete.
+ * Requirements: the world is in MPX_ENGINE_DRAIN mode (the graph carries its
+ * engine pass); every stream of the step is MPX_STREAM_EXCLUSIVE
+ * (MPX_ERR_STREAM otherwise; nothing else orders it); wait and waitall
+ * operations name request slots that isend/irecv operations of the same step
+ * write (MPX_ERR_REQUEST otherwise); a stream's part of a step fits its ring.
+ * While the step exists its streams accept no other enqueue calls
+ * (MPX_ERR_STATE) and belong to no other step.  Launches of one step, and
+ * engine passes of its world, must not overlap: launch them on one stream.
+ * Request values written during creation are placeholders: the step's waits
+ * consume them internally.  Errors: those of the single calls, MPX_ERR_STATE
+ * (world not in DRAIN mode), MPX_ERR_NO_MEM, MPX_ERR_CUDA (capture failed). */
+int mpx_step_create(mpx_world_t world, int n, const mpx_op_t ops[], mpx_step_t* step);
+int mpx_step_launch(mpx_step_t step, mpx_cuda_stream_t stream);
+/* First error of the step's publication kernel (MPX_ERR_NO_MEM when a launch
+ * found a ring still holding an earlier step's operations); synchronous. */
+int mpx_step_get_error(mpx_step_t step, int* first_error);
+/* Free the step and return its streams to host enqueue.  Every launch of the
+ * step must have completed (synchronize the launch stream first). */
+int mpx_step_free(mpx_step_t* step);
 
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);

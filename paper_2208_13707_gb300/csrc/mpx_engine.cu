@@ -1565,7 +1565,8 @@ struct Ctl {
       newdone = pc;
       ++pc;
     }
-    if (pc != S.pc) prog = true;
+    const bool advanced = pc != S.pc;
+    if (advanced) prog = true;
     S.pc = pc;
     if (newdone != S.done) {
       S.done = newdone;
@@ -1588,7 +1589,8 @@ struct Ctl {
     // stall clock: the stream sits at blocking op pc
     const bool stalled = pc <= S.ingested && S.reached >= pc;
     if (stalled) {
-      if (S.stall_t0 == 0) S.stall_t0 = now;
+      // a stream that moved on to its next blocking op starts a new stall
+      if (S.stall_t0 == 0 || advanced) S.stall_t0 = now;
     } else {
       S.stall_t0 = 0;
     }
@@ -2293,15 +2295,19 @@ extern "C" int mpxi_engine_launch(const mpxi::EngineParams* p, int nctas, int nt
     attr_set = true;
   }
   mpxi::EngineParams params = *p;
-  void* args[] = {&params};
-  cudaError_t e;
-  if (cooperative)
-    e = cudaLaunchCooperativeKernel((const void*)mpxi::engine_kernel, dim3(nctas), dim3(nthreads),
-                                    args, (size_t)smem, (cudaStream_t)cuda_stream);
-  else
-    e = cudaLaunchKernel((const void*)mpxi::engine_kernel, dim3(nctas), dim3(nthreads), args,
-                         (size_t)smem, (cudaStream_t)cuda_stream);
-  return (int)e;
+  // cooperative: every CTA resident at once (the engine's CTAs wait on each
+  // other); expressed as a launch attribute so that stream capture records it
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(nthreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = (cudaStream_t)cuda_stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = cooperative ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, mpxi::engine_kernel, params);
 }
 
 // Load the engine's module now: a module loaded lazily at its first launch

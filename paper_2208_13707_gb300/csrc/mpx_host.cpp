@@ -27,6 +27,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/mpx.h"
@@ -38,6 +39,11 @@ using namespace mpxi;
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads);
 extern "C" int mpxi_engine_preload(void);
 extern "C" int mpxi_saxpy_preload(void);
+extern "C" int mpxi_step_preload(void);
+extern "C" int mpxi_step_post_launch(const mpxi::EngineParams* P, const void* tmpl,
+                                     const void* tmpl_wl, const void* streams, int nstreams,
+                                     uint64_t* cnt_seq, uint64_t* cnt_wl, int32_t* err,
+                                     void* cuda_stream);
 
 // A cuStreamWaitValue64 that is not yet satisfied stalls the hardware queue
 // its CUDA stream is mapped to, and every other stream sharing that queue.
@@ -152,6 +158,7 @@ struct mpx_stream_s {
   uint64_t next_seq;  // next sequence number to publish
   uint64_t wl_next;   // next waitlist index
   uint64_t retired_seen;  // last value read of the engine's retirement word
+  mpx_step_s* step;   // recorded step that owns the stream's sequence numbers, or null
   uint64_t owed;      // a batch wrote descriptors up to here without releasing the tail
                       // and ringing the doorbell (0 = none)
   int ncomms;         // communicators using this stream
@@ -302,7 +309,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   if (cfg.engine_mode != MPX_ENGINE_PLAIN && !memops_ready()) { world_release(w); return MPX_ERR_CUDA; }
   // load every kernel of the library before any engine runs (lazy loading of
   // a module can wait for running kernels, and a resident engine is one)
-  if (mpxi_engine_preload() || mpxi_saxpy_preload()) { world_release(w); return MPX_ERR_CUDA; }
+  if (mpxi_engine_preload() || mpxi_saxpy_preload() || mpxi_step_preload()) { world_release(w); return MPX_ERR_CUDA; }
   MPX_TRACE("world_create: memops and kernels loaded");
   const int S = cfg.max_streams;
   w->slots_log2 = log2i(cfg.ring_slots);
@@ -452,14 +459,14 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   return MPX_SUCCESS;
 }
 
-static int launch_engine(mpx_world_s* w, cudaStream_t s, int mode) {
+static int launch_engine(mpx_world_s* w, cudaStream_t s, int mode, bool limits = true) {
   EngineParams P = w->params;
   P.mode = mode;
   P.nlimit = 0;
   if (mode == 1) {
     P.idle_ns = std::min<int64_t>(w->cfg.idle_exit_ns, 200000);
     // a pass drains what was published before it was enqueued
-    if (w->cfg.max_streams <= kMaxDrainLimits) {
+    if (limits && w->cfg.max_streams <= kMaxDrainLimits) {
       P.nlimit = w->cfg.max_streams;
       for (int g = 0; g < P.nlimit; ++g) P.limit[g] = __atomic_load_n(&w->sctl[g].tail, __ATOMIC_ACQUIRE);
     }
@@ -693,6 +700,7 @@ extern "C" int mpx_stream_free(mpx_stream_t* ps) {
   mpx_stream_s* s = *ps;
   mpx_world_s* w = s->w;
   std::lock_guard<std::mutex> g(w->mu);
+  if (s->step) return MPX_ERR_STATE;  // free the recorded step first
   if (s->ncomms > 0) return MPX_ERR_PENDING;
   if (stream_pending(s) != 0) return MPX_ERR_PENDING;
   if (w->plain) plain::stream_free(w->plain, s->id);
@@ -911,6 +919,7 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
   mpx_world_s* w = s->w;
   StreamCtl* c = &w->sctl[s->id];
   if (__atomic_load_n(&w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
+  if (s->step) return MPX_ERR_STATE;  // a recorded step publishes on this stream
   const uint64_t seq = s->next_seq;
   const uint64_t slots = 1ull << w->slots_log2;
   // read the engine-written retirement word only when the cached one says full
@@ -1197,4 +1206,224 @@ extern "C" int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done) {
   }
   if (done) *done = i;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// recorded steps: one CUDA graph per step (device-side publication, then one
+// engine pass)
+// ---------------------------------------------------------------------------
+struct mpx_step_s {
+  mpx_world_s* w;
+  std::vector<mpx_stream_s*> streams;  // streams the step publishes on
+  uint8_t* dmem;                       // templates, per-stream records, counters, error word
+  uint64_t* cnt_seq;                   // [max_streams] device: last published sequence number
+  uint64_t* cnt_wl;                    // [max_streams] device: next waitlist index
+  int32_t* err;                        // device: first publication error
+  cudaStream_t cap;                    // stream the graph was captured on
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+static void step_release(mpx_step_s* st) {
+  if (!st) return;
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->graph) cudaGraphDestroy(st->graph);
+  if (st->cap) cudaStreamDestroy(st->cap);
+  if (st->dmem) cudaFree(st->dmem);
+  delete st;
+}
+
+extern "C" int mpx_step_create(mpx_world_t w, int n, const mpx_op_t ops[], mpx_step_t* out) {
+  if (!w || !out || n < 0 || (n > 0 && !ops)) return MPX_ERR_ARG;
+  if (w->cfg.engine_mode != MPX_ENGINE_DRAIN) return MPX_ERR_STATE;
+  const int S = w->cfg.max_streams;
+  // 1. per stream, its operations in order; a request slot -> (stream, relative seq)
+  std::vector<std::vector<int>> per(S);
+  std::unordered_map<const mpx_request_t*, std::pair<int, int64_t>> reqmap;
+  std::vector<mpx_stream_s*> sof(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    const mpx_op_t& o = ops[i];
+    mpx_stream_s* st = nullptr;
+    switch (o.kind) {
+      case MPX_OP_SEND: case MPX_OP_RECV: case MPX_OP_ISEND: case MPX_OP_IRECV:
+      case MPX_OP_ALLREDUCE:
+        if (!o.comm || !o.comm->stream) return MPX_ERR_COMM;
+        if (o.comm->w != w) return MPX_ERR_ARG;
+        st = o.comm->stream;
+        break;
+      case MPX_OP_WAIT: case MPX_OP_WAITALL: {
+        const int64_t m = o.kind == MPX_OP_WAIT ? 1 : o.count;
+        if (m < 0 || (m > 0 && !o.requests)) return MPX_ERR_ARG;
+        for (int64_t k = 0; k < m; ++k) {
+          auto it = reqmap.find(o.requests + k);
+          if (it == reqmap.end()) return MPX_ERR_REQUEST;  // must name an op of this step
+          mpx_stream_s* sk = w->streams[it->second.first];
+          if (st && sk != st) return MPX_ERR_STREAM;
+          st = sk;
+        }
+        if (!st) return MPX_ERR_ARG;
+        break;
+      }
+      default:
+        return MPX_ERR_ARG;
+    }
+    if (!(st->flags & MPX_STREAM_EXCLUSIVE)) return MPX_ERR_STREAM;  // no doorbells in a graph
+    if (st->step) return MPX_ERR_STATE;
+    sof[i] = st;
+    per[st->id].push_back(i);
+    if (o.kind == MPX_OP_ISEND || o.kind == MPX_OP_IRECV) {
+      if (!o.requests) return MPX_ERR_ARG;
+      reqmap[o.requests] = {st->id, (int64_t)per[st->id].size()};
+    }
+  }
+  // 2. templates
+  std::vector<Desc> tmpl;
+  std::vector<int64_t> tmpl_wl;
+  std::vector<StepStream> recs;
+  for (int g = 0; g < S; ++g) {
+    if (per[g].empty()) continue;
+    StepStream r;
+    memset(&r, 0, sizeof(r));
+    r.g = g;
+    r.op0 = (int64_t)tmpl.size();
+    r.wl0 = (int64_t)tmpl_wl.size();
+    for (int i : per[g]) {
+      const mpx_op_t& o = ops[i];
+      Desc d;
+      memset(&d, 0, sizeof(d));
+      int rc = MPX_SUCCESS;
+      switch (o.kind) {
+        case MPX_OP_SEND: case MPX_OP_ISEND:
+          rc = fill_p2p(d, o.kind == MPX_OP_SEND ? K_SEND : K_ISEND, o.buf, o.count, o.datatype,
+                        o.peer, o.tag, o.comm, false);
+          break;
+        case MPX_OP_RECV: case MPX_OP_IRECV:
+          rc = fill_p2p(d, o.kind == MPX_OP_RECV ? K_RECV : K_IRECV, o.buf, o.count, o.datatype,
+                        o.peer, o.tag, o.comm, true);
+          if (o.kind == MPX_OP_RECV) d.status = (uint64_t)o.status;
+          break;
+        case MPX_OP_WAIT:
+          d.kw = make_kw(K_WAIT, 0, 0);
+          d.aux = (uint64_t)reqmap[o.requests].second;
+          d.status = (uint64_t)o.status;
+          break;
+        case MPX_OP_WAITALL:
+          d.kw = make_kw(K_WAITALL, 0, 0);
+          d.aux = (uint64_t)(tmpl_wl.size() - (size_t)r.wl0);
+          d.n32 = (int32_t)o.count;
+          d.status = (uint64_t)o.status;
+          for (int64_t k = 0; k < o.count; ++k) tmpl_wl.push_back(reqmap[o.requests + k].second);
+          break;
+        case MPX_OP_ALLREDUCE: {
+          if (o.op != MPX_SUM) return MPX_ERR_ARG;
+          if (o.datatype < 0 || o.datatype > MPX_DOUBLE) return MPX_ERR_TYPE;
+          const void* sb = o.buf == MPX_IN_PLACE ? o.recvbuf : o.buf;
+          if (o.count < 0 || (o.count > 0 && (!o.recvbuf || !sb))) return MPX_ERR_ARG;
+          d.kw = make_kw(K_ALLREDUCE, (uint32_t)o.datatype, (uint32_t)o.comm->shared->reduce_mode);
+          d.comm = (uint16_t)o.comm->shared->id;
+          d.rank = (uint16_t)o.comm->rank;
+          d.buf = (uint64_t)sb;
+          d.aux = (uint64_t)o.recvbuf;
+          d.count = o.count;
+          d.vcount = 1;
+          d.blocklen = 1;
+          d.stride = 1;
+          break;
+        }
+      }
+      if (rc) return rc;
+      tmpl.push_back(d);
+    }
+    r.nops = (int32_t)per[g].size();
+    r.nwl = (int32_t)(tmpl_wl.size() - (size_t)r.wl0);
+    if ((uint64_t)r.nops > (1ull << w->slots_log2) || (uint64_t)r.nwl > (1ull << w->wl_log2))
+      return MPX_ERR_NO_MEM;  // a step must fit one stream's ring
+    recs.push_back(r);
+  }
+  // 3. device memory: templates, records, counters, error word
+  mpx_step_s* st = new (std::nothrow) mpx_step_s();
+  if (!st) return MPX_ERR_NO_MEM;
+  st->w = w;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t o_t = 0, o_wl = al(tmpl.size() * sizeof(Desc));
+  const size_t o_r = o_wl + al(tmpl_wl.size() * 8 + 8);
+  const size_t o_cs = o_r + al(recs.size() * sizeof(StepStream) + 8);
+  const size_t o_cw = o_cs + al((size_t)S * 8);
+  const size_t o_e = o_cw + al((size_t)S * 8);
+  const size_t total = o_e + 256;
+  if (cudaMalloc((void**)&st->dmem, total) != cudaSuccess) { step_release(st); return MPX_ERR_NO_MEM; }
+  std::vector<uint64_t> cs((size_t)S, 0), cw((size_t)S, 0);
+  for (int g = 0; g < S; ++g) {
+    if (per[g].empty()) continue;
+    mpx_stream_s* sg = w->streams[g];
+    cs[(size_t)g] = sg->next_seq - 1;
+    cw[(size_t)g] = sg->wl_next;
+    st->streams.push_back(sg);
+  }
+  st->cnt_seq = (uint64_t*)(st->dmem + o_cs);
+  st->cnt_wl = (uint64_t*)(st->dmem + o_cw);
+  st->err = (int32_t*)(st->dmem + o_e);
+  bool ok = cudaMemset(st->dmem, 0, total) == cudaSuccess;
+  ok = ok && (tmpl.empty() || cudaMemcpy(st->dmem + o_t, tmpl.data(), tmpl.size() * sizeof(Desc), cudaMemcpyHostToDevice) == cudaSuccess);
+  ok = ok && (tmpl_wl.empty() || cudaMemcpy(st->dmem + o_wl, tmpl_wl.data(), tmpl_wl.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess);
+  ok = ok && (recs.empty() || cudaMemcpy(st->dmem + o_r, recs.data(), recs.size() * sizeof(StepStream), cudaMemcpyHostToDevice) == cudaSuccess);
+  ok = ok && cudaMemcpy(st->cnt_seq, cs.data(), (size_t)S * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(st->cnt_wl, cw.data(), (size_t)S * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) { step_release(st); return MPX_ERR_CUDA; }
+  // 4. capture: publication kernel, then one engine pass over everything visible
+  if (cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    step_release(st);
+    return MPX_ERR_CUDA;
+  }
+  int rc1 = mpxi_step_post_launch(&w->params, st->dmem + o_t, st->dmem + o_wl, st->dmem + o_r,
+                                  (int)recs.size(), st->cnt_seq, st->cnt_wl, st->err, st->cap);
+  int rc2 = launch_engine(w, st->cap, 1, false);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(st->cap, &graph);
+  st->graph = graph;
+  if (rc1 || rc2 != MPX_SUCCESS || ce != cudaSuccess || !graph ||
+      cudaGraphInstantiate(&st->exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    step_release(st);
+    return MPX_ERR_CUDA;
+  }
+  for (mpx_stream_s* sg : st->streams) sg->step = st;
+  *out = st;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_step_launch(mpx_step_t st, mpx_cuda_stream_t stream) {
+  if (!st || !st->exec) return MPX_ERR_ARG;
+  if (__atomic_load_n(&st->w->wctl->failed, __ATOMIC_ACQUIRE)) return MPX_ERR_STATE;
+  return cudaGraphLaunch(st->exec, (cudaStream_t)stream) == cudaSuccess ? MPX_SUCCESS : MPX_ERR_CUDA;
+}
+
+extern "C" int mpx_step_get_error(mpx_step_t st, int* err) {
+  if (!st || !err) return MPX_ERR_ARG;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, st->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return MPX_ERR_CUDA;
+  *err = v;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_step_free(mpx_step_t* pst) {
+  if (!pst || !*pst) return MPX_ERR_ARG;
+  mpx_step_s* st = *pst;
+  mpx_world_s* w = st->w;
+  // hand the streams' sequence numbers back to host enqueue
+  const int S = w->cfg.max_streams;
+  std::vector<uint64_t> cs((size_t)S), cw((size_t)S);
+  if (cudaMemcpy(cs.data(), st->cnt_seq, (size_t)S * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(cw.data(), st->cnt_wl, (size_t)S * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MPX_ERR_CUDA;
+  for (mpx_stream_s* sg : st->streams) {
+    sg->next_seq = cs[(size_t)sg->id] + 1;
+    sg->wl_next = cw[(size_t)sg->id];
+    sg->retired_seen = 0;
+    sg->step = nullptr;
+  }
+  step_release(st);
+  *pst = nullptr;
+  return MPX_SUCCESS;
 }

@@ -225,6 +225,20 @@ struct alignas(128) Shared {
 
 constexpr int kMaxDrainLimits = 256;
 
+// One stream's part of a recorded step (mpx_step_create): its descriptors are
+// tmpl[op0, op0 + nops), its waitall lists tmpl_wl[wl0, wl0 + nwl).  In the
+// templates a waitall's aux is its offset into the step's lists, a wait's aux
+// and every list entry are sequence numbers relative to the step (1-based;
+// 0 = null request).
+struct StepStream {
+  int32_t g;
+  int32_t nops;
+  int32_t nwl;
+  int32_t pad;
+  int64_t op0;
+  int64_t wl0;
+};
+
 // Kernel argument: pointers into world-owned memory plus configuration.
 struct EngineParams {
   int32_t nranks, max_streams, slots_log2, max_comms;

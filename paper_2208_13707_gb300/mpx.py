@@ -108,6 +108,10 @@ _SIGS = {
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
     "mpx_enqueue_batch": [ctypes.c_int, _vp, _P(ctypes.c_int)],
+    "mpx_step_create": [_vp, ctypes.c_int, _vp, _P(_vp)],
+    "mpx_step_launch": [_vp, _vp],
+    "mpx_step_get_error": [_vp, _P(ctypes.c_int)],
+    "mpx_step_free": [_P(_vp)],
     "mpx_version": [],
     "mpx_cuda_stream_create": [_P(_vp)],
     "mpx_cuda_stream_destroy": [_vp],
@@ -341,3 +345,28 @@ def mpx_enqueue_batch(ops, n: Optional[int] = None) -> int:
         e.done = done.value
         raise e
     return done.value
+
+
+def mpx_step_create(world: int, ops) -> int:
+    """Record the op_dtype() array `ops` as one step (see mpx_enqueue_batch for
+    the layout); returns the step handle."""
+    import numpy as np
+    a = np.ascontiguousarray(ops)
+    st = _vp()
+    _chk(lib.mpx_step_create(world, len(a), a.ctypes.data, ctypes.byref(st)), "mpx_step_create")
+    return st.value
+
+
+def mpx_step_launch(step: int, stream: int) -> None:
+    _chk(lib.mpx_step_launch(step, stream), "mpx_step_launch")
+
+
+def mpx_step_get_error(step: int) -> int:
+    e = ctypes.c_int(0)
+    _chk(lib.mpx_step_get_error(step, ctypes.byref(e)), "mpx_step_get_error")
+    return e.value
+
+
+def mpx_step_free(step: int) -> None:
+    st = _vp(step)
+    _chk(lib.mpx_step_free(ctypes.byref(st)), "mpx_step_free")

@@ -47,6 +47,7 @@ def _check(r, ref):
                                                   ("persistent", False, (64, 4)),
                                                   ("drain", True, (16, 1)),
                                                   ("drain", False, (16, 1)),
+                                                  ("graph", True, (64, 4)),
                                                   ("plain", True, (64, 4))])
 def test_batched_small_messages_match_the_oracle(mode, exclusive, shape):
     gpu = _gpu()
@@ -74,5 +75,33 @@ def test_batched_steps_after_buffer_reset_persistent():
             r.reset_buffers()
             assert r.step()
             _check(r, ref)
+    finally:
+        r.close()
+
+
+def test_recorded_step_replays_and_returns_streams_to_host_enqueue():
+    """A recorded step (CUDA graph) replayed five times gives the oracle's
+    bytes and statuses; after mpx_step_free the same streams take host
+    enqueue calls again (their sequence numbers continued on the device)."""
+    gpu = _gpu()
+    from paper_2208_13707_gb300 import mpx
+    p = _program(nmsg=4000, seed_off=2, nranks=8, streams_per_rank=2)
+    ref = oracle.run(p)
+    r = gpu.BatchRunner(p, mode="graph", timeout_s=60)
+    try:
+        for _ in range(5):
+            r.enqueue()
+        assert r.finish()
+        assert mpx.mpx_step_get_error(r.step_handle) == 0
+        _check(r, ref)
+        # host enqueue on a stream owned by the step is refused
+        with pytest.raises(mpx.MpxError) as e:
+            mpx.mpx_enqueue_batch(r.ops[:1])
+        assert e.value.code == mpx.ERR_STATE
+        mpx.mpx_step_free(r.step_handle)
+        r.graph = False
+        r.reset_buffers()
+        assert r.step(), "host-enqueued step after the recorded ones did not finish"
+        _check(r, ref)
     finally:
         r.close()

@@ -261,8 +261,11 @@ class BatchRunner:
         from paper_2208_13707_gb300 import mpx
         self.mpx, self.torch, self.prog, self.timeout_s = mpx, torch, prog, timeout_s
         dev = torch.device("cuda")
+        # "graph": the step is recorded once (mpx_step_create, drain-mode world)
+        # and every step() replays its CUDA graph on the engine stream
+        self.graph = mode == "graph"
         self.mode = {"persistent": mpx.ENGINE_PERSISTENT, "drain": mpx.ENGINE_DRAIN,
-                     "plain": mpx.ENGINE_PLAIN}[mode]
+                     "plain": mpx.ENGINE_PLAIN, "graph": mpx.ENGINE_DRAIN}[mode]
         over = {"task_slots": 1 << 16}
         over.update(cfg_over or {})
         cfg = make_config(prog, self.mode, **over)
@@ -292,6 +295,7 @@ class BatchRunner:
             torch.cuda.synchronize()
         self.ops = self._build_ops()
         self.messages = int((np.isin(prog.ops["kind"], [SEND, ISEND])).sum())
+        self.step_handle = mpx.mpx_step_create(self.world, self.ops) if self.graph else None
 
     def _build_ops(self):
         mpx, prog = self.mpx, self.prog
@@ -358,6 +362,9 @@ class BatchRunner:
     def enqueue(self):
         """Enqueue one step (returns once every operation is enqueued)."""
         mpx = self.mpx
+        if self.graph:
+            mpx.mpx_step_launch(self.step_handle, self.engine_stream.cuda_stream)
+            return
         done = 0
         n = len(self.ops)
         t_dl = time.perf_counter() + self.timeout_s
@@ -382,6 +389,12 @@ class BatchRunner:
         """Drive (drain mode) and wait until every stream is idle."""
         mpx = self.mpx
         t_dl = time.perf_counter() + self.timeout_s
+        if self.graph:
+            while time.perf_counter() < t_dl:
+                if self.engine_stream.query():
+                    return True
+                time.sleep(2e-5)
+            return False
         if self.mode == mpx.ENGINE_DRAIN:
             while time.perf_counter() < t_dl:
                 self.progress_once()
@@ -422,6 +435,14 @@ class BatchRunner:
 
     def close(self):
         mpx = self.mpx
+        if self.graph:
+            if not self.finish():
+                mpx.mpx_world_abort(self.world)
+                t1 = time.perf_counter()
+                while time.perf_counter() - t1 < 10 and not self.engine_stream.query():
+                    time.sleep(1e-3)
+            mpx.mpx_step_free(self.step_handle)
+            self.graph = False
         if not self.finish():
             mpx.mpx_world_abort(self.world)
             t1 = time.perf_counter()
