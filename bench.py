@@ -635,6 +635,24 @@ def halo_bench(steps=100, warmup=5, sub=256):
                  "own_moves"])}}
 
 
+def serving(requests=100000):
+    """Serving loop: 32 host threads with one MPIX stream each submit
+    requests open-loop (Poisson, mean gap 2 us per thread), sizes Zipf(1.2)
+    over 64 B - 16 MB, 70% p2p / 30% fp32 allreduce over the 32 ranks,
+    admission against a 40 GiB device budget; the same requests through the
+    plain path.  `requests` calls in total (the full workload has 10^7)."""
+    from paper_2208_13707_gb300 import mpx
+    out = {}
+    for name, mode in (("engine", mpx.ENGINE_PERSISTENT), ("plain", mpx.ENGINE_PLAIN)):
+        c = mpx.mpx_serve_config_init()
+        c.requests = requests
+        c.engine_mode = mode
+        out[name] = mpx.mpx_serve_run(c)
+    out["requests"] = requests
+    out["speedup_vs_plain"] = out["engine"]["msgs_per_s"] / max(1e-9, out["plain"]["msgs_per_s"])
+    return out
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -712,6 +730,9 @@ def main():
     ap.add_argument("--allreduce-only", action="store_true",
                     help="print only the allreduce bandwidth sweep and the halo exchange")
     ap.add_argument("--no-c4", action="store_true", help="skip the allreduce sweep and the halo exchange")
+    ap.add_argument("--serve-requests", type=int, default=100000,
+                    help="requests of the serving measurement (0 = skip it)")
+    ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -733,6 +754,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.copy_sweep:
         copy_sweep()
+        return
+    if args.serving_only:
+        print(json.dumps({"serving": serving(args.serve_requests)}), flush=True)
         return
     if args.allreduce_only:
         pk, pkind = peaks()
@@ -802,6 +826,7 @@ def main():
         for e in ar:
             e["frac_of_peak"] = e["gbs"] / pk
         c4 = {"allreduce": ar, "halo": halo_bench()}
+    serve = serving(args.serve_requests) if args.serve_requests else None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -829,6 +854,7 @@ def main():
                 "plain_path": plain,
                 "batching_small": batching,
                 "allreduce_and_halo": c4,
+                "serving": serve,
                 "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {

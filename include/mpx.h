@@ -369,6 +369,62 @@ int mpx_step_get_error(mpx_step_t step, int* first_error);
  * step must have completed (synchronize the launch stream first). */
 int mpx_step_free(mpx_step_t* step);
 
+/* Serving loop: `nthreads` host threads, one MPIX stream (exclusive) and one
+ * virtual rank each, submit enqueue requests open-loop (Poisson arrivals)
+ * to one world; each request's receive or result buffer is admitted against
+ * a device-memory budget (each thread owns budget/nthreads of it) and is
+ * released when the request completes, so requests arriving while others
+ * are on the GPU start as memory frees up.  A reaper thread reads the
+ * streams' completion words and their device timestamps; latencies run
+ * from a request's arrival (p50_us/p99_us) and from its enqueue call
+ * (svc_p50_us/svc_p99_us) to its completion.  engine_mode
+ * MPX_ENGINE_PLAIN runs the same requests through the plain path, where a
+ * thread's blocking calls return only when complete.
+ * Workload: every thread makes requests/nthreads calls; a share p_allreduce
+ * of them are fp32 SUM allreduce participations over all threads (the same
+ * instance list everywhere), the rest are isends and irecvs of messages
+ * with uniform source, uniform other destination and Zipf(zipf_s) sizes over
+ * the powers of two 2^min_log2..2^max_log2 (allreduce sizes likewise); the
+ * calls between two allreduce instances form an epoch that each thread ends
+ * with a waitall.  Items are numbered: messages first, then allreduce
+ * instances.  digests (length ndigests, may be NULL) receives, for every
+ * sampled item (item % sample_every == 0, or only_item), an
+ * order-independent digest of the delivered bytes (rank 0's result for an
+ * allreduce); only_item >= 0 runs that item alone, without pacing, so that
+ * its digest can be compared with the mix.  Errors: MPX_ERR_ARG,
+ * MPX_ERR_NO_MEM, and those of the calls it makes. */
+typedef struct {
+  int32_t nthreads;
+  int32_t engine_mode;   /* MPX_ENGINE_PERSISTENT or MPX_ENGINE_PLAIN */
+  int64_t requests;
+  double mean_gap_us;    /* mean Poisson gap per thread (0: no pacing) */
+  double zipf_s;
+  int32_t min_log2, max_log2;
+  double p_allreduce;
+  int64_t budget_bytes;
+  uint64_t seed;
+  int64_t sample_every;
+  int64_t only_item;
+} mpx_serve_config_t;
+
+typedef struct {
+  int64_t completed;       /* requests completed */
+  int64_t items;           /* messages + allreduce instances in the schedule */
+  double seconds;          /* first arrival to last completion */
+  double msgs_per_s;       /* completed requests per second */
+  double gbs;              /* delivered payload bytes per second / 1e9 */
+  double p50_us, p99_us;   /* arrival -> completion */
+  double svc_p50_us, svc_p99_us;  /* enqueue call -> completion */
+  int64_t admission_waits; /* requests that waited for budget */
+  int64_t peak_bytes;      /* peak budget in use (sum over threads) */
+} mpx_serve_result_t;
+
+/* Defaults: 32 threads, persistent engine, 10^6 requests, 2 us mean gap,
+ * Zipf 1.2 over 64 B..16 MB, 30% allreduce, 40 GiB budget. */
+int mpx_serve_config_init(mpx_serve_config_t* cfg);
+int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* result, uint64_t* digests,
+                  int64_t ndigests);
+
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);
 

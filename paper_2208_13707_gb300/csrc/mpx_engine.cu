@@ -1575,6 +1575,7 @@ struct Ctl {
       // stream's cuStreamWaitValue64 polls
       asm volatile("fence.acq_rel.gpu;" ::: "memory");
       st_rlx_sys(&P.done[g], newdone);
+      st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);  // engine clock of this advance
       st_rlx_sys(&P.sctl[g].done, newdone);
       prog = true;
     }

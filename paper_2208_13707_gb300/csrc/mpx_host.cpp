@@ -1427,3 +1427,16 @@ extern "C" int mpx_step_free(mpx_step_t* pst) {
   *pst = nullptr;
   return MPX_SUCCESS;
 }
+
+// ---------------------------------------------------------------------------
+// internal accessors for the serving loop (mpx_serve.cpp)
+// ---------------------------------------------------------------------------
+extern "C" uint64_t mpxi_stream_last_seq(mpx_stream_t s) { return s ? s->next_seq - 1 : 0; }
+
+extern "C" int mpxi_stream_done(mpx_stream_t s, uint64_t* done, uint64_t* done_t) {
+  if (!s || s->w->plain) return MPX_ERR_ARG;
+  StreamCtl* c = &s->w->sctl[s->id];
+  *done = __atomic_load_n(&c->done, __ATOMIC_ACQUIRE);
+  *done_t = __atomic_load_n(&c->done_t, __ATOMIC_ACQUIRE);
+  return MPX_SUCCESS;
+}

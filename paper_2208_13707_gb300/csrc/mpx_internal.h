@@ -61,7 +61,9 @@ struct alignas(128) StreamCtl {
   uint64_t wl_retired;  // D->H  waitlist entries no longer read
   uint64_t done;        // D->H  mirror of the completion word
   int32_t error;        // D->H  first asynchronous error
-  int32_t pad1[25];
+  int32_t pad1a;
+  uint64_t done_t;      // D->H  %globaltimer when `done` last advanced
+  int32_t pad1[22];
 };
 static_assert(sizeof(StreamCtl) == 256, "stream control: two lines");
 static_assert(offsetof(StreamCtl, retired) == 128, "engine-written line");

@@ -65,6 +65,22 @@ def op_dtype():
                      ("requests", "<u8"), ("status", "<u8"), ("op", "<i4"), ("pad", "<i4")])
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("nthreads", ctypes.c_int32), ("engine_mode", ctypes.c_int32),
+                ("requests", ctypes.c_int64), ("mean_gap_us", ctypes.c_double),
+                ("zipf_s", ctypes.c_double), ("min_log2", ctypes.c_int32), ("max_log2", ctypes.c_int32),
+                ("p_allreduce", ctypes.c_double), ("budget_bytes", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("sample_every", ctypes.c_int64), ("only_item", ctypes.c_int64)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("items", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("msgs_per_s", ctypes.c_double), ("gbs", ctypes.c_double),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("svc_p50_us", ctypes.c_double), ("svc_p99_us", ctypes.c_double),
+                ("admission_waits", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+
+
 class Status(ctypes.Structure):
     _fields_ = [("source", ctypes.c_int32), ("tag", ctypes.c_int32), ("error", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("bytes", ctypes.c_int64)]
@@ -109,6 +125,8 @@ _SIGS = {
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
     "mpx_enqueue_batch": [ctypes.c_int, _vp, _P(ctypes.c_int)],
     "mpx_step_create": [_vp, ctypes.c_int, _vp, _P(_vp)],
+    "mpx_serve_config_init": [_P(ServeConfig)],
+    "mpx_serve_run": [_P(ServeConfig), _P(ServeResult), _vp, _i64],
     "mpx_step_launch": [_vp, _vp],
     "mpx_step_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_step_free": [_P(_vp)],
@@ -370,3 +388,22 @@ def mpx_step_get_error(step: int) -> int:
 def mpx_step_free(step: int) -> None:
     st = _vp(step)
     _chk(lib.mpx_step_free(ctypes.byref(st)), "mpx_step_free")
+
+
+def mpx_serve_config_init() -> ServeConfig:
+    c = ServeConfig()
+    _chk(lib.mpx_serve_config_init(ctypes.byref(c)), "mpx_serve_config_init")
+    return c
+
+
+def mpx_serve_run(cfg: ServeConfig, digests=None) -> dict:
+    """Run the serving loop; `digests` (a uint64 numpy array, optional) receives
+    the sampled items' digests.  Returns the result fields as a dict."""
+    import numpy as np
+    r = ServeResult()
+    dp, dn = (None, 0)
+    if digests is not None:
+        assert digests.dtype == np.uint64 and digests.flags.c_contiguous
+        dp, dn = digests.ctypes.data, len(digests)
+    _chk(lib.mpx_serve_run(ctypes.byref(cfg), ctypes.byref(r), dp, dn), "mpx_serve_run")
+    return {k: getattr(r, k) for k, _ in ServeResult._fields_}

@@ -131,3 +131,35 @@ def test_enqueue_batch_stops_at_the_first_invalid_op():
         mpx.mpx_enqueue_batch(ops)
     assert e.value.code == mpx.ERR_ARG and e.value.done == 0
     assert mpx.mpx_enqueue_batch(ops[:0]) == 0
+
+
+@pytest.mark.parametrize("cname,pyname", [("mpx_serve_config_t", "ServeConfig"),
+                                          ("mpx_serve_result_t", "ServeResult"),
+                                          ("mpx_world_config_t", "WorldConfig")])
+def test_struct_layouts_match_the_binding(tmp_path, cname, pyname):
+    import subprocess
+    from paper_2208_13707_gb300 import mpx
+    cls = getattr(mpx, pyname)
+    fields = [f for f, _ in cls._fields_]
+    src = tmp_path / "l.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpx.h"\nint main(void){\n'
+                   f'  printf("%zu", sizeof({cname}));\n' +
+                   "".join(f'  printf(" %zu", offsetof({cname}, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "l"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(cls)
+    assert out[1:] == [getattr(cls, f).offset for f in fields]
+
+
+def test_serve_run_rejects_bad_configs_without_a_gpu():
+    from paper_2208_13707_gb300 import mpx
+    c = mpx.mpx_serve_config_init()
+    assert c.nthreads == 32 and c.max_log2 == 24 and abs(c.p_allreduce - 0.3) < 1e-12
+    c.nthreads = 1
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_serve_run(c)
+    assert e.value.code == mpx.ERR_ARG
