@@ -598,6 +598,20 @@ extern "C" int mpx_world_debug_dump(mpx_world_t w) {
             (unsigned long long)x.cursor, (unsigned long long)x.pc, (unsigned long long)x.retire,
             (unsigned long long)x.sched, (unsigned long long)x.done, (unsigned long long)x.reached,
             (unsigned long long)door[g], (unsigned long long)done[g], (long long)x.stall_t0, x.flags, c.error);
+    // the operations at the logical cursor and at the physical scan position
+    const uint64_t at[2] = {x.cursor, x.pc};
+    for (int k = 0; k < 2; ++k) {
+      if (at[k] == 0 || at[k] > x.ingested) continue;
+      DOp o;
+      const size_t idx = ((size_t)g << w->slots_log2) + ((at[k] - 1) & ((1ull << w->slots_log2) - 1));
+      if (cudaMemcpy(&o, w->params.ops + idx, sizeof(DOp), cudaMemcpyDeviceToHost) != cudaSuccess) break;
+      fprintf(stderr,
+              "[mpx dump]   %s seq %llu kind %u peer %d tag %d count %lld lstate %d lround %d pflags %#x "
+              "partner %#llx n32 %d wscan %u pscan %u\n",
+              k ? "pc" : "cursor", (unsigned long long)at[k], kw_kind(o.d.kw), o.d.peer, o.d.tag,
+              (long long)o.d.count, o.lstate, o.lround, o.pflags, (unsigned long long)o.partner, o.d.n32,
+              o.wscan, o.pscan);
+    }
   }
   fflush(stderr);
   return MPX_SUCCESS;

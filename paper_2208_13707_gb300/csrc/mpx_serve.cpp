@@ -23,6 +23,7 @@
 //     receive and result buffers come from the budget.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -41,8 +42,9 @@
 extern "C" uint64_t mpxi_stream_last_seq(mpx_stream_t s);
 extern "C" int mpxi_stream_done(mpx_stream_t s, uint64_t* done, uint64_t* done_t);
 extern "C" int mpxi_fill(void* p, int64_t bytes, uint64_t seed, int as_f32, void* stream);
-extern "C" int mpxi_digest(const void* p, int64_t bytes, void* out_dev, void* stream);
+extern "C" int mpxi_digest_store(const void* p, int64_t bytes, void* out_mapped, void* stream);
 extern "C" int mpxi_clock_probe(void* out_mapped, void* stream);
+extern "C" int mpxi_serve_preload(void);
 
 namespace {
 
@@ -157,6 +159,7 @@ struct Rec {  // one request in flight
 struct Batch {  // requests covered by one blocking operation
   uint64_t seq;
   std::vector<Rec> recs;
+  cudaEvent_t digested = nullptr;  // digests of sampled buffers done (stream-ordered after seq)
 };
 
 struct Shared {
@@ -177,6 +180,8 @@ struct Shared {
   int64_t clock_offset = 0;  // device globaltimer - host steady clock
   uint64_t* digests = nullptr;
   int64_t ndigests = 0;
+  uint64_t* dig_host = nullptr;  // mapped pinned digest slots [ndigests]
+  uint64_t* dig_dev = nullptr;   // their device address
   // results, per thread (merged at the end)
   std::vector<std::vector<float>> lat, svc;
   std::vector<int64_t> bytes_done, t_last;
@@ -192,27 +197,33 @@ struct Shared {
   }
 };
 
-// digest a finished request's buffer (synchronously on the caller's stream)
-void take_digest(Shared& S, const Rec& r, cudaStream_t cs, unsigned long long* dslot) {
-  if (r.item < 0 || !S.digests || r.item >= S.ndigests) return;
-  unsigned long long v = 0;
-  if (mpxi_digest(r.buf, r.bytes, dslot, cs) == 0 &&
-      cudaMemcpyAsync(&v, dslot, 8, cudaMemcpyDeviceToHost, cs) == cudaSuccess &&
-      cudaStreamSynchronize(cs) == cudaSuccess)
-    S.digests[r.item] = v;
+// Digests of a batch's sampled buffers, enqueued on the client's own stream
+// right after the blocking operation that covers them: stream order runs
+// them once the data is in place, and nothing else waits on them.  (A reaper
+// that launched them on a stream of its own could find that stream's
+// hardware queue behind a client stream's unsatisfied wait.)
+void enqueue_digests(Shared& S, Batch& b, cudaStream_t cs) {
+  bool any = false;
+  for (const Rec& r : b.recs) {
+    if (r.item < 0 || !S.dig_dev || r.item >= S.ndigests || !r.buf) continue;
+    mpxi_digest_store(r.buf, r.bytes, S.dig_dev + r.item, cs);
+    any = true;
+  }
+  if (any && cudaEventCreateWithFlags(&b.digested, cudaEventDisableTiming) == cudaSuccess)
+    cudaEventRecord(b.digested, cs);
 }
 
-void finish_batch(Shared& S, int slot, Batch& b, int64_t t_c, cudaStream_t cs,
-                  unsigned long long* dslot) {
+void finish_batch(Shared& S, int slot, Batch& b, int64_t t_c) {
   for (Rec& r : b.recs) {
     S.lat[(size_t)slot].push_back((float)((t_c - r.t_arr) / 1e3));
     S.svc[(size_t)slot].push_back((float)((t_c - r.t_enq) / 1e3));
     S.bytes_done[(size_t)slot] += r.bytes;
-    if (r.buf) {
-      take_digest(S, r, cs, dslot);
-      S.budget[(size_t)r.owner].release(r.buf);
-    }
+    if (r.item >= 0 && S.dig_host && r.item < S.ndigests)
+      S.digests[r.item] = *(volatile uint64_t*)&S.dig_host[r.item];
+    if (r.buf) S.budget[(size_t)r.owner].release(r.buf);
   }
+  if (b.digested) cudaEventDestroy(b.digested);
+  b.digested = nullptr;
   S.t_last[(size_t)slot] = std::max(S.t_last[(size_t)slot], t_c);
 }
 
@@ -299,11 +310,10 @@ struct ThreadCtx {
 void client_thread(Shared& S, ThreadCtx ctx, bool plain, int64_t t0) {
   const mpx_serve_config_t& c = *S.cfg;
   const int t = ctx.t;
-  unsigned long long* dslot = nullptr;
-  cudaMalloc((void**)&dslot, 8);
   Rng arr(c.seed, 200 + (uint64_t)t);
   const bool paced = c.only_item < 0 && c.mean_gap_us > 0;
   int64_t t_arr = t0;
+  while (now_ns() < t0) std::this_thread::yield();  // every thread starts together
   std::vector<mpx_request_t> reqs;
   std::vector<Rec> open;
   uint8_t* src = S.region[(size_t)t];
@@ -369,23 +379,22 @@ void client_thread(Shared& S, ThreadCtx ctx, bool plain, int64_t t0) {
         b.recs.push_back(Rec{t_arr, te, t, buf, x.bytes, sample ? x.item : -1});
       }
       if (plain) {
-        finish_batch(S, t, b, now_ns(), ctx.cs, dslot);
+        const int64_t t_c = now_ns();  // the blocking call returned: complete
+        enqueue_digests(S, b, ctx.cs);
+        if (b.digested) cudaEventSynchronize(b.digested);
+        finish_batch(S, t, b, t_c);
       } else {
         b.seq = mpxi_stream_last_seq(ctx.stream);
+        enqueue_digests(S, b, ctx.cs);
         std::lock_guard<std::mutex> g(S.fmu[(size_t)t]);
         S.fifo[(size_t)t].push_back(std::move(b));
       }
     }
   }
-  if (dslot) cudaFree(dslot);
   S.running--;
 }
 
 void reaper_thread(Shared& S, std::vector<ThreadCtx>& ctx) {
-  cudaStream_t cs;
-  cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  unsigned long long* dslot = nullptr;
-  cudaMalloc((void**)&dslot, 8);
   const int T = S.T;
   const int slot = T;  // the reaper's result slot
   for (;;) {
@@ -399,14 +408,15 @@ void reaper_thread(Shared& S, std::vector<ThreadCtx>& ctx) {
           std::lock_guard<std::mutex> g(S.fmu[(size_t)t]);
           auto& q = S.fifo[(size_t)t];
           if (q.empty()) break;
-          if (q.front().seq > done) {
+          if (q.front().seq > done ||
+              (q.front().digested && cudaEventQuery(q.front().digested) == cudaErrorNotReady)) {
             pending = true;
             break;
           }
           b = std::move(q.front());
           q.pop_front();
         }
-        finish_batch(S, slot, b, (int64_t)done_t - S.clock_offset, cs, dslot);
+        finish_batch(S, slot, b, (int64_t)done_t - S.clock_offset);
       }
     }
     if (!pending && S.running.load() == 0) {
@@ -419,8 +429,6 @@ void reaper_thread(Shared& S, std::vector<ThreadCtx>& ctx) {
     }
     if (S.stop.load() && S.running.load() == 0) break;
   }
-  if (dslot) cudaFree(dslot);
-  cudaStreamDestroy(cs);
 }
 
 double pct(std::vector<float>& v, double q) {
@@ -469,6 +477,22 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   S.ndigests = ndigests;
   build_schedule(S);
   res->items = S.nitems;
+  if (mpxi_serve_preload()) return MPX_ERR_CUDA;
+  struct HostSlots {
+    uint64_t* p = nullptr;
+    ~HostSlots() {
+      if (p) cudaFreeHost(p);
+    }
+  } slots;
+  if (digests && ndigests > 0) {
+    if (cudaHostAlloc((void**)&slots.p, (size_t)ndigests * 8, cudaHostAllocMapped) != cudaSuccess)
+      return MPX_ERR_NO_MEM;
+    memset(slots.p, 0, (size_t)ndigests * 8);
+    void* dp = nullptr;
+    cudaHostGetDevicePointer(&dp, slots.p, 0);
+    S.dig_host = slots.p;
+    S.dig_dev = (uint64_t*)dp;
+  }
   if (cudaMalloc((void**)&S.pool, (size_t)c.budget_bytes) != cudaSuccess) return MPX_ERR_NO_MEM;
   const int64_t share = (c.budget_bytes / T) & ~(int64_t)255;
   if (share < ((int64_t)1 << c.max_log2)) return MPX_ERR_ARG;  // a request must fit a share
@@ -478,6 +502,7 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   mpx_world_config_init(&wc);
   wc.engine_mode = c.engine_mode;
   wc.max_streams = std::max(wc.max_streams, T);
+  wc.watchdog_ns = 3000000000ll;
   mpx_world_t w = nullptr;
   int rc = mpx_world_create(T, &wc, &w);
   if (rc) return rc;
@@ -548,6 +573,10 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   }
   int err = 0;
   if (w && !plain && mpx_world_get_error(w, &err) == MPX_SUCCESS && err && !rc) rc = err;
+  if (rc && w && !plain) {
+    fprintf(stderr, "[mpx_serve_run] failed with %d (world error %d)\n", rc, err);
+    mpx_world_debug_dump(w);
+  }
   if (w && !plain) mpx_world_stop(w, 10000);
   for (int t = 0; t < T; ++t) {
     if (comm[(size_t)t]) mpx_comm_free(&comm[(size_t)t]);

@@ -1,6 +1,6 @@
 // Small device helpers of the serving loop (mpx_serve_run): deterministic
-// payload fill, an order-independent digest of a buffer, and a probe of the
-// device clock that completion times are reported in.
+// payload fill, a digest of a buffer, and a probe of the device clock that
+// completion times are reported in.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,15 +31,25 @@ __global__ void fill_kernel(uint64_t* p, int64_t nwords, uint64_t seed, int as_f
   }
 }
 
-// sum over bytes b_i of mix64((i << 8) | b_i), wrapping: equal buffers give
-// equal digests, and any byte change changes one term
-__global__ void digest_kernel(const uint8_t* p, int64_t n, unsigned long long* out) {
+// Digest of a buffer: the wrapping sum over bytes b_i of mix64((i << 8) | b_i)
+// (equal buffers give equal digests; changing any byte changes one term),
+// computed by one block and stored to `out`, which may be mapped host memory.
+__global__ void __launch_bounds__(1024) digest_store_kernel(const uint8_t* p, int64_t n,
+                                                            volatile uint64_t* out) {
+  __shared__ uint64_t part[32];
   uint64_t acc = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    acc += mix64(((uint64_t)i << 8) | p[i]);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += mix64(((uint64_t)i << 8) | p[i]);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, (unsigned long long)acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint64_t v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      *out = v;
+      __threadfence_system();
+    }
+  }
 }
 
 __global__ void clock_kernel(volatile uint64_t* out) {
@@ -56,18 +66,23 @@ extern "C" int mpxi_fill(void* p, int64_t bytes, uint64_t seed, int as_f32, void
   return (int)cudaGetLastError();
 }
 
-extern "C" int mpxi_digest(const void* p, int64_t bytes, void* out_dev, void* stream) {
-  cudaError_t e = cudaMemsetAsync(out_dev, 0, 8, (cudaStream_t)stream);
-  if (e != cudaSuccess) return (int)e;
-  if (bytes <= 0) return 0;
-  int blocks = (int)((bytes + 255) / 256);
-  if (blocks > 1024) blocks = 1024;
-  digest_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>((const uint8_t*)p, bytes,
-                                                          (unsigned long long*)out_dev);
+extern "C" int mpxi_digest_store(const void* p, int64_t bytes, void* out_mapped, void* stream) {
+  digest_store_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>((const uint8_t*)p, bytes,
+                                                           (volatile uint64_t*)out_mapped);
   return (int)cudaGetLastError();
 }
 
 extern "C" int mpxi_clock_probe(void* out_mapped, void* stream) {
   clock_kernel<<<1, 1, 0, (cudaStream_t)stream>>>((volatile uint64_t*)out_mapped);
   return (int)cudaGetLastError();
+}
+
+// Load the three kernels now: a kernel loaded lazily at its first launch may
+// wait for running kernels to finish, and the resident engine does not finish
+// while requests wait for memory that a digest would release.
+extern "C" int mpxi_serve_preload(void) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fill_kernel) != cudaSuccess) return 1;
+  if (cudaFuncGetAttributes(&a, digest_store_kernel) != cudaSuccess) return 1;
+  return cudaFuncGetAttributes(&a, clock_kernel) == cudaSuccess ? 0 : 1;
 }
