@@ -653,6 +653,27 @@ def serving(requests=100000):
     return out
 
 
+def autotune_report():
+    """Autotuner on two samples of the workloads' message mixes: small
+    (log-uniform 8 B - 64 KB) and large (log-uniform 4 KB - 64 MB, the ring
+    exchange's range); best configuration against the default one."""
+    import numpy as np
+    from paper_2208_13707_gb300 import autotune as at
+    grid = {"tile_bytes": (16 << 10, 64 << 10, 256 << 10), "bulk_min_bytes": (0, 32 << 10),
+            "engine_ctas": (0, 76), "engine_threads": (256,)}
+    rng = np.random.default_rng(0x220813707)
+    out = {}
+    for name, lo, hi, n in (("small_8B_64KB", 8, 64 << 10, 512), ("large_4KB_64MB", 4096, 64 << 20, 16)):
+        sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.int64).tolist()
+        r = at.autotune(sizes, nranks=8, rounds=3, grid=grid)
+        default = [t for t in r.table if t["config"] == {"tile_bytes": 64 << 10, "bulk_min_bytes": 32 << 10,
+                                                          "engine_ctas": 0, "engine_threads": 256}]
+        best = [t for t in r.table if t["config"] == r.best][0]
+        out[name] = {"best": r.best, "best_gbs": best["gbs"], "best_msgs_per_s": best["msgs_per_s"],
+                     "default_gbs": default[0]["gbs"] if default else None, "trials": len(r.table)}
+    return out
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -733,6 +754,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=100000,
                     help="requests of the serving measurement (0 = skip it)")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
+    ap.add_argument("--autotune-only", action="store_true", help="print only the autotuner report")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -754,6 +777,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.copy_sweep:
         copy_sweep()
+        return
+    if args.autotune_only:
+        print(json.dumps({"autotune": autotune_report()}), flush=True)
         return
     if args.serving_only:
         print(json.dumps({"serving": serving(args.serve_requests)}), flush=True)
@@ -827,6 +853,7 @@ def main():
             e["frac_of_peak"] = e["gbs"] / pk
         c4 = {"allreduce": ar, "halo": halo_bench()}
     serve = serving(args.serve_requests) if args.serve_requests else None
+    tune = None if args.no_autotune else autotune_report()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -855,6 +882,7 @@ def main():
                 "batching_small": batching,
                 "allreduce_and_halo": c4,
                 "serving": serve,
+                "autotune": tune,
                 "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {
