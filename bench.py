@@ -674,6 +674,70 @@ def autotune_report():
     return out
 
 
+def profile_steps(kind, launches=3):
+    """Profile-safe runs for a kernel profiler: the work is a recorded step
+    (one CUDA graph: descriptor publication kernel + one engine pass), so no
+    stream waits exist for a serialising profiler to block on, and the engine
+    pass reads nothing it writes in pinned memory (a replayed pass repeats the
+    same work).  kind "allreduce": 16 ranks, one fp32 fixed-order allreduce of
+    2^22 elements each (256 MiB in, 256 MiB out).  kind "batching": the
+    small-message batching step (64 ranks x 4 streams, 65536 messages,
+    8 B - 64 KB)."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    from traffic import gen, gpu
+    if kind == "batching":
+        prog = gen.batching(nranks=64, streams_per_rank=4, nmsg=65536, max_bytes=64 << 10,
+                            laminar=True, seed=gen.SEED_BASE + 2)
+        r = gpu.BatchRunner(prog, mode="graph", timeout_s=120,
+                            cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+        try:
+            for _ in range(launches):
+                r.enqueue()
+            assert r.finish()
+        finally:
+            r.close()
+        return {"profile_steps": kind, "launches": launches, "messages": 65536}
+    R, n = 16, 1 << 22
+    dev = torch.device("cuda")
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mpx.ENGINE_DRAIN
+    cfg.max_streams = R
+    w = mpx.mpx_world_create(R, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(R + 1)]
+    ms = [mpx.mpx_stream_create(w, i, raw[i], mpx.STREAM_EXCLUSIVE) for i in range(R)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    x = torch.randn((R, n), device=dev)
+    y = torch.zeros((R, n), device=dev)
+    torch.cuda.synchronize()
+    ops = np.zeros(R, mpx.op_dtype())
+    ops["kind"] = mpx.OP_ALLREDUCE
+    ops["datatype"] = mpx.FLOAT
+    ops["count"] = n
+    ops["op"] = mpx.SUM
+    ops["buf"] = [x[i].data_ptr() for i in range(R)]
+    ops["recvbuf"] = [y[i].data_ptr() for i in range(R)]
+    ops["comm"] = comm
+    step = mpx.mpx_step_create(w, ops)
+    es = torch.cuda.ExternalStream(raw[R])
+    for _ in range(launches):
+        mpx.mpx_step_launch(step, raw[R])
+    es.synchronize()
+    ok = mpx.mpx_step_get_error(step) == 0 and mpx.mpx_world_get_error(w) == 0
+    ref = x.sum(0)  # any order: a coarse sanity check of the result only
+    ok = ok and bool(torch.allclose(y[0], ref, rtol=1e-4, atol=1e-4))
+    mpx.mpx_step_free(step)
+    for c in comm:
+        mpx.mpx_comm_free(c)
+    for s_ in ms:
+        mpx.mpx_stream_free(s_)
+    mpx.mpx_world_free(w)
+    for h in raw:
+        mpx.mpx_cuda_stream_destroy(h)
+    assert ok, "profiled allreduce steps failed"
+    return {"profile_steps": kind, "launches": launches, "ranks": R, "n": n}
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -755,6 +819,8 @@ def main():
                     help="requests of the serving measurement (0 = skip it)")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
+    ap.add_argument("--profile-steps", choices=["allreduce", "batching"], default=None,
+                    help="profile-safe recorded steps for a kernel profiler (no benchmark line)")
     ap.add_argument("--autotune-only", action="store_true", help="print only the autotuner report")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
@@ -777,6 +843,9 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.copy_sweep:
         copy_sweep()
+        return
+    if args.profile_steps:
+        print(json.dumps(profile_steps(args.profile_steps)), flush=True)
         return
     if args.autotune_only:
         print(json.dumps({"autotune": autotune_report()}), flush=True)
