@@ -1501,6 +1501,51 @@ struct Ctl {
     return true;
   }
 
+  // The completion side of a blocking operation.  A waitall's statuses can
+  // be written by a whole warp (lane, nl = 32); its request with the lowest
+  // index that failed sets the stream's first error, as in the serial order.
+  __device__ void finish_blocking_warp(int g, DOp* o) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t k = kw_kind(o->d.kw);
+    if (k != K_WAITALL) {
+      if (lane == 0) finish_blocking(g, o);
+      __syncwarp();
+      return;
+    }
+    const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+    const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
+    uint32_t first_w = 0xffffffffu;
+    int32_t first_err = 0;
+    for (uint32_t w = (uint32_t)lane; w < (uint32_t)o->d.n32; w += 32) {
+      const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
+      if (rs == 0) {
+        if (o->d.status) write_status(o->d.status + 24ull * w, kAnySource, kAnyTag, 0, 0);
+        continue;
+      }
+      DOp* q = op_at(P, g, rs);
+      if (o->d.status) request_status(o->d.status + 24ull * w, q);
+      if (q->err && w < first_w) {
+        first_w = w;
+        first_err = q->err;
+      }
+      atomicOr(&q->pflags, PF_WAITED);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const uint32_t ow = __shfl_down_sync(FULL, first_w, off);
+      const int32_t oe = __shfl_down_sync(FULL, first_err, off);
+      if (ow < first_w) {
+        first_w = ow;
+        first_err = oe;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      if (first_err) set_error(P, g, first_err);
+      atomicOr(&o->pflags, PF_COMPLETE);
+    }
+    __syncwarp();
+  }
+
   __device__ void finish_blocking(int g, DOp* o) {
     const uint32_t k = kw_kind(o->d.kw);
     if (k == K_RECV) {
@@ -1614,7 +1659,162 @@ struct Ctl {
     return prog;
   }
 
+  // stream_physical with one warp per stream: lanes look at 32 operations
+  // at a time for the next blocking one and for the end of the finished prefix.
+  __device__ bool stream_physical_warp(int g, int64_t now) {
+    const int lane = threadIdx.x & 31;
+    SState& S = ss[g];
+    if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return false;
+    bool prog = false;
+    const uint64_t ing = S.ingested;
+    const uint64_t pc0 = S.pc;
+    uint64_t pc = pc0;
+    uint64_t newdone = S.done;
+    while (pc <= ing) {
+      const uint64_t seq = pc + (uint64_t)lane;
+      const bool valid = seq <= ing;
+      const uint32_t k = valid ? kw_kind(op_at(P, g, seq)->d.kw) : 0;
+      const unsigned blk = __ballot_sync(FULL, valid && is_blocking(k));
+      if (!blk) {
+        pc += (uint64_t)__popc(__ballot_sync(FULL, valid));
+        continue;
+      }
+      pc += (uint64_t)(__ffs(blk) - 1);
+      DOp* ob = op_at(P, g, pc);
+      int done = 0;
+      if (lane == 0) done = phys_done(g, ob, pc) ? 1 : 0;
+      done = __shfl_sync(FULL, done, 0);
+      if (!done) break;
+      finish_blocking_warp(g, ob);
+      newdone = pc;
+      ++pc;
+    }
+    const bool advanced = pc != pc0;
+    if (advanced) prog = true;
+    if (newdone != S.done) prog = true;
+    __syncwarp();
+    if (lane == 0) {
+      S.pc = pc;
+      if (newdone != S.done) {
+        S.done = newdone;
+        // payloads were made visible at gpu scope by the movers; order them
+        // before the word the stream's cuStreamWaitValue64 polls
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        st_rlx_sys(&P.done[g], newdone);
+        st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);
+        st_rlx_sys(&P.sctl[g].done, newdone);
+      }
+      if (S.flags & SF_EXCLUSIVE) {
+        S.reached = pc <= ing ? pc : ing;
+      } else {
+        uint64_t db;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
+        S.reached = db;
+      }
+      const bool stalled = pc <= ing && S.reached >= pc;
+      if (stalled) {
+        if (S.stall_t0 == 0 || advanced) S.stall_t0 = now;
+      } else {
+        S.stall_t0 = 0;
+      }
+    }
+    __syncwarp();
+    // retire the finished prefix
+    uint64_t rt = S.retire;
+    uint64_t wlr = S.wl_retired;
+    const uint64_t rlim = S.cursor - 1 < ing ? S.cursor - 1 : ing;  // rt + 1 < cursor, rt < ingested
+    while (rt < rlim) {
+      const uint64_t seq = rt + 1 + (uint64_t)lane;
+      const bool valid = seq <= rlim;
+      const DOp* o = valid ? op_at(P, g, seq) : nullptr;
+      const bool fin = valid && finished(o);
+      const unsigned notfin = __ballot_sync(FULL, valid && !fin);
+      const int cnt = notfin ? __ffs(notfin) - 1 : __popc(__ballot_sync(FULL, valid));
+      const bool wa = valid && lane < cnt && kw_kind(o->d.kw) == K_WAITALL;
+      const unsigned wam = __ballot_sync(FULL, wa);
+      const uint64_t wv = wa ? o->d.aux + (uint64_t)o->d.n32 : 0;
+      if (wam) wlr = __shfl_sync(FULL, wv, 31 - __clz(wam));
+      rt += (uint64_t)cnt;
+      if (notfin) break;
+    }
+    if (rt != S.retire) prog = true;
+    __syncwarp();
+    if (lane == 0 && rt != S.retire) {
+      S.retire = rt;
+      S.wl_retired = wlr;
+      st_rlx_sys(&P.sctl[g].wl_retired, wlr);
+      st_rlx_sys(&P.sctl[g].retired, rt);
+    }
+    __syncwarp();
+    return prog;
+  }
+
   // --- 3b. per stream: schedule deliveries and stage stalled sends ---
+  // One operation of stream g at or below its reached point: create the
+  // delivery of a matched receive whose send is reached (or staged), or pick a
+  // stalled send for staging.  Returns whether the operation needs no more
+  // scheduling.
+  __device__ bool schedule_op(int g, uint64_t seq, int64_t now) {
+    SState& S = ss[g];
+    DOp* o = op_at(P, g, seq);
+    const uint32_t k = kw_kind(o->d.kw);
+    bool settled = true;
+    if (is_recv(k)) {
+      const int32_t f = o->pflags;
+      if (!(f & PF_SCHED)) {
+        settled = false;
+        if (f & PF_MATCHED) {
+          const uint64_t sref = o->partner;
+          DOp* s = op_ref(P, sref);
+          const int32_t sf = *(volatile int32_t*)&s->pflags;
+          if (sf & PF_STAGED) {
+            settled = create_deliver(sref, make_ref(g, seq), true);
+          } else if (!(sf & PF_SCHED)) {
+            const SState& SS = ss[ref_stream(sref)];
+            if (*(volatile uint64_t*)&SS.reached >= ref_seq(sref)) {
+              const int32_t old = atomicOr(&s->pflags, PF_SCHED);
+              if (!(old & PF_SCHED)) {
+                settled = create_deliver(sref, make_ref(g, seq), false);
+                if (!settled) atomicAnd(&s->pflags, ~PF_SCHED);
+              }
+            }
+          }
+        }
+      }
+    } else if (is_send(k)) {
+      const int32_t f = o->pflags;
+      if (!(f & (PF_SCHED | PF_COMPLETE))) {
+        settled = false;
+        // a matched send whose receive has been reached is delivered by the
+        // receive's stream in this phase: staging it would only copy twice
+        bool partner_reached = false;
+        if (f & PF_MATCHED) {
+          const uint64_t rref = o->partner;
+          partner_reached = *(volatile uint64_t*)&ss[ref_stream(rref)].reached >= ref_seq(rref);
+        }
+        // stage when the stream sits at a blocking op at or after this send,
+        // and either the engine as a whole has stopped progressing (the
+        // stall may be a cycle only staging breaks) or the stall has lasted
+        // fifty delays (a bound while other traffic keeps the engine busy)
+        const int64_t stalled = now - S.stall_t0;
+        const bool quiet = now - sm.last_prog >= P.stage_delay_ns;
+        if (!partner_reached && S.stall_t0 != 0 && stalled >= P.stage_delay_ns &&
+            (quiet || stalled >= 50 * P.stage_delay_ns) && seq <= S.pc) {
+          const int32_t old = atomicOr(&o->pflags, PF_SCHED);
+          if (!(old & PF_SCHED)) {
+            const int slot = atomicAdd(&sm.nstage, 1);
+            if (slot < kMaxStagePerTick) {
+              sm.stage_ref[slot] = make_ref(g, seq);
+            } else {
+              atomicAnd(&o->pflags, ~PF_SCHED);
+            }
+          }
+        }
+      }
+    }
+    return settled;
+  }
+
   __device__ void stream_schedule(int g, int64_t now) {
     SState& S = ss[g];
     if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return;
@@ -1622,66 +1822,37 @@ struct Ctl {
     uint64_t sc = S.sched > S.retire ? S.sched : S.retire + 1;
     bool advancing = true;
     for (uint64_t seq = sc; seq <= lim; ++seq) {
-      DOp* o = op_at(P, g, seq);
-      const uint32_t k = kw_kind(o->d.kw);
-      bool settled = true;
-      if (is_recv(k)) {
-        const int32_t f = o->pflags;
-        if (!(f & PF_SCHED)) {
-          settled = false;
-          if (f & PF_MATCHED) {
-            const uint64_t sref = o->partner;
-            DOp* s = op_ref(P, sref);
-            const int32_t sf = *(volatile int32_t*)&s->pflags;
-            if (sf & PF_STAGED) {
-              settled = create_deliver(sref, make_ref(g, seq), true);
-            } else if (!(sf & PF_SCHED)) {
-              const SState& SS = ss[ref_stream(sref)];
-              if (*(volatile uint64_t*)&SS.reached >= ref_seq(sref)) {
-                const int32_t old = atomicOr(&s->pflags, PF_SCHED);
-                if (!(old & PF_SCHED)) {
-                  settled = create_deliver(sref, make_ref(g, seq), false);
-                  if (!settled) atomicAnd(&s->pflags, ~PF_SCHED);
-                }
-              }
-            }
-          }
-        }
-      } else if (is_send(k)) {
-        const int32_t f = o->pflags;
-        if (!(f & (PF_SCHED | PF_COMPLETE))) {
-          settled = false;
-          // a matched send whose receive has been reached is delivered by the
-          // receive's stream in this phase: staging it would only copy twice
-          bool partner_reached = false;
-          if (f & PF_MATCHED) {
-            const uint64_t rref = o->partner;
-            partner_reached = *(volatile uint64_t*)&ss[ref_stream(rref)].reached >= ref_seq(rref);
-          }
-          // stage when the stream sits at a blocking op at or after this send,
-          // and either the engine as a whole has stopped progressing (the
-          // stall may be a cycle only staging breaks) or the stall has lasted
-          // fifty delays (a bound while other traffic keeps the engine busy)
-          const int64_t stalled = now - S.stall_t0;
-          const bool quiet = now - sm.last_prog >= P.stage_delay_ns;
-          if (!partner_reached && S.stall_t0 != 0 && stalled >= P.stage_delay_ns &&
-              (quiet || stalled >= 50 * P.stage_delay_ns) && seq <= S.pc) {
-            const int32_t old = atomicOr(&o->pflags, PF_SCHED);
-            if (!(old & PF_SCHED)) {
-              const int slot = atomicAdd(&sm.nstage, 1);
-              if (slot < kMaxStagePerTick) {
-                sm.stage_ref[slot] = make_ref(g, seq);
-              } else {
-                atomicAnd(&o->pflags, ~PF_SCHED);
-              }
-            }
-          }
-        }
-      }
+      const bool settled = schedule_op(g, seq, now);
       if (advancing && settled) sc = seq + 1;
       else advancing = false;
     }
     S.sched = sc;
+  }
+
+  // The same with one warp per stream: lanes take 32 operations at a time.
+  __device__ void stream_schedule_warp(int g, int64_t now) {
+    const int lane = threadIdx.x & 31;
+    SState& S = ss[g];
+    if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) return;
+    const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+    uint64_t sc = S.sched > S.retire ? S.sched : S.retire + 1;
+    bool advancing = true;
+    for (uint64_t base = sc; base <= lim; base += 32) {
+      const uint64_t seq = base + (uint64_t)lane;
+      const bool settled = seq <= lim ? schedule_op(g, seq, now) : true;
+      const unsigned uns = __ballot_sync(FULL, !settled);
+      if (advancing) {
+        if (uns) {
+          sc = base + (uint64_t)(__ffs(uns) - 1);
+          advancing = false;
+        } else {
+          sc = base + 32 <= lim + 1 ? base + 32 : lim + 1;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) S.sched = sc;
+    __syncwarp();
   }
 
   // thread 0: create staging tasks for the collected sends
@@ -1938,6 +2109,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   }
   __syncthreads();
   C.round = (int64_t)*(volatile uint64_t*)&sh->round;
+  // small worlds: a warp per stream for completion and scheduling (the
+  // per-stream scans are chains of dependent loads); large ones: a thread
+  const bool warp_streams = P.max_streams <= 4 * (int)(blockDim.x >> 5);
   int64_t last_prog = (int64_t)now_ns();
   int64_t idle_since = last_prog;
   if (tid == 0) sm.last_prog = last_prog;
@@ -2097,10 +2271,19 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       int phys = 0, pend = 0;
       if (tid == 0) sm.pending = 0;
       __syncthreads();
-      for (int g = tid; g < P.max_streams; g += blockDim.x) {
-        if (C.stream_physical(g, now)) phys = 1;
-        const SState& S = C.ss[g];
-        if (S.retire < S.ingested) pend = 1;
+      if (warp_streams) {
+        const int warp = tid >> 5, nw = blockDim.x >> 5;
+        for (int g = warp; g < P.max_streams; g += nw) {
+          if (C.stream_physical_warp(g, now)) phys = 1;
+          const SState& S = C.ss[g];
+          if (S.retire < S.ingested) pend = 1;
+        }
+      } else {
+        for (int g = tid; g < P.max_streams; g += blockDim.x) {
+          if (C.stream_physical(g, now)) phys = 1;
+          const SState& S = C.ss[g];
+          if (S.retire < S.ingested) pend = 1;
+        }
       }
       if (phys) atomicOr(&sm.any, 1);
       if (pend) atomicOr(&sm.pending, 1);
@@ -2108,7 +2291,12 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       lap(3);
       if (tid == 0) C.task_phase_begin();
       __syncthreads();
-      for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
+      if (warp_streams) {
+        const int warp = tid >> 5, nw = blockDim.x >> 5;
+        for (int g = warp; g < P.max_streams; g += nw) C.stream_schedule_warp(g, now);
+      } else {
+        for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
+      }
       __syncthreads();
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
