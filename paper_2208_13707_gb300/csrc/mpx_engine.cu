@@ -911,6 +911,16 @@ struct Ctl {
     return any;
   }
 
+  // Bring the next eight operation records of stream g into L1 with
+  // independent prefetches (the scans over them are otherwise one dependent
+  // load per operation); returns the first sequence number not prefetched.
+  __device__ uint64_t prefetch_ops(int g, uint64_t from, uint64_t last) const {
+    uint64_t q = from;
+    for (int j = 0; j < 8 && q <= last; ++j, ++q)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(op_at(P, g, q)));
+    return q;
+  }
+
   // --- 2a. logical advance (thread per stream) ---
   __device__ bool done_before(const DOp* o) const { return o->lstate == 2 && o->lround < round; }
 
@@ -936,7 +946,9 @@ struct Ctl {
     uint64_t cur = S.cursor;
     uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
     const int ndomains_per_comm = P.nranks;
+    uint64_t pf = cur;  // operations below pf have been prefetched
     while (cur <= S.ingested) {
+      if (cur >= pf) pf = prefetch_ops(g, cur, S.ingested);
       DOp* o = op_at(P, g, cur);
       const uint32_t k = kw_kind(o->d.kw);
       if (is_send(k)) {
@@ -978,14 +990,7 @@ struct Ctl {
         break;
       }
       if (k == K_WAITALL) {
-        const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-        const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
-        uint32_t w = o->wscan;
-        while (w < (uint32_t)o->d.n32) {
-          const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
-          if (rs != 0 && !done_before(op_at(P, g, rs))) break;
-          ++w;
-        }
+        const uint32_t w = waitall_scan(g, o, o->wscan, false);
         o->wscan = w;
         if (w >= (uint32_t)o->d.n32) {
           o->lstate = 2;
@@ -1479,6 +1484,40 @@ struct Ctl {
     else write_status(addr, kAnySource, kAnyTag, q->err, 0);
   }
 
+  // First request of waitall `o` at or after w0 that is not yet complete:
+  // logically (completed in an earlier round) or physically (PF_COMPLETE).
+  // Requests are checked eight at a time with independent loads: the list
+  // entries first, then the operations they name.
+  __device__ uint32_t waitall_scan(int g, const DOp* o, uint32_t w0, bool physical) const {
+    const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+    const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
+    const uint32_t n = (uint32_t)o->d.n32;
+    uint32_t w = w0;
+    while (w < n) {
+      uint64_t rs[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        rs[j] = w + j < n ? (uint64_t)wl[(o->d.aux + w + j) & wl_mask] : 0;
+      bool ok[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (w + j >= n || rs[j] == 0) {
+          ok[j] = true;
+        } else {
+          const DOp* q = op_at(P, g, rs[j]);
+          ok[j] = physical ? (q->pflags & PF_COMPLETE) != 0 : done_before(q);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (w >= n) return n;
+        if (!ok[j]) return w;
+        ++w;
+      }
+    }
+    return w;
+  }
+
   __device__ bool phys_done(int g, DOp* o, uint64_t seq) {
     const uint32_t k = kw_kind(o->d.kw);
     if (k == K_SEND || k == K_RECV || k == K_ALLREDUCE) return (o->pflags & PF_COMPLETE) != 0;
@@ -1487,14 +1526,7 @@ struct Ctl {
       return (op_at(P, g, o->d.aux)->pflags & PF_COMPLETE) != 0;
     }
     if (k == K_WAITALL) {
-      const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-      const int64_t* wl = P.wl_dev + ((size_t)g << P.wl_log2);
-      uint32_t w = o->pscan;
-      while (w < (uint32_t)o->d.n32) {
-        const uint64_t rs = (uint64_t)wl[(o->d.aux + w) & wl_mask];
-        if (rs != 0 && !(op_at(P, g, rs)->pflags & PF_COMPLETE)) break;
-        ++w;
-      }
+      const uint32_t w = waitall_scan(g, o, o->pscan, true);
       o->pscan = w;
       return w >= (uint32_t)o->d.n32;
     }
@@ -1598,7 +1630,9 @@ struct Ctl {
     // completion word: blocking ops complete in order
     uint64_t pc = S.pc;
     uint64_t newdone = S.done;
+    uint64_t pf = pc;
     while (pc <= S.ingested) {
+      if (pc >= pf) pf = prefetch_ops(g, pc, S.ingested);
       DOp* o = op_at(P, g, pc);
       const uint32_t k = kw_kind(o->d.kw);
       if (!is_blocking(k)) {
@@ -1643,7 +1677,9 @@ struct Ctl {
     // retire in order
     uint64_t rt = S.retire;
     uint64_t wlr = S.wl_retired;
+    uint64_t rpf = rt + 1;
     while (rt < S.ingested && rt + 1 < S.cursor) {
+      if (rt + 1 >= rpf) rpf = prefetch_ops(g, rt + 1, S.ingested);
       const DOp* o = op_at(P, g, rt + 1);
       if (!finished(o)) break;
       if (kw_kind(o->d.kw) == K_WAITALL) wlr = o->d.aux + (uint64_t)o->d.n32;
@@ -1821,7 +1857,9 @@ struct Ctl {
     const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
     uint64_t sc = S.sched > S.retire ? S.sched : S.retire + 1;
     bool advancing = true;
+    uint64_t pf = sc;
     for (uint64_t seq = sc; seq <= lim; ++seq) {
+      if (seq >= pf) pf = prefetch_ops(g, seq, lim);
       const bool settled = schedule_op(g, seq, now);
       if (advancing && settled) sc = seq + 1;
       else advancing = false;
