@@ -489,7 +489,10 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
                      "rounds": int(ctr[6]), "ticks": int(ctr[1]), "staged_sends": int(ctr[5]),
                      "control_ms_by_phase": {k: ctr[12 + i] / 1e6 for i, k in enumerate(
                          ["ingest", "rounds", "finished_tasks", "completion", "scheduling",
-                          "decisions", "own_moves"])}}
+                          "decisions", "own_moves"])},
+                     "control_ms_split": {k: ctr[19 + i] / 1e6 for i, k in enumerate(
+                         ["advance", "matching", "collectives", "stream_scheduling",
+                          "reduce_and_stage"])}}
     # the same step recorded once and replayed as a CUDA graph
     gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120,
                          cfg_over={"ring_slots": 4096, "queue_slots": 4096})
@@ -632,7 +635,10 @@ def halo_bench(steps=100, warmup=5, sub=256):
             "ticks_per_step": ctr[11] / steps, "rounds": int(ctr[6]), "staged_sends": int(ctr[5]),
             "control_us_per_step_by_phase": {k: ctr[12 + i] / 1e3 / steps for i, k in enumerate(
                 ["ingest", "rounds", "finished_tasks", "completion", "scheduling", "decisions",
-                 "own_moves"])}}
+                 "own_moves"])},
+            "control_us_per_step_split": {k: ctr[19 + i] / 1e3 / steps for i, k in enumerate(
+                ["advance", "matching", "collectives", "stream_scheduling", "reduce_and_stage"])},
+            "rounds_per_tick_with_rounds": ctr[24] / max(1, ctr[25])}
 
 
 def serving(requests=100000):

@@ -211,8 +211,11 @@ int mpx_world_get_error(mpx_world_t world, int* first_error);
  * data task, [9] first task to all tasks done, [10] last task to exit;
  * [11] control ticks; control-tick time by phase in ns: [12] ingest,
  * [13] logical rounds, [14] finished tasks, [15] per-stream completion,
- * [16] scheduling, [17] decisions, [18] the control CTA's own data movement.
- * n is the array length (<= 19 filled). */
+ * [16] scheduling, [17] decisions, [18] the control CTA's own data movement;
+ * finer, in ns: [19] stream advance, [20] matching, [21] collectives (parts
+ * of [13]), [22] per-stream scheduling, [23] reductions and staging (parts of
+ * [16]); [24] logical rounds run, [25] ticks that ran rounds.
+ * n is the array length (<= 26 filled). */
 int mpx_world_get_counters(mpx_world_t world, int64_t* out, int n);
 
 /* MPIX_Stream_create (§3.1) for virtual rank `rank`, backed by a CUDA

@@ -2159,6 +2159,15 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   const uint64_t alloc0 = *(volatile uint64_t*)&sh->task_alloc;
   int64_t t_first_task = 0, t_tasks_done = 0;
   uint64_t tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint64_t sub[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // finer split (thread 0)
+  uint64_t ts = 0;
+  auto mark = [&](int k) {  // thread 0: time since the last mark into sub[k]
+    if (tid == 0) {
+      const uint64_t t = now_ns();
+      if (k >= 0) sub[k] += t - ts;
+      ts = t;
+    }
+  };
   // the host-written `failed` word is polled every few ticks (it only changes
   // on a watchdog or mpx_world_abort); logical rounds run only after new
   // descriptors arrived (physical events never change matching)
@@ -2203,11 +2212,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       __syncthreads();
     } else if (sm.dirty) {
       if (tid == 0) sm.dirty = 0;
+      if (tid == 0) ++sub[6];
       // 2. logical rounds
       for (int r = 0; r < kMaxRoundsPerTick; ++r) {
         if (tid == 0) sm.flag = 0;
         for (int g = tid; g < P.max_streams; g += blockDim.x) sm.cnt[g] = 0;
         __syncthreads();
+        mark(-1);
+        if (tid == 0) ++sub[5];
         int local_any = 0, local_left = 0;
         for (int g = tid; g < P.max_streams; g += blockDim.x) {
           SState& S = C.ss[g];
@@ -2220,6 +2232,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (local_any) atomicOr(&sm.flag, 1);
         if (local_left) atomicOr(&sm.left, 1);
         __syncthreads();
+        mark(0);
         const bool moved = sm.flag != 0;
         if (moved) {
           const int warp = tid >> 5, nw = blockDim.x >> 5;
@@ -2239,9 +2252,11 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
           }
           __syncthreads();
         }
+        mark(1);
         if (tid == 0) sm.nposts_round = 0;
         if (sm.arrivals) C.collectives();
         __syncthreads();
+        mark(2);
         if (tid == 0) {
           sm.arrivals = 0;
           sh->round = (uint64_t)(C.round + 1);
@@ -2329,6 +2344,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       lap(3);
       if (tid == 0) C.task_phase_begin();
       __syncthreads();
+      mark(-1);
       if (warp_streams) {
         const int warp = tid >> 5, nw = blockDim.x >> 5;
         for (int g = warp; g < P.max_streams; g += nw) C.stream_schedule_warp(g, now);
@@ -2336,10 +2352,12 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
       }
       __syncthreads();
+      mark(3);
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
       __syncthreads();
       if (tid == 0) C.task_phase_end();
+      mark(4);
       lap(4);
     }
     // 4. bookkeeping and exit decisions (thread 0)
@@ -2424,6 +2442,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     atomicAdd((unsigned long long*)&P.wctl->phase[3], (unsigned long long)ticks);
     atomicAdd((unsigned long long*)&P.wctl->counters[1], (unsigned long long)ticks);
     for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->tick_ns[k], (unsigned long long)tacc[k]);
+    for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->sub_ns[k], (unsigned long long)sub[k]);
     st_rel_gpu32(&sh->exit_flag, 1);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }

@@ -626,11 +626,12 @@ extern "C" int mpx_world_get_error(mpx_world_t w, int* err) {
 
 extern "C" int mpx_world_get_counters(mpx_world_t w, int64_t* outv, int n) {
   if (!w || !outv || n < 0) return MPX_ERR_ARG;
-  for (int i = 0; i < n && i < 19; ++i) {
-    if (w->plain) outv[i] = plain::counter(w->plain, i);
+  for (int i = 0; i < n && i < 26; ++i) {
+    if (w->plain) outv[i] = i < 19 ? plain::counter(w->plain, i) : 0;
     else if (i < 8) outv[i] = (int64_t)__atomic_load_n(&w->wctl->counters[i], __ATOMIC_ACQUIRE);
     else if (i < 12) outv[i] = (int64_t)__atomic_load_n(&w->wctl->phase[i - 8], __ATOMIC_ACQUIRE);
-    else outv[i] = (int64_t)__atomic_load_n(&w->wctl->tick_ns[i - 12], __ATOMIC_ACQUIRE);
+    else if (i < 19) outv[i] = (int64_t)__atomic_load_n(&w->wctl->tick_ns[i - 12], __ATOMIC_ACQUIRE);
+    else outv[i] = (int64_t)__atomic_load_n(&w->wctl->sub_ns[i - 19], __ATOMIC_ACQUIRE);
   }
   return MPX_SUCCESS;
 }

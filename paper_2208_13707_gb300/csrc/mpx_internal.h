@@ -85,7 +85,10 @@ struct alignas(128) WorldCtl {
   // D->H control-tick time by phase, summed (ns): ingest, rounds, finished
   // tasks, per-stream completion, scheduling, decision, own data movement
   uint64_t tick_ns[8];
-  int32_t pad[8];
+  // D->H finer split, summed (ns unless noted): stream advance, matching,
+  // collectives (inside rounds); per-stream scheduling, reductions and staging
+  // (inside scheduling); [5] rounds run, [6] ticks that ran rounds
+  uint64_t sub_ns[8];
 };
 static_assert(offsetof(WorldCtl, counters) == 128, "engine-updated words on their own lines");
 

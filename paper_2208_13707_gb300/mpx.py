@@ -191,8 +191,8 @@ def mpx_world_get_error(world: int) -> int:
 
 
 def mpx_world_get_counters(world: int) -> list:
-    a = (_i64 * 19)()
-    _chk(lib.mpx_world_get_counters(world, a, 19), "mpx_world_get_counters")
+    a = (_i64 * 26)()
+    _chk(lib.mpx_world_get_counters(world, a, 26), "mpx_world_get_counters")
     return list(a)
 
 
