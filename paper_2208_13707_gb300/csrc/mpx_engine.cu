@@ -1027,12 +1027,7 @@ struct Ctl {
     S.cursor = cur;
     S.nposts = n;
     sm.cnt[g] = n;
-    if (P.cnt2 && n) {
-      const int nd = P.max_comms * P.nranks;
-      int32_t* row = P.cnt2 + (size_t)g * nd;
-      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] += 1;
-      atomicAdd(&sm.nposts_round, n);
-    }
+    if (n) atomicAdd(&sm.nposts_round, n);
     if (moved) sm.any = 1;
     return moved;
   }
@@ -1198,12 +1193,19 @@ struct Ctl {
     }
   }
 
-  // Stable counting sort of this round's posts by domain (counts per
-  // (stream, domain) were taken while posting).
+  // Stable counting sort of this round's posts by domain.
   __device__ void sort_posts() {
     __shared__ int64_t part[kMaxCtaThreads];
     const int nd = P.max_comms * P.nranks;
     const int nt = blockDim.x, t = threadIdx.x;
+    // posts per (stream, domain)
+    for (int g = t; g < P.max_streams; g += nt) {
+      const int n = sm.cnt[g];
+      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      int32_t* row = P.cnt2 + (size_t)g * nd;
+      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] += 1;
+    }
+    __syncthreads();
     // each thread owns a contiguous chunk of domains: per domain, the
     // exclusive prefix over streams (in place) and the domain's total
     const int chunk = (nd + nt - 1) / nt;
@@ -1333,10 +1335,11 @@ struct Ctl {
     return &P.tasks[id & ((1ull << P.tq_log2) - 1)];
   }
   // The claim word carries id+1 in its high half, so a zeroed or recycled
-  // slot never looks published for this id.
+  // slot never looks published for this id.  Its release store orders the
+  // task's fields before it; a mover's claim (an RMW on the word) followed by
+  // its fence reads them.
   __device__ void task_publish(Task* T, uint64_t id) {
     T->tiles_done = 0;
-    __threadfence();
     st_rel_gpu(&T->claim, claim_word(id, T->ntiles));
   }
 
@@ -2245,10 +2248,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
             C.clear_counts();
           } else {
             for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
-            if (P.cnt2 && sm.nposts_round > 0) {
-              __syncthreads();
-              C.clear_counts();
-            }
           }
           __syncthreads();
         }
