@@ -43,6 +43,25 @@ WORKLOAD = ("ring exchange: 8 virtual ranks x 1 stream, fp32 axpy n=2^24 per ran
             "half MPI_Type_vector(blocklen 64, stride 128)")
 
 
+def whole_job(seconds, units, dist=None, device="cpu"):
+    """Replicas: the job's time is the slowest rank's (all-reduce MAX), its
+    value the units every rank processed divided by that time.  Returns
+    (seconds, units per second)."""
+    import torch
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+        u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = float(u.item())
+    else:
+        units = float(units) * world
+    return seconds, units / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -887,13 +906,8 @@ def main():
     sampler.start()
     res = b.run(args.warmup, args.steps)
     clocks = sampler.stop()
-    total_s = res["total_ms"] / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
     msgs_rank = 2 * b.R * args.steps
-    value = msgs_rank * world_size / total_s
+    total_s, value = whole_job(res["total_ms"] / 1e3, msgs_rank, dist, "cuda")
     payload_gbs = 2 * res["payload"] * world_size / total_s / 1e9
     peak, peak_kind = peaks()
     pass_s = sum(res["pass_ms"]) / 1e3

@@ -195,7 +195,10 @@ int mpx_world_progress(mpx_world_t world, mpx_cuda_stream_t stream);
 /* Failure recovery: mark the world failed and release every CUDA stream that
  * waits on an operation of this world (from the host, without the engine).
  * Pending operations complete with MPX_ERR_TIMEOUT and move no data; later
- * enqueue calls return MPX_ERR_STATE.  Use it when a deadline passes. */
+ * enqueue calls return MPX_ERR_STATE.  Use it when a deadline passes.  The
+ * engine writes the released operations' statuses and retires them: a
+ * running persistent engine at once, in DRAIN mode the next
+ * mpx_world_progress pass (streams can be freed after that). */
 int mpx_world_abort(mpx_world_t world);
 
 /* Diagnostic: print the engine's per-stream cursors and task-ring state to
