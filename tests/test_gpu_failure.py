@@ -32,7 +32,11 @@ def _world(mpx, torch, mode, watchdog_ns):
     return w, raw, cs, ms, comm
 
 
-def _teardown(mpx, w, raw, ms, comm):
+def _teardown(mpx, w, raw, ms, comm, cs=None):
+    if cs is not None and not all(c.query() for c in cs):
+        mpx.mpx_world_abort(w)  # never leave a stream waiting
+        for c in cs:
+            _wait_idle(c, 10.0)
     for c in comm:
         mpx.mpx_comm_free(c)
     for s in ms:
@@ -73,7 +77,7 @@ def test_watchdog_releases_a_receive_nobody_sends():
         assert e.value.code == mpx.ERR_STATE
         assert np.all(buf.cpu().numpy() == 0), "a released receive moved data"
     finally:
-        _teardown(mpx, w, raw, ms, comm)
+        _teardown(mpx, w, raw, ms, comm, cs)
 
 
 def test_host_abort_releases_waiting_streams():
@@ -91,7 +95,7 @@ def test_host_abort_releases_waiting_streams():
         assert _status(torch, st)["error"] == mpx.ERR_TIMEOUT
         assert mpx.mpx_world_get_error(w) == mpx.ERR_TIMEOUT
     finally:
-        _teardown(mpx, w, raw, ms, comm)
+        _teardown(mpx, w, raw, ms, comm, cs)
 
 
 def test_drain_pass_returns_with_an_unmatched_receive():
@@ -115,4 +119,4 @@ def test_drain_pass_returns_with_an_unmatched_receive():
         assert _wait_idle(cs[2], 10.0)
         assert mpx.mpx_stream_pending(ms[1]) == 0
     finally:
-        _teardown(mpx, w, raw, ms, comm)
+        _teardown(mpx, w, raw, ms, comm, cs)
