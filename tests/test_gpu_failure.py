@@ -39,6 +39,10 @@ def _teardown(mpx, w, raw, ms, comm, cs=None):
             _wait_idle(c, 10.0)
     for c in comm:
         mpx.mpx_comm_free(c)
+    # the engine retires released operations shortly after they were released
+    t_dl = time.perf_counter() + 10.0
+    while any(mpx.mpx_stream_pending(s) for s in ms) and time.perf_counter() < t_dl:
+        time.sleep(1e-3)
     for s in ms:
         mpx.mpx_stream_free(s)
     mpx.mpx_world_free(w)
@@ -92,8 +96,12 @@ def test_host_abort_releases_waiting_streams():
         assert not cs[1].query(), "the receive completed without a sender"
         mpx.mpx_world_abort(w)
         assert _wait_idle(cs[1], 10.0), "abort did not release the stream"
-        assert _status(torch, st)["error"] == mpx.ERR_TIMEOUT
         assert mpx.mpx_world_get_error(w) == mpx.ERR_TIMEOUT
+        # the resident engine writes the released receive's status
+        t_dl = time.perf_counter() + 10.0
+        while _status(torch, st)["error"] != mpx.ERR_TIMEOUT and time.perf_counter() < t_dl:
+            time.sleep(1e-3)
+        assert _status(torch, st)["error"] == mpx.ERR_TIMEOUT
     finally:
         _teardown(mpx, w, raw, ms, comm, cs)
 
