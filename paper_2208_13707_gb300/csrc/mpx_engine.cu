@@ -225,6 +225,7 @@ struct CtaShared {
   uint32_t t_avail;       // control: free task slots then
   uint32_t t_used;        // control: task ids handed out in this phase
   int64_t last_prog;      // control: time of the last tick that changed anything
+  int32_t released;       // control: this launch released every waiter of a failed world
   uint64_t scan_a, scan_b;  // control: parallel first-failure scans
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
@@ -2136,6 +2137,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   }
   if (tid == 0) {
     sm.limits_reached = 0;
+    sm.released = 0;
     sm.nposts_round = 0;
     sm.arrivals = 0;
     sm.ready_insts = 0;
@@ -2213,6 +2215,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
       release_all(P, C.ss, kErrTimeout);
       __syncthreads();
+      if (tid == 0) sm.released = 1;
     } else if (sm.dirty) {
       if (tid == 0) sm.dirty = 0;
       if (tid == 0) ++sub[6];
@@ -2374,7 +2377,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       const bool new_in_ring = false;  // rings were drained at the start of this tick
       if (pending || new_in_ring || any) idle_since = now;
       if (!any && !tasks_live) sm.failed = ld_vol32(&P.wctl->failed);
-      if (sm.failed && !tasks_live && !new_in_ring) decision = 1;
+      // a failed world leaves once its waiters were released by this kernel
+      if (sm.failed && sm.released && !tasks_live && !new_in_ring) decision = 1;
       if (!decision && pending && !any && now - last_prog > P.watchdog_ns) {
         // nothing moved for too long: fail the pending work and release waiters
         atomicCAS(&P.wctl->error, 0, kErrTimeout);
@@ -2411,6 +2415,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     if (sm.flag == 2) {
       if (tid == 0) abandon_tasks(P);
       release_all(P, C.ss, kErrTimeout);
+      if (tid == 0) sm.released = 1;
       __syncthreads();
       continue;
     }
