@@ -230,6 +230,7 @@ struct CtaShared {
   int32_t scanned;        // control: the tails were read at least once in this launch
   uint64_t last_pub;      // control: publication count at the last scan
   uint64_t scan_a, scan_b;  // control: parallel first-failure scans
+  uint64_t r0;              // control: task_retire at the start of the retirement scan
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
@@ -2327,7 +2328,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         const uint64_t head = ld_acq_gpu(&sh->task_head);
         uint64_t lim = a < head ? a : head;
         if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
-        sm.t_retire = r0;
+        sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
         sm.scan_b = lim;
       }
       __syncthreads();
@@ -2340,7 +2341,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
             atomicMin((unsigned long long*)&sm.scan_a, (unsigned long long)pos);
             break;
           }
-        const uint64_t r0 = sm.t_retire, lim = sm.scan_b;
+        const uint64_t r0 = sm.r0, lim = sm.scan_b;
         for (uint64_t id = r0 + tid; id < lim; id += blockDim.x) {
           const Task& T = P.tasks[id & mask];
           if (T.type != 0 || claim_idp(T.claim) != id_tag(id)) {
