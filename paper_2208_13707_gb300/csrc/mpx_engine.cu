@@ -224,7 +224,7 @@ struct CtaShared {
   uint64_t t_base;        // control: task_alloc at the start of the scheduling phase
   uint32_t t_avail;       // control: free task slots then
   uint32_t t_used;        // control: task ids handed out in this phase
-  int64_t last_prog;      // control: time of the last tick that changed anything
+  int64_t last_prog;      // control: last time a tick changed anything or tasks were in flight
   int32_t released;       // control: this launch released every waiter of a failed world
   int32_t scan;           // control: read the tails this tick
   int32_t scanned;        // control: the tails were read at least once in this launch
@@ -2073,6 +2073,11 @@ struct Ctl {
   }
 };
 
+// Tasks allocated and not yet retired (movers may be working on them).
+__device__ __forceinline__ bool tasks_live_now(const EngineParams& P) {
+  return *(volatile uint64_t*)&P.sh->task_retire != *(volatile uint64_t*)&P.sh->task_alloc;
+}
+
 // Release every stream's waiters without moving data (watchdog / failed world).
 __device__ void release_all(const EngineParams& P, SState* ss, int err) {
   for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
@@ -2404,7 +2409,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       int decision = 0;  // 0 continue, 1 exit
       const bool any = sm.any != 0;
       if (any) last_prog = now;
-      sm.last_prog = last_prog;
+      // staging reads "the engine is quiet" as: no tick changed anything and
+      // no task is in flight for as long as the staging delay
+      if (any || tasks_live_now(P)) sm.last_prog = now;
       const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
       const uint64_t rt = sh->task_retire;
       const bool tasks_live = rt != a;
