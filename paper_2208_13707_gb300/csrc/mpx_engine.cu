@@ -226,9 +226,6 @@ struct CtaShared {
   uint32_t t_used;        // control: task ids handed out in this phase
   int64_t last_prog;      // control: last time a tick changed anything or tasks were in flight
   int32_t released;       // control: this launch released every waiter of a failed world
-  int32_t scan;           // control: read the tails this tick
-  int32_t scanned;        // control: the tails were read at least once in this launch
-  uint64_t last_pub;      // control: publication count at the last scan
   uint64_t scan_a, scan_b;  // control: parallel first-failure scans
   uint64_t r0;              // control: task_retire at the start of the retirement scan
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
@@ -845,16 +842,6 @@ struct Ctl {
   __device__ bool ingest() {
     // a drain pass with limits has nothing more to poll once it reached them
     if (P.nlimit > 0 && sm.limits_reached) return false;
-    // the tails are read only when the publication count moved since the
-    // last scan (the host bumps it after releasing a tail)
-    if (threadIdx.x == 0) {
-      const uint64_t pub = ld_acq_sys(&P.wctl->pub);
-      sm.scan = pub != sm.last_pub || !sm.scanned;
-      sm.last_pub = pub;
-      sm.scanned = 1;
-    }
-    __syncthreads();
-    if (!sm.scan) return false;
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
       SState& S = ss[g];
       const uint4 line = ld_vol16(&P.sctl[g].tail);  // tail, flags, rank
@@ -2157,8 +2144,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   if (tid == 0) {
     sm.limits_reached = 0;
     sm.released = 0;
-    sm.scanned = 0;
-    sm.last_pub = 0;
     sm.nposts_round = 0;
     sm.arrivals = 0;
     sm.ready_insts = 0;
@@ -2469,8 +2454,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       run_claimed(P, sm, buf);
     } else if (!sm.any && !sm.tasks_live) {
       if (tid == 0) __nanosleep(1000);
-    } else if (!full) {
-      if (tid == 0) __nanosleep(300);
     }
     __syncthreads();
     lap(6);

@@ -912,7 +912,6 @@ static int announce(mpx_stream_s* s, uint64_t seq) {
   mpx_world_s* w = s->w;
   s->owed = 0;
   __atomic_store_n(&w->sctl[s->id].tail, seq, __ATOMIC_RELEASE);
-  __atomic_fetch_add(&w->wctl->pub, 1, __ATOMIC_SEQ_CST);
   // launch the engine (persistent mode) before a later wait can stall a
   // hardware queue the engine's stream might share
   int erc = ensure_engine(w);

@@ -76,11 +76,7 @@ struct alignas(128) WorldCtl {
   int32_t stop;       // H->D exit when idle
   int32_t error;      // D->H first world error
   int32_t failed;     // D->H watchdog fired: operations are released without data
-  int32_t pad0[28];
-  // H->D publication count: bumped after every tail release, so the engine
-  // polls one line per tick and reads the streams' tails only when it moved
-  uint64_t pub;
-  uint64_t pad_pub[15];  // the engine updates the words below all the time
+  int32_t pad0[28];   // the engine updates the words below all the time
   uint64_t counters[8];
   uint64_t heartbeat;  // D->H globaltimer of the last engine tick
   // D->H phase times summed over launches (ns): start->first task,
@@ -94,8 +90,7 @@ struct alignas(128) WorldCtl {
   // (inside scheduling); [5] rounds run, [6] ticks that ran rounds
   uint64_t sub_ns[8];
 };
-static_assert(offsetof(WorldCtl, pub) == 128, "publication count on its own line");
-static_assert(offsetof(WorldCtl, counters) == 256, "engine-updated words on their own lines");
+static_assert(offsetof(WorldCtl, counters) == 128, "engine-updated words on their own lines");
 
 // ---------------------------------------------------------------------------
 // device-side state

@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(256) step_post_kernel(EngineParams P, const De
     __threadfence_system();
     const uint64_t tail = base + (uint64_t)S.nops;
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(&P.sctl[g].tail), "l"(tail) : "memory");
-    atomicAdd_system((unsigned long long*)&P.wctl->pub, 1ull);
     cnt_seq[g] = tail;
     cnt_wl[g] = wlb + (uint64_t)S.nwl;
   }
