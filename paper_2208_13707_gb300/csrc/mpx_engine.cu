@@ -2163,7 +2163,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   const bool warp_streams = P.max_streams <= 4 * (int)(blockDim.x >> 5);
   int64_t last_prog = (int64_t)now_ns();
   int64_t idle_since = last_prog;
-  int64_t last_full = 0;  // time of the last tick that ran every phase
   if (tid == 0) sm.last_prog = last_prog;
   uint64_t ticks = 0;
   // phase timing (thread 0): first task seen, last time tasks drained
@@ -2214,28 +2213,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       sm.dirty = 1;
     }
     __syncthreads();
-    // Quiet tick: nothing the later phases react to has changed (no new
-    // operations, no logical work, no finished task, no doorbell moved) and
-    // the last full tick is recent (staging and allreduce scheduling also
-    // depend on time).  Then only the decisions run, so the engine notices
-    // the next event within a short poll rather than a full tick.
-    int changed = ing || sm.dirty || sm.failed || (int64_t)(now - last_full) >= P.stage_delay_ns;
-    if (!changed) {
-      for (int g = tid; g < P.max_streams; g += blockDim.x) {
-        const SState& S = C.ss[g];
-        if (!(S.flags & SF_ACTIVE) || (S.flags & SF_EXCLUSIVE)) continue;
-        uint64_t db;
-        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
-        if (db != S.reached) changed = 1;
-      }
-      if (tid == 0 && ld_acq_gpu(&sh->cq_tail) != sh->cq_head) changed = 1;
-    }
-    const bool full = __syncthreads_or(changed) != 0;
-    if (full) last_full = now;
     lap(0);
-    if (!full) {
-      // decisions only
-    } else if (sm.failed) {
+    if (sm.failed) {
       if (tid == 0) {
         sm.pending = 0;
         abandon_tasks(P);
@@ -2301,7 +2280,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     }
     lap(1);
-    if (full && !sm.failed) {
+    if (!sm.failed) {
       // 3. finished tasks, then per-stream completion and retirement
       if (tid == 0) {
         sm.t_retire = sh->cq_head;
