@@ -177,6 +177,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Wait for an mbarrier phase, bounded by SM cycles (about one second at the
+// GB300's clocks; the SM cycle counter does not jump like %globaltimer can).
+constexpr long long kTmaWaitCycles = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long c0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - c0 > kTmaWaitCycles) return false;
+  return true;
+}
 __device__ __forceinline__ void tma_load_1d(void* sdst, const void* gsrc, uint32_t bytes,
                                             uint64_t* bar) {
   asm volatile(
@@ -412,6 +422,10 @@ __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint6
   // One thread drives the bulk copies through kTmaStages shared-memory
   // stages: up to kTmaLead loads and kTmaStages-kTmaLead stores in flight.
   if (threadIdx.x != 0) return;
+  if (((src | dst | (uint64_t)n) & 15) != 0) {  // bulk copies need 16-byte alignment
+    set_error(P, -1, kErrIntern);
+    return;
+  }
   const uint32_t nch = (uint32_t)((n + kTmaChunk - 1) / kTmaChunk);
   uint32_t phase = sm.phase;
   auto bytes_of = [&](uint32_t j) {
@@ -429,19 +443,16 @@ __device__ void tma_contig_copy(CtaShared& sm, uint8_t* buf, uint64_t dst, uint6
   for (uint32_t j = 0; j < nch; ++j) {
     const uint32_t s = j % kTmaStages;
     const uint32_t par = (phase >> s) & 1u;
-    bool landed = true;
-    if (!mbar_try_wait(&sm.bar[s], par)) {
-      const uint64_t t0 = now_ns();
-      while (!mbar_try_wait(&sm.bar[s], par)) {
-        if (now_ns() - t0 > 50000000ull) {  // a bulk load that never lands: report and give up
-          set_error(P, -1, kErrIntern);
-          landed = false;
-          break;
-        }
+    if (!mbar_wait_bounded(&sm.bar[s], par)) {
+      // a bulk load that does not land: report it, then wait (bounded again)
+      // for every load still in flight into this CTA's stages before leaving
+      set_error(P, -1, kErrIntern);
+      for (uint32_t q = j; q < issued; ++q) {
+        const uint32_t sq = q % kTmaStages;
+        if (mbar_wait_bounded(&sm.bar[sq], (phase >> sq) & 1u)) phase ^= (1u << sq);
       }
-    }
-    if (!landed) {
       tma_wait_all();
+      sm.phase = phase;
       return;
     }
     phase ^= (1u << s);
@@ -646,14 +657,16 @@ __device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* pt
     // the stores of chunk j-2 read this stage's result chunk
     if (tid == 0 && j >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
     const uint32_t par = (phase >> s) & 1u;
-    bool landed = mbar_try_wait(&sm.bar[s], par);
-    if (!landed) {
-      const uint64_t t0 = now_ns();
-      while (!(landed = mbar_try_wait(&sm.bar[s], par)) && now_ns() - t0 < 50000000ull) {
-      }
-    }
-    phase ^= (1u << s);
+    const bool landed = mbar_wait_bounded(&sm.bar[s], par);
+    if (landed) phase ^= (1u << s);
     if (__syncthreads_or(!landed)) {
+      // wait (bounded again) for the loads still in flight, then leave
+      if (tid == 0) {
+        for (uint32_t q = landed ? j + 1 : j; q < nch && q < j + 2; ++q) {
+          const uint32_t sq = q & 1u;
+          if (mbar_wait_bounded(&sm.bar[sq], (phase >> sq) & 1u)) phase ^= (1u << sq);
+        }
+      }
       ok = false;
       break;
     }
@@ -810,8 +823,16 @@ __device__ __forceinline__ uint64_t cq_mask(const EngineParams& P) {
 
 __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
   const Task& T = sm.task;
-  if (T.type == T_COPY) copy_tile(sm, buf, T, sm.claim_tile, P);
-  else if (T.type == T_REDUCE) reduce_tile(sm, buf, T, sm.claim_tile, P);
+  // a task record that does not describe the claimed tile is reported and skipped
+  const bool sane = sm.claim_tile < T.ntiles && T.tile > 0 && T.bytes > 0 &&
+                    (int64_t)sm.claim_tile * T.tile < T.bytes;
+  if (!sane) {
+    if (threadIdx.x == 0) set_error(P, -1, kErrIntern);
+  } else if (T.type == T_COPY) {
+    copy_tile(sm, buf, T, sm.claim_tile, P);
+  } else if (T.type == T_REDUCE) {
+    reduce_tile(sm, buf, T, sm.claim_tile, P);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
