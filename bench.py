@@ -678,6 +678,19 @@ def serving(requests=100000):
     return out
 
 
+def autotune_ring():
+    """Autotuner on the ring exchange's own message sizes (one message per
+    rank and direction for 8 steps: 16 messages per rank, 8 ranks)."""
+    from paper_2208_13707_gb300 import autotune as at
+    sizes = [ring_message(step, 0, d)[0] for step in range(8) for d in (0, 1)]
+    grid = {"tile_bytes": (64 << 10, 256 << 10, 1 << 20), "bulk_min_bytes": (0, 32 << 10),
+            "engine_ctas": (0,), "engine_threads": (256,)}
+    r = at.autotune(sizes, nranks=RANKS, rounds=3, grid=grid)
+    best = [t for t in r.table if t["config"] == r.best][0]
+    return {"best": r.best, "best_gbs": best["gbs"], "trials": len(r.table),
+            "table": [{"config": t["config"], "gbs": t["gbs"]} for t in r.table]}
+
+
 def autotune_report():
     """Autotuner on two samples of the workloads' message mixes: small
     (log-uniform 8 B - 64 KB) and large (log-uniform 4 KB - 64 MB, the ring
@@ -892,7 +905,15 @@ def main():
         return
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    b = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas)
+    # the copy schedule: the autotuner's choice for this workload's message mix
+    # (sizes of the ring's own messages), unless given on the command line
+    sched = {"tile_bytes": args.tile_bytes or None, "engine_ctas": args.engine_ctas, "bulk_min": None}
+    ring_tune = None
+    if not args.no_autotune and not args.tile_bytes and not args.engine_ctas and not args.profile_safe:
+        ring_tune = autotune_ring()
+        sched = {"tile_bytes": ring_tune["best"]["tile_bytes"], "engine_ctas": ring_tune["best"]["engine_ctas"],
+                 "bulk_min": ring_tune["best"]["bulk_min_bytes"]}
+    b = RingBench(**sched)
     if args.profile_safe:
         b.run_profile_safe(args.warmup, args.steps)
         print(json.dumps({"profile_safe": True, "steps": args.steps, "warmup": args.warmup,
@@ -917,14 +938,14 @@ def main():
     e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
     b.close()
     # the same steps through the plain path (host timed: it synchronizes per call)
-    qb = RingBench(tile_bytes=args.tile_bytes or None, plain=True)
+    qb = RingBench(tile_bytes=sched["tile_bytes"], plain=True)
     qres = qb.run_plain(args.warmup, min(args.steps, 50))
     qb.close()
     plain = {"value": 2 * qb.R * min(args.steps, 50) / (qres["total_ms"] / 1e3), "unit": "msgs/s",
              "ms_per_step": qres["total_ms"] / min(args.steps, 50), "steps": min(args.steps, 50),
              "timing": "host clock (the plain path synchronizes the host on every call)"}
     # the same steps with the resident engine (no launch per step)
-    pb = RingBench(tile_bytes=args.tile_bytes or None, engine_ctas=args.engine_ctas, persistent=True)
+    pb = RingBench(**sched, persistent=True)
     pres = pb.run(args.warmup, args.steps)
     pb.mpx.mpx_world_stop(pb.world, 10000)
     pb.close()
@@ -954,6 +975,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "ranks": b.R, "n": b.n, "messages_per_step": 2 * b.R,
+                           "copy_schedule": {k: v for k, v in sched.items()},
+                           "schedule_source": "autotuner" if ring_tune else "defaults / command line",
                            "engine": "drain pass per step (mpx_world_progress after the step's axpys)",
                            "l2": "inputs larger than L2 (>1.5 GB touched per step)",
                            "parallelism": f"replicas x{world_size}"},
@@ -972,6 +995,7 @@ def main():
                 "allreduce_and_halo": c4,
                 "serving": serve,
                 "autotune": tune,
+                "autotune_ring": ring_tune,
                 "speedup_vs_plain": value / plain["value"],
                 "gpu_launches": res["launches"], "clocks": clocks,
                 "engine_phase_us_per_launch": {
