@@ -134,7 +134,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 class RingBench:
     def __init__(self, ranks=RANKS, n=N_AXPY, max_bytes=MAX_BYTES, tile_bytes=None, engine_ctas=0,
-                 bulk_min=None, persistent=False, plain=False):
+                 bulk_min=None, mover_schedule=0, persistent=False, plain=False):
         import torch
         from paper_2208_13707_gb300 import mpx
         self.torch, self.mpx = torch, mpx
@@ -164,6 +164,7 @@ class RingBench:
             cfg.tile_bytes = tile_bytes
         if bulk_min is not None:
             cfg.bulk_min_bytes = bulk_min
+        cfg.mover_schedule = mover_schedule
         self.world = mpx.mpx_world_create(ranks, cfg)
         self.raw = [mpx.mpx_cuda_stream_create() for _ in range(ranks + 1)]
         self.cs = [torch.cuda.ExternalStream(h, device=self.dev) for h in self.raw[:ranks]]
@@ -684,7 +685,7 @@ def autotune_ring():
     from paper_2208_13707_gb300 import autotune as at
     sizes = [ring_message(step, 0, d)[0] for step in range(8) for d in (0, 1)]
     grid = {"tile_bytes": (64 << 10, 256 << 10, 1 << 20), "bulk_min_bytes": (0, 32 << 10),
-            "engine_ctas": (0,), "engine_threads": (256,)}
+            "engine_ctas": (0,), "engine_threads": (256,), "mover_schedule": (0, 1)}
     r = at.autotune(sizes, nranks=RANKS, rounds=3, grid=grid)
     best = [t for t in r.table if t["config"] == r.best][0]
     return {"best": r.best, "best_gbs": best["gbs"], "trials": len(r.table),
@@ -697,15 +698,16 @@ def autotune_report():
     exchange's range); best configuration against the default one."""
     import numpy as np
     from paper_2208_13707_gb300 import autotune as at
-    grid = {"tile_bytes": (16 << 10, 64 << 10, 256 << 10), "bulk_min_bytes": (0, 32 << 10),
-            "engine_ctas": (0, 76), "engine_threads": (256,)}
+    grid = {"tile_bytes": (16 << 10, 64 << 10, 1 << 20), "bulk_min_bytes": (0, 32 << 10),
+            "engine_ctas": (0,), "engine_threads": (256,), "mover_schedule": (0, 1)}
     rng = np.random.default_rng(0x220813707)
     out = {}
     for name, lo, hi, n in (("small_8B_64KB", 8, 64 << 10, 512), ("large_4KB_64MB", 4096, 64 << 20, 16)):
         sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.int64).tolist()
         r = at.autotune(sizes, nranks=8, rounds=3, grid=grid)
         default = [t for t in r.table if t["config"] == {"tile_bytes": 64 << 10, "bulk_min_bytes": 32 << 10,
-                                                          "engine_ctas": 0, "engine_threads": 256}]
+                                                          "engine_ctas": 0, "engine_threads": 256,
+                                                          "mover_schedule": 0}]
         best = [t for t in r.table if t["config"] == r.best][0]
         out[name] = {"best": r.best, "best_gbs": best["gbs"], "best_msgs_per_s": best["msgs_per_s"],
                      "default_gbs": default[0]["gbs"] if default else None, "trials": len(r.table)}
@@ -907,12 +909,14 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     # the copy schedule: the autotuner's choice for this workload's message mix
     # (sizes of the ring's own messages), unless given on the command line
-    sched = {"tile_bytes": args.tile_bytes or None, "engine_ctas": args.engine_ctas, "bulk_min": None}
+    sched = {"tile_bytes": args.tile_bytes or None, "engine_ctas": args.engine_ctas, "bulk_min": None,
+             "mover_schedule": 0}
     ring_tune = None
     if not args.no_autotune and not args.tile_bytes and not args.engine_ctas and not args.profile_safe:
         ring_tune = autotune_ring()
         sched = {"tile_bytes": ring_tune["best"]["tile_bytes"], "engine_ctas": ring_tune["best"]["engine_ctas"],
-                 "bulk_min": ring_tune["best"]["bulk_min_bytes"]}
+                 "bulk_min": ring_tune["best"]["bulk_min_bytes"],
+                 "mover_schedule": ring_tune["best"]["mover_schedule"]}
     b = RingBench(**sched)
     if args.profile_safe:
         b.run_profile_safe(args.warmup, args.steps)
@@ -938,7 +942,7 @@ def main():
     e2e = b.run_e2e(args.warmup, min(args.e2e_steps, args.steps))
     b.close()
     # the same steps through the plain path (host timed: it synchronizes per call)
-    qb = RingBench(tile_bytes=sched["tile_bytes"], plain=True)
+    qb = RingBench(tile_bytes=sched["tile_bytes"], plain=True)  # the plain path has no movers
     qres = qb.run_plain(args.warmup, min(args.steps, 50))
     qb.close()
     plain = {"value": 2 * qb.R * min(args.steps, 50) / (qres["total_ms"] / 1e3), "unit": "msgs/s",

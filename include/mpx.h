@@ -114,6 +114,15 @@ enum {
   MPX_STREAM_EXCLUSIVE = 1
 };
 
+/* how the engine's mover CTAs take copy and reduction tiles
+ * (mpx_world_config_t.mover_schedule) */
+enum {
+  MPX_MOVERS_WORKLIST = 0, /* every mover takes the next tile of the oldest task (large messages
+                              spread over all CTAs) */
+  MPX_MOVERS_PER_CTA = 1   /* mover m owns the tasks whose id is m modulo the mover count and
+                              moves all their tiles (no shared claim point; small messages) */
+};
+
 /* engine modes (mpx_world_config_t.engine_mode) */
 enum {
   MPX_ENGINE_PERSISTENT = 0, /* one cooperative engine kernel stays resident; relaunched on demand */
@@ -154,7 +163,7 @@ typedef struct {
   int32_t tile_bytes;      /* copy tile, multiple of 16 (default 65536) */
   int32_t bulk_min_bytes;  /* contiguous tiles at least this large move by TMA bulk copy (default 32768; 0 = never) */
   int32_t reduce_mode;     /* default allreduce order, MPX_REDUCE_* (default FIXED) */
-  int32_t pad0;
+  int32_t mover_schedule;  /* MPX_MOVERS_* (default WORKLIST) */
   int64_t staging_bytes;   /* eager-send staging arena (default 256 MiB) */
   int64_t budget_bytes;    /* cap on library device memory; 0 = no cap */
   int64_t watchdog_ns;     /* pending work with no progress this long fails with MPX_ERR_TIMEOUT (default 10 s) */

@@ -1,5 +1,6 @@
 """Autotuner for the engine's copy schedule (tile size, the size from which
-contiguous tiles move by TMA bulk copy, engine CTAs and threads per CTA).
+contiguous tiles move by TMA bulk copy, engine CTAs, threads per CTA, and
+whether movers share one work list of tiles or each owns a queue of tasks).
 
 `autotune(sizes)` times each candidate world configuration on a synthetic
 sample of the caller's message mix: R ranks in a ring, every rank isends the
@@ -21,10 +22,11 @@ from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence
 
 DEFAULT_GRID = {
-    "tile_bytes": (16 << 10, 64 << 10, 256 << 10),
+    "tile_bytes": (16 << 10, 64 << 10, 256 << 10, 1 << 20),
     "bulk_min_bytes": (0, 32 << 10, 256 << 10),
     "engine_ctas": (0, 76),
     "engine_threads": (256, 512),
+    "mover_schedule": (0, 1),   # work list / CTA-per-queue (MPX_MOVERS_*)
 }
 
 

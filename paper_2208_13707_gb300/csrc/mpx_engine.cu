@@ -238,6 +238,7 @@ struct CtaShared {
   int32_t released;       // control: this launch released every waiter of a failed world
   uint64_t scan_a, scan_b;  // control: parallel first-failure scans
   uint64_t r0;              // control: task_retire at the start of the retirement scan
+  uint64_t own_next;        // mover (per-CTA schedule): next task id this CTA owns
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
@@ -819,6 +820,41 @@ __device__ bool claim_tile(const EngineParams& P, CtaShared& sm) {
 // appends one entry, and allocation keeps task_alloc - cq_head below it.
 __device__ __forceinline__ uint64_t cq_mask(const EngineParams& P) {
   return (2ull << P.tq_log2) - 1;
+}
+
+// MPX_MOVERS_PER_CTA: mover m (of M) owns the task ids congruent to m modulo
+// M and takes every tile of each in turn; its next id lives in shared memory.
+// Nothing else claims those tasks, so the claim word's fetch-and-add never
+// contends, and task_head is not used.
+__device__ bool claim_tile_own(const EngineParams& P, CtaShared& sm) {
+  if (threadIdx.x == 0) {
+    sm.claim_task = -1;
+    Shared* sh = P.sh;
+    const uint64_t mask = (1ull << P.tq_log2) - 1;
+    const uint64_t M = (uint64_t)(gridDim.x - 1);
+    for (int tries = 0; tries < 4; ++tries) {
+      const uint64_t i = sm.own_next;
+      if (i >= ld_acq_gpu(&sh->task_alloc)) break;
+      Task* T = &P.tasks[i & mask];
+      if (claim_idp(ld_acq_gpu(&T->claim)) != id_tag(i)) break;  // not published yet
+      const uint64_t c = atomicAdd((unsigned long long*)&T->claim, 1ull);
+      const uint32_t idp = claim_idp(c), k = claim_next(c), nt = claim_ntiles(c);
+      if (k + 1 >= nt) sm.own_next = i + M;  // this is the task's last tile (or none is left)
+      if (idp == id_tag(i) && k < nt) {
+        sm.claim_task = (int64_t)(i & mask);
+        sm.claim_tile = k;
+        if (sm.cached_slot != (int64_t)(i & mask) || sm.cached_idp != idp) {
+          __threadfence();
+          sm.task = *T;
+          sm.cached_slot = (int64_t)(i & mask);
+          sm.cached_idp = idp;
+        }
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return sm.claim_task >= 0;
 }
 
 __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
@@ -2315,7 +2351,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         const uint64_t r0 = sh->task_retire;
         const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
         // a slot is reused only after the movers' head has passed its task
-        const uint64_t head = ld_acq_gpu(&sh->task_head);
+        // (per-CTA schedule: its owner read the record before the last tile
+        // finished, so a processed task can be retired at once)
+        const uint64_t head = P.movers_per_cta && gridDim.x > 1 ? a : ld_acq_gpu(&sh->task_head);
         uint64_t lim = a < head ? a : head;
         if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
         sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
@@ -2483,11 +2521,19 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
 
 __device__ void mover_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
   int64_t idle_t0 = 0;
+  const bool own = P.movers_per_cta && gridDim.x > 1;
+  if (own && threadIdx.x == 0) {
+    // the first id at or after the launch's oldest task that this mover owns
+    const uint64_t M = (uint64_t)(gridDim.x - 1), m = (uint64_t)(blockIdx.x - 1);
+    const uint64_t h = P.sh->task_head;
+    sm.own_next = h + ((m + M - (h % M)) % M);
+  }
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) sm.flag = (int32_t)ld_acq_gpu32(&P.sh->exit_flag);
     __syncthreads();
     if (sm.flag) break;
-    if (claim_tile(P, sm)) {
+    if (own ? claim_tile_own(P, sm) : claim_tile(P, sm)) {
       run_claimed(P, sm, buf);
       idle_t0 = 0;
     } else if (threadIdx.x == 0) {

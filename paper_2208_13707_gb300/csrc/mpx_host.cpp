@@ -237,6 +237,7 @@ extern "C" int mpx_world_config_init(mpx_world_config_t* c) {
   c->tile_bytes = (int32_t)env_i64("MPX_TILE_BYTES", 65536);
   c->bulk_min_bytes = (int32_t)env_i64("MPX_BULK_MIN_BYTES", 32768);
   c->reduce_mode = (int32_t)env_i64("MPX_REDUCE_MODE", MPX_REDUCE_FIXED);
+  c->mover_schedule = (int32_t)env_i64("MPX_MOVER_SCHEDULE", MPX_MOVERS_WORKLIST);
   c->staging_bytes = env_i64("MPX_STAGING_BYTES", 256ll << 20);
   c->budget_bytes = env_i64("MPX_BUDGET_BYTES", 0);
   c->watchdog_ns = env_i64("MPX_WATCHDOG_NS", 10ll * 1000 * 1000 * 1000);
@@ -284,6 +285,8 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
     return MPX_ERR_ARG;
   if (cfg.engine_mode < MPX_ENGINE_PERSISTENT || cfg.engine_mode > MPX_ENGINE_PLAIN) return MPX_ERR_ARG;
   if (cfg.staging_bytes < 4096) return MPX_ERR_ARG;
+  if (cfg.mover_schedule != MPX_MOVERS_WORKLIST && cfg.mover_schedule != MPX_MOVERS_PER_CTA)
+    return MPX_ERR_ARG;
 
   mpx_world_s* w = new (std::nothrow) mpx_world_s();
   if (!w) return MPX_ERR_NO_MEM;
@@ -408,6 +411,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.wl_log2 = w->wl_log2;
   P.sr_log2 = w->sr_log2;
   P.ctl_ctas = 1;
+  P.movers_per_cta = cfg.mover_schedule == MPX_MOVERS_PER_CTA ? 1 : 0;
   P.watchdog_ns = cfg.watchdog_ns;
   P.idle_ns = cfg.idle_exit_ns;
   P.stage_delay_ns = cfg.stage_delay_ns;

@@ -27,6 +27,7 @@ SUM = 0
 REDUCE_FIXED, REDUCE_TREE = 0, 1
 STREAM_DEFAULT, STREAM_EXCLUSIVE = 0, 1
 ENGINE_PERSISTENT, ENGINE_DRAIN, ENGINE_PLAIN = 0, 1, 2
+MOVERS_WORKLIST, MOVERS_PER_CTA = 0, 1
 REQUEST_NULL = -1
 IN_PLACE = 1
 ERRORS = {0: "SUCCESS", 1: "ERR_ARG", 2: "ERR_RANK", 3: "ERR_TAG", 4: "ERR_TYPE", 5: "ERR_COMM",
@@ -48,7 +49,7 @@ class WorldConfig(ctypes.Structure):
                 ("queue_slots", ctypes.c_int32), ("task_slots", ctypes.c_int32),
                 ("engine_ctas", ctypes.c_int32), ("engine_threads", ctypes.c_int32),
                 ("tile_bytes", ctypes.c_int32), ("bulk_min_bytes", ctypes.c_int32),
-                ("reduce_mode", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("reduce_mode", ctypes.c_int32), ("mover_schedule", ctypes.c_int32),
                 ("staging_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
                 ("watchdog_ns", ctypes.c_int64), ("idle_exit_ns", ctypes.c_int64),
                 ("stage_delay_ns", ctypes.c_int64)]

@@ -105,3 +105,17 @@ def test_recorded_step_replays_and_returns_streams_to_host_enqueue():
         _check(r, ref)
     finally:
         r.close()
+
+
+def test_per_cta_mover_schedule_matches_the_oracle():
+    """Movers that each own a queue of tasks (MPX_MOVERS_PER_CTA) deliver the
+    same bytes and statuses as the shared work list."""
+    gpu = _gpu()
+    p = _program(nmsg=8000, seed_off=3)
+    ref = oracle.run(p)
+    r = gpu.BatchRunner(p, mode="persistent", cfg_over={"mover_schedule": 1}, timeout_s=60)
+    try:
+        assert r.step()
+        _check(r, ref)
+    finally:
+        r.close()

@@ -60,6 +60,13 @@ def test_ring_exchange_small(mode):
     _compare(p, mode=mode)
 
 
+@pytest.mark.parametrize("schedule", [1])
+def test_ring_exchange_per_cta_movers(schedule):
+    """Multi-tile messages and vector layouts with each mover owning its tasks."""
+    p = gen.ring_exchange(nranks=4, n=1 << 16, steps=3, min_bytes=100_000, max_bytes=3 << 20)
+    _compare(p, mode="drain", cfg_over={"mover_schedule": schedule, "tile_bytes": 16 << 10})
+
+
 def test_ring_exchange_tiles_and_ragged_tail():
     # messages up to 3 MB: many tiles per message, TMA bulk and strided paths
     p = gen.ring_exchange(nranks=4, n=1 << 16, steps=3, min_bytes=100_000, max_bytes=3 << 20)
