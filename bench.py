@@ -466,7 +466,7 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
+def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     """Small-message batching: 64 ranks x 4 MPIX streams (four stream comms),
     `nmsg` messages per step with uniform sources, destinations and tags,
     log-uniform 8 B - 64 KB sizes, mixed uint8/int32/fp32, 5% ANY_TAG and 2%
@@ -475,7 +475,8 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
     one-element allreduce on its comm that separates the steps; steps are
     enqueued back to back and the host waits once at the end.  The plain path
     runs the same step through the same call (host matching, one copy per
-    message, a host synchronization per waitall).  Wall-clock timing."""
+    message, a host synchronization per waitall).  Wall-clock timing.
+    `schedule`: world fields chosen by the autotuner for this message mix."""
     import torch
     from traffic import gen, gpu
     prog = gen.batching(nranks=64, streams_per_rank=4, nmsg=nmsg, max_bytes=64 << 10,
@@ -483,8 +484,10 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
     payload = int(prog.meta["payload_bytes"])
     out = {"messages_per_step": nmsg, "sizes": "log-uniform 8 B - 64 KB",
            "payload_bytes_per_step": payload}
-    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=120,
-                        cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+    over = {"ring_slots": 4096, "queue_slots": 4096}
+    over.update(schedule or {})
+    out["schedule"] = dict(schedule or {})
+    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=120, cfg_over=over)
     try:
         for _ in range(warmup):
             r.enqueue()
@@ -514,8 +517,7 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3):
                          ["advance", "matching", "collectives", "stream_scheduling",
                           "reduce_and_stage"])}}
     # the same step recorded once and replayed as a CUDA graph
-    gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120,
-                         cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+    gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120, cfg_over=over)
     try:
         for _ in range(warmup):
             gr.enqueue()
@@ -958,7 +960,10 @@ def main():
                   "ms_per_step": pres["total_ms"] / args.steps,
                   "payload_gbs": 2 * pres["payload"] / (pres["total_ms"] / 1e3) / 1e9,
                   "p50_us": float(np.percentile(plat, 50)), "p99_us": float(np.percentile(plat, 99))}
-    batching = batching_small(args.batch_steps, args.warmup, args.batch_msgs) if args.batch_msgs else None
+    tune = None if args.no_autotune else autotune_report()
+    small_sched = tune["small_8B_64KB"]["best"] if tune else None
+    batching = (batching_small(args.batch_steps, args.warmup, args.batch_msgs, schedule=small_sched)
+                if args.batch_msgs else None)
     c4 = None
     if not args.no_c4:
         pk, _ = peaks()
@@ -967,7 +972,6 @@ def main():
             e["frac_of_peak"] = e["gbs"] / pk
         c4 = {"allreduce": ar, "halo": halo_bench()}
     serve = serving(args.serve_requests) if args.serve_requests else None
-    tune = None if args.no_autotune else autotune_report()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
