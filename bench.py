@@ -466,6 +466,52 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batching_full(steps=16, warmup=3, nmsg=65536, schedule=None):
+    """The batching workload at its full size: 64 ranks x 4 MPIX streams,
+    steps x nmsg = 1,048,576 messages (16 epochs of 65,536 separated by a
+    one-element allreduce per comm), log-uniform 8 B - 1 MB, uint8/int32/fp32,
+    5 % ANY_TAG / 2 % ANY_SOURCE (laminar).  Persistent engine with batch
+    submission; the plain path runs one epoch.  Payload GB/s counts read +
+    write bytes."""
+    from traffic import gen, gpu
+    prog = gen.batching(nranks=64, streams_per_rank=4, nmsg=nmsg, max_bytes=1 << 20,
+                        laminar=True, seed=gen.SEED_BASE + 2)
+    payload = int(prog.meta["payload_bytes"])
+    over = {"ring_slots": 4096, "queue_slots": 4096}
+    over.update(schedule or {})
+    out = {"messages": nmsg * steps, "epochs": steps, "sizes": "log-uniform 8 B - 1 MB",
+           "payload_bytes": payload * steps, "schedule": dict(schedule or {})}
+    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=300, cfg_over=over)
+    try:
+        for _ in range(warmup):
+            r.enqueue()
+        assert r.finish(), "warm-up epochs did not finish"
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r.enqueue()
+        ok = r.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = r.errors()
+        assert ok and werr == 0 and not any(serr), "epochs failed"
+    finally:
+        r.close()
+    peak, _ = peaks()
+    gbs = 2 * payload * steps / dt / 1e9
+    out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "seconds": dt, "payload_gbs": gbs,
+                     "frac_of_peak": gbs / peak}
+    q = gpu.BatchRunner(prog, mode="plain", timeout_s=600)
+    try:
+        t0 = time.perf_counter()
+        assert q.step(), "plain epoch did not finish"
+        dt = time.perf_counter() - t0
+    finally:
+        q.close()
+    out["plain"] = {"value": nmsg / dt, "unit": "msgs/s", "seconds_per_epoch": dt,
+                    "payload_gbs": 2 * payload / dt / 1e9}
+    out["speedup_vs_plain"] = out["engine"]["value"] / out["plain"]["value"]
+    return out
+
+
 def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     """Small-message batching: 64 ranks x 4 MPIX streams (four stream comms),
     `nmsg` messages per step with uniform sources, destinations and tags,
@@ -854,6 +900,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--batching-only", action="store_true",
                     help="print only the small-message batching measurement")
+    ap.add_argument("--no-batching-full", action="store_true",
+                    help="skip the full-size (10^6 messages, 8 B - 1 MB) batching measurement")
+    ap.add_argument("--batching-full-only", action="store_true",
+                    help="print only the full-size batching measurement")
     ap.add_argument("--allreduce-only", action="store_true",
                     help="print only the allreduce bandwidth sweep and the halo exchange")
     ap.add_argument("--no-c4", action="store_true", help="skip the allreduce sweep and the halo exchange")
@@ -902,6 +952,9 @@ def main():
             e["frac_of_peak"] = e["gbs"] / pk
         print(json.dumps({"allreduce": ar, "halo": halo_bench(), "peak_gbs": pk, "peak_source": pkind}),
               flush=True)
+        return
+    if args.batching_full_only:
+        print(json.dumps({"batching_full": batching_full()}), flush=True)
         return
     if args.batching_only:
         print(json.dumps({"batching_small": batching_small(args.batch_steps, args.warmup,
@@ -964,6 +1017,8 @@ def main():
     small_sched = tune["small_8B_64KB"]["best"] if tune else None
     batching = (batching_small(args.batch_steps, args.warmup, args.batch_msgs, schedule=small_sched)
                 if args.batch_msgs else None)
+    batching_1m = None if args.no_batching_full else batching_full(
+        schedule=tune["large_4KB_64MB"]["best"] if tune else None)
     c4 = None
     if not args.no_c4:
         pk, _ = peaks()
@@ -1000,6 +1055,7 @@ def main():
                 "persistent_engine": persistent,
                 "plain_path": plain,
                 "batching_small": batching,
+                "batching_full": batching_1m,
                 "allreduce_and_halo": c4,
                 "serving": serve,
                 "autotune": tune,
