@@ -499,7 +499,10 @@ def batching_full(steps=16, warmup=3, nmsg=65536, schedule=None):
     gbs = 2 * payload * steps / dt / 1e9
     out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "seconds": dt, "payload_gbs": gbs,
                      "frac_of_peak": gbs / peak}
-    q = gpu.BatchRunner(prog, mode="plain", timeout_s=600)
+    # the plain path stages every send posted before its receive (eager
+    # protocol): give it room for a whole epoch's payload
+    q = gpu.BatchRunner(prog, mode="plain", timeout_s=120,
+                        cfg_over={"staging_bytes": ((2 * payload) >> 20) + 64 << 20})
     try:
         t0 = time.perf_counter()
         assert q.step(), "plain epoch did not finish"

@@ -375,6 +375,9 @@ class BatchRunner:
                 if e.code != mpx.ERR_AGAIN:
                     raise
                 done += e.done
+                if self.mode == mpx.ENGINE_PLAIN and e.done == 0:
+                    # nothing else runs while this thread retries: it cannot clear
+                    raise RuntimeError("plain path cannot proceed (staging arena full?)")
                 if time.perf_counter() > t_dl:
                     raise RuntimeError("batch enqueue made no progress")
                 if self.mode == mpx.ENGINE_DRAIN:
