@@ -21,7 +21,7 @@
  *  - §3.4 (last paragraph): collectives take the same enqueue form; here
  *    SUM allreduce.
  *
- * Readings where the paper is silent (listed with reasons in the design doc):
+ * Readings where the paper is silent:
  *  - Posting is logical and proceeds in rounds.  In round k every stream, in
  *    ascending stream id g, advances past each operation that is not blocked;
  *    sends and receives it passes are posted with key (k, g, program index).
