@@ -403,11 +403,13 @@ int mpx_step_free(mpx_step_t* step);
  * calls between two allreduce instances form an epoch that each thread ends
  * with a waitall.  Items are numbered: messages first, then allreduce
  * instances.  digests (length ndigests, may be NULL) receives, for every
- * sampled item (item % sample_every == 0, or only_item), an
- * order-independent digest of the delivered bytes (rank 0's result for an
- * allreduce); only_item >= 0 runs that item alone, without pacing, so that
- * its digest can be compared with the mix.  Errors: MPX_ERR_ARG,
- * MPX_ERR_NO_MEM, and those of the calls it makes. */
+ * sampled item (item % sample_every == 0, or only_item), a digest of the
+ * delivered bytes (rank 0's result for an allreduce); source_digests (may be
+ * NULL; needs digests) receives, for every sampled message, the same digest
+ * of the payload as its sender holds it, taken after the run; only_item >= 0
+ * runs that item alone, without pacing, so that its digest can be compared
+ * with the mix.  Errors: MPX_ERR_ARG, MPX_ERR_NO_MEM, and those of the calls
+ * it makes. */
 typedef struct {
   int32_t nthreads;
   int32_t engine_mode;   /* MPX_ENGINE_PERSISTENT or MPX_ENGINE_PLAIN */
@@ -438,7 +440,7 @@ typedef struct {
  * Zipf 1.2 over 64 B..16 MB, 30% allreduce, 40 GiB budget. */
 int mpx_serve_config_init(mpx_serve_config_t* cfg);
 int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* result, uint64_t* digests,
-                  int64_t ndigests);
+                  uint64_t* source_digests, int64_t ndigests);
 
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);

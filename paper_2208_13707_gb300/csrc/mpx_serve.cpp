@@ -459,7 +459,7 @@ extern "C" int mpx_serve_config_init(mpx_serve_config_t* c) {
 }
 
 extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* res,
-                             uint64_t* digests, int64_t ndigests) {
+                             uint64_t* digests, uint64_t* source_digests, int64_t ndigests) {
   if (!cfg || !res) return MPX_ERR_ARG;
   const mpx_serve_config_t& c = *cfg;
   if (c.nthreads < 2 || c.nthreads > 1024 || c.requests < 1 || c.min_log2 < 2 ||
@@ -550,6 +550,19 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
     for (auto& x : th) x.join();
     if (!plain) reaper.join();
     rc = S.error.load();
+    // the sampled messages' payloads as their senders hold them (a check that
+    // the bytes were delivered unchanged: equal digests)
+    if (!rc && source_digests && S.dig_dev) {
+      for (int t = 0; t < T; ++t) {
+        for (const Call& x : S.calls[(size_t)t]) {
+          if (x.kind != C_SEND || x.item < 0 || x.item >= ndigests || !digests[x.item]) continue;
+          mpxi_digest_store(S.region[(size_t)t] + x.off, x.bytes, S.dig_dev + x.item, ctx[0].cs);
+        }
+      }
+      cudaStreamSynchronize(ctx[0].cs);
+      for (int64_t i = 0; i < ndigests; ++i)
+        source_digests[i] = digests[i] && i < S.nitems ? S.dig_host[i] : 0;
+    }
     int64_t t_end = 0, completed = 0, bytes = 0;
     std::vector<float> lat, svc;
     for (int k = 0; k <= T; ++k) {

@@ -127,7 +127,7 @@ _SIGS = {
     "mpx_enqueue_batch": [ctypes.c_int, _vp, _P(ctypes.c_int)],
     "mpx_step_create": [_vp, ctypes.c_int, _vp, _P(_vp)],
     "mpx_serve_config_init": [_P(ServeConfig)],
-    "mpx_serve_run": [_P(ServeConfig), _P(ServeResult), _vp, _i64],
+    "mpx_serve_run": [_P(ServeConfig), _P(ServeResult), _vp, _vp, _i64],
     "mpx_step_launch": [_vp, _vp],
     "mpx_step_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_step_free": [_P(_vp)],
@@ -397,14 +397,18 @@ def mpx_serve_config_init() -> ServeConfig:
     return c
 
 
-def mpx_serve_run(cfg: ServeConfig, digests=None) -> dict:
-    """Run the serving loop; `digests` (a uint64 numpy array, optional) receives
-    the sampled items' digests.  Returns the result fields as a dict."""
+def mpx_serve_run(cfg: ServeConfig, digests=None, source_digests=None) -> dict:
+    """Run the serving loop; `digests` / `source_digests` (uint64 numpy arrays
+    of one length, optional) receive the sampled items' digests as delivered
+    and as sent.  Returns the result fields as a dict."""
     import numpy as np
     r = ServeResult()
-    dp, dn = (None, 0)
+    dp, sp, dn = (None, None, 0)
     if digests is not None:
         assert digests.dtype == np.uint64 and digests.flags.c_contiguous
         dp, dn = digests.ctypes.data, len(digests)
-    _chk(lib.mpx_serve_run(ctypes.byref(cfg), ctypes.byref(r), dp, dn), "mpx_serve_run")
+        if source_digests is not None:
+            assert source_digests.dtype == np.uint64 and len(source_digests) == dn
+            sp = source_digests.ctypes.data
+    _chk(lib.mpx_serve_run(ctypes.byref(cfg), ctypes.byref(r), dp, sp, dn), "mpx_serve_run")
     return {k: getattr(r, k) for k, _ in ServeResult._fields_}

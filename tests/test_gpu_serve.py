@@ -49,10 +49,15 @@ def test_serving_mix_alone_and_plain_agree():
     msgs, nar = _counts(c)
     items = msgs + nar
     mix = np.zeros(items, np.uint64)
-    res = mpx.mpx_serve_run(c, mix)
+    src = np.zeros(items, np.uint64)
+    res = mpx.mpx_serve_run(c, mix, src)
     assert res["items"] == items and res["completed"] == 2 * msgs + nar * c.nthreads
     sampled = np.nonzero(mix)[0]
     assert len(sampled) >= 5, "too few sampled items"
+    # every sampled message arrived as its sender holds it
+    p2p = sampled[sampled < msgs]
+    assert len(p2p) >= 3
+    assert np.array_equal(src[p2p], mix[p2p]), "a delivered payload differs from what was sent"
     # plain path: same schedule, same digests
     plain = np.zeros(items, np.uint64)
     mpx.mpx_serve_run(_cfg(mpx, engine_mode=mpx.ENGINE_PLAIN), plain)
