@@ -116,3 +116,32 @@ def test_allreduce_full_size_sampled(dt_name, lg, mode):
         mpx.mpx_world_free(world)
         for h in raw:
             mpx.mpx_cuda_stream_destroy(h)
+
+
+def test_batching_full_size_epoch():
+    """One epoch of the batching configuration at full message sizes: 64
+    ranks x 4 MPIX streams, 65,536 messages of 8 B - 1 MB with ANY_TAG and
+    ANY_SOURCE receives, through the persistent engine with batch submission
+    (the launch configuration the benchmark times).  Every status and the
+    receive buffers of a sample of streams are compared with the oracle."""
+    _torch()
+    from traffic import gpu
+    p = gen.batching(nranks=64, streams_per_rank=4, nmsg=65536, max_bytes=1 << 20,
+                     laminar=True, seed=gen.SEED_BASE + 2)
+    ref = oracle.run(p)
+    assert ref.error == 0 and not ref.deadlock
+    r = gpu.BatchRunner(p, mode="persistent", timeout_s=120,
+                        cfg_over={"ring_slots": 4096, "queue_slots": 4096})
+    try:
+        assert r.step(), "epoch did not finish"
+        serr, werr = r.errors()
+        assert werr == 0 and not any(serr)
+        st = np.frombuffer(r.st.cpu().numpy().tobytes(), ref.status.dtype)[: p.nstatus]
+        assert np.array_equal(st, ref.status), "statuses differ"
+        rng = np.random.default_rng(7)
+        nbuf = len(p.buf_init)
+        for k in sorted(rng.choice(nbuf, size=24, replace=False)):
+            got = r.dbufs[k].cpu().numpy()[: p.buf_init[k].size]
+            assert np.array_equal(got, ref.buffers[k]), f"buffer {k} differs"
+    finally:
+        r.close()
