@@ -51,7 +51,8 @@
 
 namespace {
 
-enum Kind { SEND = 0, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY };
+enum Kind { SEND = 0, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER };
+bool is_collective(int k) { return k == ALLREDUCE || k == BCAST || k == REDUCE || k == ALLGATHER; }
 constexpr int kAnySource = -2;
 constexpr int kAnyTag = -1;
 constexpr int kInPlace = -3;
@@ -274,7 +275,70 @@ struct Oracle {
   static void store(uint8_t* b, int64_t i, T v) { std::memcpy(b + sizeof(T) * i, &v, sizeof(T)); }
 
   // SUM over the R arrivals of one allreduce instance; writes every receive buffer.
-  void run_allreduce(const std::vector<int64_t>& arr, int round) {
+  // The k-th collective call on a communicator from every rank forms one
+  // instance (§3.4: collectives take the enqueue form; MPI: collective calls
+  // on a communicator are ordered).  All arrivals must be the same kind.
+  void run_collective(const std::vector<int64_t>& arr, int round) {
+    const int kind = p.ops[arr[0]].kind;
+    for (int64_t j : arr)
+      if (p.ops[j].kind != kind) { err = 5; return; }
+    if (kind == ALLREDUCE) run_allreduce(arr, round);
+    else if (kind == REDUCE) run_allreduce(arr, round, p.ops[arr[0]].peer);
+    else if (kind == BCAST) run_bcast(arr, round);
+    else run_allgather(arr, round);
+  }
+
+  // MPI_Bcast: the root's count elements replace every other rank's buffer.
+  void run_bcast(const std::vector<int64_t>& arr, int round) {
+    const Op& o0 = p.ops[arr[0]];
+    const int64_t n = o0.count;
+    for (int64_t j : arr) {
+      const Op& o = p.ops[j];
+      if (o.count != n || o.type != o0.type || o.peer != o0.peer) { err = 5; return; }
+    }
+    const int64_t bytes = p.types[o0.type].elem * n;
+    const Op& root = p.ops[arr[(size_t)o0.peer]];
+    if (!in_bounds(root.buf, root.off, bytes)) { err = 6; return; }
+    for (size_t k = 0; k < arr.size(); ++k) {
+      if ((int)k == o0.peer) continue;
+      const Op& o = p.ops[arr[k]];
+      if (!in_bounds(o.buf, o.off, bytes)) { err = 6; return; }
+      std::memcpy(p.bufs[o.buf] + o.off, p.bufs[root.buf] + root.off, (size_t)bytes);
+    }
+    for (int64_t j : arr) r.done_round[j] = round;
+  }
+
+  // MPI_Allgather: rank s's count elements land at block s of every rank's
+  // receive buffer (in place: rank s's block is already there).
+  void run_allgather(const std::vector<int64_t>& arr, int round) {
+    const Op& o0 = p.ops[arr[0]];
+    const int64_t n = o0.count;
+    for (int64_t j : arr) {
+      const Op& o = p.ops[j];
+      if (o.count != n || o.type != o0.type) { err = 5; return; }
+    }
+    const size_t R = arr.size();
+    const int64_t bytes = p.types[o0.type].elem * n;
+    std::vector<std::vector<uint8_t>> block(R);
+    for (size_t s = 0; s < R; ++s) {  // read every contribution before writing any
+      const Op& o = p.ops[arr[s]];
+      const int sb = o.buf == kInPlace ? o.buf2 : o.buf;
+      const int64_t so = o.buf == kInPlace ? o.off2 + (int64_t)s * bytes : o.off;
+      if (!in_bounds(sb, so, bytes)) { err = 6; return; }
+      block[s].assign(p.bufs[sb] + so, p.bufs[sb] + so + bytes);
+    }
+    for (size_t k = 0; k < R; ++k) {
+      const Op& o = p.ops[arr[k]];
+      if (!in_bounds(o.buf2, o.off2, bytes * (int64_t)R)) { err = 6; return; }
+      for (size_t s = 0; s < R; ++s)
+        if (bytes) std::memcpy(p.bufs[o.buf2] + o.off2 + (int64_t)s * bytes, block[s].data(), (size_t)bytes);
+    }
+    for (int64_t j : arr) r.done_round[j] = round;
+  }
+
+  // MPI_Allreduce (root < 0) or MPI_Reduce to `root`: the SUM is written to
+  // every rank's receive buffer, or to the root's only.
+  void run_allreduce(const std::vector<int64_t>& arr, int round, int root = -1) {
     const Op& o0 = p.ops[arr[0]];
     int64_t n = o0.count;
     int type = o0.type;
@@ -289,12 +353,25 @@ struct Oracle {
     std::vector<uint8_t*> out(R);
     for (size_t k = 0; k < R; ++k) {
       const Op& o = p.ops[arr[k]];
+      if (root >= 0 && o.peer != root) { err = 5; return; }
+      const bool writes = root < 0 || (int)k == root;
       int sb = o.buf == kInPlace ? o.buf2 : o.buf;
       int64_t so = o.buf == kInPlace ? o.off2 : o.off;
-      if (!in_bounds(sb, so, esz * n) || !in_bounds(o.buf2, o.off2, esz * n)) { err = 6; return; }
+      if (!in_bounds(sb, so, esz * n) || (writes && !in_bounds(o.buf2, o.off2, esz * n))) { err = 6; return; }
       in[k] = p.bufs[sb] + so;
-      out[k] = p.bufs[o.buf2] + o.off2;
+      out[k] = writes ? p.bufs[o.buf2] + o.off2 : nullptr;
     }
+    // inputs are read in full before any output is written (a root reducing
+    // in place reads its own receive buffer)
+    std::vector<std::vector<uint8_t>> copy(R);
+    for (size_t k = 0; k < R; ++k) {
+      copy[k].assign(in[k], in[k] + esz * n);
+      in[k] = copy[k].data();
+    }
+    // non-writing ranks store into a scratch row
+    std::vector<uint8_t> scratch((size_t)(esz * n));
+    for (size_t k = 0; k < R; ++k)
+      if (!out[k]) out[k] = scratch.data();
     for (int64_t i = 0; i < n; ++i) {
       switch (type) {
         case T_BYTE: {
@@ -346,10 +423,11 @@ struct Oracle {
   // Arguments an enqueue call would reject up front.
   bool valid(const Op& o, int64_t j) const {
     bool p2p = o.kind == SEND || o.kind == ISEND || o.kind == RECV || o.kind == IRECV;
-    if (p2p || o.kind == ALLREDUCE) {
+    if (p2p || is_collective(o.kind)) {
       if (o.comm < 0 || o.comm >= p.ncomms || op_rank[(size_t)j] < 0) return false;
       if (o.type < 0 || o.type >= p.ntypes || o.count < 0) return false;
     }
+    if (o.kind == BCAST || o.kind == REDUCE) return o.peer >= 0 && o.peer < p.nranks;
     if (o.kind == SEND || o.kind == ISEND)
       return o.peer >= 0 && o.peer < p.nranks && o.tag >= 0;
     if (o.kind == RECV || o.kind == IRECV)
@@ -448,7 +526,7 @@ struct Oracle {
             write_wait_status(o);
             ++cursor[g];
             progress = true;
-          } else if (o.kind == ALLREDUCE) {
+          } else if (is_collective(o.kind)) {
             if (r.post_round[j] < 0) {
               r.post_round[j] = round;
               int rk = op_rank[(size_t)j];
@@ -492,7 +570,7 @@ struct Oracle {
           if (j < 0) { full = false; break; }
           if (r.done_round[j] < 0) pending = true;
         }
-        if (full && pending) run_allreduce(v, round);
+        if (full && pending) run_collective(v, round);
         if (err) break;
       }
       if (err) break;

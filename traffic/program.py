@@ -16,8 +16,10 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 # --- operation kinds (the enqueue calls of §3.4 plus the user compute op) ---
-SEND, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY = range(8)
-KIND_NAMES = ["send", "recv", "isend", "irecv", "wait", "waitall", "allreduce", "axpy"]
+SEND, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER = range(11)
+KIND_NAMES = ["send", "recv", "isend", "irecv", "wait", "waitall", "allreduce", "axpy",
+              "bcast", "reduce", "allgather"]
+COLLECTIVES = (ALLREDUCE, BCAST, REDUCE, ALLGATHER)
 
 ANY_SOURCE = -2
 ANY_TAG = -1
@@ -215,6 +217,24 @@ class ProgramBuilder:
                   mode=MODE_FIXED):
         return self._op(g, kind=ALLREDUCE, comm=comm, buf=sendbuf, off=sendoff,
                         buf2=recvbuf, off2=recvoff, count=count, type=type_, mode=mode)
+
+    def bcast(self, g, comm, buf, off, count, type_, root):
+        """MPI_Bcast: the root's count elements replace every other rank's."""
+        return self._op(g, kind=BCAST, comm=comm, buf=buf, off=off, count=count, type=type_,
+                        peer=root)
+
+    def reduce(self, g, comm, sendbuf, sendoff, recvbuf, recvoff, count, type_, root,
+               mode=MODE_FIXED):
+        """MPI_Reduce (SUM) to `root`; recvbuf matters at the root only (-1 elsewhere);
+        sendbuf IN_PLACE at the root reduces its receive buffer."""
+        return self._op(g, kind=REDUCE, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
+                        off2=recvoff, count=count, type=type_, peer=root, mode=mode)
+
+    def allgather(self, g, comm, sendbuf, sendoff, recvbuf, recvoff, count, type_):
+        """MPI_Allgather: count elements per rank into R blocks of every receive
+        buffer; sendbuf IN_PLACE: the rank's block is already in place."""
+        return self._op(g, kind=ALLGATHER, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
+                        off2=recvoff, count=count, type=type_)
 
     def axpy(self, g, alpha, xbuf, xoff, ybuf, yoff, n):
         """y[i] = alpha*x[i] + y[i] in fp32 with one rounding (fused multiply-add)."""
