@@ -323,7 +323,11 @@ enum {
   MPX_OP_IRECV = 3,     /* mpx_irecv_enqueue(buf, count, datatype, peer, tag, comm, requests) */
   MPX_OP_WAIT = 4,      /* mpx_wait_enqueue(requests, status) */
   MPX_OP_WAITALL = 5,   /* mpx_waitall_enqueue(count, requests, status) */
-  MPX_OP_ALLREDUCE = 6  /* mpx_allreduce_enqueue(buf, recvbuf, count, datatype, op, comm) */
+  MPX_OP_ALLREDUCE = 6, /* mpx_allreduce_enqueue(buf, recvbuf, count, datatype, op, comm) */
+  MPX_OP_BCAST = 7,     /* mpx_bcast_enqueue(buf, count, datatype, peer = root, comm) */
+  MPX_OP_REDUCE = 8,    /* mpx_reduce_enqueue(buf, recvbuf, count, datatype, op, peer = root, comm) */
+  MPX_OP_ALLGATHER = 9, /* mpx_allgather_enqueue(buf, recvbuf, count, datatype, comm) */
+  MPX_OP_BARRIER = 10   /* mpx_barrier_enqueue(comm) */
 };
 
 typedef struct {
@@ -441,6 +445,32 @@ typedef struct {
 int mpx_serve_config_init(mpx_serve_config_t* cfg);
 int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* result, uint64_t* digests,
                   uint64_t* source_digests, int64_t ndigests);
+
+/* Further enqueued collectives (§3.4, last paragraph: collectives take the
+ * enqueue form).  Like allreduce, every collective call on a communicator is
+ * blocking in stream order, and the k-th collective call of every rank, of
+ * whatever kind, forms instance k: the ranks must call the same kinds in the
+ * same order with the same count, datatype and root (else MPX_ERR_ARG in
+ * the status and the sticky errors).  Predefined datatypes only.  The plain
+ * path (MPX_ENGINE_PLAIN) has allreduce only: these return
+ * MPX_ERR_UNSUPPORTED there.
+ *  - mpx_bcast_enqueue: MPI_Bcast; the root's count elements of buf replace
+ *    every other rank's.
+ *  - mpx_reduce_enqueue: MPI_Reduce with op = MPX_SUM; the root's recvbuf
+ *    receives the sum (recvbuf is ignored elsewhere and may be NULL);
+ *    sendbuf may be MPX_IN_PLACE at the root.  Floating-point order as for
+ *    allreduce (the communicator's reduce mode).
+ *  - mpx_allgather_enqueue: MPI_Allgather; recvbuf holds nranks blocks of
+ *    count elements, block s receives rank s's sendbuf; sendbuf may be
+ *    MPX_IN_PLACE (the rank's block of recvbuf is its contribution).
+ *  - mpx_barrier_enqueue: MPI_Barrier; work enqueued after it on any rank's
+ *    stream runs once every rank's stream has reached it. */
+int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int root, mpx_comm_t comm);
+int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t datatype,
+                       int op, int root, mpx_comm_t comm);
+int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                          mpx_datatype_t datatype, mpx_comm_t comm);
+int mpx_barrier_enqueue(mpx_comm_t comm);
 
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);

@@ -169,6 +169,7 @@ struct Oracle {
   }
 
   bool in_bounds(int buf, int64_t off, int64_t nbytes_span) const {
+    if (nbytes_span == 0) return true;  // nothing is read or written (MPI: count 0)
     if (buf < 0 || buf >= p.nbufs) return false;
     return off >= 0 && off + nbytes_span <= p.buf_size[buf];
   }

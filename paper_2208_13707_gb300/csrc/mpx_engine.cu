@@ -253,7 +253,7 @@ __device__ __forceinline__ DOp* op_ref(const EngineParams& P, uint64_t ref) {
 __device__ __forceinline__ bool is_send(uint32_t k) { return k == K_SEND || k == K_ISEND; }
 __device__ __forceinline__ bool is_recv(uint32_t k) { return k == K_RECV || k == K_IRECV; }
 __device__ __forceinline__ bool is_blocking(uint32_t k) {
-  return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL || k == K_ALLREDUCE;
+  return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL || is_collective_kind(k);
 }
 
 __device__ void set_error(const EngineParams& P, int g, int err) {
@@ -619,30 +619,34 @@ __device__ __forceinline__ uint32_t bulk_reduce_chunk(int nr) {
   return c >= 4096 ? 4096 : (c & ~255u);
 }
 
-// Elements [v0, v1) of a tile (16-byte aligned buffers, v1 - v0 a multiple of
-// 16 bytes) reduced through shared memory: one thread bulk-loads the R input
-// chunks of a stage (one mbarrier per stage), every thread reduces 16-byte
-// columns across the R rows in shared memory into the stage's result chunk,
-// and one thread bulk-stores that chunk to all R outputs.  Two stages: the
-// loads of chunk j+1 and the stores of chunk j-1 are in flight while chunk j
-// is reduced.  Returns false (error recorded) if a load never landed.
-__device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* ptrs, int nr,
-                                 uint32_t dt, bool tree, int64_t boff0, int64_t nbytes,
+// A span of a collective tile through shared memory (16-byte aligned
+// addresses, nbytes a multiple of 16): one thread bulk-loads the nin input
+// chunks of a stage (one mbarrier per stage); for a SUM every thread reduces
+// 16-byte columns across the rows into the stage's result chunk, for a copy
+// the input chunk is the result; one thread bulk-stores the result to the
+// nout outputs.  Two stages: the loads of chunk j+1 and the stores of chunk
+// j-1 are in flight while chunk j is reduced.  Input r is read at
+// in[r] + in_boff, output o written at out[o] + out_boff.  Returns false
+// (error recorded) if a load never landed.
+__device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* in, int nin,
+                                 int64_t in_boff, const uint64_t* out, int nout, int64_t out_boff,
+                                 uint32_t dt, bool tree, bool sum, int64_t nbytes,
                                  const EngineParams& P) {
-  const uint32_t C = bulk_reduce_chunk(nr);
+  const uint32_t C = bulk_reduce_chunk(nin);
   const uint32_t nch = (uint32_t)((nbytes + C - 1) / C);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const size_t stage_bytes = (size_t)(nr + 1) * C;
+  const size_t stage_bytes = (size_t)(nin + 1) * C;
   auto cbytes = [&](uint32_t j) {
     const int64_t rem = nbytes - (int64_t)j * C;
     return (uint32_t)(rem < (int64_t)C ? rem : (int64_t)C);
   };
   auto issue_loads = [&](uint32_t j) {
     const uint32_t s = j & 1u, b = cbytes(j);
-    uint8_t* in = buf + s * stage_bytes;
-    mbar_expect_tx(&sm.bar[s], b * (uint32_t)nr);
-    for (int r = 0; r < nr; ++r)
-      tma_load_1d(in + (size_t)r * C, (const void*)(ptrs[r] + boff0 + (int64_t)j * C), b, &sm.bar[s]);
+    uint8_t* inb = buf + s * stage_bytes;
+    mbar_expect_tx(&sm.bar[s], b * (uint32_t)nin);
+    for (int r = 0; r < nin; ++r)
+      tma_load_1d(inb + (size_t)r * C, (const void*)(in[r] + in_boff + (int64_t)j * C), b,
+                  &sm.bar[s]);
   };
   uint32_t phase = sm.phase;
   __syncthreads();  // every thread has read the phase bits before thread 0 moves on
@@ -653,9 +657,9 @@ __device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* pt
   bool ok = true;
   for (uint32_t j = 0; j < nch; ++j) {
     const uint32_t s = j & 1u, b = cbytes(j);
-    uint8_t* in = buf + s * stage_bytes;
-    uint8_t* res = in + (size_t)nr * C;
-    // the stores of chunk j-2 read this stage's result chunk
+    uint8_t* inb = buf + s * stage_bytes;
+    uint8_t* res = sum ? inb + (size_t)nin * C : inb;  // a copy stores its input chunk
+    // the stores of chunk j-2 read this stage's chunks
     if (tid == 0 && j >= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
     const uint32_t par = (phase >> s) & 1u;
     const bool landed = mbar_wait_bounded(&sm.bar[s], par);
@@ -671,30 +675,37 @@ __device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* pt
       ok = false;
       break;
     }
-    const uint32_t ncol = b >> 4;
-    for (uint32_t v = tid; v < ncol; v += nt) {
-      uint4* col = reinterpret_cast<uint4*>(in) + v;
-      const size_t rs = C >> 4;  // row stride in uint4
-      uint4 acc;
-      if (tree) {
-        // pairwise by doubling strides, in place in this column
-        for (int st = 1; st < nr; st <<= 1)
-          for (int i = 0; i + st < nr; i += 2 * st)
-            col[(size_t)i * rs] = vadd(dt, col[(size_t)i * rs], col[(size_t)(i + st) * rs]);
-        acc = col[0];
-      } else {
-        acc = col[0];
-        for (int r = 1; r < nr; ++r) acc = vadd(dt, acc, col[(size_t)r * rs]);
+    if (sum) {
+      const uint32_t ncol = b >> 4;
+      for (uint32_t v = tid; v < ncol; v += nt) {
+        uint4* col = reinterpret_cast<uint4*>(inb) + v;
+        const size_t rs = C >> 4;  // row stride in uint4
+        uint4 acc;
+        if (tree) {
+          // pairwise by doubling strides, in place in this column
+          for (int st = 1; st < nin; st <<= 1)
+            for (int i = 0; i + st < nin; i += 2 * st)
+              col[(size_t)i * rs] = vadd(dt, col[(size_t)i * rs], col[(size_t)(i + st) * rs]);
+          acc = col[0];
+        } else {
+          acc = col[0];
+          for (int r = 1; r < nin; ++r) acc = vadd(dt, acc, col[(size_t)r * rs]);
+        }
+        reinterpret_cast<uint4*>(res)[v] = acc;
       }
-      reinterpret_cast<uint4*>(res)[v] = acc;
+      fence_proxy_async();  // result chunk written by this thread -> visible to the bulk stores
     }
-    fence_proxy_async();  // result chunk written by this thread -> visible to the bulk stores
     __syncthreads();
     if (tid == 0) {
-      for (int r = 0; r < nr; ++r)
-        tma_store_1d((void*)(ptrs[nr + r] + boff0 + (int64_t)j * C), res, b);
+      for (int o = 0; o < nout; ++o)
+        tma_store_1d((void*)(out[o] + out_boff + (int64_t)j * C), res, b);
       tma_commit();
-      if (j + 2 < nch) issue_loads(j + 2);  // this stage's inputs were consumed above
+      if (j + 2 < nch) {
+        // this stage's inputs were consumed above; a copy's stores read them
+        // directly, so they must have finished reading first
+        if (!sum) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        issue_loads(j + 2);
+      }
     }
   }
   if (tid == 0) {
@@ -706,58 +717,46 @@ __device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* pt
   return ok;
 }
 
-__device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
-                            const EngineParams& P) {
-  const int64_t e0 = (int64_t)k * T.tile;
-  const int64_t e1 = (e0 + T.tile) < T.bytes ? (e0 + T.tile) : T.bytes;
-  if (e1 <= e0) return;
-  const uint64_t* ptrs = (const uint64_t*)T.ptrs;
-  const int nr = (int)T.nr;
+// Elements [e_in, e_in + n) of the inputs combined into elements
+// [e_out, e_out + n) of the outputs: bulk copies through shared memory for the
+// 16-byte part when every address allows, else 16-byte vectors, else elements.
+__device__ void reduce_span(CtaShared& sm, uint8_t* buf, const Task& T, const uint64_t* in,
+                            int nin, int64_t e_in, const uint64_t* out, int nout, int64_t e_out,
+                            int64_t n, bool sum, const EngineParams& P) {
+  if (n <= 0) return;
   const uint32_t dt = T.dtype;
   const int64_t es = base_size(dt);
-  const bool tree = (T.mode == 1) && (dt == 3 || dt == 4);
+  const bool tree = sum && (T.mode == 1) && (dt == 3 || dt == 4);
   const int tid = threadIdx.x, nt = blockDim.x;
-  int64_t vstart = e0, vend = e0;
-  if (T.unit == 16 && bulk_reduce_chunk(nr) >= 256) {
+  int64_t done = 0;
+  if (T.unit == 16) {
     const int64_t per = 16 / es;
-    vend = e0 + ((e1 - e0) / per) * per;
-    if (vend > e0 && !reduce_span_bulk(sm, buf, ptrs, nr, dt, tree, e0 * es, (vend - e0) * es, P))
-      return;
-    vstart = vend;
-  } else if (T.unit == 16) {
-    const int64_t per = 16 / es;
-    vend = e0 + ((e1 - e0) / per) * per;
-    const int64_t nv = (vend - e0) / per;
-    for (int64_t v = tid; v < nv; v += nt) {
-      const int64_t boff = (e0 + v * per) * es;
-      uint4 acc;
-      if (tree) {
-        acc = tree_sum<uint4>(
-            nr, [&](int r) { return ld_cg16((const void*)(ptrs[r] + boff)); },
-            [&](uint4 a, uint4 b) { return vadd(dt, a, b); });
-      } else {
-        acc = ld_cg16((const void*)(ptrs[0] + boff));
-        int r = 1;
-        for (; r + 3 < nr; r += 4) {
-          uint4 a = ld_cg16((const void*)(ptrs[r] + boff));
-          uint4 b = ld_cg16((const void*)(ptrs[r + 1] + boff));
-          uint4 c = ld_cg16((const void*)(ptrs[r + 2] + boff));
-          uint4 d = ld_cg16((const void*)(ptrs[r + 3] + boff));
-          acc = vadd(dt, acc, a);
-          acc = vadd(dt, acc, b);
-          acc = vadd(dt, acc, c);
-          acc = vadd(dt, acc, d);
+    const int64_t nv = n / per;
+    if (nv > 0 && bulk_reduce_chunk(nin) >= 256) {
+      if (!reduce_span_bulk(sm, buf, in, nin, e_in * es, out, nout, e_out * es, dt, tree, sum,
+                            nv * 16, P))
+        return;
+    } else {
+      for (int64_t v = tid; v < nv; v += nt) {
+        const int64_t bi = (e_in + v * per) * es, bo = (e_out + v * per) * es;
+        uint4 acc;
+        if (tree) {
+          acc = tree_sum<uint4>(
+              nin, [&](int r) { return ld_cg16((const void*)(in[r] + bi)); },
+              [&](uint4 a, uint4 b) { return vadd(dt, a, b); });
+        } else {
+          acc = ld_cg16((const void*)(in[0] + bi));
+          for (int r = 1; r < nin; ++r) acc = vadd(dt, acc, ld_cg16((const void*)(in[r] + bi)));
         }
-        for (; r < nr; ++r) acc = vadd(dt, acc, ld_cg16((const void*)(ptrs[r] + boff)));
+        for (int o = 0; o < nout; ++o) st16((void*)(out[o] + bo), acc);
       }
-      for (int r = 0; r < nr; ++r) st16((void*)(ptrs[nr + r] + boff), acc);
     }
-    vstart = vend;
+    done = nv * per;
   }
-  for (int64_t e = vstart + tid; e < e1; e += nt) {
-    const int64_t boff = e * es;
+  for (int64_t e = done + tid; e < n; e += nt) {
+    const int64_t bi = (e_in + e) * es, bo = (e_out + e) * es;
     auto ld = [&](int r) -> uint64_t {
-      const uint64_t a = ptrs[r] + boff;
+      const uint64_t a = in[r] + bi;
       if (es == 1) return ld_cg1((const void*)a);
       if (es == 4) return ld_cg4((const void*)a);
       uint2 v = ld_cg8((const void*)a);
@@ -765,18 +764,41 @@ __device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t
     };
     uint64_t acc;
     if (tree) {
-      acc = tree_sum<uint64_t>(nr, ld, [&](uint64_t a, uint64_t b) { return sadd(dt, a, b); });
+      acc = tree_sum<uint64_t>(nin, ld, [&](uint64_t a, uint64_t b) { return sadd(dt, a, b); });
     } else {
       acc = ld(0);
-      for (int r = 1; r < nr; ++r) acc = sadd(dt, acc, ld(r));
+      for (int r = 1; r < nin; ++r) acc = sadd(dt, acc, ld(r));
     }
-    for (int r = 0; r < nr; ++r) {
-      const uint64_t a = ptrs[nr + r] + boff;
+    for (int o = 0; o < nout; ++o) {
+      const uint64_t a = out[o] + bo;
       if (es == 1) st1((void*)a, (uint8_t)acc);
       else if (es == 4) st4((void*)a, (uint32_t)acc);
       else st8((void*)a, make_uint2((uint32_t)acc, (uint32_t)(acc >> 32)));
     }
   }
+}
+
+// One tile of a collective task: a SUM (allreduce, reduce), a copy of one
+// input (broadcast), or, for an allgather, the copies of the input blocks the
+// tile covers (element e of the outputs comes from input e / gcount).
+__device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
+                            const EngineParams& P) {
+  const int64_t e0 = (int64_t)k * T.tile;
+  const int64_t e1 = (e0 + T.tile) < T.bytes ? (e0 + T.tile) : T.bytes;
+  if (e1 <= e0) return;
+  const uint64_t* ptrs = (const uint64_t*)T.ptrs;
+  const uint64_t* out = ptrs + T.nr;
+  if (T.cop == CO_GATHER) {
+    const int64_t n = T.gcount;
+    for (int64_t a = e0; a < e1;) {
+      const int64_t s = a / n;
+      const int64_t b = e1 < (s + 1) * n ? e1 : (s + 1) * n;
+      reduce_span(sm, buf, T, ptrs + s, 1, a - s * n, out, (int)T.nout, a, b - a, false, P);
+      a = b;
+    }
+    return;
+  }
+  reduce_span(sm, buf, T, ptrs, (int)T.nin, e0, out, (int)T.nout, e0, e1 - e0, T.cop == CO_SUM, P);
 }
 
 // Claim one tile: thread 0 fetch-and-adds the claim word of the task at
@@ -1059,7 +1081,7 @@ struct Ctl {
         }
         break;
       }
-      if (k == K_ALLREDUCE) {
+      if (is_collective_kind(k)) {
         if (o->lstate == 0) {
           if (arrive(g, o, cur)) {
             o->lstate = 1;
@@ -1346,10 +1368,14 @@ struct Ctl {
       // all arrivals must agree on count, type and mode
       const DOp* o0 = op_ref(P, refs[0]);
       int err = 0;
+      const uint32_t k0 = kw_kind(o0->d.kw);
+      const bool rooted = k0 == K_BCAST || k0 == K_REDUCE;
       for (int r = 1; r < P.nranks; ++r) {
         const DOp* o = op_ref(P, refs[r]);
         if (o->d.count != o0->d.count || o->d.kw != o0->d.kw) err = kErrArg;
+        if (rooted && o->d.peer != o0->d.peer) err = kErrArg;
       }
+      if (rooted && (o0->d.peer < 0 || o0->d.peer >= P.nranks)) err = kErrArg;
       s->err = err;
       for (int r = 0; r < P.nranks; ++r) {
         DOp* o = op_ref(P, refs[r]);
@@ -1582,7 +1608,7 @@ struct Ctl {
 
   __device__ bool phys_done(int g, DOp* o, uint64_t seq) {
     const uint32_t k = kw_kind(o->d.kw);
-    if (k == K_SEND || k == K_RECV || k == K_ALLREDUCE) return (o->pflags & PF_COMPLETE) != 0;
+    if (k == K_SEND || k == K_RECV || is_collective_kind(k)) return (o->pflags & PF_COMPLETE) != 0;
     if (k == K_WAIT) {
       if (o->d.aux == 0) return true;
       return (op_at(P, g, o->d.aux)->pflags & PF_COMPLETE) != 0;
@@ -1666,7 +1692,7 @@ struct Ctl {
         if (q->err) set_error(P, g, q->err);
         atomicOr(&q->pflags, PF_WAITED);
       }
-    } else if (k == K_ALLREDUCE || k == K_SEND) {
+    } else if (is_collective_kind(k) || k == K_SEND) {
       if (o->err) set_error(P, g, o->err);
     }
     // a blocking send stays unfinished until its payload is delivered
@@ -2026,30 +2052,59 @@ struct Ctl {
         sm.dirty = 1;
         continue;
       }
+      // inputs at ptrs[0, nin), outputs at ptrs[R, R + nout)
       uint64_t* ptrs = P.reduce_ptrs + (size_t)i * 2 * P.nranks;
-      bool aligned = true;
-      for (int r = 0; r < P.nranks; ++r) {
-        const DOp* o = op_ref(P, refs[r]);
-        ptrs[r] = o->d.buf;
-        ptrs[P.nranks + r] = o->d.aux;
-        if (((o->d.buf | o->d.aux) & 15) != 0) aligned = false;
-      }
+      const uint32_t kind = kw_kind(o0->d.kw);
       const uint32_t dt = kw_base(o0->d.kw);
       const int64_t es = base_size(dt);
+      const int R = P.nranks, root = o0->d.peer;
+      uint32_t nin = (uint32_t)R, nout = (uint32_t)R, cop = CO_SUM;
+      int64_t total = n;
+      if (kind == K_BCAST) {
+        nin = 1;
+        nout = 0;
+        cop = CO_COPY;
+        ptrs[0] = op_ref(P, refs[root])->d.buf;
+        for (int r = 0; r < R; ++r)
+          if (r != root) ptrs[R + (int)nout++] = op_ref(P, refs[r])->d.buf;
+      } else {
+        for (int r = 0; r < R; ++r) {
+          const DOp* o = op_ref(P, refs[r]);
+          // an in-place allgather contribution is the rank's block of its output
+          ptrs[r] = kind == K_ALLGATHER && o->d.buf == o->d.aux ? o->d.aux + (uint64_t)(r * n * es)
+                                                              : o->d.buf;
+          ptrs[R + r] = o->d.aux;
+        }
+        if (kind == K_REDUCE) {
+          nout = 1;
+          ptrs[R] = op_ref(P, refs[root])->d.aux;
+        } else if (kind == K_ALLGATHER) {
+          cop = CO_GATHER;
+          total = n * R;
+        }
+      }
+      bool aligned = true;
+      for (uint32_t r = 0; r < nin; ++r) aligned = aligned && (ptrs[r] & 15) == 0;
+      for (uint32_t r = 0; r < nout; ++r) aligned = aligned && (ptrs[R + r] & 15) == 0;
+      if (cop == CO_GATHER && ((n * es) & 15) != 0) aligned = false;  // block starts
       uint64_t id;
       Task* T = task_new(id);
       if (!T) continue;
       T->type = T_REDUCE;
       T->action = A_REDUCE;
-      T->bytes = n;
+      T->bytes = total;
+      T->nin = nin;
+      T->nout = nout;
+      T->cop = cop;
+      T->gcount = n;
       // about four tiles per engine CTA, within [tile_bytes*8/R, 256 KiB] per rank
       const int64_t tmin = P.tile_bytes / (es * (P.nranks < 8 ? 1 : P.nranks / 8));
       const int64_t tmax = ((int64_t)256 << 10) / es;
-      int64_t tile = n / (4 * (int64_t)(P.nctas > 0 ? P.nctas : 1));
+      int64_t tile = total / (4 * (int64_t)(P.nctas > 0 ? P.nctas : 1));
       tile = tile < tmin ? tmin : (tile > tmax ? tmax : tile);
       tile = tile < 256 ? 256 : (tile & ~(int64_t)255);
       T->tile = tile;
-      T->ntiles = (uint32_t)((n + tile - 1) / tile);
+      T->ntiles = (uint32_t)((total + tile - 1) / tile);
       T->nr = (uint32_t)P.nranks;
       T->dtype = dt;
       T->mode = kw_mode(o0->d.kw);
@@ -2271,7 +2326,12 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     }
     __syncthreads();
     lap(0);
-    if (sm.failed) {
+    // every thread takes its branch from one snapshot of the flags: thread 0
+    // clears `dirty` below, and a warp that read it after that would skip the
+    // rounds and meet the others' barriers at different points of the tick
+    const bool failed_now = sm.failed != 0, dirty_now = sm.dirty != 0;
+    __syncthreads();
+    if (failed_now) {
       if (tid == 0) {
         sm.pending = 0;
         abandon_tasks(P);
@@ -2279,7 +2339,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       release_all(P, C.ss, kErrTimeout);
       __syncthreads();
       if (tid == 0) sm.released = 1;
-    } else if (sm.dirty) {
+    } else if (dirty_now) {
       if (tid == 0) sm.dirty = 0;
       if (tid == 0) ++sub[6];
       // 2. logical rounds
@@ -2337,7 +2397,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     }
     lap(1);
-    if (!sm.failed) {
+    if (!failed_now) {
       // 3. finished tasks, then per-stream completion and retirement
       if (tid == 0) {
         sm.t_retire = sh->cq_head;

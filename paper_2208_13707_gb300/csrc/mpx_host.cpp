@@ -587,10 +587,35 @@ extern "C" int mpx_world_debug_dump(mpx_world_t w) {
   const bool ok = cudaStreamQuery(st) == cudaSuccess;
   cudaStreamDestroy(st);
   if (!ok) return MPX_ERR_TIMEOUT;
-  fprintf(stderr, "[mpx dump] state %d failed %d error %d tasks head %llu alloc %llu retire %llu round %llu\n",
+  fprintf(stderr, "[mpx dump] state %d failed %d error %d tasks head %llu alloc %llu retire %llu round %llu"
+          " cq head %llu tail %llu\n",
           w->wctl->state, w->wctl->failed, w->wctl->error, (unsigned long long)sh.task_head,
           (unsigned long long)sh.task_alloc, (unsigned long long)sh.task_retire,
-          (unsigned long long)sh.round);
+          (unsigned long long)sh.round, (unsigned long long)sh.cq_head, (unsigned long long)sh.cq_tail);
+  // the live tasks: how many are unfinished, and where their tiles stand
+  const uint64_t cap = 1ull << w->tq_log2;
+  if (sh.task_alloc > sh.task_retire && sh.task_alloc - sh.task_retire <= cap) {
+    std::vector<Task> tk(cap);
+    if (cudaMemcpy(tk.data(), w->params.tasks, cap * sizeof(Task), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      uint64_t open = 0, unclaimed = 0, ran = 0, shown = 0;
+      for (uint64_t id = sh.task_retire; id < sh.task_alloc; ++id) {
+        const Task& t = tk[id & (cap - 1)];
+        if (t.type == 0) continue;
+        ++open;
+        const uint32_t nx = claim_next(t.claim), nt = claim_ntiles(t.claim);
+        if (nx < nt) ++unclaimed;
+        if (t.tiles_done >= t.ntiles) ++ran;
+        if (shown++ < 8)
+          fprintf(stderr,
+                  "[mpx dump]   task %llu type %u action %u bytes %lld tile %lld ntiles %u done %u claim idp %u"
+                  " nt %u next %u (tag %u) chunk %lld unit %u\n",
+                  (unsigned long long)id, t.type, t.action, (long long)t.bytes, (long long)t.tile, t.ntiles,
+                  t.tiles_done, claim_idp(t.claim), nt, nx, id_tag(id), (long long)t.chunk, t.unit);
+      }
+      fprintf(stderr, "[mpx dump]   open tasks %llu: tiles unclaimed %llu, all tiles counted done %llu\n",
+              (unsigned long long)open, (unsigned long long)unclaimed, (unsigned long long)ran);
+    }
+  }
   for (int g = 0; g < S; ++g) {
     const StreamCtl& c = w->sctl[g];
     if (!c.flags && !c.tail) continue;
@@ -1124,6 +1149,70 @@ extern "C" int mpx_waitall_enqueue(int n, mpx_request_t reqs[], mpx_status_t sta
   return wait_common(n, reqs, statuses, false);
 }
 
+// Descriptor of a collective call (allreduce, bcast, reduce, allgather):
+// buf = input, aux = output, peer = root.
+static void fill_collective(Desc& d, uint32_t kind, mpx_datatype_t dt, mpx_comm_t c,
+                            const void* in, void* out, int64_t count, int root) {
+  memset(&d, 0, sizeof(d));
+  d.kw = make_kw(kind, (uint32_t)dt, (uint32_t)c->shared->reduce_mode);
+  d.comm = (uint16_t)c->shared->id;
+  d.rank = (uint16_t)c->rank;
+  d.peer = root;
+  d.buf = (uint64_t)in;
+  d.aux = (uint64_t)out;
+  d.count = count;
+  d.vcount = 1;
+  d.blocklen = 1;
+  d.stride = 1;
+}
+
+extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int root,
+                                 mpx_comm_t c) {
+  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
+  if (root < 0 || root >= c->size) return MPX_ERR_RANK;
+  if (count < 0 || (count > 0 && !buf)) return MPX_ERR_ARG;
+  if (c->w->plain) return MPX_ERR_UNSUPPORTED;
+  Desc d;
+  fill_collective(d, K_BCAST, dt, c, buf, buf, count, root);
+  return publish(c->stream, d, true, nullptr);
+}
+
+extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                  mpx_datatype_t dt, int op, int root, mpx_comm_t c) {
+  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (op != MPX_SUM) return MPX_ERR_ARG;
+  if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
+  if (root < 0 || root >= c->size) return MPX_ERR_RANK;
+  const bool at_root = c->rank == root;
+  if (sendbuf == MPX_IN_PLACE) {
+    if (!at_root) return MPX_ERR_ARG;
+    sendbuf = recvbuf;
+  }
+  if (count < 0 || (count > 0 && (!sendbuf || (at_root && !recvbuf)))) return MPX_ERR_ARG;
+  if (c->w->plain) return MPX_ERR_UNSUPPORTED;
+  Desc d;
+  fill_collective(d, K_REDUCE, dt, c, sendbuf, at_root ? recvbuf : nullptr, count, root);
+  return publish(c->stream, d, true, nullptr);
+}
+
+extern "C" int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                     mpx_datatype_t dt, mpx_comm_t c) {
+  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
+  if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;  // the rank's block is already in place
+  if (count < 0 || (count > 0 && (!sendbuf || !recvbuf))) return MPX_ERR_ARG;
+  if (c->w->plain) return MPX_ERR_UNSUPPORTED;
+  Desc d;
+  fill_collective(d, K_ALLGATHER, dt, c, sendbuf, recvbuf, count, 0);
+  return publish(c->stream, d, true, nullptr);
+}
+
+extern "C" int mpx_barrier_enqueue(mpx_comm_t c) {
+  // an allreduce of no elements: complete once every rank has arrived
+  return mpx_allreduce_enqueue(nullptr, nullptr, 0, MPX_BYTE, MPX_SUM, c);
+}
+
 extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                                      mpx_datatype_t dt, int op, mpx_comm_t c) {
   if (!c || !c->stream) return MPX_ERR_COMM;
@@ -1136,16 +1225,7 @@ extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t
     return plain::allreduce(c->w->plain, sendbuf, recvbuf, count, dt, c->shared->reduce_mode,
                             c->shared->id, c->rank, c->stream->id);
   Desc d;
-  memset(&d, 0, sizeof(d));
-  d.kw = make_kw(K_ALLREDUCE, (uint32_t)dt, (uint32_t)c->shared->reduce_mode);
-  d.comm = (uint16_t)c->shared->id;
-  d.rank = (uint16_t)c->rank;
-  d.buf = (uint64_t)sendbuf;
-  d.aux = (uint64_t)recvbuf;
-  d.count = count;
-  d.vcount = 1;
-  d.blocklen = 1;
-  d.stride = 1;
+  fill_collective(d, K_ALLREDUCE, dt, c, sendbuf, recvbuf, count, 0);
   return publish(c->stream, d, true, nullptr);
 }
 
@@ -1156,7 +1236,8 @@ extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t
 static mpx_stream_s* batch_op_stream(const mpx_op_t& o) {
   switch (o.kind) {
     case MPX_OP_SEND: case MPX_OP_RECV: case MPX_OP_ISEND: case MPX_OP_IRECV:
-    case MPX_OP_ALLREDUCE:
+    case MPX_OP_ALLREDUCE: case MPX_OP_BCAST: case MPX_OP_REDUCE: case MPX_OP_ALLGATHER:
+    case MPX_OP_BARRIER:
       return o.comm ? o.comm->stream : nullptr;
     case MPX_OP_WAIT: case MPX_OP_WAITALL:
       if (!o.requests) return nullptr;
@@ -1202,6 +1283,18 @@ extern "C" int mpx_enqueue_batch(int n, const mpx_op_t ops[], int* done) {
         break;
       case MPX_OP_ALLREDUCE:
         rc = mpx_allreduce_enqueue(o.buf, o.recvbuf, o.count, o.datatype, o.op, o.comm);
+        break;
+      case MPX_OP_BCAST:
+        rc = mpx_bcast_enqueue((void*)o.buf, o.count, o.datatype, o.peer, o.comm);
+        break;
+      case MPX_OP_REDUCE:
+        rc = mpx_reduce_enqueue(o.buf, o.recvbuf, o.count, o.datatype, o.op, o.peer, o.comm);
+        break;
+      case MPX_OP_ALLGATHER:
+        rc = mpx_allgather_enqueue(o.buf, o.recvbuf, o.count, o.datatype, o.comm);
+        break;
+      case MPX_OP_BARRIER:
+        rc = mpx_barrier_enqueue(o.comm);
         break;
       default:
         rc = MPX_ERR_ARG;
@@ -1265,7 +1358,8 @@ extern "C" int mpx_step_create(mpx_world_t w, int n, const mpx_op_t ops[], mpx_s
     mpx_stream_s* st = nullptr;
     switch (o.kind) {
       case MPX_OP_SEND: case MPX_OP_RECV: case MPX_OP_ISEND: case MPX_OP_IRECV:
-      case MPX_OP_ALLREDUCE:
+      case MPX_OP_ALLREDUCE: case MPX_OP_BCAST: case MPX_OP_REDUCE: case MPX_OP_ALLGATHER:
+      case MPX_OP_BARRIER:
         if (!o.comm || !o.comm->stream) return MPX_ERR_COMM;
         if (o.comm->w != w) return MPX_ERR_ARG;
         st = o.comm->stream;
@@ -1333,20 +1427,29 @@ extern "C" int mpx_step_create(mpx_world_t w, int n, const mpx_op_t ops[], mpx_s
           d.status = (uint64_t)o.status;
           for (int64_t k = 0; k < o.count; ++k) tmpl_wl.push_back(reqmap[o.requests + k].second);
           break;
-        case MPX_OP_ALLREDUCE: {
-          if (o.op != MPX_SUM) return MPX_ERR_ARG;
-          if (o.datatype < 0 || o.datatype > MPX_DOUBLE) return MPX_ERR_TYPE;
+        case MPX_OP_ALLREDUCE: case MPX_OP_BARRIER: {
+          const bool bar = o.kind == MPX_OP_BARRIER;
+          const int64_t cnt = bar ? 0 : o.count;
+          if (!bar && o.op != MPX_SUM) return MPX_ERR_ARG;
+          if (!bar && (o.datatype < 0 || o.datatype > MPX_DOUBLE)) return MPX_ERR_TYPE;
           const void* sb = o.buf == MPX_IN_PLACE ? o.recvbuf : o.buf;
-          if (o.count < 0 || (o.count > 0 && (!o.recvbuf || !sb))) return MPX_ERR_ARG;
-          d.kw = make_kw(K_ALLREDUCE, (uint32_t)o.datatype, (uint32_t)o.comm->shared->reduce_mode);
-          d.comm = (uint16_t)o.comm->shared->id;
-          d.rank = (uint16_t)o.comm->rank;
-          d.buf = (uint64_t)sb;
-          d.aux = (uint64_t)o.recvbuf;
-          d.count = o.count;
-          d.vcount = 1;
-          d.blocklen = 1;
-          d.stride = 1;
+          if (cnt < 0 || (cnt > 0 && (!o.recvbuf || !sb))) return MPX_ERR_ARG;
+          fill_collective(d, K_ALLREDUCE, bar ? MPX_BYTE : o.datatype, o.comm, bar ? nullptr : sb,
+                          bar ? nullptr : o.recvbuf, cnt, 0);
+          break;
+        }
+        case MPX_OP_BCAST: case MPX_OP_REDUCE: case MPX_OP_ALLGATHER: {
+          if (o.datatype < 0 || o.datatype > MPX_DOUBLE) return MPX_ERR_TYPE;
+          if (o.kind != MPX_OP_ALLGATHER && (o.peer < 0 || o.peer >= o.comm->size)) return MPX_ERR_RANK;
+          if (o.kind == MPX_OP_REDUCE && o.op != MPX_SUM) return MPX_ERR_ARG;
+          const bool at_root = o.comm->rank == o.peer;
+          const void* in = o.buf == MPX_IN_PLACE ? o.recvbuf : o.buf;
+          void* outp = o.kind == MPX_OP_BCAST ? (void*)o.buf
+                       : (o.kind == MPX_OP_REDUCE && !at_root ? nullptr : o.recvbuf);
+          if (o.count < 0 || (o.count > 0 && (!in || (o.kind != MPX_OP_BCAST && o.kind != MPX_OP_REDUCE && !outp))))
+            return MPX_ERR_ARG;
+          const uint32_t kind = o.kind == MPX_OP_BCAST ? K_BCAST : o.kind == MPX_OP_REDUCE ? K_REDUCE : K_ALLGATHER;
+          fill_collective(d, kind, o.datatype, o.comm, in, outp, o.count, o.kind == MPX_OP_ALLGATHER ? 0 : o.peer);
           break;
         }
       }

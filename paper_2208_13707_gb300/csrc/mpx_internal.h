@@ -12,7 +12,8 @@ namespace mpxi {
 // the engine into its device-resident operation table.
 // ---------------------------------------------------------------------------
 enum OpKind : uint32_t {
-  K_SEND = 0, K_RECV = 1, K_ISEND = 2, K_IRECV = 3, K_WAIT = 4, K_WAITALL = 5, K_ALLREDUCE = 6
+  K_SEND = 0, K_RECV = 1, K_ISEND = 2, K_IRECV = 3, K_WAIT = 4, K_WAITALL = 5, K_ALLREDUCE = 6,
+  K_BCAST = 7, K_REDUCE = 8, K_ALLGATHER = 9
 };
 
 // kind word: bits 0-7 kind, 8-11 base type (MPX_BYTE..MPX_DOUBLE),
@@ -181,10 +182,17 @@ struct alignas(128) Task {
   Layout src, dst;      // COPY
   uint64_t ref_s, ref_r;  // COPY: send / recv ops; REDUCE: instance slot
   uint32_t nr, dtype, mode, unit;   // unit: bytes moved per access (16/8/4/2/1)
-  uint64_t ptrs;        // REDUCE: device array of nr inputs then nr outputs
+  uint64_t ptrs;        // REDUCE: device array: inputs at [0, nin), outputs at [nr, nr + nout)
+  uint32_t nin, nout;   // REDUCE: inputs and outputs used
+  uint32_t cop, pad_c;  // REDUCE: CO_SUM, CO_COPY (one input) or CO_GATHER (input e / gcount)
+  int64_t gcount;       // REDUCE, CO_GATHER: elements per input
   int64_t chunk;        // COPY: bytes contiguous on both sides (kContig = whole tile)
 };
 static_assert(sizeof(Task) <= 256, "task record");
+enum CollOp : uint32_t { CO_SUM = 0, CO_COPY = 1, CO_GATHER = 2 };
+__host__ __device__ inline bool is_collective_kind(uint32_t k) {
+  return k == K_ALLREDUCE || k == K_BCAST || k == K_REDUCE || k == K_ALLGATHER;
+}
 
 struct InstSlot {
   uint64_t k1;      // instance number + 1, 0 = free

@@ -55,7 +55,8 @@ class WorldConfig(ctypes.Structure):
                 ("stage_delay_ns", ctypes.c_int64)]
 
 
-OP_SEND, OP_RECV, OP_ISEND, OP_IRECV, OP_WAIT, OP_WAITALL, OP_ALLREDUCE = range(7)
+(OP_SEND, OP_RECV, OP_ISEND, OP_IRECV, OP_WAIT, OP_WAITALL, OP_ALLREDUCE, OP_BCAST, OP_REDUCE,
+ OP_ALLGATHER, OP_BARRIER) = range(11)
 
 
 def op_dtype():
@@ -121,6 +122,10 @@ _SIGS = {
     "mpx_wait_enqueue": [_P(_i64), _vp],
     "mpx_waitall_enqueue": [ctypes.c_int, _P(_i64), _vp],
     "mpx_allreduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp],
+    "mpx_bcast_enqueue": [_vp, _i64, _i32, ctypes.c_int, _vp],
+    "mpx_reduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp],
+    "mpx_allgather_enqueue": [_vp, _vp, _i64, _i32, _vp],
+    "mpx_barrier_enqueue": [_vp],
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
@@ -315,6 +320,23 @@ def mpx_waitall_enqueue(requests: Sequence[int], statuses: int = 0) -> None:
 
 def mpx_allreduce_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, comm: int) -> None:
     _chk(lib.mpx_allreduce_enqueue(sendbuf, recvbuf, count, datatype, op, comm), "mpx_allreduce_enqueue")
+
+
+def mpx_bcast_enqueue(buf: int, count: int, datatype: int, root: int, comm: int) -> None:
+    _chk(lib.mpx_bcast_enqueue(buf, count, datatype, root, comm), "mpx_bcast_enqueue")
+
+
+def mpx_reduce_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, root: int,
+                       comm: int) -> None:
+    _chk(lib.mpx_reduce_enqueue(sendbuf, recvbuf, count, datatype, op, root, comm), "mpx_reduce_enqueue")
+
+
+def mpx_allgather_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, comm: int) -> None:
+    _chk(lib.mpx_allgather_enqueue(sendbuf, recvbuf, count, datatype, comm), "mpx_allgather_enqueue")
+
+
+def mpx_barrier_enqueue(comm: int) -> None:
+    _chk(lib.mpx_barrier_enqueue(comm), "mpx_barrier_enqueue")
 
 
 def mpx_get_count(status: Status, datatype: int) -> int:

@@ -14,8 +14,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .program import (ALLREDUCE, AXPY, IN_PLACE, IRECV, ISEND, RECV, SEND, STATUS_DTYPE, WAIT,
-                      WAITALL, Program)
+from .program import (ALLGATHER, ALLREDUCE, AXPY, BCAST, IN_PLACE, IRECV, ISEND, RECV, REDUCE, SEND,
+                      STATUS_DTYPE, WAIT, WAITALL, Program)
 
 
 @dataclass
@@ -135,9 +135,20 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             else:
                 retry(lambda: mpx.mpx_waitall_enqueue(hs, sptr(int(o["status"]))))
         elif k == ALLREDUCE:
-            rb = ptr[int(o["buf2"])] + int(o["off2"])
+            rb = ptr[int(o["buf2"])] + int(o["off2"]) if int(o["buf2"]) >= 0 else 0
             sb = mpx.IN_PLACE if b == IN_PLACE else p
             retry(lambda: mpx.mpx_allreduce_enqueue(sb, rb, cnt, ty, mpx.SUM, comm))
+        elif k == BCAST:
+            retry(lambda: mpx.mpx_bcast_enqueue(p, cnt, ty, peer, comm))
+        elif k == REDUCE:
+            b2 = int(o["buf2"])
+            rb = ptr[b2] + int(o["off2"]) if b2 >= 0 else 0
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            retry(lambda: mpx.mpx_reduce_enqueue(sb, rb, cnt, ty, mpx.SUM, peer, comm))
+        elif k == ALLGATHER:
+            rb = ptr[int(o["buf2"])] + int(o["off2"])
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            retry(lambda: mpx.mpx_allgather_enqueue(sb, rb, cnt, ty, comm))
         elif k == AXPY:
             yb = ptr[int(o["buf2"])] + int(o["off2"])
             mpx.mpx_saxpy_enqueue(cnt, float(o["alpha"]), p, yb, cstreams[g].cuda_stream)
