@@ -45,7 +45,8 @@ class _Program(ctypes.Structure):
                 ("stream_rank", ctypes.c_void_p), ("comm_stream", ctypes.c_void_p),
                 ("stream_op_lo", ctypes.c_void_p), ("ops", ctypes.c_void_p),
                 ("types", ctypes.c_void_p), ("bufs", ctypes.c_void_p),
-                ("buf_size", ctypes.c_void_p), ("reqlist", ctypes.c_void_p)]
+                ("buf_size", ctypes.c_void_p), ("reqlist", ctypes.c_void_p),
+                ("mux_off", ctypes.c_void_p), ("mux_stream", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -101,10 +102,20 @@ def run(prog, buffers: Optional[List[np.ndarray]] = None) -> OracleOutcome:
     reqlist = np.ascontiguousarray(prog.reqlist, np.int64)
     ptrs = (ctypes.c_void_p * max(1, len(bufs)))(*[b.ctypes.data for b in bufs])
     sizes = np.array([b.size for b in bufs] or [0], np.int64)
+    # multiplex comms: each rank's local streams, flattened (empty ranges elsewhere)
+    mux_off = np.zeros(prog.ncomms * prog.nranks + 1, np.int64)
+    mux_list: List[int] = []
+    for c in range(prog.ncomms):
+        m = prog.mux(c)
+        for r in range(prog.nranks):
+            if m is not None:
+                mux_list.extend(int(g) for g in m[r])
+            mux_off[c * prog.nranks + r + 1] = len(mux_list)
+    mux_stream = np.array(mux_list or [0], np.int32)
     P = _Program(prog.nranks, prog.nstreams, prog.ncomms, len(types), len(ops), len(bufs),
                  len(reqlist), prog.nstatus, _ptr(stream_rank), _ptr(comm_stream), _ptr(lo),
                  _ptr(ops), _ptr(types), ctypes.cast(ptrs, ctypes.c_void_p).value,
-                 _ptr(sizes), _ptr(reqlist))
+                 _ptr(sizes), _ptr(reqlist), _ptr(mux_off), _ptr(mux_stream))
     nops = len(ops)
     match = np.full(max(1, nops), -1, np.int64)
     post = np.full(max(1, nops), -1, np.int32)

@@ -20,6 +20,13 @@
  *    data received is visible to work enqueued after the completing call.
  *  - §3.4 (last paragraph): collectives take the same enqueue form; here
  *    SUM allreduce.
+ *  - §3.5: a multiplex stream communicator attaches several local streams
+ *    per process, addressed by index; a send names its own stream (src_idx)
+ *    and the destination's (dst_idx), a receive its own stream (dst_idx) and
+ *    the sender's (src_idx, or any index).  A communicator with one stream
+ *    per rank is the case where every index is 0, so one rule covers both:
+ *    matching is per (comm, destination rank, destination index), and a
+ *    receive accepts a sender whose rank and index both fit its pattern.
  *
  * Readings where the paper is silent:
  *  - Posting is logical and proceeds in rounds.  In round k every stream, in
@@ -41,11 +48,13 @@
  *  - The user compute op AXPY (Listing 4's saxpy) is y = a*x + y with a
  *    single rounding (fused multiply-add).
  */
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <list>
 #include <map>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -55,6 +64,7 @@ enum Kind { SEND = 0, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST,
 bool is_collective(int k) { return k == ALLREDUCE || k == BCAST || k == REDUCE || k == ALLGATHER; }
 constexpr int kAnySource = -2;
 constexpr int kAnyTag = -1;
+constexpr int kAnyIndex = -1;
 constexpr int kInPlace = -3;
 constexpr int kErrTruncate = 15;
 enum BasicType { T_BYTE = 0, T_INT32, T_INT64, T_FLOAT, T_DOUBLE };
@@ -67,9 +77,10 @@ struct Op {
   int64_t off, off2;
   int32_t req_lo, req_n, status, mode;
   float alpha;
+  int32_t sidx, didx;  // multiplex comm: sender's / receiver's local stream index
   int32_t pad;
 };
-static_assert(sizeof(Op) == 80, "op record is 80 bytes");
+static_assert(sizeof(Op) == 88, "op record is 88 bytes");
 
 struct Type {
   int32_t kind, base, elem, vcount, blocklen, stride;
@@ -77,7 +88,7 @@ struct Type {
 static_assert(sizeof(Type) == 24, "type record is 24 bytes");
 
 struct Status {
-  int32_t source, tag, error, pad;
+  int32_t source, tag, error, source_index;
   int64_t bytes;
 };
 static_assert(sizeof(Status) == 24, "status record is 24 bytes");
@@ -97,6 +108,11 @@ struct OracleProgram {
   uint8_t* const* bufs;         // [nbufs] mutated in place
   const int64_t* buf_size;      // [nbufs]
   const int64_t* reqlist;       // [nreq]
+  // multiplex comms (§3.5): the local streams of rank r in comm c are
+  // mux_stream[mux_off[c * nranks + r] .. mux_off[c * nranks + r + 1]);
+  // an empty range marks a comm with one stream per rank.  Both may be null.
+  const int64_t* mux_off;       // [ncomms * nranks + 1]
+  const int32_t* mux_stream;
 };
 
 struct OracleResult {
@@ -153,9 +169,11 @@ struct Oracle {
   std::vector<std::vector<uint8_t>> snapshot;  // eager send payloads
   std::vector<Status> op_status;               // status of completed receives
   std::vector<int32_t> op_rank;                // comm rank of the issuing stream
-  // matching domains, one per (comm, destination rank)
-  std::vector<std::list<int64_t>> posted;      // receives waiting, in post order
-  std::vector<std::list<int64_t>> unexpected;  // sends waiting, in post order
+  std::vector<int32_t> op_index;               // its local stream index in the comm
+  // matching domains, one per (comm, destination rank, destination index)
+  using Domain = std::tuple<int, int, int>;
+  std::map<Domain, std::list<int64_t>> posted;      // receives waiting, in post order
+  std::map<Domain, std::list<int64_t>> unexpected;  // sends waiting, in post order
   // collectives: per (comm, rank) next instance; per (comm, instance) arrivals
   std::vector<int64_t> next_instance;
   std::map<std::pair<int, int64_t>, std::vector<int64_t>> instances;
@@ -167,6 +185,30 @@ struct Oracle {
       if (p.comm_stream[(int64_t)c * p.nranks + k] == g) return k;
     return -1;
   }
+
+  // streams rank r attached to multiplex comm c (0: not a multiplex comm)
+  int64_t mux_count(int c, int r) const {
+    if (!p.mux_off) return 0;
+    const int64_t i = (int64_t)c * p.nranks + r;
+    return p.mux_off[i + 1] - p.mux_off[i];
+  }
+  bool is_mux(int c) const {
+    for (int r = 0; r < p.nranks; ++r)
+      if (mux_count(c, r) > 0) return true;
+    return false;
+  }
+  // (rank, index) of stream g in comm c; rank -1 when g is not a member
+  std::pair<int, int> member(int c, int g) const {
+    if (!is_mux(c)) return {rank_in_comm(c, g), 0};
+    for (int r = 0; r < p.nranks; ++r) {
+      const int64_t a = p.mux_off[(int64_t)c * p.nranks + r];
+      for (int64_t k = 0; k < mux_count(c, r); ++k)
+        if (p.mux_stream[a + k] == g) return {r, (int)k};
+    }
+    return {-1, 0};
+  }
+  // how many streams a rank attached (1 on a plain stream comm)
+  int64_t streams_of(int c, int r) const { return is_mux(c) ? mux_count(c, r) : 1; }
 
   bool in_bounds(int buf, int64_t off, int64_t nbytes_span) const {
     if (nbytes_span == 0) return true;  // nothing is read or written (MPI: count 0)
@@ -199,10 +241,11 @@ struct Oracle {
     for (int64_t q = 0; q < n; ++q) base[packed_byte_offset(L, q)] = data[(size_t)q];
   }
 
-  static bool accepts(const Op& recv, int src_rank, int tag) {
+  static bool accepts(const Op& recv, int src_rank, int src_index, int tag) {
     bool src_ok = recv.peer == kAnySource || recv.peer == src_rank;
+    bool idx_ok = recv.sidx == kAnyIndex || recv.sidx == src_index;
     bool tag_ok = recv.tag == kAnyTag || recv.tag == tag;
-    return src_ok && tag_ok;
+    return src_ok && idx_ok && tag_ok;
   }
 
   void deliver(int64_t s, int64_t q, int round) {
@@ -218,6 +261,7 @@ struct Oracle {
     r.done_round[q] = round;
     Status st{};
     st.source = op_rank[(size_t)s];
+    st.source_index = op_index[(size_t)s];
     st.tag = so.tag;
     st.error = sent > cap ? kErrTruncate : 0;
     st.bytes = n;
@@ -227,33 +271,33 @@ struct Oracle {
 
   void match_send(int64_t s, int round) {
     const Op& so = p.ops[s];
-    int d = so.comm * p.nranks + so.peer;
-    auto& lst = posted[(size_t)d];
+    const Domain d{so.comm, so.peer, so.didx};
+    auto& lst = posted[d];
     for (auto it = lst.begin(); it != lst.end(); ++it) {
-      if (accepts(p.ops[*it], op_rank[(size_t)s], so.tag)) {
+      if (accepts(p.ops[*it], op_rank[(size_t)s], op_index[(size_t)s], so.tag)) {
         int64_t q = *it;
         lst.erase(it);
         deliver(s, q, round);
         return;
       }
     }
-    unexpected[(size_t)d].push_back(s);
+    unexpected[d].push_back(s);
   }
 
   void match_recv(int64_t q, int round) {
     const Op& ro = p.ops[q];
-    int d = ro.comm * p.nranks + op_rank[(size_t)q];
-    auto& lst = unexpected[(size_t)d];
+    const Domain d{ro.comm, op_rank[(size_t)q], op_index[(size_t)q]};
+    auto& lst = unexpected[d];
     for (auto it = lst.begin(); it != lst.end(); ++it) {
       const Op& so = p.ops[*it];
-      if (accepts(ro, op_rank[(size_t)*it], so.tag)) {
+      if (accepts(ro, op_rank[(size_t)*it], op_index[(size_t)*it], so.tag)) {
         int64_t s = *it;
         lst.erase(it);
         deliver(s, q, round);
         return;
       }
     }
-    posted[(size_t)d].push_back(q);
+    posted[d].push_back(q);
   }
 
   void run_axpy(const Op& o) {
@@ -428,12 +472,21 @@ struct Oracle {
       if (o.comm < 0 || o.comm >= p.ncomms || op_rank[(size_t)j] < 0) return false;
       if (o.type < 0 || o.type >= p.ntypes || o.count < 0) return false;
     }
-    if (o.kind == BCAST || o.kind == REDUCE) return o.peer >= 0 && o.peer < p.nranks;
+    // a multiplex comm carries point-to-point traffic only (§3.5)
+    if (is_collective(o.kind)) return !is_mux(o.comm) && (o.kind == ALLREDUCE || o.kind == ALLGATHER ||
+                                                         (o.peer >= 0 && o.peer < p.nranks));
     if (o.kind == SEND || o.kind == ISEND)
-      return o.peer >= 0 && o.peer < p.nranks && o.tag >= 0;
-    if (o.kind == RECV || o.kind == IRECV)
-      return (o.peer == kAnySource || (o.peer >= 0 && o.peer < p.nranks)) &&
-             (o.tag == kAnyTag || o.tag >= 0);
+      return o.peer >= 0 && o.peer < p.nranks && o.tag >= 0 && o.sidx == op_index[(size_t)j] &&
+             o.didx >= 0 && o.didx < streams_of(o.comm, o.peer);
+    if (o.kind == RECV || o.kind == IRECV) {
+      if (!(o.peer == kAnySource || (o.peer >= 0 && o.peer < p.nranks))) return false;
+      if (!(o.tag == kAnyTag || o.tag >= 0) || o.didx != op_index[(size_t)j]) return false;
+      if (o.sidx == kAnyIndex) return is_mux(o.comm);  // ANY_INDEX only on a multiplex comm
+      if (o.peer != kAnySource) return o.sidx >= 0 && o.sidx < streams_of(o.comm, o.peer);
+      int64_t most = 0;
+      for (int r = 0; r < p.nranks; ++r) most = std::max(most, streams_of(o.comm, r));
+      return o.sidx >= 0 && o.sidx < most;
+    }
     if (o.kind == WAIT || o.kind == WAITALL) {
       for (int k = 0; k < o.req_n; ++k) {
         int64_t q = p.reqlist[o.req_lo + k];
@@ -470,16 +523,21 @@ struct Oracle {
     snapshot.assign((size_t)nops, {});
     op_status.assign((size_t)nops, Status{});
     op_rank.assign((size_t)nops, -1);
+    op_index.assign((size_t)nops, 0);
     for (int64_t j = 0; j < nops; ++j) {
       r.match[j] = -1;
       r.post_round[j] = -1;
       r.done_round[j] = -1;
       const Op& o = p.ops[j];
-      if (o.comm >= 0 && o.comm < p.ncomms) op_rank[(size_t)j] = rank_in_comm(o.comm, o.stream);
+      if (o.comm >= 0 && o.comm < p.ncomms) {
+        const std::pair<int, int> m = member(o.comm, o.stream);
+        op_rank[(size_t)j] = m.first;
+        op_index[(size_t)j] = m.second;
+      }
     }
     for (int64_t s = 0; s < p.nstatus; ++s) r.status[s] = Status{};
-    posted.assign((size_t)p.ncomms * p.nranks, {});
-    unexpected.assign((size_t)p.ncomms * p.nranks, {});
+    posted.clear();
+    unexpected.clear();
     next_instance.assign((size_t)p.ncomms * p.nranks, 0);
     std::vector<int64_t> cursor(p.nstreams);
     for (int g = 0; g < p.nstreams; ++g) cursor[g] = p.stream_op_lo[g];
@@ -617,6 +675,6 @@ void oracle_sum_f32_ref(int32_t nranks, int64_t n, const float* const* xs, doubl
   }
 }
 
-int oracle_abi_version(void) { return 1; }
+int oracle_abi_version(void) { return 2; }
 
 }  // extern "C"

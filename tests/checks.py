@@ -7,6 +7,8 @@ MPIX Stream paper in forms different from the oracle's code:
   * `closed_form_matches`: with no wildcards, the k-th send on
     (comm, src -> dst, tag) matches the k-th receive dst posts for
     (comm, src, tag) (§2.1: matching order is the outcome; non-overtaking).
+    On a multiplex stream communicator (§3.5) src and dst are (rank, local
+    stream index) pairs; a comm with one stream per rank has index 0 only.
   * `validity_violations`: necessary conditions any MPI-legal match map meets.
   * `legal_outcomes`: brute-force enumeration of every MPI-legal execution of a
     tiny program (arbitrary stream interleavings and per-channel FIFO message
@@ -19,17 +21,22 @@ from typing import Dict, FrozenSet, List, Set, Tuple
 
 import numpy as np
 
-from traffic.program import (ALLREDUCE, ANY_SOURCE, ANY_TAG, AXPY, IRECV, ISEND, RECV, SEND,
-                             WAIT, WAITALL, Program)
+from traffic.program import (ALLREDUCE, ANY_INDEX, ANY_SOURCE, ANY_TAG, AXPY, IRECV, ISEND, RECV,
+                             SEND, WAIT, WAITALL, Program)
 
 SEND_KINDS = (SEND, ISEND)
 RECV_KINDS = (RECV, IRECV)
 
 
 def comm_rank(prog: Program, comm: int, g: int) -> int:
-    row = prog.comm_stream[comm]
-    hits = np.nonzero(row == g)[0]
-    return int(hits[0]) if len(hits) else -1
+    m = prog.member(comm, g)
+    return m[0] if m is not None else -1
+
+
+def comm_member(prog: Program, comm: int, g: int) -> Tuple[int, int]:
+    """(rank, local stream index) of stream g in comm (index 0 on a plain comm)."""
+    m = prog.member(comm, g)
+    return m if m is not None else (-1, -1)
 
 
 # ---------------------------------------------------------------------------
@@ -92,12 +99,15 @@ def closed_form_matches(prog: Program) -> Dict[int, int]:
             o = prog.ops[j]
             k = int(o["kind"])
             if k in SEND_KINDS:
-                me = comm_rank(prog, int(o["comm"]), g)
-                sends[(int(o["comm"]), me, int(o["peer"]), int(o["tag"]))].append(j)
+                me = comm_member(prog, int(o["comm"]), g)
+                dst = (int(o["peer"]), int(o["didx"]))
+                sends[(int(o["comm"]), me, dst, int(o["tag"]))].append(j)
             elif k in RECV_KINDS:
                 assert int(o["peer"]) != ANY_SOURCE and int(o["tag"]) != ANY_TAG
-                me = comm_rank(prog, int(o["comm"]), g)
-                recvs[(int(o["comm"]), int(o["peer"]), me, int(o["tag"]))].append(j)
+                assert int(o["sidx"]) != ANY_INDEX
+                me = comm_member(prog, int(o["comm"]), g)
+                src = (int(o["peer"]), int(o["sidx"]))
+                recvs[(int(o["comm"]), src, me, int(o["tag"]))].append(j)
     out = {}
     for key, ss in sends.items():
         for s, r in zip(ss, recvs.get(key, [])):
@@ -109,10 +119,11 @@ def accepts(prog: Program, r: int, s: int) -> bool:
     ro, so = prog.ops[r], prog.ops[s]
     if int(ro["comm"]) != int(so["comm"]):
         return False
-    if comm_rank(prog, int(ro["comm"]), int(ro["stream"])) != int(so["peer"]):
+    if comm_member(prog, int(ro["comm"]), int(ro["stream"])) != (int(so["peer"]), int(so["didx"])):
         return False
-    src = comm_rank(prog, int(so["comm"]), int(so["stream"]))
-    return (int(ro["peer"]) in (ANY_SOURCE, src)) and (int(ro["tag"]) in (ANY_TAG, int(so["tag"])))
+    src, sidx = comm_member(prog, int(so["comm"]), int(so["stream"]))
+    return (int(ro["peer"]) in (ANY_SOURCE, src)) and (int(ro["sidx"]) in (ANY_INDEX, sidx)) and \
+        (int(ro["tag"]) in (ANY_TAG, int(so["tag"])))
 
 
 def validity_violations(prog: Program, match: np.ndarray, require_complete: bool) -> List[str]:
@@ -139,7 +150,8 @@ def validity_violations(prog: Program, match: np.ndarray, require_complete: bool
     by_channel = defaultdict(list)
     for s, r in pairs:
         o = prog.ops[s]
-        by_channel[(int(o["stream"]), int(o["comm"]), int(o["peer"]), int(prog.ops[r]["stream"]))].append((s, r))
+        by_channel[(int(o["stream"]), int(o["comm"]), int(o["peer"]), int(o["didx"]),
+                    int(prog.ops[r]["stream"]))].append((s, r))
     for lst in by_channel.values():
         lst.sort()
         for a in range(len(lst)):
@@ -169,20 +181,21 @@ def legal_outcomes(prog: Program, max_states: int = 2_000_000) -> Set[Tuple[Froz
             a = int(ops[j]["req_lo"])
             reqs[j] = [int(q) for q in prog.reqlist[a: a + int(ops[j]["req_n"])]]
         assert int(ops[j]["kind"]) not in (ALLREDUCE, AXPY)
-    rank = {j: comm_rank(prog, int(ops[j]["comm"]), int(ops[j]["stream"]))
-            for j in range(len(ops)) if int(ops[j]["comm"]) >= 0}
+    member = {j: comm_member(prog, int(ops[j]["comm"]), int(ops[j]["stream"]))
+              for j in range(len(ops)) if int(ops[j]["comm"]) >= 0}
 
     def dom_of_send(s):
-        return (int(ops[s]["comm"]), int(ops[s]["peer"]))
+        return (int(ops[s]["comm"]), int(ops[s]["peer"]), int(ops[s]["didx"]))
 
     def dom_of_recv(r):
-        return (int(ops[r]["comm"]), rank[r])
+        return (int(ops[r]["comm"]),) + member[r]
 
     def chan_of(s):
-        return (int(ops[s]["stream"]), int(ops[s]["comm"]), int(ops[s]["peer"]))
+        return (int(ops[s]["stream"]), int(ops[s]["comm"]), int(ops[s]["peer"]), int(ops[s]["didx"]))
 
     def ok(r, s):
-        return (int(ops[r]["peer"]) in (ANY_SOURCE, rank[s])) and \
+        return (int(ops[r]["peer"]) in (ANY_SOURCE, member[s][0])) and \
+               (int(ops[r]["sidx"]) in (ANY_INDEX, member[s][1])) and \
                (int(ops[r]["tag"]) in (ANY_TAG, int(ops[s]["tag"])))
 
     # state: (cursors, posted_recv_ops, chans, posted(dom->tuple), unexp(dom->tuple), matches)

@@ -11,7 +11,7 @@ from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
-from .program import (ANY_SOURCE, ANY_TAG, IN_PLACE, MODE_FIXED, MODE_TREE, T_BYTE,
+from .program import (ANY_INDEX, ANY_SOURCE, ANY_TAG, IN_PLACE, MODE_FIXED, MODE_TREE, T_BYTE,
                       T_DOUBLE, T_FLOAT, T_INT32, T_INT64, BASIC_SIZES, Program,
                       ProgramBuilder)
 from .rng import Rng
@@ -519,4 +519,97 @@ def random_small(seed: int, nranks: int = 3, nmsg: int = 5, p_any_src: float = 0
                     b.waitall(gs[r], chosen, b.status_slots(len(chosen)))
         if pending:
             b.waitall(gs[r], pending, b.status_slots(len(pending)))
+    return b.build()
+
+
+# ----------------------------------------------------------------------------
+# Multiplex stream communicators (§3.5)
+# ----------------------------------------------------------------------------
+def multiplex_small(seed: int, nranks: int = 2, counts: Sequence[int] = (2, 3), nmsg: int = 6,
+                    p_any_src: float = 0.3, p_any_idx: float = 0.3, p_any_tag: float = 0.3,
+                    ntags: int = 2, p_blocking: float = 0.3, max_count: int = 4,
+                    p_wait: float = 0.35) -> Program:
+    """A handful of messages between the (rank, local index) members of one
+    multiplex stream communicator: rank r attaches counts[r] streams.  Sends
+    name the destination's stream; receives name the source rank and index,
+    either of which may be a wildcard, and the tag.  Blocking and nonblocking
+    calls mix as in `random_small` (a waitall over some pending requests
+    follows a call with probability p_wait); capacities are the largest
+    message."""
+    assert len(counts) == nranks
+    rng = Rng(seed, 61)
+    b = ProgramBuilder(nranks, "multiplex_small")
+    local = [[b.stream(r) for _ in range(int(counts[r]))] for r in range(nranks)]
+    c = b.comm_multiple(local)
+    members = [(r, i) for r in range(nranks) for i in range(int(counts[r]))]
+    src = rng.integers(0, len(members) - 1, nmsg)
+    dst = rng.integers(0, len(members) - 1, nmsg)
+    tags = rng.integers(0, ntags - 1, nmsg)
+    cnts = rng.integers(1, max_count, nmsg)
+    anys = rng.uniform(nmsg) < p_any_src
+    anyi = rng.uniform(nmsg) < p_any_idx
+    anyt = rng.uniform(nmsg) < p_any_tag
+    keys = rng.uniform(2 * nmsg)
+    blocking = rng.uniform(2 * nmsg) < p_blocking
+    sbuf = {m: b.buffer(rng.bytes(4 * max_count * nmsg)) for m in members}
+    rbuf = {m: b.buffer(4 * max_count * nmsg) for m in members}
+    items = {m: [] for m in members}
+    for k in range(nmsg):
+        items[members[int(src[k])]].append((keys[2 * k], "s", k, bool(blocking[2 * k])))
+        items[members[int(dst[k])]].append((keys[2 * k + 1], "r", k, bool(blocking[2 * k + 1])))
+    for m in members:
+        g = local[m[0]][m[1]]
+        pending = []
+        for key, kind, k, blk in sorted(items[m]):
+            k = int(k)
+            off = 4 * max_count * k
+            if kind == "s":
+                dr, di = members[int(dst[k])]
+                h = b.stream_send(g, c, sbuf[m], off, int(cnts[k]), T_INT32, dr, di, int(tags[k]),
+                                  blocking=blk)
+            else:
+                sr, si = members[int(src[k])]
+                h = b.stream_recv(g, c, rbuf[m], off, max_count, T_INT32,
+                                  ANY_SOURCE if anys[k] else sr, ANY_INDEX if anyi[k] else si,
+                                  ANY_TAG if anyt[k] else int(tags[k]), blocking=blk,
+                                  status=b.status_slots(1) if blk else -1)
+            if not blk:
+                pending.append(h)
+            if pending and float(rng.uniform(1)[0]) < p_wait:
+                n = int(rng.integers(1, len(pending), 1)[0])
+                chosen, pending = pending[:n], pending[n:]
+                b.waitall(g, chosen, b.status_slots(len(chosen)))
+        if pending:
+            b.waitall(g, pending, b.status_slots(len(pending)))
+    return b.build()
+
+
+def n_to_one(nranks: int = 4, threads: int = 4, msgs: int = 8, max_bytes: int = 4096,
+             seed: int = SEED_BASE + 5) -> Program:
+    """The N-to-1 pattern of §3.5: every rank attaches `threads` streams to
+    one multiplex stream communicator; every stream except rank 0's stream 0
+    sends `msgs` messages to that polling stream, whose receives are all
+    (ANY_SOURCE, ANY_INDEX, ANY_TAG).  Message k of sender (r, i) has tag k
+    and log-uniform size (bytes of int32 elements); every receive has the
+    largest capacity.  Each sender ends with a waitall, the poller with one
+    waitall over all its receives (statuses recorded)."""
+    rng = Rng(seed, 62)
+    b = ProgramBuilder(nranks, "n_to_one")
+    local = [[b.stream(r) for _ in range(threads)] for r in range(nranks)]
+    c = b.comm_multiple(local)
+    senders = [(r, i) for r in range(nranks) for i in range(threads) if (r, i) != (0, 0)]
+    maxc = max(1, max_bytes // 4)
+    nrecv = len(senders) * msgs
+    rb = b.buffer(4 * maxc * nrecv)
+    for (r, i) in senders:
+        sizes = np.maximum(1, np.exp(rng.uniform(msgs) * np.log(maxc)).astype(np.int64))
+        sb = b.buffer(rng.bytes(4 * maxc * msgs))
+        g = local[r][i]
+        reqs = [b.stream_send(g, c, sb, 4 * maxc * k, int(sizes[k]), T_INT32, 0, 0, k)
+                for k in range(msgs)]
+        b.waitall(g, reqs)
+    poll = local[0][0]
+    reqs = [b.stream_recv(poll, c, rb, 4 * maxc * q, maxc, T_INT32, ANY_SOURCE, ANY_INDEX, ANY_TAG)
+            for q in range(nrecv)]
+    b.waitall(poll, reqs, b.status_slots(nrecv))
     return b.build()

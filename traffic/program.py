@@ -23,6 +23,7 @@ COLLECTIVES = (ALLREDUCE, BCAST, REDUCE, ALLGATHER)
 
 ANY_SOURCE = -2
 ANY_TAG = -1
+ANY_INDEX = -1         # multiplex stream communicators: any of the source rank's streams
 IN_PLACE = -3          # allreduce send buffer id meaning "use the receive buffer"
 
 # --- predefined datatypes (ids 0..4); derived vector types are appended ---
@@ -40,16 +41,18 @@ ERR_TRUNCATE = 15
 ERR_TIMEOUT = 16
 
 # One record per operation.  Field order and offsets are an interface format
-# shared with the oracle's C struct (80 bytes, little endian).
+# shared with the oracle's C struct (88 bytes, little endian).  sidx / didx:
+# on a multiplex stream communicator (§3.5) the sender's and the receiver's
+# local stream index (a receive's sidx may be ANY_INDEX); 0 on other comms.
 OP_DTYPE = np.dtype({
     "names": ["stream", "kind", "comm", "peer", "tag", "type", "count",
               "buf", "buf2", "off", "off2", "req_lo", "req_n", "status",
-              "mode", "alpha", "pad"],
+              "mode", "alpha", "sidx", "didx", "pad"],
     "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<i8",
                 "<i4", "<i4", "<i8", "<i8", "<i4", "<i4", "<i4",
-                "<i4", "<f4", "<i4"],
-    "offsets": [0, 4, 8, 12, 16, 20, 24, 32, 36, 40, 48, 56, 60, 64, 68, 72, 76],
-    "itemsize": 80,
+                "<i4", "<f4", "<i4", "<i4", "<i4"],
+    "offsets": [0, 4, 8, 12, 16, 20, 24, 32, 36, 40, 48, 56, 60, 64, 68, 72, 76, 80, 84],
+    "itemsize": 88,
 })
 
 # kind 0 = predefined, 1 = vector(vcount, blocklen, stride) of a predefined type
@@ -60,8 +63,9 @@ TYPE_DTYPE = np.dtype({
     "itemsize": 24,
 })
 
+# source_index: the sender's local stream index on a multiplex comm, else 0
 STATUS_DTYPE = np.dtype({
-    "names": ["source", "tag", "error", "pad", "bytes"],
+    "names": ["source", "tag", "error", "source_index", "bytes"],
     "formats": ["<i4", "<i4", "<i4", "<i4", "<i8"],
     "offsets": [0, 4, 8, 12, 16],
     "itemsize": 24,
@@ -113,6 +117,23 @@ class Program:
     issue_order: np.ndarray            # int64 op indices in host enqueue order
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # per comm: None, or (multiplex stream comm, §3.5) per rank the list of its
+    # local streams in index order; comm_stream then holds each rank's index 0
+    comm_mux: List[Optional[List[List[int]]]] = field(default_factory=list)
+
+    def mux(self, c: int) -> Optional[List[List[int]]]:
+        return self.comm_mux[c] if c < len(self.comm_mux) else None
+
+    def member(self, c: int, g: int):
+        """(rank, local index) of stream g in comm c, or None."""
+        m = self.mux(c)
+        if m is None:
+            hits = np.nonzero(self.comm_stream[c] == g)[0]
+            return (int(hits[0]), 0) if len(hits) else None
+        for r, lst in enumerate(m):
+            if g in lst:
+                return (r, lst.index(g))
+        return None
 
     @property
     def nstreams(self) -> int:
@@ -134,6 +155,7 @@ class ProgramBuilder:
         self.name = name
         self.stream_rank: List[int] = []
         self.comms: List[List[int]] = []
+        self.comm_mux: List[Optional[List[List[int]]]] = []
         self.per_stream: List[List[dict]] = []
         self.types = list(basic_types())
         self.bufs: List[np.ndarray] = []
@@ -153,7 +175,27 @@ class ProgramBuilder:
         for r, g in enumerate(streams):
             assert self.stream_rank[g] == r, "comm member r must be a stream of rank r"
         self.comms.append(list(streams))
+        self.comm_mux.append(None)
         return len(self.comms) - 1
+
+    def comm_multiple(self, local_streams: Sequence[Sequence[int]]) -> int:
+        """MPIX_Stream_comm_create_multiple (§3.5): rank r attaches the streams
+        local_streams[r] (at least one), addressed by their index in that list."""
+        assert len(local_streams) == self.nranks
+        lists = []
+        for r, lst in enumerate(local_streams):
+            assert len(lst) >= 1 and len(set(lst)) == len(lst)
+            for g in lst:
+                assert self.stream_rank[g] == r, "rank r attaches streams of rank r"
+            lists.append(list(lst))
+        self.comms.append([lst[0] for lst in lists])
+        self.comm_mux.append(lists)
+        return len(self.comms) - 1
+
+    def _index(self, comm: int, g: int) -> int:
+        lists = self.comm_mux[comm]
+        assert lists is not None, "a multiplex stream communicator"
+        return lists[self.stream_rank[g]].index(g)
 
     def vector(self, vcount: int, blocklen: int, stride: int, base: int) -> int:
         assert base in BASIC_SIZES and vcount >= 1 and blocklen >= 1 and stride >= blocklen
@@ -181,7 +223,7 @@ class ProgramBuilder:
     def _op(self, g: int, **kw) -> tuple:
         rec = dict(stream=g, kind=0, comm=-1, peer=0, tag=0, type=0, count=0,
                    buf=-1, buf2=-1, off=0, off2=0, req_lo=0, req_n=0,
-                   status=-1, mode=0, alpha=0.0, reqs=None)
+                   status=-1, mode=0, alpha=0.0, sidx=0, didx=0, reqs=None)
         rec.update(kw)
         self.per_stream[g].append(rec)
         h = (g, len(self.per_stream[g]) - 1)
@@ -203,6 +245,19 @@ class ProgramBuilder:
     def irecv(self, g, comm, buf, off, count, type_, source, tag):
         return self._op(g, kind=IRECV, comm=comm, buf=buf, off=off, count=count,
                         type=type_, peer=source, tag=tag)
+
+    # MPIX_Stream_send / recv / isend / irecv (§3.5): stream g is the caller's
+    # local stream (src_idx for sends, dst_idx for receives)
+    def stream_send(self, g, comm, buf, off, count, type_, dest, dst_idx, tag, blocking=False):
+        return self._op(g, kind=SEND if blocking else ISEND, comm=comm, buf=buf, off=off,
+                        count=count, type=type_, peer=dest, tag=tag,
+                        sidx=self._index(comm, g), didx=dst_idx)
+
+    def stream_recv(self, g, comm, buf, off, count, type_, source, src_idx, tag, blocking=False,
+                    status=-1):
+        return self._op(g, kind=RECV if blocking else IRECV, comm=comm, buf=buf, off=off,
+                        count=count, type=type_, peer=source, tag=tag, status=status,
+                        sidx=src_idx, didx=self._index(comm, g))
 
     def wait(self, g, req, status=-1):
         assert req[0] == g
@@ -271,4 +326,5 @@ class ProgramBuilder:
                        types=np.array(self.types, TYPE_DTYPE),
                        buf_init=self.bufs, reqlist=np.array(reqlist, np.int64),
                        nstatus=self.nstatus, issue_order=issue, name=self.name,
-                       meta=dict(self.meta))
+                       meta=dict(self.meta), comm_mux=[None if m is None else [list(l) for l in m]
+                                                       for m in self.comm_mux])
