@@ -72,7 +72,7 @@ typedef struct {
   int32_t source; /* sender's rank in the communicator */
   int32_t tag;    /* sender's tag */
   int32_t error;  /* MPX_SUCCESS, MPX_ERR_TRUNCATE, MPX_ERR_TIMEOUT, ... */
-  int32_t pad;
+  int32_t source_index; /* multiplex stream communicator: the sender's local stream index; else 0 */
   int64_t bytes;  /* bytes delivered */
 } mpx_status_t;   /* 24 bytes */
 
@@ -84,6 +84,7 @@ typedef struct {
 enum {
   MPX_ANY_SOURCE = -2,
   MPX_ANY_TAG = -1,
+  MPX_ANY_INDEX = -1,   /* MPIX_ANY_INDEX: any local stream of the source (multiplex comms) */
   MPX_TAG_UB = (1 << 30) - 1,
   MPX_UNDEFINED = -32766
 };
@@ -257,6 +258,21 @@ int mpx_stream_pending(mpx_stream_t stream, int64_t* pending);
 int mpx_stream_comm_create(mpx_world_t parent, int nranks, const mpx_stream_t streams[],
                            mpx_comm_t comms_out[]);
 
+/* MPIX_Stream_comm_create_multiple (§3.5): a multiplex stream communicator
+ * in which rank r attaches counts[r] >= 1 of its own streams, addressed by
+ * their local index 0..counts[r]-1.  streams[] lists rank 0's streams in
+ * index order, then rank 1's, ... (sum of counts entries; no stream twice
+ * within one rank).  comms_out[r] receives rank r's handle.  It carries the
+ * mpx_stream_* point-to-point calls below only: the plain p2p calls and the
+ * collectives answer MPX_ERR_COMM on it, and so do mpx_enqueue_batch and
+ * mpx_step_create.  Every member (rank, index) is a matching domain: a
+ * communicator of M = sum(counts) members takes ceil(M / nranks) of the
+ * world's max_comms slots (MPX_ERR_NO_MEM when they are used up).  M is at
+ * most 65535 and counts[r] at most 32766.  MPX_ERR_UNSUPPORTED on the plain
+ * path (MPX_ENGINE_PLAIN). */
+int mpx_stream_comm_create_multiple(mpx_world_t parent, int nranks, const int counts[],
+                                    const mpx_stream_t streams[], mpx_comm_t comms_out[]);
+
 /* Free one rank's handle; the communicator dies with its last handle. */
 int mpx_comm_free(mpx_comm_t* comm);
 int mpx_comm_rank(mpx_comm_t comm, int* rank);
@@ -297,6 +313,31 @@ int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t datatype, i
                       mpx_comm_t comm, mpx_request_t* request);
 int mpx_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int source, int tag,
                       mpx_comm_t comm, mpx_request_t* request);
+
+/* MPIX_Stream_send / recv / isend / irecv (§3.5) on a multiplex stream
+ * communicator, in enqueue form: a send is enqueued on the caller's local
+ * stream src_idx and addresses stream dst_idx of rank dest; a receive is
+ * enqueued on the caller's local stream dst_idx and accepts a message from
+ * stream src_idx of rank source, where source may be MPX_ANY_SOURCE and
+ * src_idx MPX_ANY_INDEX.  Messages between one (rank, index) pair and
+ * another do not overtake; matching is otherwise as for the plain calls.
+ * Requests belong to the local stream the call was enqueued on (wait for
+ * them there).  status->source / source_index give the sender's rank and
+ * local index.  Errors: MPX_ERR_COMM (not a multiplex handle), MPX_ERR_RANK,
+ * MPX_ERR_TAG, MPX_ERR_ARG (an index out of range: src_idx on a receive is
+ * checked against the source's stream count, or the largest count when
+ * source is MPX_ANY_SOURCE), MPX_ERR_TYPE, and those of the plain calls. */
+int mpx_stream_send_enqueue(const void* buf, int64_t count, mpx_datatype_t datatype, int dest,
+                            int tag, mpx_comm_t comm, int src_idx, int dst_idx);
+int mpx_stream_recv_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int source,
+                            int tag, mpx_comm_t comm, int src_idx, int dst_idx,
+                            mpx_status_t* status);
+int mpx_stream_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t datatype, int dest,
+                             int tag, mpx_comm_t comm, int src_idx, int dst_idx,
+                             mpx_request_t* request);
+int mpx_stream_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int source,
+                             int tag, mpx_comm_t comm, int src_idx, int dst_idx,
+                             mpx_request_t* request);
 
 /* MPIX_Wait_enqueue (§3.4): enqueued on the request's stream; work enqueued
  * after it runs once the request completed.  *request becomes

@@ -251,6 +251,17 @@ __device__ __forceinline__ DOp* op_ref(const EngineParams& P, uint64_t ref) {
   return op_at(P, ref_stream(ref), ref_seq(ref));
 }
 __device__ __forceinline__ bool is_send(uint32_t k) { return k == K_SEND || k == K_ISEND; }
+
+// Source matching (§2.1, §3.5).  A send's key is (local index << 16 | rank);
+// a receive's pattern is kAnySource, or the same packing with 0xFFFF for any
+// rank and 0x7FFF for any index.  On a communicator with one stream per rank
+// every index is 0, so a key is the rank and an exact pattern is the source.
+__device__ __forceinline__ bool src_accepts(int32_t pattern, int32_t key) {
+  if (pattern == kAnySource) return true;
+  const uint32_t p = (uint32_t)pattern, k = (uint32_t)key;
+  const uint32_t pr = p & 0xFFFFu, pi = p >> 16;
+  return (pr == 0xFFFFu || pr == (k & 0xFFFFu)) && (pi == 0x7FFFu || pi == (k >> 16));
+}
 __device__ __forceinline__ bool is_recv(uint32_t k) { return k == K_RECV || k == K_IRECV; }
 __device__ __forceinline__ bool is_blocking(uint32_t k) {
   return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL || is_collective_kind(k);
@@ -1124,9 +1135,9 @@ struct Ctl {
         const QEntry e = q[idx & qmask];
         if (e.ref != 0) {
           if (is_send_post)  // looking for a posted receive accepting (src, tag)
-            hit = (e.src == kAnySource || e.src == src) && (e.tag == kAnyTag || e.tag == tag);
+            hit = src_accepts(e.src, src) && (e.tag == kAnyTag || e.tag == tag);
           else  // looking for an unexpected send the receive (src, tag) accepts
-            hit = (src == kAnySource || src == e.src) && (tag == kAnyTag || tag == e.tag);
+            hit = src_accepts(src, e.src) && (tag == kAnyTag || tag == e.tag);
         }
       }
       const unsigned b = __ballot_sync(FULL, hit);
@@ -1175,7 +1186,7 @@ struct Ctl {
     r->partner = sref;
     r->bytes = sent < cap ? sent : cap;
     r->err = sent > cap ? kErrTruncate : 0;
-    r->msrc = s->d.rank;
+    r->msrc = s->d.n32;  // the sender's key: rank and local index
     r->mtag = s->d.tag;
     r->lstate = 2;
     r->lround = (int32_t)round;
@@ -1192,7 +1203,7 @@ struct Ctl {
           const uint32_t kind = kw_kind(o->d.kw);
           const uint64_t ref = make_ref(g, seq);
           if (is_send(kind)) {
-            const int32_t src = o->d.rank, tag = o->d.tag;
+            const int32_t src = o->d.n32, tag = o->d.tag;  // sender key
             const int64_t hit = q_find(pq, ph, qmask, true, src, tag);
             if (hit >= 0) {
               const uint64_t rref = pq[(uint32_t)hit & qmask].ref;
@@ -1558,17 +1569,22 @@ struct Ctl {
   }
 
   // --- 3a. per stream: physical completion, completion word, retirement ---
-  __device__ void write_status(uint64_t addr, int32_t src, int32_t tag, int32_t err, int64_t bytes) {
+  __device__ void write_status(uint64_t addr, int32_t src, int32_t tag, int32_t err, int64_t bytes,
+                               int32_t src_index = 0) {
     if (!addr) return;
     int32_t* p = (int32_t*)addr;
     p[0] = src;
     p[1] = tag;
     p[2] = err;
-    p[3] = 0;
+    p[3] = src_index;
     *(int64_t*)(p + 4) = bytes;
   }
+  // a receive's status: the matched sender's key split into rank and index
+  __device__ void recv_status(uint64_t addr, const DOp* q) {
+    write_status(addr, q->msrc & 0xFFFF, q->mtag, q->err, q->bytes, (int32_t)((uint32_t)q->msrc >> 16));
+  }
   __device__ void request_status(uint64_t addr, const DOp* q) {
-    if (is_recv(kw_kind(q->d.kw))) write_status(addr, q->msrc, q->mtag, q->err, q->bytes);
+    if (is_recv(kw_kind(q->d.kw))) recv_status(addr, q);
     else write_status(addr, kAnySource, kAnyTag, q->err, 0);
   }
 
@@ -1669,7 +1685,7 @@ struct Ctl {
   __device__ void finish_blocking(int g, DOp* o) {
     const uint32_t k = kw_kind(o->d.kw);
     if (k == K_RECV) {
-      write_status(o->d.status, o->msrc, o->mtag, o->err, o->bytes);
+      recv_status(o->d.status, o);
       if (o->err) set_error(P, g, o->err);
     } else if (k == K_WAIT) {
       if (o->d.aux) {

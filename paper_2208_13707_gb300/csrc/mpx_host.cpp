@@ -168,6 +168,11 @@ struct CommShared {
   std::atomic<int> handles;
   int id;
   int reduce_mode;
+  // multiplex stream communicator (§3.5): member (rank r, local index i) is
+  // mux_off[r] + i; empty for a communicator with one stream per rank
+  std::vector<int> mux_off;
+  int mux_max = 0;  // most streams any rank attached
+  bool mux() const { return !mux_off.empty(); }
 };
 
 struct mpx_comm_s {
@@ -175,7 +180,8 @@ struct mpx_comm_s {
   CommShared* shared;
   int rank;
   int size;
-  mpx_stream_s* stream;
+  mpx_stream_s* stream;              // the rank's stream (multiplex: its index 0)
+  std::vector<mpx_stream_s*> local;  // multiplex: the rank's streams by local index
 };
 
 struct mpx_world_s {
@@ -816,12 +822,75 @@ extern "C" int mpx_stream_comm_create(mpx_world_t w, int nranks, const mpx_strea
   return MPX_SUCCESS;
 }
 
+extern "C" int mpx_stream_comm_create_multiple(mpx_world_t w, int nranks, const int counts[],
+                                               const mpx_stream_t streams[],
+                                               mpx_comm_t comms_out[]) {
+  if (!w || !counts || !streams || !comms_out) return MPX_ERR_ARG;
+  if (nranks != w->nranks) return MPX_ERR_ARG;
+  if (w->plain) return MPX_ERR_UNSUPPORTED;
+  std::vector<int> off((size_t)nranks + 1, 0);
+  int most = 0;
+  for (int r = 0; r < nranks; ++r) {
+    if (counts[r] < 1 || counts[r] > 0x7FFE) return MPX_ERR_ARG;
+    off[(size_t)r + 1] = off[(size_t)r] + counts[r];
+    if (off[(size_t)r + 1] > 0xFFFF) return MPX_ERR_ARG;  // members fit the 16-bit rank field
+    most = std::max(most, counts[r]);
+  }
+  for (int r = 0; r < nranks; ++r) {
+    for (int i = 0; i < counts[r]; ++i) {
+      mpx_stream_s* st = streams[off[(size_t)r] + i];
+      if (!st) return MPX_ERR_COMM;
+      if (st->w != w || st->rank != r) return MPX_ERR_ARG;
+      for (int k = 0; k < i; ++k)
+        if (streams[off[(size_t)r] + k] == st) return MPX_ERR_ARG;
+    }
+  }
+  // every member is a matching domain: ceil(M / nranks) consecutive slots
+  const int slots = (off[(size_t)nranks] + nranks - 1) / nranks;
+  std::lock_guard<std::mutex> g(w->mu);
+  if (w->comms_used + slots > w->cfg.max_comms) return MPX_ERR_NO_MEM;
+  CommShared* sh = new (std::nothrow) CommShared();
+  if (!sh) return MPX_ERR_NO_MEM;
+  sh->id = w->comms_used;
+  sh->reduce_mode = w->cfg.reduce_mode;
+  sh->handles.store(nranks);
+  sh->mux_off = off;
+  sh->mux_max = most;
+  std::vector<mpx_comm_s*> made;
+  for (int r = 0; r < nranks; ++r) {
+    mpx_comm_s* c = new (std::nothrow) mpx_comm_s();
+    if (!c) {
+      for (auto* m : made) delete m;
+      delete sh;
+      return MPX_ERR_NO_MEM;
+    }
+    c->w = w;
+    c->shared = sh;
+    c->rank = r;
+    c->size = nranks;
+    c->local.assign(streams + off[(size_t)r], streams + off[(size_t)r + 1]);
+    c->stream = c->local[0];
+    made.push_back(c);
+  }
+  w->comms_used += slots;
+  for (int r = 0; r < nranks; ++r) {
+    for (mpx_stream_s* st : made[(size_t)r]->local) st->ncomms++;
+    comms_out[r] = made[(size_t)r];
+  }
+  w->live_comm_handles += nranks;
+  return MPX_SUCCESS;
+}
+
 extern "C" int mpx_comm_free(mpx_comm_t* pc) {
   if (!pc || !*pc) return MPX_ERR_ARG;
   mpx_comm_s* c = *pc;
   mpx_world_s* w = c->w;
   std::lock_guard<std::mutex> g(w->mu);
-  c->stream->ncomms--;
+  if (c->shared->mux()) {
+    for (mpx_stream_s* st : c->local) st->ncomms--;
+  } else {
+    c->stream->ncomms--;
+  }
   w->live_comm_handles--;
   if (c->shared->handles.fetch_sub(1) == 1) delete c->shared;
   delete c;
@@ -1004,7 +1073,7 @@ static int publish(mpx_stream_s* s, Desc& d, bool blocking, uint64_t* seq_out,
 
 static int fill_p2p(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt,
                     int peer, int tag, mpx_comm_s* c, bool is_recv) {
-  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (count < 0) return MPX_ERR_ARG;
   const TypeRec* t = type_get(dt);
   if (!t) return MPX_ERR_TYPE;
@@ -1027,6 +1096,67 @@ static int fill_p2p(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_
   d.vcount = t->vcount;
   d.blocklen = t->blocklen;
   d.stride = t->stride;
+  if (!is_recv) d.n32 = (int32_t)c->rank;  // sender key (rank, local index 0)
+  return MPX_SUCCESS;
+}
+
+// A point-to-point call on a multiplex stream communicator (§3.5).  The
+// engine matches per member: a send's domain is the destination member
+// (d.peer), a receive's its own member (d.rank).  A send carries its sender
+// key (local index << 16 | rank) in d.n32; a receive carries its source
+// pattern in d.peer: MPX_ANY_SOURCE when both rank and index are wildcards,
+// else (index or 0x7FFF) << 16 | (rank or 0xFFFF).  Returns the local stream
+// the call is enqueued on through *st.
+static int fill_mux(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt,
+                    int peer, int tag, mpx_comm_s* c, int src_idx, int dst_idx,
+                    mpx_stream_s** st) {
+  if (!c || !c->shared->mux()) return MPX_ERR_COMM;
+  const CommShared* sh = c->shared;
+  if (count < 0) return MPX_ERR_ARG;
+  const TypeRec* t = type_get(dt);
+  if (!t) return MPX_ERR_TYPE;
+  auto nloc = [&](int r) { return sh->mux_off[(size_t)r + 1] - sh->mux_off[(size_t)r]; };
+  const bool is_recv = kind == K_RECV || kind == K_IRECV;
+  int own;
+  if (is_recv) {
+    if (peer != MPX_ANY_SOURCE && (peer < 0 || peer >= c->size)) return MPX_ERR_RANK;
+    if (tag != MPX_ANY_TAG && (tag < 0 || tag > MPX_TAG_UB)) return MPX_ERR_TAG;
+    if (dst_idx < 0 || dst_idx >= nloc(c->rank)) return MPX_ERR_ARG;
+    if (src_idx != MPX_ANY_INDEX &&
+        (src_idx < 0 || src_idx >= (peer == MPX_ANY_SOURCE ? sh->mux_max : nloc(peer))))
+      return MPX_ERR_ARG;
+    own = dst_idx;
+  } else {
+    if (peer < 0 || peer >= c->size) return MPX_ERR_RANK;
+    if (tag < 0 || tag > MPX_TAG_UB) return MPX_ERR_TAG;
+    if (src_idx < 0 || src_idx >= nloc(c->rank)) return MPX_ERR_ARG;
+    if (dst_idx < 0 || dst_idx >= nloc(peer)) return MPX_ERR_ARG;
+    own = src_idx;
+  }
+  if (count > 0 && !buf) return MPX_ERR_ARG;
+  memset(&d, 0, sizeof(d));
+  d.kw = make_kw(kind, (uint32_t)t->base, 0);
+  d.comm = (uint16_t)sh->id;
+  d.rank = (uint16_t)(sh->mux_off[(size_t)c->rank] + own);
+  if (is_recv) {
+    if (peer == MPX_ANY_SOURCE && src_idx == MPX_ANY_INDEX) {
+      d.peer = MPX_ANY_SOURCE;
+    } else {
+      const uint32_t pi = src_idx == MPX_ANY_INDEX ? 0x7FFFu : (uint32_t)src_idx;
+      const uint32_t pr = peer == MPX_ANY_SOURCE ? 0xFFFFu : (uint32_t)peer;
+      d.peer = (int32_t)((pi << 16) | pr);
+    }
+  } else {
+    d.peer = sh->mux_off[(size_t)peer] + dst_idx;
+    d.n32 = (int32_t)(((uint32_t)src_idx << 16) | (uint32_t)c->rank);
+  }
+  d.tag = tag;
+  d.buf = (uint64_t)buf;
+  d.count = count;
+  d.vcount = t->vcount;
+  d.blocklen = t->blocklen;
+  d.stride = t->stride;
+  *st = c->local[(size_t)own];
   return MPX_SUCCESS;
 }
 
@@ -1072,6 +1202,51 @@ extern "C" int mpx_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t 
 extern "C" int mpx_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source, int tag,
                                  mpx_comm_t c, mpx_request_t* req) {
   return nb_p2p(K_IRECV, buf, count, dt, source, tag, c, req, false);
+}
+
+extern "C" int mpx_stream_send_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
+                                       int tag, mpx_comm_t c, int src_idx, int dst_idx) {
+  Desc d;
+  mpx_stream_s* st = nullptr;
+  int rc = fill_mux(d, K_SEND, buf, count, dt, dest, tag, c, src_idx, dst_idx, &st);
+  if (rc) return rc;
+  return publish(st, d, true, nullptr);
+}
+
+extern "C" int mpx_stream_recv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source,
+                                       int tag, mpx_comm_t c, int src_idx, int dst_idx,
+                                       mpx_status_t* status) {
+  Desc d;
+  mpx_stream_s* st = nullptr;
+  int rc = fill_mux(d, K_RECV, buf, count, dt, source, tag, c, src_idx, dst_idx, &st);
+  if (rc) return rc;
+  d.status = (uint64_t)status;
+  return publish(st, d, true, nullptr);
+}
+
+static int mux_nb(uint32_t kind, const void* buf, int64_t count, mpx_datatype_t dt, int peer,
+                  int tag, mpx_comm_t c, int src_idx, int dst_idx, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  Desc d;
+  mpx_stream_s* st = nullptr;
+  int rc = fill_mux(d, kind, buf, count, dt, peer, tag, c, src_idx, dst_idx, &st);
+  if (rc) return rc;
+  uint64_t seq = 0;
+  rc = publish(st, d, false, &seq);
+  if (seq) *req = make_request(st, seq);
+  return rc;
+}
+
+extern "C" int mpx_stream_isend_enqueue(const void* buf, int64_t count, mpx_datatype_t dt, int dest,
+                                        int tag, mpx_comm_t c, int src_idx, int dst_idx,
+                                        mpx_request_t* req) {
+  return mux_nb(K_ISEND, buf, count, dt, dest, tag, c, src_idx, dst_idx, req);
+}
+
+extern "C" int mpx_stream_irecv_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int source,
+                                        int tag, mpx_comm_t c, int src_idx, int dst_idx,
+                                        mpx_request_t* req) {
+  return mux_nb(K_IRECV, buf, count, dt, source, tag, c, src_idx, dst_idx, req);
 }
 
 static mpx_stream_s* request_stream(mpx_request_t r) {
@@ -1168,7 +1343,7 @@ static void fill_collective(Desc& d, uint32_t kind, mpx_datatype_t dt, mpx_comm_
 
 extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int root,
                                  mpx_comm_t c) {
-  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (root < 0 || root >= c->size) return MPX_ERR_RANK;
   if (count < 0 || (count > 0 && !buf)) return MPX_ERR_ARG;
@@ -1180,7 +1355,7 @@ extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, in
 
 extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                                   mpx_datatype_t dt, int op, int root, mpx_comm_t c) {
-  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (op != MPX_SUM) return MPX_ERR_ARG;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (root < 0 || root >= c->size) return MPX_ERR_RANK;
@@ -1198,7 +1373,7 @@ extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t co
 
 extern "C" int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                                      mpx_datatype_t dt, mpx_comm_t c) {
-  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;  // the rank's block is already in place
   if (count < 0 || (count > 0 && (!sendbuf || !recvbuf))) return MPX_ERR_ARG;
@@ -1215,7 +1390,7 @@ extern "C" int mpx_barrier_enqueue(mpx_comm_t c) {
 
 extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                                      mpx_datatype_t dt, int op, mpx_comm_t c) {
-  if (!c || !c->stream) return MPX_ERR_COMM;
+  if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (op != MPX_SUM) return MPX_ERR_ARG;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (count < 0 || (count > 0 && !recvbuf)) return MPX_ERR_ARG;
@@ -1360,7 +1535,7 @@ extern "C" int mpx_step_create(mpx_world_t w, int n, const mpx_op_t ops[], mpx_s
       case MPX_OP_SEND: case MPX_OP_RECV: case MPX_OP_ISEND: case MPX_OP_IRECV:
       case MPX_OP_ALLREDUCE: case MPX_OP_BCAST: case MPX_OP_REDUCE: case MPX_OP_ALLGATHER:
       case MPX_OP_BARRIER:
-        if (!o.comm || !o.comm->stream) return MPX_ERR_COMM;
+        if (!o.comm || !o.comm->stream || o.comm->shared->mux()) return MPX_ERR_COMM;
         if (o.comm->w != w) return MPX_ERR_ARG;
         st = o.comm->stream;
         break;

@@ -183,7 +183,7 @@ mpx_status_t make_status(int src, int tag, int err, int64_t bytes) {
   st.source = src;
   st.tag = tag;
   st.error = err;
-  st.pad = 0;
+  st.source_index = 0;
   st.bytes = bytes;
   return st;
 }

@@ -21,6 +21,7 @@ lib = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
 
 # --- constants (include/mpx.h) ---
 ANY_SOURCE, ANY_TAG, TAG_UB, UNDEFINED = -2, -1, (1 << 30) - 1, -32766
+ANY_INDEX = -1
 BYTE = UINT8 = 0
 INT32, INT64, FLOAT, DOUBLE = 1, 2, 3, 4
 SUM = 0
@@ -85,7 +86,7 @@ class ServeResult(ctypes.Structure):
 
 class Status(ctypes.Structure):
     _fields_ = [("source", ctypes.c_int32), ("tag", ctypes.c_int32), ("error", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("bytes", ctypes.c_int64)]
+                ("source_index", ctypes.c_int32), ("bytes", ctypes.c_int64)]
 
 
 _vp, _i32, _i64, _u32, _f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
@@ -107,6 +108,7 @@ _SIGS = {
     "mpx_stream_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_stream_pending": [_vp, _P(_i64)],
     "mpx_stream_comm_create": [_vp, ctypes.c_int, _P(_vp), _P(_vp)],
+    "mpx_stream_comm_create_multiple": [_vp, ctypes.c_int, _P(ctypes.c_int), _P(_vp), _P(_vp)],
     "mpx_comm_free": [_P(_vp)],
     "mpx_comm_rank": [_vp, _P(ctypes.c_int)],
     "mpx_comm_size": [_vp, _P(ctypes.c_int)],
@@ -119,6 +121,14 @@ _SIGS = {
     "mpx_recv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _vp],
     "mpx_isend_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
     "mpx_irecv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_stream_send_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                ctypes.c_int],
+    "mpx_stream_recv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                ctypes.c_int, _vp],
+    "mpx_stream_isend_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                 ctypes.c_int, _P(_i64)],
+    "mpx_stream_irecv_enqueue": [_vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                 ctypes.c_int, _P(_i64)],
     "mpx_wait_enqueue": [_P(_i64), _vp],
     "mpx_waitall_enqueue": [ctypes.c_int, _P(_i64), _vp],
     "mpx_allreduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp],
@@ -240,6 +250,18 @@ def mpx_stream_comm_create(world: int, streams: Sequence[int]) -> list:
     return [out[i] for i in range(n)]
 
 
+def mpx_stream_comm_create_multiple(world: int, local_streams: Sequence[Sequence[int]]) -> list:
+    """local_streams[r]: rank r's streams in local-index order; returns one handle per rank."""
+    n = len(local_streams)
+    counts = (ctypes.c_int * n)(*[len(l) for l in local_streams])
+    flat = [h for l in local_streams for h in l]
+    arr = (_vp * max(1, len(flat)))(*flat)
+    out = (_vp * n)()
+    _chk(lib.mpx_stream_comm_create_multiple(world, n, counts, arr, out),
+         "mpx_stream_comm_create_multiple")
+    return [out[i] for i in range(n)]
+
+
 def mpx_comm_free(comm: int) -> None:
     c = _vp(comm)
     _chk(lib.mpx_comm_free(ctypes.byref(c)), "mpx_comm_free")
@@ -304,6 +326,34 @@ def mpx_isend_enqueue(buf: int, count: int, datatype: int, dest: int, tag: int, 
 def mpx_irecv_enqueue(buf: int, count: int, datatype: int, source: int, tag: int, comm: int) -> int:
     r = _i64()
     _chk(lib.mpx_irecv_enqueue(buf, count, datatype, source, tag, comm, ctypes.byref(r)), "mpx_irecv_enqueue")
+    return r.value
+
+
+def mpx_stream_send_enqueue(buf: int, count: int, datatype: int, dest: int, tag: int, comm: int,
+                            src_idx: int, dst_idx: int) -> None:
+    _chk(lib.mpx_stream_send_enqueue(buf, count, datatype, dest, tag, comm, src_idx, dst_idx),
+         "mpx_stream_send_enqueue")
+
+
+def mpx_stream_recv_enqueue(buf: int, count: int, datatype: int, source: int, tag: int, comm: int,
+                            src_idx: int, dst_idx: int, status: int = 0) -> None:
+    _chk(lib.mpx_stream_recv_enqueue(buf, count, datatype, source, tag, comm, src_idx, dst_idx,
+                                     status or None), "mpx_stream_recv_enqueue")
+
+
+def mpx_stream_isend_enqueue(buf: int, count: int, datatype: int, dest: int, tag: int, comm: int,
+                             src_idx: int, dst_idx: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_stream_isend_enqueue(buf, count, datatype, dest, tag, comm, src_idx, dst_idx,
+                                      ctypes.byref(r)), "mpx_stream_isend_enqueue")
+    return r.value
+
+
+def mpx_stream_irecv_enqueue(buf: int, count: int, datatype: int, source: int, tag: int, comm: int,
+                             src_idx: int, dst_idx: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_stream_irecv_enqueue(buf, count, datatype, source, tag, comm, src_idx, dst_idx,
+                                      ctypes.byref(r)), "mpx_stream_irecv_enqueue")
     return r.value
 
 

@@ -44,7 +44,13 @@ def make_config(prog: Program, mode: int, **over):
     cfg.max_streams = max(cfg.max_streams, prog.nstreams)
     per_stream = int(np.max(np.diff(prog.stream_op_lo))) if prog.nstreams else 1
     cfg.ring_slots = _pow2_at_least(per_stream + 1, 256)
-    cfg.max_comms = max(1, prog.ncomms)
+    # a multiplex comm of M members takes ceil(M / nranks) comm slots
+    slots = 0
+    for c in range(prog.ncomms):
+        m = prog.mux(c)
+        members = prog.nranks if m is None else sum(len(l) for l in m)
+        slots += -(-members // prog.nranks)
+    cfg.max_comms = max(1, slots)
     cfg.queue_slots = _pow2_at_least(per_stream + 1, 256)
     cfg.watchdog_ns = int(5e9)
     for k, v in over.items():
@@ -81,6 +87,8 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
         ms.append(mpx.mpx_stream_create(world, int(prog.stream_rank[g]), cstreams[g].cuda_stream, flags))
         assert mpx.mpx_stream_get_id(ms[g]) == g
     comms = [mpx.mpx_stream_comm_create(world, [ms[int(g)] for g in prog.comm_stream[c]])
+             if prog.mux(c) is None else
+             mpx.mpx_stream_comm_create_multiple(world, [[ms[int(g)] for g in l] for l in prog.mux(c)])
              for c in range(prog.ncomms)]
     tmap = {}
     for t in range(len(prog.types)):
@@ -91,6 +99,9 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
     for c in range(prog.ncomms):
         for r, g in enumerate(prog.comm_stream[c]):
             rank_in[(c, int(g))] = r
+        for r, l in enumerate(prog.mux(c) or []):
+            for g in l:
+                rank_in[(c, int(g))] = r
     engine_stream = torch.cuda.ExternalStream(raw_streams[-1], device=dev)
     req: Dict[int, int] = {}
     ops = prog.ops
@@ -119,7 +130,22 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
         b = int(o["buf"])
         p = ptr[b] + int(o["off"]) if b >= 0 else 0
         cnt, ty, peer, tag = int(o["count"]), tmap.get(int(o["type"]), 0), int(o["peer"]), int(o["tag"])
-        if k == SEND:
+        si, di = int(o["sidx"]), int(o["didx"])
+        if c >= 0 and prog.mux(c) is not None:  # MPIX_Stream_* on a multiplex comm (§3.5)
+            if k == SEND:
+                retry(lambda: mpx.mpx_stream_send_enqueue(p, cnt, ty, peer, tag, comm, si, di))
+            elif k == RECV:
+                retry(lambda: mpx.mpx_stream_recv_enqueue(p, cnt, ty, peer, tag, comm, si, di,
+                                                          sptr(int(o["status"]))))
+            elif k == ISEND:
+                req[int(j)] = retry(lambda: mpx.mpx_stream_isend_enqueue(p, cnt, ty, peer, tag, comm,
+                                                                         si, di))
+            elif k == IRECV:
+                req[int(j)] = retry(lambda: mpx.mpx_stream_irecv_enqueue(p, cnt, ty, peer, tag, comm,
+                                                                         si, di))
+            else:
+                raise ValueError(f"kind {k} on a multiplex comm")
+        elif k == SEND:
             retry(lambda: mpx.mpx_send_enqueue(p, cnt, ty, peer, tag, comm))
         elif k == RECV:
             retry(lambda: mpx.mpx_recv_enqueue(p, cnt, ty, peer, tag, comm, sptr(int(o["status"]))))
