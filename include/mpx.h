@@ -67,6 +67,7 @@ typedef struct mpx_comm_s* mpx_comm_t;     /* one rank's handle of a stream comm
 typedef struct mpx_step_s* mpx_step_t;     /* a recorded step replayed as one CUDA graph */
 typedef int64_t mpx_request_t;             /* opaque: (world << 56) | (stream << 40) | seq; MPX_REQUEST_NULL = -1 */
 typedef int32_t mpx_datatype_t;
+typedef struct mpx_info_s* mpx_info_t;     /* MPI_Info: (key, value) string hints; NULL = MPI_INFO_NULL */
 
 typedef struct {
   int32_t source; /* sender's rank in the communicator */
@@ -86,6 +87,8 @@ enum {
   MPX_ANY_TAG = -1,
   MPX_ANY_INDEX = -1,   /* MPIX_ANY_INDEX: any local stream of the source (multiplex comms) */
   MPX_TAG_UB = (1 << 30) - 1,
+  MPX_MAX_INFO_KEY = 255,   /* MPI_MAX_INFO_KEY */
+  MPX_MAX_INFO_VAL = 1024,  /* MPI_MAX_INFO_VAL */
   MPX_UNDEFINED = -32766
 };
 
@@ -239,9 +242,44 @@ int mpx_world_get_counters(mpx_world_t world, int64_t* out, int n);
 int mpx_stream_create(mpx_world_t world, int rank, mpx_cuda_stream_t cuda_stream, unsigned flags,
                       mpx_stream_t* stream);
 
+/* MPIX_Stream_create(info, &stream) (§3.1, §3.2; Listing 4): the queue
+ * comes from info hints.  "type" = "cudaStream_t" with "value" = the
+ * cudaStream_t handle as written by mpx_info_set_hex binds that CUDA stream
+ * (the caller keeps it alive until mpx_stream_free); the optional hint
+ * "mpx_exclusive" = "true" or "false" selects MPX_STREAM_EXCLUSIVE.  info =
+ * NULL (MPI_INFO_NULL): the library creates a non-blocking CUDA stream for
+ * the MPIX stream, owns it and destroys it in mpx_stream_free
+ * (mpx_stream_get_cuda_stream returns it).  MPX_ERR_ARG for another "type",
+ * a "value" that is not 8 bytes of hex, a "value" without "type", or an
+ * exclusive hint other than "true"/"false"; otherwise as mpx_stream_create. */
+int mpx_stream_create_info(mpx_world_t world, int rank, mpx_info_t info, mpx_stream_t* stream);
+
+/* The CUDA stream an MPIX stream's operations are enqueued on. */
+int mpx_stream_get_cuda_stream(mpx_stream_t stream, mpx_cuda_stream_t* cuda_stream);
+
 /* MPIX_Stream_free (§3.1): fails with MPX_ERR_PENDING while operations
  * enqueued on the stream have not completed; *stream is then unchanged. */
 int mpx_stream_free(mpx_stream_t* stream);
+
+/* MPI_Info objects and MPIX_Info_set_hex (§3.2).  Keys are 1..MPX_MAX_INFO_KEY
+ * characters, values at most MPX_MAX_INFO_VAL; setting a key again replaces
+ * its value; keys keep their insertion order.  mpx_info_set_hex stores vallen
+ * bytes as 2 * vallen lowercase hexadecimal digits, bytes in memory order
+ * (the paper leaves the encoding to the implementation); mpx_info_get_hex
+ * reverses it (MPX_ERR_ARG when the value is not 2 * vallen hex digits).
+ * mpx_info_get copies at most buflen - 1 characters and a terminating NUL.
+ * *flag = 1 when the key is present, else 0 (the output is then untouched).
+ * Host-only: these need no GPU.  Errors: MPX_ERR_ARG for a null object, a key
+ * out of bounds, a value too long, n out of range; MPX_ERR_NO_MEM. */
+int mpx_info_create(mpx_info_t* info);
+int mpx_info_free(mpx_info_t* info);
+int mpx_info_set(mpx_info_t info, const char* key, const char* value);
+int mpx_info_get(mpx_info_t info, const char* key, char* value, int buflen, int* flag);
+int mpx_info_get_valuelen(mpx_info_t info, const char* key, int* valuelen, int* flag);
+int mpx_info_get_nkeys(mpx_info_t info, int* nkeys);
+int mpx_info_get_nthkey(mpx_info_t info, int n, char* key, int buflen);
+int mpx_info_set_hex(mpx_info_t info, const char* key, const void* value, int vallen);
+int mpx_info_get_hex(mpx_info_t info, const char* key, void* value, int vallen, int* flag);
 
 /* Endpoint id of the stream (the order key used for matching ties). */
 int mpx_stream_get_id(mpx_stream_t stream, int* id);

@@ -162,6 +162,7 @@ struct mpx_stream_s {
   uint64_t owed;      // a batch wrote descriptors up to here without releasing the tail
                       // and ringing the doorbell (0 = none)
   int ncomms;         // communicators using this stream
+  bool owns_cs;       // the library created cs (MPI_INFO_NULL) and destroys it at free
 };
 
 struct CommShared {
@@ -756,8 +757,46 @@ extern "C" int mpx_stream_free(mpx_stream_t* ps) {
   if (w->plain) plain::stream_free(w->plain, s->id);
   else __atomic_store_n(&w->sctl[s->id].flags, 0, __ATOMIC_RELEASE);
   w->streams[s->id] = nullptr;
+  if (s->owns_cs) cudaStreamDestroy(s->cs);  // queued work finishes first
   delete s;
   *ps = nullptr;
+  return MPX_SUCCESS;
+}
+
+extern "C" int mpx_stream_create_info(mpx_world_t w, int rank, mpx_info_t info, mpx_stream_t* out) {
+  if (!w || !out) return MPX_ERR_ARG;
+  if (!info) {
+    // MPI_INFO_NULL: an MPIX stream with a queue of its own
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return MPX_ERR_CUDA;
+    int rc = mpx_stream_create(w, rank, (mpx_cuda_stream_t)cs, MPX_STREAM_DEFAULT, out);
+    if (rc) {
+      cudaStreamDestroy(cs);
+      return rc;
+    }
+    (*out)->owns_cs = true;
+    return MPX_SUCCESS;
+  }
+  char type[64];
+  int has_type = 0, has_value = 0, has_excl = 0;
+  if (mpx_info_get(info, "type", type, (int)sizeof(type), &has_type)) return MPX_ERR_ARG;
+  mpx_cuda_stream_t cs = nullptr;
+  if (mpx_info_get_hex(info, "value", &cs, (int)sizeof(cs), &has_value)) return MPX_ERR_ARG;
+  char excl[8];
+  if (mpx_info_get(info, "mpx_exclusive", excl, (int)sizeof(excl), &has_excl)) return MPX_ERR_ARG;
+  unsigned flags = MPX_STREAM_DEFAULT;
+  if (has_excl) {
+    if (strcmp(excl, "true") == 0) flags = MPX_STREAM_EXCLUSIVE;
+    else if (strcmp(excl, "false") != 0) return MPX_ERR_ARG;
+  }
+  // only a CUDA stream can back an MPIX stream here, and it must be given
+  if (!has_type || strcmp(type, "cudaStream_t") != 0 || !has_value) return MPX_ERR_ARG;
+  return mpx_stream_create(w, rank, cs, flags, out);
+}
+
+extern "C" int mpx_stream_get_cuda_stream(mpx_stream_t s, mpx_cuda_stream_t* cs) {
+  if (!s || !cs) return MPX_ERR_ARG;
+  *cs = (mpx_cuda_stream_t)s->cs;
   return MPX_SUCCESS;
 }
 

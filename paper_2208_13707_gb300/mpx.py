@@ -22,6 +22,7 @@ lib = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
 # --- constants (include/mpx.h) ---
 ANY_SOURCE, ANY_TAG, TAG_UB, UNDEFINED = -2, -1, (1 << 30) - 1, -32766
 ANY_INDEX = -1
+MAX_INFO_KEY, MAX_INFO_VAL = 255, 1024
 BYTE = UINT8 = 0
 INT32, INT64, FLOAT, DOUBLE = 1, 2, 3, 4
 SUM = 0
@@ -107,6 +108,17 @@ _SIGS = {
     "mpx_stream_get_id": [_vp, _P(ctypes.c_int)],
     "mpx_stream_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_stream_pending": [_vp, _P(_i64)],
+    "mpx_stream_create_info": [_vp, ctypes.c_int, _vp, _P(_vp)],
+    "mpx_stream_get_cuda_stream": [_vp, _P(_vp)],
+    "mpx_info_create": [_P(_vp)],
+    "mpx_info_free": [_P(_vp)],
+    "mpx_info_set": [_vp, ctypes.c_char_p, ctypes.c_char_p],
+    "mpx_info_get": [_vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, _P(ctypes.c_int)],
+    "mpx_info_get_valuelen": [_vp, ctypes.c_char_p, _P(ctypes.c_int), _P(ctypes.c_int)],
+    "mpx_info_get_nkeys": [_vp, _P(ctypes.c_int)],
+    "mpx_info_get_nthkey": [_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int],
+    "mpx_info_set_hex": [_vp, ctypes.c_char_p, _vp, ctypes.c_int],
+    "mpx_info_get_hex": [_vp, ctypes.c_char_p, _vp, ctypes.c_int, _P(ctypes.c_int)],
     "mpx_stream_comm_create": [_vp, ctypes.c_int, _P(_vp), _P(_vp)],
     "mpx_stream_comm_create_multiple": [_vp, ctypes.c_int, _P(ctypes.c_int), _P(_vp), _P(_vp)],
     "mpx_comm_free": [_P(_vp)],
@@ -248,6 +260,73 @@ def mpx_stream_comm_create(world: int, streams: Sequence[int]) -> list:
     out = (_vp * n)()
     _chk(lib.mpx_stream_comm_create(world, n, arr, out), "mpx_stream_comm_create")
     return [out[i] for i in range(n)]
+
+
+def mpx_stream_create_info(world: int, rank: int, info: Optional[int]) -> int:
+    """MPIX_Stream_create from info hints; info None = MPI_INFO_NULL."""
+    out = _vp()
+    _chk(lib.mpx_stream_create_info(world, rank, info, ctypes.byref(out)), "mpx_stream_create_info")
+    return out.value
+
+
+def mpx_stream_get_cuda_stream(stream: int) -> int:
+    out = _vp()
+    _chk(lib.mpx_stream_get_cuda_stream(stream, ctypes.byref(out)), "mpx_stream_get_cuda_stream")
+    return out.value or 0
+
+
+def mpx_info_create() -> int:
+    out = _vp()
+    _chk(lib.mpx_info_create(ctypes.byref(out)), "mpx_info_create")
+    return out.value
+
+
+def mpx_info_free(info: int) -> None:
+    h = _vp(info)
+    _chk(lib.mpx_info_free(ctypes.byref(h)), "mpx_info_free")
+
+
+def mpx_info_set(info: int, key: str, value: str) -> None:
+    _chk(lib.mpx_info_set(info, key.encode(), value.encode()), "mpx_info_set")
+
+
+def mpx_info_get(info: int, key: str, buflen: int = MAX_INFO_VAL + 1) -> Optional[str]:
+    buf = ctypes.create_string_buffer(max(1, buflen))
+    flag = ctypes.c_int()
+    _chk(lib.mpx_info_get(info, key.encode(), buf, buflen, ctypes.byref(flag)), "mpx_info_get")
+    return buf.value.decode() if flag.value else None
+
+
+def mpx_info_get_valuelen(info: int, key: str) -> Optional[int]:
+    n, flag = ctypes.c_int(), ctypes.c_int()
+    _chk(lib.mpx_info_get_valuelen(info, key.encode(), ctypes.byref(n), ctypes.byref(flag)),
+         "mpx_info_get_valuelen")
+    return n.value if flag.value else None
+
+
+def mpx_info_get_nkeys(info: int) -> int:
+    n = ctypes.c_int()
+    _chk(lib.mpx_info_get_nkeys(info, ctypes.byref(n)), "mpx_info_get_nkeys")
+    return n.value
+
+
+def mpx_info_get_nthkey(info: int, n: int) -> str:
+    buf = ctypes.create_string_buffer(MAX_INFO_KEY + 1)
+    _chk(lib.mpx_info_get_nthkey(info, n, buf, MAX_INFO_KEY + 1), "mpx_info_get_nthkey")
+    return buf.value.decode()
+
+
+def mpx_info_set_hex(info: int, key: str, value: bytes) -> None:
+    """MPIX_Info_set_hex: store the bytes of `value` under `key`."""
+    b = ctypes.create_string_buffer(bytes(value), len(value))
+    _chk(lib.mpx_info_set_hex(info, key.encode(), b, len(value)), "mpx_info_set_hex")
+
+
+def mpx_info_get_hex(info: int, key: str, vallen: int) -> Optional[bytes]:
+    b = ctypes.create_string_buffer(max(1, vallen))
+    flag = ctypes.c_int()
+    _chk(lib.mpx_info_get_hex(info, key.encode(), b, vallen, ctypes.byref(flag)), "mpx_info_get_hex")
+    return b.raw[:vallen] if flag.value else None
 
 
 def mpx_stream_comm_create_multiple(world: int, local_streams: Sequence[Sequence[int]]) -> list:
