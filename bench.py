@@ -731,6 +731,31 @@ def halo_bench(steps=100, warmup=5, sub=256):
             "rounds_per_tick_with_rounds": ctr[24] / max(1, ctr[25])}
 
 
+def host_msgrate(seconds=0.15):
+    """The multithreaded 8-byte message-rate experiment (§5.3, Fig. 3) on the
+    host cores: pairs of host threads, each pair over a channel of its own,
+    under a global mutex, a mutex per channel, and the MPIX stream
+    serial-context discipline (lock-free single-producer rings).  Each point
+    runs about `seconds`; no GPU is involved."""
+    from paper_2208_13707_gb300 import mpx
+    cores = os.cpu_count() or 1
+    counts = [t for t in (1, 2, 4, 8, 16) if 2 * t <= max(2, cores)]
+    modes = {"global_lock": mpx.HOSTRATE_GLOBAL_LOCK, "endpoint_lock": mpx.HOSTRATE_ENDPOINT_LOCK,
+             "stream": mpx.HOSTRATE_STREAM}
+    out = {"cores": cores, "message_bytes": 8, "window": 64, "threads": counts}
+    for name, mode in modes.items():
+        rates = []
+        for t in counts:
+            probe = mpx.mpx_hostrate_run(t, mode, messages=20000)
+            n = int(min(5e7, max(20000, probe["msgs_per_s"] * seconds / t)))
+            r = mpx.mpx_hostrate_run(t, mode, messages=n)
+            assert r["errors"] == 0
+            rates.append(r["msgs_per_s"])
+        out[name] = rates
+    out["stream_vs_endpoint_lock"] = [a / b for a, b in zip(out["stream"], out["endpoint_lock"])]
+    return out
+
+
 def serving(requests=100000):
     """Serving loop: 32 host threads with one MPIX stream each submit
     requests open-loop (Poisson, mean gap 2 us per thread), sizes Zipf(1.2)
@@ -933,6 +958,10 @@ def main():
                     help="requests of the serving measurement (0 = skip it)")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
+    ap.add_argument("--no-host-msgrate", action="store_true",
+                    help="skip the host-thread message-rate experiment")
+    ap.add_argument("--host-msgrate-only", action="store_true",
+                    help="print only the host-thread message-rate experiment (no GPU)")
     ap.add_argument("--profile-steps", choices=["allreduce", "batching"], default=None,
                     help="profile-safe recorded steps for a kernel profiler (no benchmark line)")
     ap.add_argument("--autotune-only", action="store_true", help="print only the autotuner report")
@@ -951,6 +980,9 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
     if args.impl == "reference":
         reference_arm(args, rank, world_size)
+        return
+    if args.host_msgrate_only:  # host cores only
+        print(json.dumps({"host_msgrate": host_msgrate()}), flush=True)
         return
 
     import torch
@@ -1049,6 +1081,7 @@ def main():
             e["frac_of_peak"] = e["gbs"] / pk
         c4 = {"allreduce": ar, "halo": halo_bench()}
     serve = serving(args.serve_requests) if args.serve_requests else None
+    hostr = None if args.no_host_msgrate else host_msgrate()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, msgs = oracle_sample(1)
@@ -1082,6 +1115,7 @@ def main():
                 "batching_full": batching_1m,
                 "allreduce_and_halo": c4,
                 "serving": serve,
+                "host_msgrate": hostr,
                 "autotune": tune,
                 "autotune_ring": ring_tune,
                 "speedup_vs_plain": value / plain["value"],

@@ -551,6 +551,38 @@ int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                           mpx_datatype_t datatype, mpx_comm_t comm);
 int mpx_barrier_enqueue(mpx_comm_t comm);
 
+/* Host-thread message rate (§5.3, Fig. 3, on host cores): `threads` pairs of
+ * host threads, sender t sending `messages` 8-byte messages to receiver t
+ * over a channel of its own (a per-thread communicator), `window` sends or
+ * receives per wait.  The mode picks the discipline around each channel's
+ * matching state: MPX_HOSTRATE_GLOBAL_LOCK (one mutex for every channel, a
+ * global critical section), MPX_HOSTRATE_ENDPOINT_LOCK (a mutex per channel,
+ * taken by every send, receive post and completion poll) or
+ * MPX_HOSTRATE_STREAM (the MPIX stream serial-context guarantee: one
+ * producer and one consumer per channel, a lock-free ring).  No GPU is used.
+ * result: wall seconds from the release of all threads to the last join,
+ * messages per second over all pairs, and payloads received out of order
+ * (0 when correct).  MPX_ERR_ARG: threads outside 1..512, messages < 1,
+ * window outside 1..1024, an unknown mode. */
+enum { MPX_HOSTRATE_GLOBAL_LOCK = 0, MPX_HOSTRATE_ENDPOINT_LOCK = 1, MPX_HOSTRATE_STREAM = 2 };
+
+typedef struct {
+  int32_t threads;   /* sender/receiver pairs (default 1) */
+  int32_t mode;      /* MPX_HOSTRATE_* (default STREAM) */
+  int64_t messages;  /* per pair (default 2^20) */
+  int32_t window;    /* operations per wait (default 64) */
+  int32_t pad;
+} mpx_hostrate_config_t;
+
+typedef struct {
+  double seconds;
+  double msgs_per_s;
+  int64_t errors;
+} mpx_hostrate_result_t;
+
+int mpx_hostrate_config_init(mpx_hostrate_config_t* cfg);
+int mpx_hostrate_run(const mpx_hostrate_config_t* cfg, mpx_hostrate_result_t* result);
+
 /* MPI_Get_count: elements of `datatype` in status->bytes, or MPX_UNDEFINED. */
 int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* count);
 

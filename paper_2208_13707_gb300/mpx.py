@@ -90,6 +90,19 @@ class Status(ctypes.Structure):
                 ("source_index", ctypes.c_int32), ("bytes", ctypes.c_int64)]
 
 
+HOSTRATE_GLOBAL_LOCK, HOSTRATE_ENDPOINT_LOCK, HOSTRATE_STREAM = 0, 1, 2
+
+
+class HostrateConfig(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("mode", ctypes.c_int32), ("messages", ctypes.c_int64),
+                ("window", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class HostrateResult(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("msgs_per_s", ctypes.c_double),
+                ("errors", ctypes.c_int64)]
+
+
 _vp, _i32, _i64, _u32, _f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
 _P = ctypes.POINTER
 _SIGS = {
@@ -108,6 +121,8 @@ _SIGS = {
     "mpx_stream_get_id": [_vp, _P(ctypes.c_int)],
     "mpx_stream_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_stream_pending": [_vp, _P(_i64)],
+    "mpx_hostrate_config_init": [_P(HostrateConfig)],
+    "mpx_hostrate_run": [_P(HostrateConfig), _P(HostrateResult)],
     "mpx_stream_create_info": [_vp, ctypes.c_int, _vp, _P(_vp)],
     "mpx_stream_get_cuda_stream": [_vp, _P(_vp)],
     "mpx_info_create": [_P(_vp)],
@@ -260,6 +275,16 @@ def mpx_stream_comm_create(world: int, streams: Sequence[int]) -> list:
     out = (_vp * n)()
     _chk(lib.mpx_stream_comm_create(world, n, arr, out), "mpx_stream_comm_create")
     return [out[i] for i in range(n)]
+
+
+def mpx_hostrate_run(threads: int, mode: int, messages: int = 1 << 20, window: int = 64) -> dict:
+    """Host-thread 8-byte message rate under one locking discipline (HOSTRATE_*)."""
+    cfg = HostrateConfig()
+    _chk(lib.mpx_hostrate_config_init(ctypes.byref(cfg)), "mpx_hostrate_config_init")
+    cfg.threads, cfg.mode, cfg.messages, cfg.window = threads, mode, messages, window
+    res = HostrateResult()
+    _chk(lib.mpx_hostrate_run(ctypes.byref(cfg), ctypes.byref(res)), "mpx_hostrate_run")
+    return {"seconds": res.seconds, "msgs_per_s": res.msgs_per_s, "errors": int(res.errors)}
 
 
 def mpx_stream_create_info(world: int, rank: int, info: Optional[int]) -> int:
