@@ -277,10 +277,15 @@ def mpx_stream_comm_create(world: int, streams: Sequence[int]) -> list:
     return [out[i] for i in range(n)]
 
 
-def mpx_hostrate_run(threads: int, mode: int, messages: int = 1 << 20, window: int = 64) -> dict:
-    """Host-thread 8-byte message rate under one locking discipline (HOSTRATE_*)."""
+def mpx_hostrate_config_init() -> HostrateConfig:
     cfg = HostrateConfig()
     _chk(lib.mpx_hostrate_config_init(ctypes.byref(cfg)), "mpx_hostrate_config_init")
+    return cfg
+
+
+def mpx_hostrate_run(threads: int, mode: int, messages: int = 1 << 20, window: int = 64) -> dict:
+    """Host-thread 8-byte message rate under one locking discipline (HOSTRATE_*)."""
+    cfg = mpx_hostrate_config_init()
     cfg.threads, cfg.mode, cfg.messages, cfg.window = threads, mode, messages, window
     res = HostrateResult()
     _chk(lib.mpx_hostrate_run(ctypes.byref(cfg), ctypes.byref(res)), "mpx_hostrate_run")
