@@ -19,7 +19,9 @@
  *    Isend/Irecv lets later enqueued work go on until the matching Wait;
  *    data received is visible to work enqueued after the completing call.
  *  - §3.4 (last paragraph): collectives take the same enqueue form; here
- *    SUM allreduce.
+ *    SUM allreduce, bcast, reduce and allgather, blocking or nonblocking.  A
+ *    nonblocking one lets the stream go on at once and completes through a
+ *    wait; as in MPI it never forms an instance with a blocking call.
  *  - §3.5: a multiplex stream communicator attaches several local streams
  *    per process, addressed by index; a send names its own stream (src_idx)
  *    and the destination's (dst_idx), a receive its own stream (dst_idx) and
@@ -60,8 +62,24 @@
 
 namespace {
 
-enum Kind { SEND = 0, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER };
-bool is_collective(int k) { return k == ALLREDUCE || k == BCAST || k == REDUCE || k == ALLGATHER; }
+enum Kind { SEND = 0, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER,
+            IALLREDUCE, IBCAST, IREDUCE, IALLGATHER };
+// nonblocking collectives: the call returns a request at once, a wait completes it
+bool is_nonblocking_collective(int k) { return k >= IALLREDUCE && k <= IALLGATHER; }
+// the blocking kind a collective computes like
+int collective_base(int k) {
+  switch (k) {
+    case IALLREDUCE: return ALLREDUCE;
+    case IBCAST: return BCAST;
+    case IREDUCE: return REDUCE;
+    case IALLGATHER: return ALLGATHER;
+    default: return k;
+  }
+}
+bool is_collective(int k) {
+  const int b = collective_base(k);
+  return b == ALLREDUCE || b == BCAST || b == REDUCE || b == ALLGATHER;
+}
 constexpr int kAnySource = -2;
 constexpr int kAnyTag = -1;
 constexpr int kAnyIndex = -1;
@@ -324,9 +342,10 @@ struct Oracle {
   // instance (§3.4: collectives take the enqueue form; MPI: collective calls
   // on a communicator are ordered).  All arrivals must be the same kind.
   void run_collective(const std::vector<int64_t>& arr, int round) {
-    const int kind = p.ops[arr[0]].kind;
+    const int call = p.ops[arr[0]].kind;
     for (int64_t j : arr)
-      if (p.ops[j].kind != kind) { err = 5; return; }
+      if (p.ops[j].kind != call) { err = 5; return; }
+    const int kind = collective_base(call);
     if (kind == ALLREDUCE) run_allreduce(arr, round);
     else if (kind == REDUCE) run_allreduce(arr, round, p.ops[arr[0]].peer);
     else if (kind == BCAST) run_bcast(arr, round);
@@ -473,8 +492,10 @@ struct Oracle {
       if (o.type < 0 || o.type >= p.ntypes || o.count < 0) return false;
     }
     // a multiplex comm carries point-to-point traffic only (§3.5)
-    if (is_collective(o.kind)) return !is_mux(o.comm) && (o.kind == ALLREDUCE || o.kind == ALLGATHER ||
-                                                         (o.peer >= 0 && o.peer < p.nranks));
+    if (is_collective(o.kind)) {
+      const int b = collective_base(o.kind);
+      return !is_mux(o.comm) && (b == ALLREDUCE || b == ALLGATHER || (o.peer >= 0 && o.peer < p.nranks));
+    }
     if (o.kind == SEND || o.kind == ISEND)
       return o.peer >= 0 && o.peer < p.nranks && o.tag >= 0 && o.sidx == op_index[(size_t)j] &&
              o.didx >= 0 && o.didx < streams_of(o.comm, o.peer);
@@ -595,6 +616,10 @@ struct Oracle {
               v[(size_t)rk] = j;
               arrived_now.push_back({o.comm, k});
               progress = true;
+              if (is_nonblocking_collective(o.kind)) {  // the stream goes on; a wait completes it
+                ++cursor[g];
+                continue;
+              }
               break;
             }
             if (complete_before(j, round)) { ++cursor[g]; progress = true; continue; }

@@ -16,10 +16,12 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 # --- operation kinds (the enqueue calls of §3.4 plus the user compute op) ---
-SEND, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER = range(11)
+(SEND, RECV, ISEND, IRECV, WAIT, WAITALL, ALLREDUCE, AXPY, BCAST, REDUCE, ALLGATHER,
+ IALLREDUCE, IBCAST, IREDUCE, IALLGATHER) = range(15)
 KIND_NAMES = ["send", "recv", "isend", "irecv", "wait", "waitall", "allreduce", "axpy",
-              "bcast", "reduce", "allgather"]
-COLLECTIVES = (ALLREDUCE, BCAST, REDUCE, ALLGATHER)
+              "bcast", "reduce", "allgather", "iallreduce", "ibcast", "ireduce", "iallgather"]
+NONBLOCKING_COLLECTIVES = (IALLREDUCE, IBCAST, IREDUCE, IALLGATHER)
+COLLECTIVES = (ALLREDUCE, BCAST, REDUCE, ALLGATHER) + NONBLOCKING_COLLECTIVES
 
 ANY_SOURCE = -2
 ANY_TAG = -1
@@ -289,6 +291,25 @@ class ProgramBuilder:
         """MPI_Allgather: count elements per rank into R blocks of every receive
         buffer; sendbuf IN_PLACE: the rank's block is already in place."""
         return self._op(g, kind=ALLGATHER, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
+                        off2=recvoff, count=count, type=type_)
+
+    # nonblocking forms (MPI_Iallreduce, ...): the handle goes to wait / waitall
+    def iallreduce(self, g, comm, sendbuf, sendoff, recvbuf, recvoff, count, type_,
+                   mode=MODE_FIXED):
+        return self._op(g, kind=IALLREDUCE, comm=comm, buf=sendbuf, off=sendoff,
+                        buf2=recvbuf, off2=recvoff, count=count, type=type_, mode=mode)
+
+    def ibcast(self, g, comm, buf, off, count, type_, root):
+        return self._op(g, kind=IBCAST, comm=comm, buf=buf, off=off, count=count, type=type_,
+                        peer=root)
+
+    def ireduce(self, g, comm, sendbuf, sendoff, recvbuf, recvoff, count, type_, root,
+                mode=MODE_FIXED):
+        return self._op(g, kind=IREDUCE, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
+                        off2=recvoff, count=count, type=type_, peer=root, mode=mode)
+
+    def iallgather(self, g, comm, sendbuf, sendoff, recvbuf, recvoff, count, type_):
+        return self._op(g, kind=IALLGATHER, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
                         off2=recvoff, count=count, type=type_)
 
     def axpy(self, g, alpha, xbuf, xoff, ybuf, yoff, n):
