@@ -551,6 +551,30 @@ int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                           mpx_datatype_t datatype, mpx_comm_t comm);
 int mpx_barrier_enqueue(mpx_comm_t comm);
 
+/* Nonblocking collectives (MPI_Iallreduce, MPI_Ibcast, MPI_Ireduce,
+ * MPI_Iallgather, MPI_Ibarrier) in enqueue form (§3.4): the call returns a
+ * request at once and the stream goes on; the collective completes once
+ * every rank has called it (and, for data, once each rank's stream has
+ * reached its call), and mpx_wait(all)_enqueue on the request orders later
+ * work on the stream after it.  Arguments, buffers and results are those of
+ * the blocking call; the buffers must not be touched until the wait.
+ * Blocking and nonblocking calls share one instance order per communicator
+ * but never match each other: an instance that mixes them completes with
+ * MPX_ERR_ARG (as a kind mismatch).  *request receives the request
+ * (MPX_ERR_ARG when request is NULL).  MPX_ERR_UNSUPPORTED on the plain path
+ * (MPX_ENGINE_PLAIN). */
+int mpx_iallreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                           mpx_datatype_t datatype, int op, mpx_comm_t comm,
+                           mpx_request_t* request);
+int mpx_ibcast_enqueue(void* buf, int64_t count, mpx_datatype_t datatype, int root,
+                       mpx_comm_t comm, mpx_request_t* request);
+int mpx_ireduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                        mpx_datatype_t datatype, int op, int root, mpx_comm_t comm,
+                        mpx_request_t* request);
+int mpx_iallgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                           mpx_datatype_t datatype, mpx_comm_t comm, mpx_request_t* request);
+int mpx_ibarrier_enqueue(mpx_comm_t comm, mpx_request_t* request);
+
 /* Host-thread message rate (§5.3, Fig. 3, on host cores): `threads` pairs of
  * host threads, sender t sending `messages` 8-byte messages to receiver t
  * over a channel of its own (a per-thread communicator), `window` sends or

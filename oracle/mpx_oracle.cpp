@@ -234,6 +234,12 @@ struct Oracle {
     return off >= 0 && off + nbytes_span <= p.buf_size[buf];
   }
 
+  // address of a buffer offset; null for a buffer id that names none, which
+  // callers reach only for spans of zero bytes (MPI: a count of 0 moves nothing)
+  uint8_t* at(int buf, int64_t off) const {
+    return buf >= 0 && buf < p.nbufs ? p.bufs[buf] + off : nullptr;
+  }
+
   // bytes spanned in memory by `count` instances of layout L
   static int64_t span(const Layout& L, int64_t count) {
     return count <= 0 ? 0 : (count - 1) * L.extent + L.extent;
@@ -367,7 +373,7 @@ struct Oracle {
       if ((int)k == o0.peer) continue;
       const Op& o = p.ops[arr[k]];
       if (!in_bounds(o.buf, o.off, bytes)) { err = 6; return; }
-      std::memcpy(p.bufs[o.buf] + o.off, p.bufs[root.buf] + root.off, (size_t)bytes);
+      if (bytes) std::memcpy(at(o.buf, o.off), at(root.buf, root.off), (size_t)bytes);
     }
     for (int64_t j : arr) r.done_round[j] = round;
   }
@@ -389,13 +395,13 @@ struct Oracle {
       const int sb = o.buf == kInPlace ? o.buf2 : o.buf;
       const int64_t so = o.buf == kInPlace ? o.off2 + (int64_t)s * bytes : o.off;
       if (!in_bounds(sb, so, bytes)) { err = 6; return; }
-      block[s].assign(p.bufs[sb] + so, p.bufs[sb] + so + bytes);
+      if (bytes) block[s].assign(at(sb, so), at(sb, so) + bytes);
     }
     for (size_t k = 0; k < R; ++k) {
       const Op& o = p.ops[arr[k]];
       if (!in_bounds(o.buf2, o.off2, bytes * (int64_t)R)) { err = 6; return; }
       for (size_t s = 0; s < R; ++s)
-        if (bytes) std::memcpy(p.bufs[o.buf2] + o.off2 + (int64_t)s * bytes, block[s].data(), (size_t)bytes);
+        if (bytes) std::memcpy(at(o.buf2, o.off2) + (int64_t)s * bytes, block[s].data(), (size_t)bytes);
     }
     for (int64_t j : arr) r.done_round[j] = round;
   }
@@ -422,8 +428,8 @@ struct Oracle {
       int sb = o.buf == kInPlace ? o.buf2 : o.buf;
       int64_t so = o.buf == kInPlace ? o.off2 : o.off;
       if (!in_bounds(sb, so, esz * n) || (writes && !in_bounds(o.buf2, o.off2, esz * n))) { err = 6; return; }
-      in[k] = p.bufs[sb] + so;
-      out[k] = writes ? p.bufs[o.buf2] + o.off2 : nullptr;
+      in[k] = at(sb, so);
+      out[k] = writes ? at(o.buf2, o.off2) : nullptr;
     }
     // inputs are read in full before any output is written (a root reducing
     // in place reads its own receive buffer)

@@ -263,8 +263,11 @@ __device__ __forceinline__ bool src_accepts(int32_t pattern, int32_t key) {
   return (pr == 0xFFFFu || pr == (k & 0xFFFFu)) && (pi == 0x7FFFu || pi == (k >> 16));
 }
 __device__ __forceinline__ bool is_recv(uint32_t k) { return k == K_RECV || k == K_IRECV; }
-__device__ __forceinline__ bool is_blocking(uint32_t k) {
-  return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL || is_collective_kind(k);
+// operations the stream's completion word waits for (kind word)
+__device__ __forceinline__ bool is_blocking(uint32_t kw) {
+  const uint32_t k = kw_kind(kw);
+  return k == K_SEND || k == K_RECV || k == K_WAIT || k == K_WAITALL ||
+         (is_collective_kind(k) && !kw_nonblocking(kw));
 }
 
 __device__ void set_error(const EngineParams& P, int g, int err) {
@@ -1098,6 +1101,10 @@ struct Ctl {
             o->lstate = 1;
             arrived = true;
             sm.arrivals = 1;
+            if (kw_nonblocking(o->d.kw)) {  // the stream goes on; a wait completes it
+              ++cur;
+              continue;
+            }
           }
           break;
         }
@@ -1723,7 +1730,10 @@ struct Ctl {
       case K_ISEND: return (f & PF_DELIVERED) && (f & PF_WAITED);
       case K_RECV: return (f & PF_COMPLETE) != 0;
       case K_IRECV: return (f & PF_COMPLETE) && (f & PF_WAITED);
-      default: return (f & PF_COMPLETE) != 0;
+      default:
+        // a nonblocking collective's request stays valid until waited
+        if (kw_nonblocking(o->d.kw)) return (f & PF_COMPLETE) && (f & PF_WAITED);
+        return (f & PF_COMPLETE) != 0;
     }
   }
 
@@ -1738,8 +1748,7 @@ struct Ctl {
     while (pc <= S.ingested) {
       if (pc >= pf) pf = prefetch_ops(g, pc, S.ingested);
       DOp* o = op_at(P, g, pc);
-      const uint32_t k = kw_kind(o->d.kw);
-      if (!is_blocking(k)) {
+      if (!is_blocking(o->d.kw)) {
         ++pc;
         continue;
       }
@@ -1813,8 +1822,8 @@ struct Ctl {
     while (pc <= ing) {
       const uint64_t seq = pc + (uint64_t)lane;
       const bool valid = seq <= ing;
-      const uint32_t k = valid ? kw_kind(op_at(P, g, seq)->d.kw) : 0;
-      const unsigned blk = __ballot_sync(FULL, valid && is_blocking(k));
+      const uint32_t kw = valid ? op_at(P, g, seq)->d.kw : 0;
+      const unsigned blk = __ballot_sync(FULL, valid && is_blocking(kw));
       if (!blk) {
         pc += (uint64_t)__popc(__ballot_sync(FULL, valid));
         continue;

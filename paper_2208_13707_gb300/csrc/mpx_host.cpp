@@ -1380,8 +1380,21 @@ static void fill_collective(Desc& d, uint32_t kind, mpx_datatype_t dt, mpx_comm_
   d.stride = 1;
 }
 
-extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int root,
-                                 mpx_comm_t c) {
+// Blocking collectives (req == nullptr) stop their stream until complete; a
+// nonblocking one (MPI_I*) returns a request at once and carries the
+// nonblocking bit in its kind word, so it never forms an instance with a
+// blocking call of another rank (MPI: they do not match).
+static int publish_collective(mpx_comm_t c, Desc& d, mpx_request_t* req) {
+  if (!req) return publish(c->stream, d, true, nullptr);
+  d.kw |= kKwNonblocking;
+  uint64_t seq = 0;
+  const int rc = publish(c->stream, d, false, &seq);
+  if (seq) *req = make_request(c->stream, seq);
+  return rc;
+}
+
+static int bcast_common(void* buf, int64_t count, mpx_datatype_t dt, int root, mpx_comm_t c,
+                        mpx_request_t* req) {
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (root < 0 || root >= c->size) return MPX_ERR_RANK;
@@ -1389,11 +1402,11 @@ extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, in
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
   fill_collective(d, K_BCAST, dt, c, buf, buf, count, root);
-  return publish(c->stream, d, true, nullptr);
+  return publish_collective(c, d, req);
 }
 
-extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
-                                  mpx_datatype_t dt, int op, int root, mpx_comm_t c) {
+static int reduce_common(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t dt,
+                         int op, int root, mpx_comm_t c, mpx_request_t* req) {
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (op != MPX_SUM) return MPX_ERR_ARG;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
@@ -1407,11 +1420,11 @@ extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t co
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
   fill_collective(d, K_REDUCE, dt, c, sendbuf, at_root ? recvbuf : nullptr, count, root);
-  return publish(c->stream, d, true, nullptr);
+  return publish_collective(c, d, req);
 }
 
-extern "C" int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
-                                     mpx_datatype_t dt, mpx_comm_t c) {
+static int allgather_common(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t dt,
+                            mpx_comm_t c, mpx_request_t* req) {
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;  // the rank's block is already in place
@@ -1419,28 +1432,81 @@ extern "C" int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
   fill_collective(d, K_ALLGATHER, dt, c, sendbuf, recvbuf, count, 0);
-  return publish(c->stream, d, true, nullptr);
+  return publish_collective(c, d, req);
 }
 
-extern "C" int mpx_barrier_enqueue(mpx_comm_t c) {
-  // an allreduce of no elements: complete once every rank has arrived
-  return mpx_allreduce_enqueue(nullptr, nullptr, 0, MPX_BYTE, MPX_SUM, c);
-}
-
-extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
-                                     mpx_datatype_t dt, int op, mpx_comm_t c) {
+static int allreduce_common(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t dt,
+                            int op, mpx_comm_t c, mpx_request_t* req) {
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (op != MPX_SUM) return MPX_ERR_ARG;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (count < 0 || (count > 0 && !recvbuf)) return MPX_ERR_ARG;
   if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;
   if (count > 0 && !sendbuf) return MPX_ERR_ARG;
-  if (c->w->plain)
+  if (c->w->plain) {
+    if (req) return MPX_ERR_UNSUPPORTED;
     return plain::allreduce(c->w->plain, sendbuf, recvbuf, count, dt, c->shared->reduce_mode,
                             c->shared->id, c->rank, c->stream->id);
+  }
   Desc d;
   fill_collective(d, K_ALLREDUCE, dt, c, sendbuf, recvbuf, count, 0);
-  return publish(c->stream, d, true, nullptr);
+  return publish_collective(c, d, req);
+}
+
+extern "C" int mpx_bcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int root,
+                                 mpx_comm_t c) {
+  return bcast_common(buf, count, dt, root, c, nullptr);
+}
+
+extern "C" int mpx_reduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                  mpx_datatype_t dt, int op, int root, mpx_comm_t c) {
+  return reduce_common(sendbuf, recvbuf, count, dt, op, root, c, nullptr);
+}
+
+extern "C" int mpx_allgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                     mpx_datatype_t dt, mpx_comm_t c) {
+  return allgather_common(sendbuf, recvbuf, count, dt, c, nullptr);
+}
+
+extern "C" int mpx_barrier_enqueue(mpx_comm_t c) {
+  // an allreduce of no elements: complete once every rank has arrived
+  return allreduce_common(nullptr, nullptr, 0, MPX_BYTE, MPX_SUM, c, nullptr);
+}
+
+extern "C" int mpx_allreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                     mpx_datatype_t dt, int op, mpx_comm_t c) {
+  return allreduce_common(sendbuf, recvbuf, count, dt, op, c, nullptr);
+}
+
+extern "C" int mpx_iallreduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                      mpx_datatype_t dt, int op, mpx_comm_t c,
+                                      mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  return allreduce_common(sendbuf, recvbuf, count, dt, op, c, req);
+}
+
+extern "C" int mpx_ibcast_enqueue(void* buf, int64_t count, mpx_datatype_t dt, int root,
+                                  mpx_comm_t c, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  return bcast_common(buf, count, dt, root, c, req);
+}
+
+extern "C" int mpx_ireduce_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                   mpx_datatype_t dt, int op, int root, mpx_comm_t c,
+                                   mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  return reduce_common(sendbuf, recvbuf, count, dt, op, root, c, req);
+}
+
+extern "C" int mpx_iallgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
+                                      mpx_datatype_t dt, mpx_comm_t c, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  return allgather_common(sendbuf, recvbuf, count, dt, c, req);
+}
+
+extern "C" int mpx_ibarrier_enqueue(mpx_comm_t c, mpx_request_t* req) {
+  if (!req) return MPX_ERR_ARG;
+  return allreduce_common(nullptr, nullptr, 0, MPX_BYTE, MPX_SUM, c, req);
 }
 
 

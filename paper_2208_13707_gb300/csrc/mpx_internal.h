@@ -17,10 +17,12 @@ enum OpKind : uint32_t {
 };
 
 // kind word: bits 0-7 kind, 8-11 base type (MPX_BYTE..MPX_DOUBLE),
-// 12-13 reduce mode
+// 12-13 reduce mode, 14 nonblocking collective (completed by a wait)
 __host__ __device__ inline uint32_t kw_kind(uint32_t kw) { return kw & 0xffu; }
 __host__ __device__ inline uint32_t kw_base(uint32_t kw) { return (kw >> 8) & 0xfu; }
 __host__ __device__ inline uint32_t kw_mode(uint32_t kw) { return (kw >> 12) & 0x3u; }
+constexpr uint32_t kKwNonblocking = 1u << 14;
+__host__ __device__ inline bool kw_nonblocking(uint32_t kw) { return (kw & kKwNonblocking) != 0; }
 __host__ __device__ inline uint32_t make_kw(uint32_t kind, uint32_t base, uint32_t mode) {
   return kind | (base << 8) | (mode << 12);
 }

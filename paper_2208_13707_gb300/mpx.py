@@ -163,6 +163,11 @@ _SIGS = {
     "mpx_reduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp],
     "mpx_allgather_enqueue": [_vp, _vp, _i64, _i32, _vp],
     "mpx_barrier_enqueue": [_vp],
+    "mpx_iallreduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_ibcast_enqueue": [_vp, _i64, _i32, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_ireduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_iallgather_enqueue": [_vp, _vp, _i64, _i32, _vp, _P(_i64)],
+    "mpx_ibarrier_enqueue": [_vp, _P(_i64)],
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
@@ -496,6 +501,41 @@ def mpx_allgather_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int,
 
 def mpx_barrier_enqueue(comm: int) -> None:
     _chk(lib.mpx_barrier_enqueue(comm), "mpx_barrier_enqueue")
+
+
+def mpx_iallreduce_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int,
+                           comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_iallreduce_enqueue(sendbuf, recvbuf, count, datatype, op, comm, ctypes.byref(r)),
+         "mpx_iallreduce_enqueue")
+    return r.value
+
+
+def mpx_ibcast_enqueue(buf: int, count: int, datatype: int, root: int, comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_ibcast_enqueue(buf, count, datatype, root, comm, ctypes.byref(r)), "mpx_ibcast_enqueue")
+    return r.value
+
+
+def mpx_ireduce_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, root: int,
+                        comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_ireduce_enqueue(sendbuf, recvbuf, count, datatype, op, root, comm, ctypes.byref(r)),
+         "mpx_ireduce_enqueue")
+    return r.value
+
+
+def mpx_iallgather_enqueue(sendbuf: int, recvbuf: int, count: int, datatype: int, comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_iallgather_enqueue(sendbuf, recvbuf, count, datatype, comm, ctypes.byref(r)),
+         "mpx_iallgather_enqueue")
+    return r.value
+
+
+def mpx_ibarrier_enqueue(comm: int) -> int:
+    r = _i64()
+    _chk(lib.mpx_ibarrier_enqueue(comm, ctypes.byref(r)), "mpx_ibarrier_enqueue")
+    return r.value
 
 
 def mpx_get_count(status: Status, datatype: int) -> int:

@@ -63,10 +63,10 @@ def test_nonblocking_allreduce_resolves_the_crossing_deadlock():
     _check_crossing()
 
 
-def _check_definitions():
-    """Each nonblocking kind against its definition, with point-to-point
-    traffic between the call and its wait, and waits in a different order."""
-    R, n, root = 4, 29, 2
+def _definitions(n=29):
+    """Every rank: iallreduce, ibcast, ireduce, iallgather, then a ring
+    isend/irecv, then one waitall over all six requests in another order."""
+    R, root = 4, 2
     rng = np.random.default_rng(7)
     b, gs, c = _world(R)
     a = [rng.integers(-2 ** 40, 2 ** 40, n) for _ in range(R)]
@@ -88,7 +88,17 @@ def _check_definitions():
         hs = b.isend(gs[r], c, ring[r], 0, 8, T_INT32, (r + 1) % R, 0)
         hr = b.irecv(gs[r], c, ring_got[r], 0, 8, T_INT32, (r - 1) % R, 0)
         b.waitall(gs[r], [h4, hr, h1, hs, h3, h2])
-    o = oracle.run(b.build())
+    return b.build(), dict(R=R, n=n, root=root, a=a, ar=ar, bc=bc, bc_data=bc_data, rd=rd,
+                           canary=canary, ag=ag, ring_got=ring_got)
+
+
+def _check_definitions():
+    """Each nonblocking kind against its definition, with point-to-point
+    traffic between the call and its wait, and waits in a different order."""
+    p, m = _definitions()
+    R, n, root, a, ar, bc, bc_data, rd, canary, ag, ring_got = (
+        m[k] for k in ("R", "n", "root", "a", "ar", "bc", "bc_data", "rd", "canary", "ag", "ring_got"))
+    o = oracle.run(p)
     assert o.error == 0 and not o.deadlock
     total = np.sum(np.stack(a), axis=0)  # |values| < 2^40: exact in int64
     for r in range(R):

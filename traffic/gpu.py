@@ -14,8 +14,9 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from .program import (ALLGATHER, ALLREDUCE, AXPY, BCAST, IN_PLACE, IRECV, ISEND, RECV, REDUCE, SEND,
-                      STATUS_DTYPE, WAIT, WAITALL, Program)
+from .program import (ALLGATHER, ALLREDUCE, AXPY, BCAST, IALLGATHER, IALLREDUCE, IBCAST, IN_PLACE,
+                      IRECV, IREDUCE, ISEND, RECV, REDUCE, SEND, STATUS_DTYPE, WAIT, WAITALL,
+                      Program)
 
 
 @dataclass
@@ -175,6 +176,21 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             rb = ptr[int(o["buf2"])] + int(o["off2"])
             sb = mpx.IN_PLACE if b == IN_PLACE else p
             retry(lambda: mpx.mpx_allgather_enqueue(sb, rb, cnt, ty, comm))
+        elif k == IALLREDUCE:
+            rb = ptr[int(o["buf2"])] + int(o["off2"]) if int(o["buf2"]) >= 0 else 0
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            req[int(j)] = retry(lambda: mpx.mpx_iallreduce_enqueue(sb, rb, cnt, ty, mpx.SUM, comm))
+        elif k == IBCAST:
+            req[int(j)] = retry(lambda: mpx.mpx_ibcast_enqueue(p, cnt, ty, peer, comm))
+        elif k == IREDUCE:
+            b2 = int(o["buf2"])
+            rb = ptr[b2] + int(o["off2"]) if b2 >= 0 else 0
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            req[int(j)] = retry(lambda: mpx.mpx_ireduce_enqueue(sb, rb, cnt, ty, mpx.SUM, peer, comm))
+        elif k == IALLGATHER:
+            rb = ptr[int(o["buf2"])] + int(o["off2"])
+            sb = mpx.IN_PLACE if b == IN_PLACE else p
+            req[int(j)] = retry(lambda: mpx.mpx_iallgather_enqueue(sb, rb, cnt, ty, comm))
         elif k == AXPY:
             yb = ptr[int(o["buf2"])] + int(o["off2"])
             mpx.mpx_saxpy_enqueue(cnt, float(o["alpha"]), p, yb, cstreams[g].cuda_stream)
