@@ -135,7 +135,10 @@ def test_enqueue_batch_stops_at_the_first_invalid_op():
 
 @pytest.mark.parametrize("cname,pyname", [("mpx_serve_config_t", "ServeConfig"),
                                           ("mpx_serve_result_t", "ServeResult"),
-                                          ("mpx_world_config_t", "WorldConfig")])
+                                          ("mpx_world_config_t", "WorldConfig"),
+                                          ("mpx_status_t", "Status"),
+                                          ("mpx_hostrate_config_t", "HostrateConfig"),
+                                          ("mpx_hostrate_result_t", "HostrateResult")])
 def test_struct_layouts_match_the_binding(tmp_path, cname, pyname):
     import subprocess
     from paper_2208_13707_gb300 import mpx
