@@ -185,3 +185,57 @@ def test_planted_multiplex_mistake_is_caught(k, tmp_path, monkeypatch):
         assert caught, f"mutant {k} survived"
     finally:
         sys.modules["oracle"] = saved
+
+
+def test_multiplex_truncation_and_zero_count_statuses():
+    """A receive shorter than the message takes its capacity and reports
+    TRUNCATE; a zero-count message matches and delivers nothing; both
+    statuses name the sender's rank and local index."""
+    from traffic.program import ERR_TRUNCATE
+    b = ProgramBuilder(2)
+    g00 = b.stream(0)
+    g10, g11 = b.stream(1), b.stream(1)
+    c = b.comm_multiple([[g00], [g10, g11]])
+    sb = b.buffer(np.arange(8, dtype=np.int32))
+    rb = b.buffer(np.full(8, -1, np.int32))
+    s1 = b.stream_send(g11, c, sb, 0, 8, T_INT32, 0, 0, 5)
+    s0 = b.stream_send(g10, c, sb, 0, 0, T_INT32, 0, 0, 6)
+    r1 = b.stream_recv(g00, c, rb, 0, 3, T_INT32, 1, 1, 5)
+    r0 = b.stream_recv(g00, c, rb, 16, 4, T_INT32, ANY_SOURCE, ANY_INDEX, 6)
+    b.waitall(g11, [s1])
+    b.waitall(g10, [s0])
+    b.waitall(g00, [r1, r0], b.status_slots(2))
+    o = oracle.run(b.build())
+    assert o.error == 0 and not o.deadlock
+    assert o.buffers[rb].view(np.int32).tolist() == [0, 1, 2, -1, -1, -1, -1, -1]
+    st = [(int(x["source"]), int(x["source_index"]), int(x["tag"]), int(x["error"]), int(x["bytes"]))
+          for x in o.status]
+    assert st == [(1, 1, 5, ERR_TRUNCATE, 12), (1, 0, 6, 0, 0)]
+
+
+def test_multiplex_sender_order_is_kept_per_member_pair():
+    """Non-overtaking per (sender member, receiver member): two messages from
+    rank 1's stream 1 with one tag reach rank 0's stream 1 in send order even
+    when the receives are (ANY_SOURCE, ANY_INDEX) and a message from another
+    member arrives between them."""
+    b = ProgramBuilder(2)
+    g00, g01 = b.stream(0), b.stream(0)
+    g10, g11 = b.stream(1), b.stream(1)
+    c = b.comm_multiple([[g00, g01], [g10, g11]])
+    bufs = [b.buffer(np.full(2, v, np.int32)) for v in (1, 2, 3)]
+    rb = b.buffer(24)
+    h1 = b.stream_send(g11, c, bufs[0], 0, 2, T_INT32, 0, 1, 0)
+    h2 = b.stream_send(g10, c, bufs[1], 0, 2, T_INT32, 0, 1, 0)
+    h3 = b.stream_send(g11, c, bufs[2], 0, 2, T_INT32, 0, 1, 0)
+    rs = [b.stream_recv(g01, c, rb, 8 * k, 2, T_INT32, ANY_SOURCE, ANY_INDEX, 0) for k in range(3)]
+    b.waitall(g11, [h1, h3])
+    b.waitall(g10, [h2])
+    b.waitall(g01, rs, b.status_slots(3))
+    p = b.build()
+    o = oracle.run(p)
+    assert o.error == 0 and not o.deadlock
+    got = o.buffers[rb].view(np.int32)[::2].tolist()
+    assert got.index(1) < got.index(3)
+    assert validity_violations(p, o.match, require_complete=True) == []
+    legal = legal_outcomes(p)
+    assert (match_set(o.match, p), False) in legal
