@@ -322,7 +322,11 @@ int mpx_comm_set_reduce_mode(mpx_comm_t comm, int mode);
  * `blocklength` old elements whose starts are `stride` elements apart.  One
  * instance spans ((count-1)*stride+blocklength) elements (its extent);
  * instance i of a message starts at i*extent.  oldtype must be predefined.
- * Process-wide handle; stays valid until mpx_type_free. */
+ * Process-wide handle; stays valid until mpx_type_free.  MPX_ERR_ARG when an
+ * instance's extent exceeds 2^48 bytes.  Every call that takes a count of a
+ * datatype rejects, with MPX_ERR_ARG, a count whose instances would span more
+ * than 2^60 bytes (collectives: count * 8 * communicator size), so no byte
+ * count derived from it can overflow. */
 int mpx_type_vector(int count, int blocklength, int stride, mpx_datatype_t oldtype,
                     mpx_datatype_t* newtype);
 int mpx_type_free(mpx_datatype_t* type);
@@ -525,6 +529,54 @@ int mpx_serve_config_init(mpx_serve_config_t* cfg);
 int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* result, uint64_t* digests,
                   uint64_t* source_digests, int64_t ndigests);
 
+/* The serving loop over a schedule the caller supplies instead of the one
+ * generated from cfg (zipf_s, min/max_log2, p_allreduce, requests, seed and
+ * sample_every are then unused; nthreads, engine_mode, mean_gap_us,
+ * budget_bytes keep their meaning), so that the same requests can be run
+ * through an independent implementation and compared item by item.
+ * Thread t issues calls[call_lo[t] .. call_lo[t+1]) in order:
+ *  - MPX_SERVE_SEND: isend of `bytes` bytes (MPX_BYTE) at regions[t] + off
+ *    to thread `peer` with `tag`;
+ *  - MPX_SERVE_RECV: irecv of `bytes` bytes from thread `peer` with `tag`
+ *    into a buffer admitted from the thread's budget share;
+ *  - MPX_SERVE_WAITALL: waitall over the thread's requests since its last
+ *    waitall (blocking); its statuses go to statuses[capture ...] when
+ *    capture >= 0 and statuses is not NULL;
+ *  - MPX_SERVE_ALLREDUCE: blocking fp32 SUM allreduce of bytes/4 elements at
+ *    regions[t] + off over all threads into a budget buffer.
+ * A RECV or ALLREDUCE call with capture >= 0 has its delivered bytes copied
+ * to (char*)capture + capture, in stream order after the blocking call that
+ * covers it and before its buffer returns to the budget.  Calls of one item
+ * (a message's send and receive, an instance's allreduces) share `item`.
+ * Ownership: every array is the caller's; regions, capture and statuses are
+ * device memory (statuses may be mapped pinned host memory).  Errors:
+ * MPX_ERR_ARG (a call out of range: kind, peer, bytes, offsets, capture or
+ * status ranges, or call_lo not monotone), MPX_ERR_NO_MEM, and those of the
+ * calls it makes.  `result` as for mpx_serve_run. */
+enum { MPX_SERVE_SEND = 0, MPX_SERVE_RECV = 1, MPX_SERVE_WAITALL = 2, MPX_SERVE_ALLREDUCE = 3 };
+typedef struct {
+  int32_t kind;      /* MPX_SERVE_* */
+  int32_t peer;      /* send: destination thread; recv: source thread */
+  int32_t tag;
+  int32_t pad;
+  int64_t item;      /* message or allreduce instance the call belongs to (>= 0) */
+  int64_t bytes;     /* payload bytes; an allreduce's are a multiple of 4 */
+  int64_t off;       /* send, allreduce: payload offset in the thread's source region */
+  int64_t capture;   /* see above; -1: none */
+} mpx_serve_call_t;  /* 48 bytes */
+typedef struct {
+  const mpx_serve_call_t* calls;
+  const int64_t* call_lo;   /* nthreads + 1 entries */
+  void* const* regions;     /* nthreads device source regions of region_bytes each */
+  int64_t region_bytes;
+  void* capture;            /* device memory of capture_bytes, or NULL */
+  int64_t capture_bytes;
+  mpx_status_t* statuses;   /* nstatuses device-accessible statuses, or NULL */
+  int64_t nstatuses;
+} mpx_serve_schedule_t;
+int mpx_serve_run_schedule(const mpx_serve_config_t* cfg, const mpx_serve_schedule_t* sched,
+                           mpx_serve_result_t* result);
+
 /* Further enqueued collectives (§3.4, last paragraph: collectives take the
  * enqueue form).  Like allreduce, every collective call on a communicator is
  * blocking in stream order, and the k-th collective call of every rank, of
@@ -629,13 +681,17 @@ int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y, mpx_cuda_str
  * The staging area is a 16 MiB array in the library's device memory (a
  * file-scope __device__ array that every GPU which loads the library holds
  * until the process exits); the call returns MPX_ERR_NO_MEM when more than
- * 16 MiB would be delivered, and allocates nothing itself.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
- * Every call shares the one array, so calls that overlap on the GPU (on
- * different streams, or on devices sharing nothing but this process)
- * race: order them in one stream.  Errors: MPX_ERR_TYPE, MPX_ERR_ARG,
- * MPX_ERR_NO_MEM, MPX_ERR_CUDA. */
+ * 16 MiB would be delivered, and allocates nothing itself.  Each device has
+ * its own copy of the array.  Its device address is looked up once per
+ * device (cudaGetSymbolAddress, with that device current) by mpx_world_create
+ * or by the first call on the device, whichever comes first; make that first
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset it is stale, and the function must not be
+ * called again.  Every call on one device shares that device's array, which
+ * keeps the last call's bytes, so calls that overlap on the same device (on
+ * different streams) race: order them in one stream.  Counts whose byte span
+ * exceeds 2^60 are rejected with MPX_ERR_ARG.  Errors: MPX_ERR_TYPE,
+ * MPX_ERR_ARG, MPX_ERR_NO_MEM, MPX_ERR_CUDA. */
 int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, mpx_datatype_t sendtype,
                         void* recvbuf, int64_t recvcount, mpx_datatype_t recvtype,
                         mpx_cuda_stream_t stream, int64_t* bytes_delivered);

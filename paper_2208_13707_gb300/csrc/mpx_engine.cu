@@ -39,14 +39,15 @@ constexpr int kErrTruncate = 15;
 constexpr int kErrTimeout = 16;
 constexpr int kMaxRoundsPerTick = 64;
 constexpr int kMaxStagePerTick = 128;
+constexpr int kMaxDeferred = 512;  // deliveries a scheduling phase sizes together
 constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipeline
 constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
 constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
-constexpr int kSmemStreams = 128;
+constexpr int kSmemStreams = 128;  // worlds up to this many streams keep per-stream state in shared memory
 constexpr int kMaxCtaThreads = 512;  // engine block size bound (launch bounds)
-constexpr int kSortMinPosts = 128;
-constexpr uint64_t kCqDone = ~0ull;  // completion-queue entry already processed   // rounds with more posts match from domain-sorted lists  // worlds up to this many streams keep per-stream state in shared memory
+constexpr int kSortMinPosts = 128;   // rounds with more posts match from domain-sorted lists
+constexpr uint64_t kCqDone = ~0ull;  // completion-queue entry already processed
 
 // ------------------------------------------------------------------------
 // memory-model helpers
@@ -225,6 +226,11 @@ struct CtaShared {
   int32_t dirty;          // control: logical rounds needed
   int32_t tasks_live;     // control: tasks in flight at the last decision
   uint64_t stage_ref[kMaxStagePerTick];
+  // control: deliveries found by this scheduling phase, created after the scan
+  // with one tile size for all (bit 63 of the send ref: from staging)
+  uint64_t dlv_s[kMaxDeferred], dlv_r[kMaxDeferred];
+  int32_t ndlv;
+  unsigned long long dlv_bytes;
   int32_t cnt[kMaxStreamsPerCta];
   int32_t arrivals;       // control: allreduce arrivals this round
   int32_t limits_reached; // control: a drain pass has ingested up to all its limits
@@ -240,6 +246,15 @@ struct CtaShared {
   uint64_t r0;              // control: task_retire at the start of the retirement scan
   uint64_t own_next;        // mover (per-CTA schedule): next task id this CTA owns
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
+  // control: its own copies of the task-ring words only it writes (task_alloc,
+  // task_retire, cq_head); the global words are written through for the movers
+  uint64_t c_alloc, c_retire, c_cqh;
+  int32_t unretired;      // control: tasks processed (completion queue) and not yet retired
+  int32_t scan_now;       // control: this tick runs the completion-queue / retirement scans
+  int32_t all_dirty;      // control: this tick rescans every stream's completion state
+  // control: streams with an event since their last completion scan (new
+  // operations, a moved cursor, a finished task, a doorbell change)
+  uint8_t sdirty[kMaxStreamsPerCta];
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
 };
@@ -982,19 +997,36 @@ struct Ctl {
         o->wscan = 0;
         o->pscan = 0;
         o->t_ingest = (int64_t)t0;
-        if (kw_kind(o->d.kw) == K_WAITALL) {
-          // request lists are read many times: keep a device copy
-          const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
-          const int64_t* hw = P.waitlists + ((size_t)g << P.wl_log2);
-          int64_t* dw = P.wl_dev + ((size_t)g << P.wl_log2);
-          for (int32_t k = 0; k < o->d.n32; ++k) {
-            const uint64_t idx = (o->d.aux + (uint64_t)k) & wl_mask;
-            dw[idx] = *(const volatile int64_t*)&hw[idx];
+      }
+      __syncwarp();
+      // request lists are read many times: keep a device copy, read by all
+      // lanes of the warp at once (one host round trip per 32 entries)
+      {
+        const uint64_t wl_mask = (1ull << P.wl_log2) - 1;
+        const int64_t* hw = P.waitlists + ((size_t)g << P.wl_log2);
+        int64_t* dw = P.wl_dev + ((size_t)g << P.wl_log2);
+        for (int64_t i0 = 0; i0 < n; i0 += 32) {
+          const int64_t i = i0 + lane;
+          const DOp* o = i < n ? op_at(P, g, ing + 1 + (uint64_t)i) : nullptr;
+          const bool wa = o && kw_kind(o->d.kw) == K_WAITALL;
+          unsigned m = __ballot_sync(FULL, wa);
+          while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t aux = __shfl_sync(FULL, wa ? o->d.aux : 0ull, src);
+            const int32_t cnt = __shfl_sync(FULL, wa ? o->d.n32 : 0, src);
+            for (int32_t k = lane; k < cnt; k += 32) {
+              const uint64_t idx = (aux + (uint64_t)k) & wl_mask;
+              dw[idx] = *(const volatile int64_t*)&hw[idx];
+            }
           }
         }
       }
       __syncwarp();
-      if (lane == 0) S.ingested = tail;
+      if (lane == 0) {
+        S.ingested = tail;
+        touch(g);
+      }
     }
     __syncthreads();
     if (P.nlimit > 0) {
@@ -1127,7 +1159,10 @@ struct Ctl {
     S.nposts = n;
     sm.cnt[g] = n;
     if (n) atomicAdd(&sm.nposts_round, n);
-    if (moved) sm.any = 1;
+    if (moved) {
+      sm.any = 1;
+      touch(g);
+    }
     return moved;
   }
 
@@ -1414,19 +1449,24 @@ struct Ctl {
   // advancing task_alloc over the ids handed out.  Every id handed out is
   // published before that.
   __device__ void task_phase_begin() {
-    Shared* sh = P.sh;
     const uint64_t cap = 1ull << P.tq_log2;
-    const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
-    const uint64_t r = *(volatile uint64_t*)&sh->task_retire;
+    const uint64_t a = sm.c_alloc;
     sm.t_base = a;
-    const uint64_t free_tasks = cap - (a - r);
-    const uint64_t free_cq = 2 * cap - (a - *(volatile uint64_t*)&sh->cq_head);
+    const uint64_t free_tasks = cap - (a - sm.c_retire);
+    const uint64_t free_cq = 2 * cap - (a - sm.c_cqh);
     sm.t_avail = (uint32_t)(free_tasks < free_cq ? free_tasks : free_cq);
     sm.t_used = 0;
   }
   __device__ void task_phase_end() {
     const uint32_t n = sm.t_used < sm.t_avail ? sm.t_used : sm.t_avail;
-    if (n) st_rel_gpu(&P.sh->task_alloc, sm.t_base + n);
+    if (n) {
+      sm.c_alloc = sm.t_base + n;
+      st_rel_gpu(&P.sh->task_alloc, sm.c_alloc);
+    }
+  }
+  // stream g has an event its completion scan must see
+  __device__ __forceinline__ void touch(int g) {
+    if (g >= 0 && g < P.max_streams) sm.sdirty[g] = 1;
   }
   __device__ Task* task_new(uint64_t& id) {
     const uint32_t idx = atomicAdd(&sm.t_used, 1u);
@@ -1446,7 +1486,8 @@ struct Ctl {
     st_rel_gpu(&T->claim, claim_word(id, T->ntiles));
   }
 
-  __device__ void fill_copy(Task* T, const Layout& src, const Layout& dst, int64_t bytes) {
+  __device__ void fill_copy(Task* T, const Layout& src, const Layout& dst, int64_t bytes,
+                            int64_t tile_hint = 0) {
     T->type = T_COPY;
     T->src = src;
     T->dst = dst;
@@ -1468,19 +1509,41 @@ struct Ctl {
       while (U > 1 && bad(U)) U >>= 1;
     }
     T->unit = U;
-    // about two tiles per engine CTA, never below tile_bytes or above 1 MiB
-    int64_t tile = (bytes + 2 * P.nctas - 1) / (2 * P.nctas);
-    tile = tile < P.tile_bytes ? P.tile_bytes : (tile > (1 << 20) ? (1 << 20) : tile);
+    int64_t tile;
+    if (tile_hint > 0) {
+      // the scheduling phase's bytes per mover: every mover gets about one
+      // tile of the phase's work, never below tile_bytes
+      tile = tile_hint < P.tile_bytes ? P.tile_bytes : tile_hint;
+    } else {
+      // about two tiles per engine CTA, never below tile_bytes or above 1 MiB
+      tile = (bytes + 2 * P.nctas - 1) / (2 * P.nctas);
+      tile = tile < P.tile_bytes ? P.tile_bytes : (tile > (1 << 20) ? (1 << 20) : tile);
+    }
     tile = (tile + 255) & ~(int64_t)255;
+    if ((bytes + tile - 1) / tile > 0xFFFFF) tile = ((bytes + 0xFFFFE) / 0xFFFFF + 255) & ~(int64_t)255;
     if (C != kContig) tile = C >= tile ? C : (tile / C) * C;
     T->tile = tile;
     T->ntiles = (uint32_t)((bytes + tile - 1) / tile);
   }
 
-  // deliver send s (payload in its buffer or in staging) into recv r
-  __device__ bool create_deliver(uint64_t sref, uint64_t rref, bool from_stage) {
+  // deliver send s (payload in its buffer or in staging) into recv r.  In the
+  // scheduling phase a delivery with bytes to move is deferred (the phase
+  // sizes its tiles together, make_deferred); `now` creates it at once.
+  __device__ bool create_deliver(uint64_t sref, uint64_t rref, bool from_stage, bool now = false,
+                                 int64_t tile_hint = 0) {
     DOp* s = op_ref(P, sref);
     DOp* r = op_ref(P, rref);
+    if (!now && r->bytes > 0) {
+      const int k = atomicAdd(&sm.ndlv, 1);
+      if (k < kMaxDeferred) {
+        atomicOr(&r->pflags, PF_SCHED);
+        sm.dlv_s[k] = sref | (from_stage ? (1ull << 63) : 0ull);
+        sm.dlv_r[k] = rref;
+        atomicAdd(&sm.dlv_bytes, (unsigned long long)r->bytes);
+        return true;
+      }
+      // list full: create this one at once with the default tiling
+    }
     Layout src, dst;
     if (from_stage) {
       src.base = (uint64_t)(P.stage + (s->stage - 1));
@@ -1498,6 +1561,8 @@ struct Ctl {
       atomicOr(&r->pflags, PF_DELIVERED | PF_COMPLETE);
       if (from_stage) stage_free(s);
       atomicOr(&s->pflags, PF_DELIVERED | PF_COMPLETE);
+      touch(ref_stream(sref));
+      touch(ref_stream(rref));
       sm.any = 1;
       return true;
     }
@@ -1507,7 +1572,7 @@ struct Ctl {
       atomicAnd(&r->pflags, ~PF_SCHED);
       return false;
     }
-    fill_copy(T, src, dst, bytes);
+    fill_copy(T, src, dst, bytes, tile_hint);
     T->action = from_stage ? A_DELIVER_STAGED : A_DELIVER;
     T->ref_s = sref;
     T->ref_r = rref;
@@ -1771,14 +1836,8 @@ struct Ctl {
       st_rlx_sys(&P.sctl[g].done, newdone);
       prog = true;
     }
-    // how far the stream has executed
-    if (S.flags & SF_EXCLUSIVE) {
-      S.reached = pc <= S.ingested ? pc : S.ingested;
-    } else {
-      uint64_t db;
-      asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
-      S.reached = db;
-    }
+    // how far the stream has executed (non-exclusive: the tick's doorbell pass)
+    if (S.flags & SF_EXCLUSIVE) S.reached = pc <= S.ingested ? pc : S.ingested;
     // stall clock: the stream sits at blocking op pc
     const bool stalled = pc <= S.ingested && S.reached >= pc;
     if (stalled) {
@@ -1853,13 +1912,7 @@ struct Ctl {
         st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);
         st_rlx_sys(&P.sctl[g].done, newdone);
       }
-      if (S.flags & SF_EXCLUSIVE) {
-        S.reached = pc <= ing ? pc : ing;
-      } else {
-        uint64_t db;
-        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
-        S.reached = db;
-      }
+      if (S.flags & SF_EXCLUSIVE) S.reached = pc <= ing ? pc : ing;
       const bool stalled = pc <= ing && S.reached >= pc;
       if (stalled) {
         if (S.stall_t0 == 0 || advanced) S.stall_t0 = now;
@@ -2006,6 +2059,28 @@ struct Ctl {
     __syncwarp();
   }
 
+  // Create the deliveries the scheduling scan deferred, every one with the
+  // tile size that spreads the phase's bytes evenly over the movers.  A
+  // delivery whose task cannot be created now (ring full) is undone and its
+  // receive's stream rescans from it next tick.
+  __device__ void make_deferred() {
+    const int n = sm.ndlv < kMaxDeferred ? sm.ndlv : kMaxDeferred;
+    if (n == 0) return;
+    const int64_t movers = P.nctas > 1 ? P.nctas - 1 : 1;
+    const int64_t hint = (int64_t)((sm.dlv_bytes + (unsigned long long)movers - 1) / (unsigned long long)movers);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t sv = sm.dlv_s[i], rref = sm.dlv_r[i];
+      const bool from_stage = (sv >> 63) != 0;
+      const uint64_t sref = sv & ~(1ull << 63);
+      if (create_deliver(sref, rref, from_stage, true, hint)) continue;
+      // undo: the send is reached again (or still staged) and the receive unscheduled
+      DOp* r = op_ref(P, rref);
+      if (!from_stage) atomicAnd(&op_ref(P, sref)->pflags, ~PF_SCHED);
+      atomicAnd(&r->pflags, ~PF_SCHED);
+      atomicMin((unsigned long long*)&ss[ref_stream(rref)].sched, (unsigned long long)ref_seq(rref));
+    }
+  }
+
   // thread 0: create staging tasks for the collected sends
   __device__ void make_stage_tasks() {
     const int n = sm.nstage < kMaxStagePerTick ? sm.nstage : kMaxStagePerTick;
@@ -2022,6 +2097,7 @@ struct Ctl {
         s->stage = 1;
         atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
         atomicAnd(&s->pflags, ~PF_SCHED);
+        touch(ref_stream(sref));
         continue;
       }
       s->stage = off + 1;
@@ -2067,7 +2143,10 @@ struct Ctl {
       const DOp* o0 = op_ref(P, refs[0]);
       const int64_t n = o0->d.count;
       if (s->err || n <= 0) {
-        for (int r = 0; r < P.nranks; ++r) atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+        for (int r = 0; r < P.nranks; ++r) {
+          atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+          touch(ref_stream(refs[r]));
+        }
         s->state = 0;
         s->arrived = 0;
         __threadfence();
@@ -2162,11 +2241,13 @@ struct Ctl {
       Task* T = &P.tasks[v - 1];
       if (T->type == T_COPY) {
         DOp* s = op_ref(P, T->ref_s);
+        touch(ref_stream(T->ref_s));
         if (T->action == A_STAGE) {
           atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
           atomicAnd(&s->pflags, ~(PF_SCHED | PF_STAGING));
         } else {
           DOp* r = op_ref(P, T->ref_r);
+          touch(ref_stream(T->ref_r));
           if (T->action == A_DELIVER_STAGED) stage_free(s);
           atomicOr(&r->pflags, PF_DELIVERED | PF_COMPLETE);
           atomicOr(&s->pflags, PF_DELIVERED | PF_COMPLETE);
@@ -2176,8 +2257,10 @@ struct Ctl {
       } else if (T->type == T_REDUCE) {
         InstSlot* s = &P.inst[T->ref_s];
         const uint64_t* refs = P.inst_refs + (size_t)T->ref_s * P.nranks;
-        for (int r = 0; r < P.nranks; ++r)
+        for (int r = 0; r < P.nranks; ++r) {
           atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+          touch(ref_stream(refs[r]));
+        }
         s->state = 0;
         s->arrived = 0;
         __threadfence();
@@ -2190,6 +2273,7 @@ struct Ctl {
       sm.any = 1;
     }
     if (n_tasks) {
+      atomicAdd(&sm.unretired, (int32_t)n_tasks);
       if (n_msg) atomicAdd((unsigned long long*)&P.wctl->counters[2], n_msg);
       atomicAdd((unsigned long long*)&P.wctl->counters[3], n_bytes);
       atomicAdd((unsigned long long*)&P.wctl->counters[4], n_tasks);
@@ -2197,10 +2281,6 @@ struct Ctl {
   }
 };
 
-// Tasks allocated and not yet retired (movers may be working on them).
-__device__ __forceinline__ bool tasks_live_now(const EngineParams& P) {
-  return *(volatile uint64_t*)&P.sh->task_retire != *(volatile uint64_t*)&P.sh->task_alloc;
-}
 
 // Release every stream's waiters without moving data (watchdog / failed world).
 __device__ void release_all(const EngineParams& P, SState* ss, int err) {
@@ -2234,16 +2314,19 @@ __device__ void release_all(const EngineParams& P, SState* ss, int err) {
 }
 
 // A failed world moves no more data: drop every task that was not finished.
-__device__ void abandon_tasks(const EngineParams& P) {
+__device__ void abandon_tasks(const EngineParams& P, CtaShared& sm) {
   Shared* sh = P.sh;
-  const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
+  const uint64_t a = sm.c_alloc;
   st_rel_gpu(&sh->task_head, a);
   sh->task_retire = a;
+  sm.c_retire = a;
+  sm.unretired = 0;
   // forget queued completions of the abandoned tasks
   const uint64_t mask = cq_mask(P);
   const uint64_t t = ld_acq_gpu(&sh->cq_tail);
-  for (uint64_t h = sh->cq_head; h < t; ++h) P.cq[h & mask] = 0;
+  for (uint64_t h = sm.c_cqh; h < t; ++h) P.cq[h & mask] = 0;
   sh->cq_head = t;
+  sm.c_cqh = t;
 }
 
 __device__ void grid_barrier(const EngineParams& P, int nctas) {
@@ -2284,7 +2367,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     sm.nposts_round = 0;
     sm.arrivals = 0;
     sm.ready_insts = 0;
+    sm.c_alloc = *(volatile uint64_t*)&sh->task_alloc;
+    sm.c_retire = *(volatile uint64_t*)&sh->task_retire;
+    sm.c_cqh = *(volatile uint64_t*)&sh->cq_head;
+    sm.unretired = 0;  // a launch starts with every task retired or abandoned
+    sm.all_dirty = 0;
   }
+  for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 1;
   __syncthreads();
   for (int i = tid; i < P.max_comms * P.iw; i += blockDim.x)
     if (P.inst[i].k1 != 0 && P.inst[i].state == 1) atomicAdd(&sm.ready_insts, 1);
@@ -2304,13 +2393,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   uint64_t ticks = 0;
   // phase timing (thread 0): first task seen, last time tasks drained
   const int64_t t_launch = last_prog;
-  const uint64_t alloc0 = *(volatile uint64_t*)&sh->task_alloc;
+  const uint64_t alloc0 = sm.c_alloc;
   int64_t t_first_task = 0, t_tasks_done = 0;
   uint64_t tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   uint64_t sub[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // finer split (thread 0)
   uint64_t ts = 0;
+  const bool timing = P.timing != 0;
   auto mark = [&](int k) {  // thread 0: time since the last mark into sub[k]
-    if (tid == 0) {
+    if (timing && tid == 0) {
       const uint64_t t = now_ns();
       if (k >= 0) sub[k] += t - ts;
       ts = t;
@@ -2335,9 +2425,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     }
     __syncthreads();
-    uint64_t tp = tid == 0 ? now_ns() : 0;
+    uint64_t tp = timing && tid == 0 ? now_ns() : 0;
     auto lap = [&](int k) {
-      if (tid == 0) {
+      if (timing && tid == 0) {
         const uint64_t t = now_ns();
         tacc[k] += t - tp;
         tp = t;
@@ -2359,7 +2449,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     if (failed_now) {
       if (tid == 0) {
         sm.pending = 0;
-        abandon_tasks(P);
+        abandon_tasks(P, sm);
       }
       release_all(P, C.ss, kErrTimeout);
       __syncthreads();
@@ -2425,27 +2515,31 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     if (!failed_now) {
       // 3. finished tasks, then per-stream completion and retirement
       if (tid == 0) {
-        sm.t_retire = sh->cq_head;
+        sm.t_retire = sm.c_cqh;
         sm.t_alloc = ld_acq_gpu(&sh->cq_tail);
+        // the scans below can move something only after new completions, or
+        // while processed tasks wait for the movers' head to pass them
+        sm.scan_now = sm.t_alloc != sm.t_retire || sm.unretired > 0;
+        sm.all_dirty = (ticks & 63) == 0;  // a periodic full completion scan
       }
       __syncthreads();
       const uint64_t cq_h = sm.t_retire, cq_t = sm.t_alloc;
       if (cq_h != cq_t) C.complete_tasks(cq_h, cq_t);
-      if (tid == 0) {
-        sm.scan_a = cq_t;
-        const uint64_t r0 = sh->task_retire;
-        const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
-        // a slot is reused only after the movers' head has passed its task
-        // (per-CTA schedule: its owner read the record before the last tile
-        // finished, so a processed task can be retired at once)
-        const uint64_t head = P.movers_per_cta && gridDim.x > 1 ? a : ld_acq_gpu(&sh->task_head);
-        uint64_t lim = a < head ? a : head;
-        if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
-        sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
-        sm.scan_b = lim;
-      }
-      __syncthreads();
-      {
+      if (sm.scan_now) {
+        if (tid == 0) {
+          sm.scan_a = cq_t;
+          const uint64_t r0 = sm.c_retire;
+          const uint64_t a = sm.c_alloc;
+          // a slot is reused only after the movers' head has passed its task
+          // (per-CTA schedule: its owner read the record before the last tile
+          // finished, so a processed task can be retired at once)
+          const uint64_t head = P.movers_per_cta && gridDim.x > 1 ? a : ld_acq_gpu(&sh->task_head);
+          uint64_t lim = a < head ? a : head;
+          if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
+          sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
+          sm.scan_b = lim;
+        }
+        __syncthreads();
         // parallel: the completion-queue head moves over processed entries,
         // task_retire over processed tasks (a window of 8 per thread a tick)
         const uint64_t mask = (1ull << P.tq_log2) - 1, qmask = cq_mask(P);
@@ -2466,9 +2560,28 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         const uint64_t newh = sm.scan_a;
         for (uint64_t pos = cq_h + tid; pos < newh; pos += blockDim.x) P.cq[pos & qmask] = 0;
         if (tid == 0) {
-          sh->cq_head = newh;
-          sh->task_retire = sm.scan_b;
+          if (newh != sm.c_cqh) {
+            sm.c_cqh = newh;
+            sh->cq_head = newh;
+          }
+          if (sm.scan_b != sm.c_retire) {
+            sm.unretired -= (int32_t)(sm.scan_b - sm.c_retire);
+            sm.c_retire = sm.scan_b;
+            sh->task_retire = sm.scan_b;
+          }
           C.stage_reclaim();
+        }
+      }
+      // doorbells: how far each non-exclusive stream has executed; a change is
+      // an event for that stream's completion scan
+      for (int g = tid; g < P.max_streams; g += blockDim.x) {
+        SState& S = C.ss[g];
+        if ((S.flags & SF_EXCLUSIVE) || (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested)) continue;
+        uint64_t db;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
+        if (db != S.reached) {
+          S.reached = db;
+          sm.sdirty[g] = 1;
         }
       }
       __syncthreads();
@@ -2476,16 +2589,19 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       int phys = 0, pend = 0;
       if (tid == 0) sm.pending = 0;
       __syncthreads();
+      // only streams with an event since their last scan (every stream on
+      // the periodic full scan): nothing else can change a completion word
+      const bool all = sm.all_dirty != 0;
       if (warp_streams) {
         const int warp = tid >> 5, nw = blockDim.x >> 5;
         for (int g = warp; g < P.max_streams; g += nw) {
-          if (C.stream_physical_warp(g, now)) phys = 1;
+          if ((all || sm.sdirty[g]) && C.stream_physical_warp(g, now)) phys = 1;
           const SState& S = C.ss[g];
           if (S.retire < S.ingested) pend = 1;
         }
       } else {
         for (int g = tid; g < P.max_streams; g += blockDim.x) {
-          if (C.stream_physical(g, now)) phys = 1;
+          if ((all || sm.sdirty[g]) && C.stream_physical(g, now)) phys = 1;
           const SState& S = C.ss[g];
           if (S.retire < S.ingested) pend = 1;
         }
@@ -2493,8 +2609,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if (phys) atomicOr(&sm.any, 1);
       if (pend) atomicOr(&sm.pending, 1);
       __syncthreads();
+      for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 0;
       lap(3);
-      if (tid == 0) C.task_phase_begin();
+      if (tid == 0) {
+        C.task_phase_begin();
+        sm.ndlv = 0;
+        sm.dlv_bytes = 0;
+      }
       __syncthreads();
       mark(-1);
       if (warp_streams) {
@@ -2503,6 +2624,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       } else {
         for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
       }
+      __syncthreads();
+      C.make_deferred();
       __syncthreads();
       mark(3);
       C.schedule_reduce();
@@ -2519,10 +2642,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if (any) last_prog = now;
       // staging reads "the engine is quiet" as: no tick changed anything and
       // no task is in flight for as long as the staging delay
-      if (any || tasks_live_now(P)) sm.last_prog = now;
-      const uint64_t a = *(volatile uint64_t*)&sh->task_alloc;
-      const uint64_t rt = sh->task_retire;
+      const uint64_t a = sm.c_alloc;
+      const uint64_t rt = sm.c_retire;
       const bool tasks_live = rt != a;
+      if (any || tasks_live) sm.last_prog = now;
       if (a != alloc0 && t_first_task == 0) t_first_task = now;
       if (a != alloc0 && !tasks_live) t_tasks_done = now;
       const bool pending = tasks_live || sm.pending != 0;
@@ -2565,7 +2688,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     lap(5);
     if (sm.flag == 1) break;
     if (sm.flag == 2) {
-      if (tid == 0) abandon_tasks(P);
+      if (tid == 0) abandon_tasks(P, sm);
       release_all(P, C.ss, kErrTimeout);
       if (tid == 0) sm.released = 1;
       __syncthreads();
@@ -2626,8 +2749,10 @@ __device__ void mover_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
       if (idle_t0 == 0) idle_t0 = t;
       // the control CTA always raises exit_flag before leaving; this bound only
       // guards against a control CTA that never got scheduled
-      const uint64_t hb = ld_rlx_sys(&P.wctl->heartbeat);
-      if (t - idle_t0 > 4 * P.watchdog_ns && (int64_t)(t - (int64_t)hb) > 4 * P.watchdog_ns) {
+      // the host-memory heartbeat is read only once the idle bound is reached
+      // (idle movers polling it would load the chip-to-chip link)
+      if (t - idle_t0 > 4 * P.watchdog_ns &&
+          (int64_t)(t - (int64_t)ld_rlx_sys(&P.wctl->heartbeat)) > 4 * P.watchdog_ns) {
         set_error(P, -1, kErrTimeout);
         sm.flag = 1;
       }
@@ -2818,7 +2943,38 @@ mpxi::Task host_copy_task(const mpxi::Layout& src, const mpxi::Layout& dst, int6
   return T;
 }
 
+// Once per device, with that device current: the device address of the
+// staging array (its host-side name is not one) and the SM count.  The
+// address is kept for the life of the process; a cudaDeviceReset destroys
+// the context it belongs to, so it must not be followed by further calls.
+int static_setup(int dev, void** stage) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return 1;
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_stage) != cudaSuccess || !p) return 1;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    g_static_nsm[dev] = nsm;
+    g_static_addr[dev] = p;
+  }
+  *stage = g_static_addr[dev];
+  return 0;
+}
+
 }  // namespace
+
+// Load the standalone copy kernel and set up the current device's static
+// staging array now: a module loaded lazily at a first launch may wait for
+// running kernels, and a resident engine is one.
+extern "C" int mpxi_static_preload(void) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, mpxi::static_copy_kernel) != cudaSuccess) return 1;
+  int dev = 0;
+  void* stage = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  return static_setup(dev, &stage);
+}
 
 // Launch the packed-stream copy of `n` bytes between two typed layouts on
 // `stream` (the plain path uses it: one kernel per operation).
@@ -2851,6 +3007,10 @@ extern "C" int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, int32
     return 4;  // MPX_ERR_TYPE
   if (sendcount < 0 || recvcount < 0) return 1;  // MPX_ERR_ARG
   const int64_t se = mpxi::base_size((uint32_t)sb), re = mpxi::base_size((uint32_t)rb);
+  // byte spans above 2^60 are rejected by division before any product is formed
+  const int64_t sext = se * ((int64_t)(sv - 1) * sst + sbl), rext = re * ((int64_t)(rv - 1) * rst + rbl);
+  if (sendcount > (1ll << 60) / (sext > 0 ? sext : 1) || recvcount > (1ll << 60) / (rext > 0 ? rext : 1))
+    return 1;  // MPX_ERR_ARG
   const int64_t sbytes = sendcount * sv * sbl * se;
   const int64_t cap = recvcount * rv * rbl * re;
   const int64_t n = sbytes < cap ? sbytes : cap;  // MPI truncation: the receive capacity
@@ -2859,21 +3019,9 @@ extern "C" int mpx_sendrecv_static(const void* sendbuf, int64_t sendcount, int32
   if (bytes_delivered) *bytes_delivered = n;
   if (n == 0) return 0;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return 10;  // MPX_ERR_CUDA
+  if (cudaGetDevice(&dev) != cudaSuccess) return 10;  // MPX_ERR_CUDA
   void* stage = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_static_mu);
-    if (!g_static_addr[dev]) {
-      // the array's host-side name is not a device address: ask the runtime
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_static_stage) != cudaSuccess || !p) return 10;
-      int nsm = 0;
-      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 10;
-      g_static_nsm[dev] = nsm;
-      g_static_addr[dev] = p;
-    }
-    stage = g_static_addr[dev];
-  }
+  if (static_setup(dev, &stage)) return 10;
   const mpxi::Layout lsend = host_layout((uint64_t)sendbuf, (int32_t)se, sv, sbl, sst);
   const mpxi::Layout lrecv = host_layout((uint64_t)recvbuf, (int32_t)re, rv, rbl, rst);
   const mpxi::Layout lstage = host_layout((uint64_t)stage, 1, 1, 1, 1);

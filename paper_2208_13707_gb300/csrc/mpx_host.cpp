@@ -40,6 +40,8 @@ extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads);
 extern "C" int mpxi_engine_preload(void);
 extern "C" int mpxi_saxpy_preload(void);
 extern "C" int mpxi_step_preload(void);
+extern "C" int mpxi_static_preload(void);
+extern "C" int mpxi_plain_preload(void);
 extern "C" int mpxi_step_post_launch(const mpxi::EngineParams* P, const void* tmpl,
                                      const void* tmpl_wl, const void* streams, int nstreams,
                                      uint64_t* cnt_seq, uint64_t* cnt_wl, int32_t* err,
@@ -110,6 +112,8 @@ struct TypeRec {
 };
 
 constexpr int kMaxTypes = 1 << 16;
+constexpr int64_t kMaxTypeExtent = 1ll << 48;  // bytes of one instance of a derived type
+constexpr int64_t kMaxSpan = 1ll << 60;        // bytes one call may span
 constexpr int kFirstDerived = 16;
 TypeRec g_types[kMaxTypes];
 std::mutex g_types_mu;
@@ -127,6 +131,14 @@ const TypeRec* type_get(mpx_datatype_t t) {
   const TypeRec* r = &g_types[t];
   if (!__atomic_load_n(&r->alive, __ATOMIC_ACQUIRE)) return nullptr;
   return r;
+}
+
+// `count` instances of type t span at most kMaxSpan bytes (so the packed size,
+// the extent and every offset the engine derives from them fit in int64).
+// Checked by division before anything multiplies the count.
+bool span_ok(const TypeRec* t, int64_t count) {
+  const int64_t ext = base_size((uint32_t)t->base) * ((int64_t)(t->vcount - 1) * t->stride + t->blocklen);
+  return count >= 0 && (count == 0 || count <= kMaxSpan / (ext > 0 ? ext : 1));
 }
 
 int64_t now_ms() {
@@ -319,7 +331,11 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   if (cfg.engine_mode != MPX_ENGINE_PLAIN && !memops_ready()) { world_release(w); return MPX_ERR_CUDA; }
   // load every kernel of the library before any engine runs (lazy loading of
   // a module can wait for running kernels, and a resident engine is one)
-  if (mpxi_engine_preload() || mpxi_saxpy_preload() || mpxi_step_preload()) { world_release(w); return MPX_ERR_CUDA; }
+  if (mpxi_engine_preload() || mpxi_saxpy_preload() || mpxi_step_preload() || mpxi_static_preload() ||
+      mpxi_plain_preload()) {
+    world_release(w);
+    return MPX_ERR_CUDA;
+  }
   MPX_TRACE("world_create: memops and kernels loaded");
   const int S = cfg.max_streams;
   w->slots_log2 = log2i(cfg.ring_slots);
@@ -348,7 +364,10 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
     w->plain = plain::create(nranks, cfg.max_streams, cfg.staging_bytes);
     if (!w->plain) { world_release(w); return MPX_ERR_NO_MEM; }
     plain::set_world_index(w->plain, w->widx);
-    if (mpxi_saxpy_preload()) { world_release(w); return MPX_ERR_CUDA; }
+    if (mpxi_saxpy_preload() || mpxi_static_preload() || mpxi_plain_preload()) {
+      world_release(w);
+      return MPX_ERR_CUDA;
+    }
     *out = w;
     return MPX_SUCCESS;
   }
@@ -419,6 +438,9 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.sr_log2 = w->sr_log2;
   P.ctl_ctas = 1;
   P.movers_per_cta = cfg.mover_schedule == MPX_MOVERS_PER_CTA ? 1 : 0;
+  // per-phase timers of the control CTA (diagnostic; reported through
+  // mpx_world_get_counters); MPX_ENGINE_TIMING=0 leaves them out
+  P.timing = env_i64("MPX_ENGINE_TIMING", 1) != 0 ? 1 : 0;
   P.watchdog_ns = cfg.watchdog_ns;
   P.idle_ns = cfg.idle_exit_ns;
   P.stage_delay_ns = cfg.stage_delay_ns;
@@ -962,6 +984,10 @@ extern "C" int mpx_type_vector(int count, int blocklength, int stride, mpx_datat
                                mpx_datatype_t* newtype) {
   if (!newtype || count < 1 || blocklength < 1 || stride < blocklength) return MPX_ERR_ARG;
   if (oldtype < 0 || oldtype > MPX_DOUBLE) return MPX_ERR_TYPE;
+  // one instance's extent in bytes stays below 2^48, so that byte counts of
+  // whole messages can be checked against int64 with one division
+  const int64_t ext = ((int64_t)count - 1) * stride + blocklength;  // < 2^62: no overflow
+  if (ext > (kMaxTypeExtent >> 3)) return MPX_ERR_ARG;
   std::lock_guard<std::mutex> g(g_types_mu);
   int id;
   if (!g_types_free.empty()) {
@@ -1116,6 +1142,7 @@ static int fill_p2p(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_
   if (count < 0) return MPX_ERR_ARG;
   const TypeRec* t = type_get(dt);
   if (!t) return MPX_ERR_TYPE;
+  if (!span_ok(t, count)) return MPX_ERR_ARG;
   if (is_recv) {
     if (peer != MPX_ANY_SOURCE && (peer < 0 || peer >= c->size)) return MPX_ERR_RANK;
     if (tag != MPX_ANY_TAG && (tag < 0 || tag > MPX_TAG_UB)) return MPX_ERR_TAG;
@@ -1154,6 +1181,7 @@ static int fill_mux(Desc& d, uint32_t kind, const void* buf, int64_t count, mpx_
   if (count < 0) return MPX_ERR_ARG;
   const TypeRec* t = type_get(dt);
   if (!t) return MPX_ERR_TYPE;
+  if (!span_ok(t, count)) return MPX_ERR_ARG;
   auto nloc = [&](int r) { return sh->mux_off[(size_t)r + 1] - sh->mux_off[(size_t)r]; };
   const bool is_recv = kind == K_RECV || kind == K_IRECV;
   int own;
@@ -1365,6 +1393,12 @@ extern "C" int mpx_waitall_enqueue(int n, mpx_request_t reqs[], mpx_status_t sta
 
 // Descriptor of a collective call (allreduce, bcast, reduce, allgather):
 // buf = input, aux = output, peer = root.
+// A collective's element count, times the element size and the number of
+// ranks (an allgather's receive buffer), stays within kMaxSpan bytes.
+static bool coll_count_ok(int64_t count, mpx_comm_t c) {
+  return count >= 0 && count <= kMaxSpan / (8 * (int64_t)(c->size > 0 ? c->size : 1));
+}
+
 static void fill_collective(Desc& d, uint32_t kind, mpx_datatype_t dt, mpx_comm_t c,
                             const void* in, void* out, int64_t count, int root) {
   memset(&d, 0, sizeof(d));
@@ -1398,6 +1432,7 @@ static int bcast_common(void* buf, int64_t count, mpx_datatype_t dt, int root, m
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (root < 0 || root >= c->size) return MPX_ERR_RANK;
+  if (!coll_count_ok(count, c)) return MPX_ERR_ARG;
   if (count < 0 || (count > 0 && !buf)) return MPX_ERR_ARG;
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
@@ -1416,6 +1451,7 @@ static int reduce_common(const void* sendbuf, void* recvbuf, int64_t count, mpx_
     if (!at_root) return MPX_ERR_ARG;
     sendbuf = recvbuf;
   }
+  if (!coll_count_ok(count, c)) return MPX_ERR_ARG;
   if (count < 0 || (count > 0 && (!sendbuf || (at_root && !recvbuf)))) return MPX_ERR_ARG;
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
@@ -1428,6 +1464,7 @@ static int allgather_common(const void* sendbuf, void* recvbuf, int64_t count, m
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
   if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;  // the rank's block is already in place
+  if (!coll_count_ok(count, c)) return MPX_ERR_ARG;
   if (count < 0 || (count > 0 && (!sendbuf || !recvbuf))) return MPX_ERR_ARG;
   if (c->w->plain) return MPX_ERR_UNSUPPORTED;
   Desc d;
@@ -1440,6 +1477,7 @@ static int allreduce_common(const void* sendbuf, void* recvbuf, int64_t count, m
   if (!c || !c->stream || c->shared->mux()) return MPX_ERR_COMM;
   if (op != MPX_SUM) return MPX_ERR_ARG;
   if (dt < 0 || dt > MPX_DOUBLE) return MPX_ERR_TYPE;
+  if (!coll_count_ok(count, c)) return MPX_ERR_ARG;
   if (count < 0 || (count > 0 && !recvbuf)) return MPX_ERR_ARG;
   if (sendbuf == MPX_IN_PLACE) sendbuf = recvbuf;
   if (count > 0 && !sendbuf) return MPX_ERR_ARG;

@@ -260,7 +260,7 @@ struct EngineParams {
   int32_t qcap_log2, tq_log2, iw, mode;   // mode: 0 persistent, 1 drain
   int32_t wl_log2, sr_log2, ctl_ctas, nctas;
   int32_t movers_per_cta;     // MPX_MOVERS_PER_CTA: mover m owns the task ids = m mod movers
-  int32_t pad_p;
+  int32_t timing;             // control CTA times its phases (WorldCtl tick_ns, sub_ns)
   int64_t watchdog_ns, idle_ns, stage_delay_ns;
   int64_t tile_bytes, bulk_min;
   int64_t stage_bytes;

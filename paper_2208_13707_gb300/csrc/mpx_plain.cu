@@ -94,6 +94,15 @@ int64_t type_bytes(int32_t t) {
   return mpxi::base_size((uint32_t)b) * v * bl;
 }
 
+// `count` instances of type t span at most 2^60 bytes (the engine path's rule):
+// checked by division, before anything multiplies the count.
+bool span_ok(int32_t t, int64_t count) {
+  int32_t b, v, bl, st;
+  if (mpxi_type_desc(t, &b, &v, &bl, &st)) return false;
+  const int64_t ext = mpxi::base_size((uint32_t)b) * ((int64_t)(v - 1) * st + bl);
+  return count >= 0 && (count == 0 || count <= (1ll << 60) / (ext > 0 ? ext : 1));
+}
+
 struct Msg {
   int stream;
   uint64_t seq;
@@ -282,7 +291,7 @@ int p2p(PlainWorld* pw, uint32_t kind, const void* buf, int64_t count, mpx_datat
         int tag, int comm, int rank, int sid, mpx_status_t* status, mpx_request_t* req) {
   const int64_t tb = type_bytes(dt);
   if (tb < 0) return MPX_ERR_TYPE;
-  if (count < 0) return MPX_ERR_ARG;
+  if (count < 0 || !span_ok(dt, count)) return MPX_ERR_ARG;
   const bool is_send = kind == mpxi::K_SEND || kind == mpxi::K_ISEND;
   if (is_send) {
     if (peer < 0 || peer >= pw->nranks) return MPX_ERR_RANK;
@@ -457,3 +466,10 @@ int allreduce(PlainWorld* pw, const void* sendbuf, void* recvbuf, int64_t count,
 }
 
 }  // namespace plain
+
+// Load the plain path's reduction kernel now (its copies use the library's
+// standalone copy kernel, which mpxi_static_preload loads).
+extern "C" int mpxi_plain_preload(void) {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, plain::reduce_kernel) == cudaSuccess ? 0 : 1;
+}

@@ -146,7 +146,8 @@ struct Call {
   int tag;
   int64_t item;
   int64_t bytes;
-  int64_t off;  // payload offset in the caller's source region
+  int64_t off;           // payload offset in the caller's source region
+  int64_t capture = -1;  // caller schedules: capture offset (recv, allreduce) or first status (waitall)
 };
 
 struct Rec {  // one request in flight
@@ -155,11 +156,12 @@ struct Rec {  // one request in flight
   void* buf;
   int64_t bytes;   // payload delivered by this request (for GB/s)
   int64_t item;    // >= 0: digest this buffer
+  int64_t capture; // >= 0: copy the delivered bytes to the capture area here
 };
 struct Batch {  // requests covered by one blocking operation
   uint64_t seq;
   std::vector<Rec> recs;
-  cudaEvent_t digested = nullptr;  // digests of sampled buffers done (stream-ordered after seq)
+  cudaEvent_t digested = nullptr;  // digests and captures done (stream-ordered after seq)
 };
 
 struct Shared {
@@ -182,6 +184,9 @@ struct Shared {
   int64_t ndigests = 0;
   uint64_t* dig_host = nullptr;  // mapped pinned digest slots [ndigests]
   uint64_t* dig_dev = nullptr;   // their device address
+  uint8_t* capture = nullptr;    // caller schedules: where delivered bytes are copied
+  mpx_status_t* statuses = nullptr;  // caller schedules: waitall statuses
+  bool own_regions = true;       // regions allocated (and filled) here
   // results, per thread (merged at the end)
   std::vector<std::vector<float>> lat, svc;
   std::vector<int64_t> bytes_done, t_last;
@@ -205,6 +210,10 @@ struct Shared {
 void enqueue_digests(Shared& S, Batch& b, cudaStream_t cs) {
   bool any = false;
   for (const Rec& r : b.recs) {
+    if (r.capture >= 0 && S.capture && r.buf && r.bytes > 0) {
+      cudaMemcpyAsync(S.capture + r.capture, r.buf, (size_t)r.bytes, cudaMemcpyDeviceToDevice, cs);
+      any = true;
+    }
     if (r.item < 0 || !S.dig_dev || r.item >= S.ndigests || !r.buf) continue;
     mpxi_digest_store(r.buf, r.bytes, S.dig_dev + r.item, cs);
     any = true;
@@ -340,7 +349,7 @@ void client_thread(Shared& S, ThreadCtx ctx, bool plain, int64_t t0) {
       while (rc == MPX_ERR_AGAIN && !S.stop.load());
       if (rc) { fail(rc); break; }
       reqs.push_back(r);
-      open.push_back(Rec{t_arr, te, t, nullptr, 0, -1});
+      open.push_back(Rec{t_arr, te, t, nullptr, 0, -1, -1});
     } else if (x.kind == C_RECV) {
       bool waited = false;
       void* buf = S.budget[(size_t)t].admit(x.bytes, &waited, S.stop);
@@ -353,14 +362,15 @@ void client_thread(Shared& S, ThreadCtx ctx, bool plain, int64_t t0) {
       if (rc) { fail(rc); break; }
       reqs.push_back(r);
       const bool sample = c.only_item >= 0 || (c.sample_every > 0 && x.item % c.sample_every == 0);
-      open.push_back(Rec{t_arr, te, t, buf, x.bytes, sample ? x.item : -1});
+      open.push_back(Rec{t_arr, te, t, buf, x.bytes, sample ? x.item : -1, x.capture});
     } else {
       // a blocking call: waitall over the epoch's requests, or an allreduce
       Batch b;
       if (x.kind == C_WAITALL) {
         // engine: MPX_ERR_AGAIN only while the waitlist is full; plain path:
         // until the requests complete (the host thread waits here)
-        do rc = mpx_waitall_enqueue((int)reqs.size(), reqs.data(), nullptr);
+        mpx_status_t* sts = x.capture >= 0 && S.statuses ? S.statuses + x.capture : nullptr;
+        do rc = mpx_waitall_enqueue((int)reqs.size(), reqs.data(), sts);
         while (rc == MPX_ERR_AGAIN && !S.stop.load());
         if (rc) { fail(rc); break; }
         b.recs.swap(open);
@@ -376,7 +386,7 @@ void client_thread(Shared& S, ThreadCtx ctx, bool plain, int64_t t0) {
         while (rc == MPX_ERR_AGAIN && !S.stop.load());
         if (rc) { fail(rc); break; }
         const bool sample = t == 0 && (c.only_item >= 0 || (c.sample_every > 0 && x.item % c.sample_every == 0));
-        b.recs.push_back(Rec{t_arr, te, t, buf, x.bytes, sample ? x.item : -1});
+        b.recs.push_back(Rec{t_arr, te, t, buf, x.bytes, sample ? x.item : -1, x.capture});
       }
       if (plain) {
         const int64_t t_c = now_ns();  // the blocking call returned: complete
@@ -458,14 +468,65 @@ extern "C" int mpx_serve_config_init(mpx_serve_config_t* c) {
   return MPX_SUCCESS;
 }
 
-extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* res,
-                             uint64_t* digests, uint64_t* source_digests, int64_t ndigests) {
+namespace {
+
+// A caller's schedule into the threads' call lists, every call checked
+// against the thread count and the regions, capture and status ranges.
+int load_schedule(Shared& S, const mpx_serve_schedule_t& q, int64_t* max_buf) {
+  const int T = S.T;
+  if (!q.calls || !q.call_lo || !q.regions || q.region_bytes < 0 || q.call_lo[0] != 0) return MPX_ERR_ARG;
+  if ((q.capture_bytes > 0 && !q.capture) || (q.nstatuses > 0 && !q.statuses)) return MPX_ERR_ARG;
+  S.calls.assign((size_t)T, {});
+  S.nitems = 0;
+  *max_buf = 0;
+  for (int t = 0; t < T; ++t) {
+    if (q.call_lo[t + 1] < q.call_lo[t] || !q.regions[t]) return MPX_ERR_ARG;
+    int64_t nreq = 0;
+    for (int64_t i = q.call_lo[t]; i < q.call_lo[t + 1]; ++i) {
+      const mpx_serve_call_t& x = q.calls[i];
+      const bool p2p = x.kind == MPX_SERVE_SEND || x.kind == MPX_SERVE_RECV;
+      if (x.kind < MPX_SERVE_SEND || x.kind > MPX_SERVE_ALLREDUCE || x.item < 0) return MPX_ERR_ARG;
+      if (x.kind != MPX_SERVE_WAITALL && (x.bytes < 0 || x.bytes > q.region_bytes)) return MPX_ERR_ARG;
+      if (p2p && (x.peer < 0 || x.peer >= T || x.tag < 0 || x.tag > MPX_TAG_UB)) return MPX_ERR_ARG;
+      if ((x.kind == MPX_SERVE_SEND || x.kind == MPX_SERVE_ALLREDUCE) &&
+          (x.off < 0 || x.off > q.region_bytes - x.bytes))
+        return MPX_ERR_ARG;
+      if (x.kind == MPX_SERVE_ALLREDUCE && (x.bytes & 3)) return MPX_ERR_ARG;
+      if ((x.kind == MPX_SERVE_RECV || x.kind == MPX_SERVE_ALLREDUCE) && x.capture >= 0 &&
+          (!q.capture || x.capture > q.capture_bytes - x.bytes))
+        return MPX_ERR_ARG;
+      if (x.kind == MPX_SERVE_WAITALL && x.capture >= 0 &&
+          (!q.statuses || x.capture > q.nstatuses - nreq))
+        return MPX_ERR_ARG;
+      if (x.kind == MPX_SERVE_WAITALL) nreq = 0;
+      else if (p2p) ++nreq;
+      if (x.kind == MPX_SERVE_RECV || x.kind == MPX_SERVE_ALLREDUCE) *max_buf = std::max(*max_buf, x.bytes);
+      Call y{x.kind == MPX_SERVE_SEND ? C_SEND : x.kind == MPX_SERVE_RECV ? C_RECV
+             : x.kind == MPX_SERVE_WAITALL ? C_WAITALL : C_ALLREDUCE,
+             x.peer, x.tag, x.item, x.bytes, x.off};
+      y.capture = x.capture;
+      S.calls[(size_t)t].push_back(y);
+      S.nitems = std::max(S.nitems, x.item + 1);
+    }
+  }
+  S.region_bytes = q.region_bytes;
+  S.region.assign((size_t)T, nullptr);
+  for (int t = 0; t < T; ++t) S.region[(size_t)t] = (uint8_t*)q.regions[t];
+  S.own_regions = false;
+  S.capture = (uint8_t*)q.capture;
+  S.statuses = q.statuses;
+  return MPX_SUCCESS;
+}
+
+int serve(const mpx_serve_config_t* cfg, const mpx_serve_schedule_t* sched, mpx_serve_result_t* res,
+          uint64_t* digests, uint64_t* source_digests, int64_t ndigests) {
   if (!cfg || !res) return MPX_ERR_ARG;
   const mpx_serve_config_t& c = *cfg;
-  if (c.nthreads < 2 || c.nthreads > 1024 || c.requests < 1 || c.min_log2 < 2 ||
-      c.max_log2 < c.min_log2 || c.max_log2 > 30 || c.p_allreduce < 0 || c.p_allreduce > 1 ||
-      c.budget_bytes <= 0 ||
+  if (c.nthreads < 2 || c.nthreads > 1024 || c.budget_bytes <= 0 ||
       (c.engine_mode != MPX_ENGINE_PERSISTENT && c.engine_mode != MPX_ENGINE_PLAIN))
+    return MPX_ERR_ARG;
+  if (!sched && (c.requests < 1 || c.min_log2 < 2 || c.max_log2 < c.min_log2 || c.max_log2 > 30 ||
+                 c.p_allreduce < 0 || c.p_allreduce > 1))
     return MPX_ERR_ARG;
   memset(res, 0, sizeof(*res));
   const int T = c.nthreads;
@@ -475,7 +536,14 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   S.T = T;
   S.digests = digests;
   S.ndigests = ndigests;
-  build_schedule(S);
+  int64_t max_buf = 0;
+  if (sched) {
+    const int lrc = load_schedule(S, *sched, &max_buf);
+    if (lrc) return lrc;
+  } else {
+    max_buf = (int64_t)1 << c.max_log2;
+    build_schedule(S);
+  }
   res->items = S.nitems;
   if (mpxi_serve_preload()) return MPX_ERR_CUDA;
   struct HostSlots {
@@ -495,7 +563,7 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   }
   if (cudaMalloc((void**)&S.pool, (size_t)c.budget_bytes) != cudaSuccess) return MPX_ERR_NO_MEM;
   const int64_t share = (c.budget_bytes / T) & ~(int64_t)255;
-  if (share < ((int64_t)1 << c.max_log2)) return MPX_ERR_ARG;  // a request must fit a share
+  if (share < max_buf) return MPX_ERR_ARG;  // a request must fit a share
   for (int t = 0; t < T; ++t) S.budget[(size_t)t].init(S.pool + (size_t)t * (size_t)share, share);
   // world, streams, comm
   mpx_world_config_t wc;
@@ -509,12 +577,13 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
   std::vector<ThreadCtx> ctx((size_t)T);
   std::vector<mpx_stream_t> ms((size_t)T);
   std::vector<mpx_comm_t> comm((size_t)T);
-  S.region.assign((size_t)T, nullptr);
+  if (S.own_regions) S.region.assign((size_t)T, nullptr);
   for (int t = 0; t < T && rc == 0; ++t) {
     ctx[(size_t)t].t = t;
     if (cudaStreamCreateWithFlags(&ctx[(size_t)t].cs, cudaStreamNonBlocking) != cudaSuccess) rc = MPX_ERR_CUDA;
     if (!rc) rc = mpx_stream_create(w, t, (mpx_cuda_stream_t)ctx[(size_t)t].cs, MPX_STREAM_EXCLUSIVE, &ms[(size_t)t]);
     ctx[(size_t)t].stream = ms[(size_t)t];
+    if (!S.own_regions) continue;  // the caller's regions hold the caller's data
     if (!rc && cudaMalloc((void**)&S.region[(size_t)t], (size_t)S.region_bytes) != cudaSuccess) rc = MPX_ERR_NO_MEM;
     // first half raw bytes (messages), second half fp32 (allreduce inputs) would
     // split the region; instead every slice is valid fp32 data and raw bytes alike
@@ -598,8 +667,21 @@ extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* 
     if (ctx[(size_t)t].cs) cudaStreamSynchronize(ctx[(size_t)t].cs);
     if (ms[(size_t)t]) mpx_stream_free(&ms[(size_t)t]);
     if (ctx[(size_t)t].cs) cudaStreamDestroy(ctx[(size_t)t].cs);
-    if (S.region[(size_t)t]) cudaFree(S.region[(size_t)t]);
+    if (S.own_regions && S.region[(size_t)t]) cudaFree(S.region[(size_t)t]);
   }
   if (w) mpx_world_free(&w);
   return rc;
+}
+
+}  // namespace
+
+extern "C" int mpx_serve_run(const mpx_serve_config_t* cfg, mpx_serve_result_t* res,
+                             uint64_t* digests, uint64_t* source_digests, int64_t ndigests) {
+  return serve(cfg, nullptr, res, digests, source_digests, ndigests);
+}
+
+extern "C" int mpx_serve_run_schedule(const mpx_serve_config_t* cfg, const mpx_serve_schedule_t* sched,
+                                      mpx_serve_result_t* res) {
+  if (!sched) return MPX_ERR_ARG;
+  return serve(cfg, sched, res, nullptr, nullptr, 0);
 }

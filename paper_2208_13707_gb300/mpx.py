@@ -85,6 +85,23 @@ class ServeResult(ctypes.Structure):
                 ("admission_waits", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
 
 
+SERVE_SEND, SERVE_RECV, SERVE_WAITALL, SERVE_ALLREDUCE = 0, 1, 2, 3
+
+
+def serve_call_dtype():
+    """numpy layout of mpx_serve_call_t."""
+    import numpy as np
+    return np.dtype([("kind", "<i4"), ("peer", "<i4"), ("tag", "<i4"), ("pad", "<i4"),
+                     ("item", "<i8"), ("bytes", "<i8"), ("off", "<i8"), ("capture", "<i8")])
+
+
+class ServeSchedule(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_void_p), ("call_lo", ctypes.c_void_p), ("regions", ctypes.c_void_p),
+                ("region_bytes", ctypes.c_int64), ("capture", ctypes.c_void_p),
+                ("capture_bytes", ctypes.c_int64), ("statuses", ctypes.c_void_p),
+                ("nstatuses", ctypes.c_int64)]
+
+
 class Status(ctypes.Structure):
     _fields_ = [("source", ctypes.c_int32), ("tag", ctypes.c_int32), ("error", ctypes.c_int32),
                 ("source_index", ctypes.c_int32), ("bytes", ctypes.c_int64)]
@@ -175,6 +192,7 @@ _SIGS = {
     "mpx_step_create": [_vp, ctypes.c_int, _vp, _P(_vp)],
     "mpx_serve_config_init": [_P(ServeConfig)],
     "mpx_serve_run": [_P(ServeConfig), _P(ServeResult), _vp, _vp, _i64],
+    "mpx_serve_run_schedule": [_P(ServeConfig), _P(ServeSchedule), _P(ServeResult)],
     "mpx_step_launch": [_vp, _vp],
     "mpx_step_get_error": [_vp, _P(ctypes.c_int)],
     "mpx_step_free": [_P(_vp)],
@@ -632,4 +650,24 @@ def mpx_serve_run(cfg: ServeConfig, digests=None, source_digests=None) -> dict:
             assert source_digests.dtype == np.uint64 and len(source_digests) == dn
             sp = source_digests.ctypes.data
     _chk(lib.mpx_serve_run(ctypes.byref(cfg), ctypes.byref(r), dp, sp, dn), "mpx_serve_run")
+    return {k: getattr(r, k) for k, _ in ServeResult._fields_}
+
+
+def mpx_serve_run_schedule(cfg: ServeConfig, calls, call_lo, regions, region_bytes: int,
+                           capture: int = 0, capture_bytes: int = 0, statuses: int = 0,
+                           nstatuses: int = 0) -> dict:
+    """Run the serving loop over a caller-supplied schedule.  `calls` is a
+    numpy array of serve_call_dtype(), `call_lo` int64 (nthreads + 1),
+    `regions` a sequence of device pointers; capture / statuses are device
+    pointers (0: none).  Returns the result fields as a dict."""
+    import numpy as np
+    calls = np.ascontiguousarray(calls, dtype=serve_call_dtype())
+    call_lo = np.ascontiguousarray(call_lo, dtype=np.int64)
+    regs = (ctypes.c_void_p * len(regions))(*[int(x) for x in regions])
+    q = ServeSchedule(calls.ctypes.data, call_lo.ctypes.data, ctypes.cast(regs, ctypes.c_void_p),
+                      int(region_bytes), capture or None, int(capture_bytes), statuses or None,
+                      int(nstatuses))
+    r = ServeResult()
+    _chk(lib.mpx_serve_run_schedule(ctypes.byref(cfg), ctypes.byref(q), ctypes.byref(r)),
+         "mpx_serve_run_schedule")
     return {k: getattr(r, k) for k, _ in ServeResult._fields_}

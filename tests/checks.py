@@ -21,8 +21,8 @@ from typing import Dict, FrozenSet, List, Set, Tuple
 
 import numpy as np
 
-from traffic.program import (ALLREDUCE, ANY_INDEX, ANY_SOURCE, ANY_TAG, AXPY, IRECV, ISEND, RECV,
-                             SEND, WAIT, WAITALL, Program)
+from traffic.program import (ALLREDUCE, ANY_INDEX, ANY_SOURCE, ANY_TAG, AXPY, ERR_TRUNCATE, IRECV,
+                             ISEND, RECV, SEND, WAIT, WAITALL, Program)
 
 SEND_KINDS = (SEND, ISEND)
 RECV_KINDS = (RECV, IRECV)
@@ -288,3 +288,70 @@ def match_set(match: np.ndarray, prog: Program) -> FrozenSet:
     kinds = prog.ops["kind"]
     return frozenset((s, int(match[s])) for s in range(len(match))
                      if kinds[s] in SEND_KINDS and match[s] >= 0)
+
+
+# ---------------------------------------------------------------------------
+# the outcome of a run whose matching may legally differ (live traffic)
+# ---------------------------------------------------------------------------
+def status_slot_of(prog: Program) -> Dict[int, int]:
+    """Receive op -> the status slot a wait or waitall (or the receive itself)
+    writes for it."""
+    slot = {}
+    kinds = prog.ops["kind"]
+    for j, o in enumerate(prog.ops):
+        k = int(kinds[j])
+        if k == RECV and int(o["status"]) >= 0:
+            slot[j] = int(o["status"])
+        elif k in (WAIT, WAITALL) and int(o["status"]) >= 0:
+            lo, n = int(o["req_lo"]), int(o["req_n"])
+            for q in range(n):
+                slot[int(prog.reqlist[lo + q])] = int(o["status"]) + q
+    return slot
+
+
+def infer_match_from_payloads(prog: Program, buffers, status) -> Tuple[np.ndarray, List[str]]:
+    """The match map a run produced, read from what it delivered: each
+    receive's status names (source, tag, bytes), and among the sends on that
+    channel the one whose packed payload begins with the delivered bytes is
+    its partner.  Needs payloads that tell sends apart (random bytes).
+    Returns (match, problems): problems lists receives whose status or bytes
+    no send explains, or a send claimed twice."""
+    kinds = prog.ops["kind"]
+    init = prog.fresh_buffers()
+    types = prog.types
+    match = np.full(len(prog.ops), -1, np.int64)
+    problems = []
+    by_channel = defaultdict(list)
+    for s in np.nonzero(np.isin(kinds, SEND_KINDS))[0]:
+        o = prog.ops[s]
+        c = int(o["comm"])
+        src, _ = comm_member(prog, c, int(o["stream"]))
+        by_channel[(c, src, int(o["peer"]), int(o["tag"]))].append(int(s))
+    slots = status_slot_of(prog)
+    for r in np.nonzero(np.isin(kinds, RECV_KINDS))[0]:
+        r = int(r)
+        if r not in slots:
+            problems.append(f"recv {r}: no status slot")
+            continue
+        st = status[slots[r]]
+        o = prog.ops[r]
+        c = int(o["comm"])
+        dst, _ = comm_member(prog, c, int(o["stream"]))
+        n = int(st["bytes"])
+        got = np_pack(buffers[int(o["buf"])], int(o["off"]), types, int(o["type"]), int(o["count"]))[:n]
+        cands = []
+        for s in by_channel.get((c, int(st["source"]), dst, int(st["tag"])), []):
+            so = prog.ops[s]
+            sent = np_pack(init[int(so["buf"])], int(so["off"]), types, int(so["type"]), int(so["count"]))
+            if len(sent) >= n and np.array_equal(sent[:n], got) and match[s] < 0:
+                cands.append((s, len(sent)))
+        if len(cands) != 1:
+            problems.append(f"recv {r}: {len(cands)} sends explain status {tuple(st)}")
+            continue
+        s, sent_n = cands[0]
+        cap = len(np_pack(init[int(o["buf"])], int(o["off"]), types, int(o["type"]), int(o["count"])))
+        want_err = ERR_TRUNCATE if sent_n > cap else 0   # MPI truncation
+        if n != min(sent_n, cap) or int(st["error"]) != want_err:
+            problems.append(f"recv {r}: bytes {n} / error {int(st['error'])} do not fit send {s}")
+        match[s], match[r] = r, s
+    return match, problems

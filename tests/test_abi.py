@@ -94,6 +94,28 @@ def test_sendrecv_static_rejects_bad_arguments_before_touching_the_gpu():
     assert e.value.code == mpx.ERR_NO_MEM
 
 
+def test_byte_spans_that_would_overflow_are_rejected():
+    """Byte counts are products of counts, vector shapes and element sizes;
+    spans beyond 2^60 bytes are refused with MPX_ERR_ARG before any product is
+    formed (a wrapped count could otherwise look small)."""
+    from paper_2208_13707_gb300 import mpx
+    with pytest.raises(mpx.MpxError) as e:       # one instance spans about 2^62 bytes
+        mpx.mpx_type_vector(1 << 30, 1, 1 << 30, mpx.FLOAT)
+    assert e.value.code == mpx.ERR_ARG
+    big = mpx.mpx_type_vector(1 << 16, 1, 1 << 20, mpx.DOUBLE)  # 2^39-byte extent: accepted
+    try:
+        for cnt in ((1 << 62), (1 << 40)):        # 2^62 * 8 and 2^40 * 2^39 bytes
+            ty = mpx.DOUBLE if cnt == (1 << 62) else big
+            with pytest.raises(mpx.MpxError) as e:
+                mpx.mpx_sendrecv_static(16, cnt, ty, 32, 1, mpx.BYTE, 0)
+            assert e.value.code == mpx.ERR_ARG
+            with pytest.raises(mpx.MpxError) as e:
+                mpx.mpx_sendrecv_static(16, 1, mpx.BYTE, 32, cnt, ty, 0)
+            assert e.value.code == mpx.ERR_ARG
+    finally:
+        mpx.mpx_type_free(big)
+
+
 def test_op_struct_layout_matches_the_binding(tmp_path):
     """mpx_op_t as the C compiler lays it out equals the binding's numpy layout."""
     from paper_2208_13707_gb300 import mpx
@@ -112,6 +134,52 @@ def test_op_struct_layout_matches_the_binding(tmp_path):
                                           check=True).stdout.split()]
     assert out[0] == dt.itemsize
     assert out[1:] == [dt.fields[f][1] for f in fields]
+
+
+def test_serve_call_layout_matches_the_binding(tmp_path):
+    """mpx_serve_call_t as the C compiler lays it out equals the numpy layout
+    the binding and the schedule generator use."""
+    import subprocess
+    from paper_2208_13707_gb300 import mpx
+    from traffic.gen import SERVE_CALL_DTYPE
+    dt = mpx.serve_call_dtype()
+    assert dt == SERVE_CALL_DTYPE
+    fields = list(dt.names)
+    src = tmp_path / "call.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpx.h"\nint main(void){\n'
+                   '  printf("%zu", sizeof(mpx_serve_call_t));\n' +
+                   "".join(f'  printf(" %zu", offsetof(mpx_serve_call_t, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "call"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == dt.itemsize
+    assert out[1:] == [dt.fields[f][1] for f in fields]
+    assert (mpx.SERVE_SEND, mpx.SERVE_RECV, mpx.SERVE_WAITALL, mpx.SERVE_ALLREDUCE) == (0, 1, 2, 3)
+
+
+def test_serve_schedule_rejects_out_of_range_calls():
+    """Schedule checks run before any GPU work: a peer outside the threads,
+    an offset past the region, a capture past the capture area."""
+    import numpy as np
+    from paper_2208_13707_gb300 import mpx
+    c = mpx.mpx_serve_config_init()
+    c.nthreads = 2
+    calls = np.zeros(2, mpx.serve_call_dtype())
+    calls["kind"] = [mpx.SERVE_SEND, mpx.SERVE_RECV]
+    calls["peer"] = [1, 0]
+    calls["bytes"] = 64
+    calls["capture"] = -1
+    lo = np.array([0, 1, 2], np.int64)
+    bad = [("peer", 0, 2), ("off", 0, 4050), ("capture", 1, 64)]
+    for field, i, v in bad:
+        x = calls.copy()
+        x[field][i] = v
+        with pytest.raises(mpx.MpxError) as e:
+            mpx.mpx_serve_run_schedule(c, x, lo, [64, 128], 4096, capture=256, capture_bytes=64)
+        assert e.value.code == mpx.ERR_ARG, field
 
 
 def test_enqueue_batch_stops_at_the_first_invalid_op():
@@ -138,7 +206,8 @@ def test_enqueue_batch_stops_at_the_first_invalid_op():
                                           ("mpx_world_config_t", "WorldConfig"),
                                           ("mpx_status_t", "Status"),
                                           ("mpx_hostrate_config_t", "HostrateConfig"),
-                                          ("mpx_hostrate_result_t", "HostrateResult")])
+                                          ("mpx_hostrate_result_t", "HostrateResult"),
+                                          ("mpx_serve_schedule_t", "ServeSchedule")])
 def test_struct_layouts_match_the_binding(tmp_path, cname, pyname):
     import subprocess
     from paper_2208_13707_gb300 import mpx

@@ -10,6 +10,9 @@ import pytest
 
 import oracle
 from traffic import gen
+from traffic.program import ERR_TRUNCATE
+
+from checks import infer_match_from_payloads, validity_violations
 
 pytestmark = pytest.mark.gpu
 
@@ -119,3 +122,66 @@ def test_per_cta_mover_schedule_matches_the_oracle():
         _check(r, ref)
     finally:
         r.close()
+
+
+# ---------------------------------------------------------------------------
+# non-laminar wildcards: (ANY_SOURCE, exact tag) receives next to (s, ANY_TAG)
+# ones, widened to (ANY_SOURCE, ANY_TAG) only where the oracle finds a
+# receive that can never match; some exact receives truncate
+# ---------------------------------------------------------------------------
+def _unmatched(prog):
+    o = oracle.run(prog)
+    if not o.deadlock:
+        return None
+    k = prog.ops["kind"]
+    return [j for j in range(len(prog.ops)) if k[j] in (1, 3) and o.match[j] < 0]
+
+
+def _nonlaminar(nranks=64, streams_per_rank=4, nmsg=8000, seed_off=7):
+    p = gen.batching(nranks=nranks, streams_per_rank=streams_per_rank, nmsg=nmsg,
+                     max_bytes=64 << 10, seed=gen.SEED_BASE + 2 + 1000 * seed_off, fixup=_unmatched)
+    ref = oracle.run(p)
+    assert ref.error == 0 and not ref.deadlock
+    assert np.any(p.ops["peer"] == -2) and np.any(ref.status["error"] == ERR_TRUNCATE)
+    return p, ref
+
+
+def test_nonlaminar_wildcards_recorded_step_exact():
+    """The recorded step publishes every descriptor before its engine pass, so
+    the canonical round order holds and the outcome equals the oracle's, byte
+    for byte and status for status, on two replays."""
+    gpu = _gpu()
+    p, ref = _nonlaminar()
+    r = gpu.BatchRunner(p, mode="graph", timeout_s=60)
+    try:
+        for _ in range(2):
+            r.enqueue()
+            assert r.finish(), "step did not finish"
+            bufs, status = r.results()
+            for k, (a, b) in enumerate(zip(bufs, ref.buffers)):
+                assert np.array_equal(a, b), f"buffer {k} differs"
+            assert np.array_equal(status, ref.status), "statuses differ"
+            serr, werr = r.errors()
+            assert werr == ERR_TRUNCATE
+    finally:
+        r.close()
+
+
+def test_nonlaminar_wildcards_persistent_engine_is_legal():
+    """Live traffic into a resident engine: descriptors of different streams
+    arrive at different ticks, so an ANY_SOURCE receive may legally take
+    another sender's message than in the canonical order.  The matching read
+    back from the delivered bytes must be an MPI-legal outcome (every receive
+    matched once, compatible, no overtaking), with statuses and truncation
+    errors that fit the sends it names."""
+    gpu = _gpu()
+    p, ref = _nonlaminar(seed_off=8)
+    r = gpu.BatchRunner(p, mode="persistent", timeout_s=60)
+    try:
+        assert r.step(), "step did not finish"
+        bufs, status = r.results()
+    finally:
+        r.close()
+    match, problems = infer_match_from_payloads(p, bufs, status)
+    assert problems == [], problems[:5]
+    assert validity_violations(p, match, require_complete=True) == []

@@ -9,7 +9,9 @@ benchmark times.
   property at any size), and sampled elements (both ends, tile edges, random
   positions) must equal what the oracle computes for those elements' inputs:
   bit-exact for int64 and the fixed order, within |y - s| <= 1e-6 * sum|x|
-  of the oracle's double sum for the tree order."""
+  of the oracle's double sum for the tree order.
+* One step of the 512^3 halo exchange (8 subdomains of 256^3, six faces
+  each, vector-typed x and y faces), every buffer compared with the oracle."""
 import numpy as np
 import pytest
 
@@ -34,6 +36,23 @@ def test_ring_exchange_full_size_three_steps():
     ref = oracle.run(p)
     assert ref.error == 0 and not ref.deadlock
     out = gpu.run(p, mode="drain", timeout_s=120)
+    assert out.finished and out.world_error == 0
+    for k, (a, b) in enumerate(zip(out.buffers, ref.buffers)):
+        assert np.array_equal(a, b), f"buffer {k} differs"
+
+
+def test_halo_exchange_full_size_step():
+    """One step of the 512^3 halo exchange at its full size: 8 subdomains of
+    256^3 fp32, each sending its 6 faces (x faces vector(65536, 1, 256) with
+    4-byte blocks, y faces vector(256, 256, 65536), z faces contiguous) into
+    the neighbours' contiguous ghost buffers; every subdomain and ghost buffer
+    compared byte for byte with the oracle."""
+    _torch()
+    from traffic import gpu
+    p = gen.halo3d(sub=256, steps=1)
+    ref = oracle.run(p)
+    assert ref.error == 0 and not ref.deadlock
+    out = gpu.run(p, mode="persistent", timeout_s=120)
     assert out.finished and out.world_error == 0
     for k, (a, b) in enumerate(zip(out.buffers, ref.buffers)):
         assert np.array_equal(a, b), f"buffer {k} differs"

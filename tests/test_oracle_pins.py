@@ -248,6 +248,102 @@ def test_round_model_hand_worked_wildcard_order():
     assert list(o.post_round[:3]) == [1, 2, 2]
 
 
+def test_round_model_causal_order_beats_stream_order():
+    """Hand-worked: rank 1 first receives from rank 2 (blocking) and only then
+    sends P to rank 0; rank 2 sends Q to rank 0 and then T to rank 1; rank 0
+    posts two ANY_SOURCE receives R1, R2 and waits for both.
+    Round 1 posts, in key order (stream, then program order): R1, R2 (rank 0),
+    rank 1's receive, Q and T (rank 2).  Q finds R1 posted and takes it; T
+    completes rank 1's receive at the end of round 1.  Round 2 posts P, which
+    takes R2.  So R1 <- Q (source 2) and R2 <- P (source 1), although rank 1's
+    stream precedes rank 2's: the round (causal) order decides before the
+    stream id.  MPI allows the other assignment too, so this pins the reading,
+    not MPI alone: both assignments are among the enumerated legal outcomes."""
+    b = ProgramBuilder(3)
+    g = [b.stream(r) for r in range(3)]
+    c = b.comm(g)
+    pbuf = b.buffer(np.full(4, 0x11, np.uint8))
+    qbuf = b.buffer(np.full(4, 0x22, np.uint8))
+    tbuf = b.buffer(np.full(4, 0x33, np.uint8))
+    rbuf = b.buffer(8)
+    x = b.buffer(4)
+    st = b.status_slots(2)
+    h1 = b.irecv(g[0], c, rbuf, 0, 4, T_BYTE, ANY_SOURCE, 0)
+    h2 = b.irecv(g[0], c, rbuf, 4, 4, T_BYTE, ANY_SOURCE, 0)
+    b.waitall(g[0], [h1, h2], st)
+    b.recv(g[1], c, x, 0, 4, T_BYTE, 2, 5)
+    b.send(g[1], c, pbuf, 0, 4, T_BYTE, 0, 0)
+    b.send(g[2], c, qbuf, 0, 4, T_BYTE, 0, 0)
+    b.send(g[2], c, tbuf, 0, 4, T_BYTE, 1, 5)
+    p = b.build()
+    o = oracle.run(p)
+    assert not o.deadlock and o.error == 0
+    assert list(o.buffers[rbuf]) == [0x22] * 4 + [0x11] * 4
+    assert [int(v) for v in o.status["source"][st: st + 2]] == [2, 1]
+    legal = legal_outcomes(p)
+    outcomes = {ms for ms, dead in legal if not dead}
+    assert match_set(o.match, p) in outcomes and len(outcomes) == 2
+
+
+def test_round_model_wildcard_patterns_in_key_order():
+    """Hand-worked, one round: rank 0 posts R1 (source 1, tag 7), R2 (ANY_SOURCE,
+    ANY_TAG), R3 (ANY_SOURCE, tag 7), R4 (source 2, tag 3), then waits; rank 1
+    sends A and B (tag 7); rank 2 sends C (tag 3) and D (tag 7).  In key order
+    the receives are posted first; A takes the first receive accepting
+    (1, 7), R1; B takes R2 (R1 is gone, R2 accepts anything); C (2, 3) skips
+    R3 (tag 7) and takes R4; D takes R3."""
+    b = ProgramBuilder(3)
+    g = [b.stream(r) for r in range(3)]
+    c = b.comm(g)
+    src = {k: b.buffer(np.full(2, v, np.uint8)) for k, v in zip("ABCD", (0xA, 0xB, 0xC, 0xD))}
+    rbuf = b.buffer(8)
+    st = b.status_slots(4)
+    pats = [(1, 7), (ANY_SOURCE, ANY_TAG), (ANY_SOURCE, 7), (2, 3)]
+    hs = [b.irecv(g[0], c, rbuf, 2 * k, 2, T_BYTE, s_, t_) for k, (s_, t_) in enumerate(pats)]
+    b.waitall(g[0], hs, st)
+    b.send(g[1], c, src["A"], 0, 2, T_BYTE, 0, 7)
+    b.send(g[1], c, src["B"], 0, 2, T_BYTE, 0, 7)
+    b.send(g[2], c, src["C"], 0, 2, T_BYTE, 0, 3)
+    b.send(g[2], c, src["D"], 0, 2, T_BYTE, 0, 7)
+    p = b.build()
+    o = oracle.run(p)
+    assert not o.deadlock and o.error == 0
+    assert list(o.buffers[rbuf]) == [0xA] * 2 + [0xB] * 2 + [0xD] * 2 + [0xC] * 2
+    s = o.status[st: st + 4]
+    assert [int(v) for v in s["source"]] == [1, 1, 2, 2]
+    assert [int(v) for v in s["tag"]] == [7, 7, 7, 3]
+    legal = legal_outcomes(p)
+    assert (match_set(o.match, p), False) in legal
+
+
+def test_send_request_status_is_the_empty_status():
+    """A wait on a send request writes MPI's empty status (fixture with its
+    citation), as does every send entry of a waitall; a receive entry of the
+    same waitall carries the message's source, tag and bytes."""
+    empty = _golden_kv("empty_status.txt")
+    b = ProgramBuilder(2)
+    g0, g1 = b.stream(0), b.stream(1)
+    c = b.comm([g0, g1])
+    sbuf = b.buffer(np.arange(32, dtype=np.uint8))
+    rbuf = b.buffer(32)
+    st = b.status_slots(3)
+    h = b.isend(g0, c, sbuf, 0, 4, T_INT32, 1, 9)
+    b.wait(g0, h, st)
+    h2 = b.isend(g1, c, sbuf, 16, 2, T_INT32, 0, 4)
+    h3 = b.irecv(g1, c, rbuf, 0, 4, T_INT32, 0, 9)
+    b.waitall(g1, [h2, h3], st + 1)
+    b.recv(g0, c, rbuf, 16, 2, T_INT32, 1, 4)
+    p = b.build()
+    o = oracle.run(p)
+    assert not o.deadlock and o.error == 0
+    for k in (0, 1):
+        s = o.status[st + k]
+        assert (int(s["source"]), int(s["tag"]), int(s["error"]), int(s["bytes"])) == \
+            (empty["source"], empty["tag"], empty["error"], empty["bytes"])
+    r = o.status[st + 2]
+    assert (int(r["source"]), int(r["tag"]), int(r["error"]), int(r["bytes"])) == (0, 9, 0, 16)
+
+
 def test_deadlock_detected_on_cyclic_blocking_receives():
     b = ProgramBuilder(2)
     g0, g1 = b.stream(0), b.stream(1)

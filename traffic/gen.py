@@ -613,3 +613,137 @@ def n_to_one(nranks: int = 4, threads: int = 4, msgs: int = 8, max_bytes: int = 
             for q in range(nrecv)]
     b.waitall(poll, reqs, b.status_slots(nrecv))
     return b.build()
+
+
+# ----------------------------------------------------------------------------
+# Serving: open-loop requests of many host threads (reading A12)
+# ----------------------------------------------------------------------------
+SERVE_SEND, SERVE_RECV, SERVE_WAITALL, SERVE_ALLREDUCE = 0, 1, 2, 3
+SERVE_CALL_DTYPE = np.dtype([("kind", "<i4"), ("peer", "<i4"), ("tag", "<i4"), ("pad", "<i4"),
+                             ("item", "<i8"), ("bytes", "<i8"), ("off", "<i8"), ("capture", "<i8")])
+
+
+def serving_schedule(nthreads: int = 8, requests: int = 2000, p_allreduce: float = 0.3,
+                     min_log2: int = 6, max_log2: int = 14, zipf_s: float = 1.2,
+                     seed: int = SEED_BASE + 4, only_items: Optional[Sequence[int]] = None) -> dict:
+    """The serving workload as explicit per-thread call lists: every thread
+    makes requests/nthreads calls, a share p_allreduce of them fp32 SUM
+    allreduce participations (the same instance list on every thread), the
+    rest isends and irecvs of messages with a uniform source, a uniform other
+    destination, Zipf(zipf_s) power-of-two sizes over 2^min_log2..2^max_log2
+    and a tag counting the messages of their (source, destination) pair.  The
+    calls between two allreduce instances form an epoch: each thread issues
+    its sends and receives of the epoch in a seeded order, a waitall, then the
+    epoch's allreduce.  Items: messages 0..M-1, then instances M..M+nar-1.
+
+    Every receive and every thread's allreduce result gets its own slice of
+    one capture area, and every waitall its own status slots, so a run's
+    delivered bytes can be compared item by item.  `only_items` keeps just
+    those items' calls (an item run alone).  Returns calls (SERVE_CALL_DTYPE,
+    thread after thread), call_lo, regions (per thread fp32 N(0,1) data, as
+    bytes), capture_bytes, nstatuses, and the item bookkeeping."""
+    T = nthreads
+    per = max(1, requests // T)
+    nar = int(np.floor(p_allreduce * per + 0.5))
+    M = (per - nar) * T // 2
+    nb = max_log2 - min_log2 + 1
+    w = 1.0 / np.arange(1, nb + 1, dtype=np.float64) ** zipf_s
+    cdf = np.cumsum(w / w.sum())
+    cdf[-1] = 1.0
+
+    def zipf(rng, n):
+        k = np.searchsorted(cdf, rng.uniform(n), side="left")
+        return np.left_shift(1, min_log2 + np.minimum(k, nb - 1)).astype(np.int64)
+
+    maxb = 1 << max_log2
+    region_bytes = 2 * maxb
+    rm = Rng(seed, 70)
+    src = rm.integers(0, T - 1, M)
+    dst = rm.integers(0, T - 2, M)
+    dst = dst + (dst >= src)
+    epoch = rm.integers(0, nar, M)
+    mbytes = zipf(rm, M)
+    moff = (rm.integers(0, region_bytes, M) % (region_bytes - mbytes + 1)) & ~255
+    tags = np.zeros(M, np.int64)
+    pair = {}
+    for m in range(M):
+        k = (int(src[m]), int(dst[m]))
+        tags[m] = pair.get(k, 0)
+        pair[k] = tags[m] + 1
+    ra = Rng(seed, 71)
+    abytes = zipf(ra, nar) & ~3
+    aoff = (ra.integers(0, region_bytes, nar) % (region_bytes - abytes + 1)) & ~255
+    keep = None if only_items is None else set(int(i) for i in only_items)
+    # capture slices: messages in item order, then each instance's T results
+    cap_off = {}
+    pos = 0
+    for m in range(M):
+        cap_off[m] = pos
+        pos += (int(mbytes[m]) + 255) // 256 * 256
+    for e in range(nar):
+        for t in range(T):
+            cap_off[(M + e, t)] = pos
+            pos += (int(abytes[e]) + 255) // 256 * 256
+    capture_bytes = max(pos, 256)
+    ep = [[[] for _ in range(nar + 1)] for _ in range(T)]
+    for m in range(M):
+        if keep is not None and m not in keep:
+            continue
+        s_, d_, e_ = int(src[m]), int(dst[m]), int(epoch[m])
+        ep[s_][e_].append((SERVE_SEND, d_, int(tags[m]), m, int(mbytes[m]), int(moff[m]), -1))
+        ep[d_][e_].append((SERVE_RECV, s_, int(tags[m]), m, int(mbytes[m]), 0, cap_off[m]))
+    rows, lo, nstat = [], [0], 0
+    for t in range(T):
+        rs = Rng(seed, 72, t)
+        for e in range(nar + 1):
+            v = ep[t][e]
+            if v:
+                order = rs.permutation(len(v))
+                v = [v[int(i)] for i in order]
+                rows.extend(v)
+                n_req = len(v)
+                rows.append((SERVE_WAITALL, 0, 0, 0, 0, 0, nstat))
+                nstat += n_req
+            if e < nar and (keep is None or M + e in keep):
+                rows.append((SERVE_ALLREDUCE, 0, 0, M + e, int(abytes[e]), int(aoff[e]),
+                             cap_off[(M + e, t)]))
+        lo.append(len(rows))
+    calls = np.zeros(len(rows), SERVE_CALL_DTYPE)
+    for i, (k, peer, tag, item, b, off, cap) in enumerate(rows):
+        calls[i] = (k, peer, tag, 0, item, b, off, cap)
+    regions = [Rng(seed, 73, t).normal(region_bytes // 4).astype(np.float32).view(np.uint8)
+               for t in range(T)]
+    return dict(calls=calls, call_lo=np.array(lo, np.int64), regions=regions,
+                region_bytes=region_bytes, capture_bytes=capture_bytes, nstatuses=max(nstat, 1),
+                nthreads=T, messages=M, instances=nar, cap_off=cap_off, mbytes=mbytes, abytes=abytes)
+
+
+def serving_program(sched: dict) -> Program:
+    """The same calls as a closed program for the oracle: thread t is rank t
+    with one stream; receives land in one capture buffer at their capture
+    offsets, allreduce results too, waitall statuses in their slots."""
+    T = sched["nthreads"]
+    b = ProgramBuilder(T, "serving")
+    gs = [b.stream(t) for t in range(T)]
+    c = b.comm(gs)
+    regs = [b.buffer(r) for r in sched["regions"]]
+    cap = b.buffer(int(sched["capture_bytes"]))
+    st0 = b.status_slots(int(sched["nstatuses"]))
+    calls, lo = sched["calls"], sched["call_lo"]
+    for t in range(T):
+        reqs = []
+        for x in calls[int(lo[t]): int(lo[t + 1])]:
+            k = int(x["kind"])
+            if k == SERVE_SEND:
+                reqs.append(b.isend(gs[t], c, regs[t], int(x["off"]), int(x["bytes"]), T_BYTE,
+                                    int(x["peer"]), int(x["tag"])))
+            elif k == SERVE_RECV:
+                reqs.append(b.irecv(gs[t], c, cap, int(x["capture"]), int(x["bytes"]), T_BYTE,
+                                    int(x["peer"]), int(x["tag"])))
+            elif k == SERVE_WAITALL:
+                b.waitall(gs[t], reqs, st0 + int(x["capture"]))
+                reqs = []
+            else:
+                b.allreduce(gs[t], c, regs[t], int(x["off"]), cap, int(x["capture"]),
+                            int(x["bytes"]) // 4, T_FLOAT, MODE_FIXED)
+    return b.build()

@@ -299,8 +299,10 @@ class BatchRunner:
     """A closed program in which every stream's only blocking operation is its
     last one (a waitall over all of the stream's requests), run repeatedly
     through mpx_enqueue_batch: one call enqueues every stream's non-blocking
-    operations, then every stream's waitall.  Holds the world, streams,
-    buffers and the prebuilt operation array between steps."""
+    operations, then every stream's waitall.  A stream may begin with axpy
+    compute ops (Listing 4's kernel): they are launched on the stream before
+    its communication, and a recorded step is ordered after them.  Holds the
+    world, streams, buffers and the prebuilt operation array between steps."""
 
     def __init__(self, prog: Program, mode: str = "persistent", exclusive: bool = True,
                  cfg_over: Optional[dict] = None, timeout_s: float = 60.0,
@@ -347,6 +349,10 @@ class BatchRunner:
             self.bar = torch.zeros(prog.nstreams * 4, dtype=torch.int32, device=dev)
             torch.cuda.synchronize()
         self.ops = self._build_ops()
+        # an exclusive stream has no doorbell: the engine takes its operations
+        # as reached at once, which a compute op ahead of them would break
+        assert not (self.axpys and exclusive and not self.graph), \
+            "leading compute ops need doorbells (non-exclusive streams) or a recorded step"
         self.messages = int((np.isin(prog.ops["kind"], [SEND, ISEND])).sum())
         self.step_handle = mpx.mpx_step_create(self.world, self.ops) if self.graph else None
 
@@ -368,8 +374,15 @@ class BatchRunner:
         kind = ops["kind"].astype(np.int64)
         lo = prog.stream_op_lo
         nb_idx, wait_idx = [], []
+        self.axpys = []  # (stream, n, alpha, x pointer, y pointer): leading compute ops
         for g in range(prog.nstreams):
             a, b = int(lo[g]), int(lo[g + 1])
+            while a < b and kind[a] == AXPY:
+                o = ops[a]
+                self.axpys.append((g, int(o["count"]), float(o["alpha"]),
+                                   int(ptr[int(o["buf"])]) + int(o["off"]),
+                                   int(ptr[int(o["buf2"])]) + int(o["off2"])))
+                a += 1
             if b == a:
                 continue
             assert kind[b - 1] == WAITALL and np.isin(kind[a:b - 1], [ISEND, IRECV]).all(), \
@@ -412,9 +425,21 @@ class BatchRunner:
             out = np.concatenate([out, bar])
         return out
 
+    def _launch_axpys(self):
+        """The streams' leading compute ops; in graph mode the engine stream
+        (which replays the recorded step) waits for them."""
+        if not self.axpys:
+            return
+        for g, n, alpha, xp, yp in self.axpys:
+            self.mpx.mpx_saxpy_enqueue(n, alpha, xp, yp, self.cstreams[g].cuda_stream)
+        if self.graph:
+            for g in sorted({a[0] for a in self.axpys}):
+                self.engine_stream.wait_stream(self.cstreams[g])
+
     def enqueue(self):
         """Enqueue one step (returns once every operation is enqueued)."""
         mpx = self.mpx
+        self._launch_axpys()
         if self.graph:
             mpx.mpx_step_launch(self.step_handle, self.engine_stream.cuda_stream)
             return
@@ -521,3 +546,68 @@ class BatchRunner:
             mpx.mpx_cuda_stream_destroy(h)
         for t in self.tmap[5:]:
             mpx.mpx_type_free(int(t))
+
+
+def run_recorded_allreduce(prog: Program, timeout_s: float = 60.0) -> GpuOutcome:
+    """A program whose streams hold only blocking allreduces in the comm's
+    reduce mode, run as one recorded step (drain-mode world, exclusive
+    streams): one CUDA graph of the descriptor publication kernel and one
+    engine pass, launched on the engine stream.  No user stream waits on
+    anything, so a kernel-serialising profiler can replay every launch."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    assert np.all(prog.ops["kind"] == ALLREDUCE), "allreduce-only programs"
+    dev = torch.device("cuda")
+    cfg = make_config(prog, mpx.ENGINE_DRAIN)
+    dbufs = [torch.from_numpy(np.ascontiguousarray(b)).to(dev) if b.size else
+             torch.empty(16, dtype=torch.uint8, device=dev) for b in prog.buf_init]
+    torch.cuda.current_stream(dev).synchronize()
+    ptr = [b.data_ptr() for b in dbufs]
+    world = mpx.mpx_world_create(prog.nranks, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(prog.nstreams + 1)]
+    ms = [mpx.mpx_stream_create(world, int(prog.stream_rank[g]), raw[g], mpx.STREAM_EXCLUSIVE)
+          for g in range(prog.nstreams)]
+    comms = [mpx.mpx_stream_comm_create(world, [ms[int(g)] for g in prog.comm_stream[c]])
+             for c in range(prog.ncomms)]
+    rank_in = {(c, int(g)): r for c in range(prog.ncomms) for r, g in enumerate(prog.comm_stream[c])}
+    ops = np.zeros(len(prog.ops), mpx.op_dtype())
+    for j, o in enumerate(prog.ops):
+        c, g = int(o["comm"]), int(o["stream"])
+        ops[j]["kind"] = mpx.OP_ALLREDUCE
+        ops[j]["datatype"] = int(o["type"])
+        ops[j]["count"] = int(o["count"])
+        ops[j]["op"] = mpx.SUM
+        ops[j]["buf"] = mpx.IN_PLACE if int(o["buf"]) == IN_PLACE else ptr[int(o["buf"])] + int(o["off"])
+        ops[j]["recvbuf"] = ptr[int(o["buf2"])] + int(o["off2"])
+        ops[j]["comm"] = comms[c][rank_in[(c, g)]]
+    t0 = time.perf_counter()
+    step = mpx.mpx_step_create(world, ops)
+    es = torch.cuda.ExternalStream(raw[-1], device=dev)
+    mpx.mpx_step_launch(step, raw[-1])
+    finished = False
+    while time.perf_counter() - t0 < timeout_s:
+        if es.query():
+            finished = True
+            break
+        time.sleep(1e-4)
+    if not finished:
+        mpx.mpx_world_abort(world)
+        t1 = time.perf_counter()
+        while time.perf_counter() - t1 < 10 and not es.query():
+            time.sleep(1e-3)
+    out = [b.cpu().numpy()[: prog.buf_init[i].size].copy() for i, b in enumerate(dbufs)] if finished else []
+    werr = mpx.mpx_world_get_error(world)
+    serr = [mpx.mpx_step_get_error(step)]
+    counters = mpx.mpx_world_get_counters(world)
+    mpx.mpx_step_free(step)
+    if finished:
+        for cl in comms:
+            for h in cl:
+                mpx.mpx_comm_free(h)
+        for s in ms:
+            mpx.mpx_stream_free(s)
+        mpx.mpx_world_free(world)
+        for h in raw:
+            mpx.mpx_cuda_stream_destroy(h)
+    return GpuOutcome(buffers=out, status=np.zeros(0, STATUS_DTYPE), stream_errors=serr, world_error=werr,
+                      counters=counters, finished=finished, seconds=time.perf_counter() - t0)
