@@ -627,6 +627,42 @@ int mpx_iallgather_enqueue(const void* sendbuf, void* recvbuf, int64_t count,
                            mpx_datatype_t datatype, mpx_comm_t comm, mpx_request_t* request);
 int mpx_ibarrier_enqueue(mpx_comm_t comm, mpx_request_t* request);
 
+/* Persistent collectives (§3.4 last paragraph: collectives, nonblocking and
+ * persistent ones included, take the enqueue form; MPI-4's
+ * MPI_Allreduce_init, MPI_Bcast_init, MPI_Reduce_init, MPI_Allgather_init,
+ * MPI_Barrier_init with MPI_Start / MPI_Startall and MPI_Request_free).
+ * mpx_*_init records the call's arguments (those of the nonblocking call,
+ * checked as far as they can be without enqueueing) in a persistent request
+ * and enqueues nothing; *request receives a handle that is never
+ * MPX_REQUEST_NULL and never equal to an operation's request.
+ * mpx_start_enqueue starts one instance: exactly the nonblocking call
+ * (mpx_i*_enqueue) with the recorded arguments, enqueued on the
+ * communicator's stream at this point, so the buffers are read and written
+ * when the stream reaches the start.  mpx_wait_enqueue / mpx_waitall_enqueue
+ * on the handle complete the started instance (statuses as for the
+ * nonblocking call) and leave the handle valid and inactive for the next
+ * start; a wait on an inactive handle completes at once with the empty
+ * status.  Starting an active handle gives MPX_ERR_STATE; mpx_startall_enqueue
+ * starts n handles in array order and stops at the first error.
+ * mpx_request_free frees an inactive persistent request and sets *request to
+ * MPX_REQUEST_NULL (MPX_ERR_PENDING while started and not waited for;
+ * MPX_ERR_REQUEST for any other request, which completes by a wait).  A
+ * persistent request is used by one host thread at a time, like its stream.
+ * Errors: those of the nonblocking calls; MPX_ERR_UNSUPPORTED on the plain
+ * path. */
+int mpx_allreduce_init(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t datatype,
+                       int op, mpx_comm_t comm, mpx_request_t* request);
+int mpx_bcast_init(void* buf, int64_t count, mpx_datatype_t datatype, int root, mpx_comm_t comm,
+                   mpx_request_t* request);
+int mpx_reduce_init(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t datatype,
+                    int op, int root, mpx_comm_t comm, mpx_request_t* request);
+int mpx_allgather_init(const void* sendbuf, void* recvbuf, int64_t count, mpx_datatype_t datatype,
+                       mpx_comm_t comm, mpx_request_t* request);
+int mpx_barrier_init(mpx_comm_t comm, mpx_request_t* request);
+int mpx_start_enqueue(mpx_request_t* request);
+int mpx_startall_enqueue(int n, mpx_request_t requests[]);
+int mpx_request_free(mpx_request_t* request);
+
 /* Host-thread message rate (§5.3, Fig. 3, on host cores): `threads` pairs of
  * host threads, sender t sending `messages` 8-byte messages to receiver t
  * over a channel of its own (a per-thread communicator), `window` sends or

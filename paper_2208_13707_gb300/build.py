@@ -15,7 +15,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["mpx_engine.cu", "mpx_host.cpp", "mpx_plain.cu", "mpx_saxpy.cu", "mpx_step.cu",
            "mpx_serve.cpp", "mpx_serve_kernels.cu", "mpx_info.cpp",
-           "mpx_hostrate.cpp"]
+           "mpx_hostrate.cpp", "mpx_persist.cpp"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-Xcompiler", "-Wall"]
 

@@ -40,13 +40,13 @@ constexpr int kErrTimeout = 16;
 constexpr int kMaxRoundsPerTick = 64;
 constexpr int kMaxStagePerTick = 128;
 constexpr int kMaxDeferred = 512;  // deliveries a scheduling phase sizes together
+constexpr int kSmallPosts = 256;   // rounds up to this many posts match from shared memory
 constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipeline
 constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
 constexpr uint32_t kTmaChunk = 16384;
 constexpr int kMaxStreamsPerCta = 1024;
 constexpr int kSmemStreams = 128;  // worlds up to this many streams keep per-stream state in shared memory
 constexpr int kMaxCtaThreads = 512;  // engine block size bound (launch bounds)
-constexpr int kSortMinPosts = 128;   // rounds with more posts match from domain-sorted lists
 constexpr uint64_t kCqDone = ~0ull;  // completion-queue entry already processed
 
 // ------------------------------------------------------------------------
@@ -231,6 +231,8 @@ struct CtaShared {
   uint64_t dlv_s[kMaxDeferred], dlv_r[kMaxDeferred];
   int32_t ndlv;
   unsigned long long dlv_bytes;
+  // control: a small round's posts in key order (PostRec, 32 bytes each)
+  alignas(16) uint64_t prec[kSmallPosts * 4];
   int32_t cnt[kMaxStreamsPerCta];
   int32_t arrivals;       // control: allreduce arrivals this round
   int32_t limits_reached; // control: a drain pass has ingested up to all its limits
@@ -255,6 +257,13 @@ struct CtaShared {
   // control: streams with an event since their last completion scan (new
   // operations, a moved cursor, a finished task, a doorbell change)
   uint8_t sdirty[kMaxStreamsPerCta];
+  // control: streams whose host-visible words (StreamCtl done, done_t,
+  // retired, wl_retired) changed this tick; written at the end of the tick,
+  // where no fence of this tick waits for those host-memory stores
+  uint8_t smirror[kMaxStreamsPerCta];
+  // control: WorldCtl counters accumulated here, added to host memory every
+  // 64 ticks and at exit (a host-memory atomic costs a chip-to-chip round trip)
+  unsigned long long ctr[8];
   SState ss_cache[kSmemStreams];
   Task task;              // claimed task (copy)
 };
@@ -910,6 +919,7 @@ __device__ bool claim_tile_own(const EngineParams& P, CtaShared& sm) {
 
 __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
   const Task& T = sm.task;
+  const uint64_t t_tile0 = P.trace && threadIdx.x == 0 ? now_ns() : 0;
   // a task record that does not describe the claimed tile is reported and skipped
   const bool sane = sm.claim_tile < T.ntiles && T.tile > 0 && T.bytes > 0 &&
                     (int64_t)sm.claim_tile * T.tile < T.bytes;
@@ -922,6 +932,19 @@ __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (P.trace) {
+      const uint64_t k = atomicAdd((unsigned long long*)P.trace_pos, 1ull);
+      if ((int64_t)k < P.trace_cap) {
+        const int64_t p0 = (int64_t)sm.claim_tile * T.tile;
+        const int64_t nb = (p0 + T.tile < T.bytes ? T.tile : T.bytes - p0);
+        uint64_t* rec = P.trace + 4 * k;
+        rec[0] = t_tile0;
+        rec[1] = now_ns();
+        rec[2] = ((uint64_t)sm.claim_task << 32) | sm.claim_tile;
+        rec[3] = ((uint64_t)nb << 8) | (T.type == T_REDUCE ? 0x40u : 0u) |
+                 (T.chunk == kContig ? 0x80u : 0u) | (T.unit & 0x3Fu);
+      }
+    }
     __threadfence();
     const uint32_t done = atomicAdd(&P.tasks[(uint64_t)sm.claim_task].tiles_done, 1u) + 1u;
     if (done == T.ntiles) {  // the task's last tile: hand the task to the control CTA
@@ -1071,8 +1094,19 @@ struct Ctl {
     int n = 0;
     bool arrived = false;
     uint64_t cur = S.cursor;
-    uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+    PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
     const int ndomains_per_comm = P.nranks;
+    // a post carries what matching reads: key or source pattern, tag, bytes
+    auto post = [&](const DOp* o, uint64_t seq, uint32_t dom, bool send) {
+      PostRec r;
+      r.ref = make_ref(g, seq);
+      r.key = send ? o->d.n32 : o->d.peer;
+      r.tag = o->d.tag;
+      r.bytes = o->bytes;
+      r.dom = dom;
+      r.send = send ? 1u : 0u;
+      posts[n++] = r;
+    };
     uint64_t pf = cur;  // operations below pf have been prefetched
     while (cur <= S.ingested) {
       if (cur >= pf) pf = prefetch_ops(g, cur, S.ingested);
@@ -1081,23 +1115,20 @@ struct Ctl {
       if (is_send(k)) {
         o->lstate = 2;  // eager: complete at post
         o->lround = (int32_t)round;
-        const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.peer;
-        posts[n++] = (dom << 40) | cur;
+        post(o, cur, (uint32_t)((uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.peer), true);
         ++cur;
         continue;
       }
       if (k == K_IRECV) {
         o->lstate = 1;
-        const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank;
-        posts[n++] = (dom << 40) | cur;
+        post(o, cur, (uint32_t)((uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank), false);
         ++cur;
         continue;
       }
       if (k == K_RECV) {
         if (o->lstate == 0) {
           o->lstate = 1;
-          const uint64_t dom = (uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank;
-          posts[n++] = (dom << 40) | cur;
+          post(o, cur, (uint32_t)((uint64_t)o->d.comm * ndomains_per_comm + (uint64_t)o->d.rank), false);
           break;
         }
         if (done_before(o)) {
@@ -1167,69 +1198,86 @@ struct Ctl {
   }
 
   // --- 2b. matching (warp per domain) ---
-  __device__ int64_t q_find(const QEntry* q, const QHead& h, uint32_t qmask, bool is_send_post,
-                            int32_t src, int32_t tag) {
+  // Take the first entry of queue q (in queue order) that accepts, or is
+  // accepted by, a post with key/pattern `src` and tag `tag`: a send post
+  // looks for a posted receive accepting it, a receive post for an
+  // unexpected send it accepts.  The entry is tombstoned, the head moves
+  // over leading tombstones, and the entry is returned in `found` (every
+  // lane).  Warp-cooperative: 32 entries per load and ballot.
+  __device__ bool q_take(QEntry* q, QHead& h, uint32_t qmask, bool is_send_post, int32_t src,
+                         int32_t tag, QEntry& found) {
     const int lane = threadIdx.x & 31;
     for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32) {
       const uint32_t idx = base + (uint32_t)lane;
+      const bool inr = (int32_t)(h.tail - idx) > 0;
+      QEntry e = {0, 0, 0, 0};
+      if (inr) e = q[idx & qmask];
+      const bool live = inr && e.ref != 0;
       bool hit = false;
-      if ((int32_t)(h.tail - idx) > 0) {
-        const QEntry e = q[idx & qmask];
-        if (e.ref != 0) {
-          if (is_send_post)  // looking for a posted receive accepting (src, tag)
-            hit = src_accepts(e.src, src) && (e.tag == kAnyTag || e.tag == tag);
-          else  // looking for an unexpected send the receive (src, tag) accepts
-            hit = src_accepts(src, e.src) && (tag == kAnyTag || tag == e.tag);
-        }
+      if (live) {
+        if (is_send_post)  // a posted receive accepting (src, tag)
+          hit = src_accepts(e.src, src) && (e.tag == kAnyTag || e.tag == tag);
+        else  // an unexpected send the receive (src, tag) accepts
+          hit = src_accepts(src, e.src) && (tag == kAnyTag || tag == e.tag);
       }
       const unsigned b = __ballot_sync(FULL, hit);
-      if (b) return (int64_t)(base + (uint32_t)(__ffs(b) - 1));
-    }
-    return -1;
-  }
-
-  __device__ void q_remove(QEntry* q, QHead& h, uint32_t qmask, uint32_t idx) {
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) q[idx & qmask].ref = 0;
-    __syncwarp();
-    if (idx != h.head) return;
-    // advance head over tombstones
-    uint32_t head = h.head;
-    while ((int32_t)(h.tail - head) > 0) {
-      const uint32_t i = head + (uint32_t)lane;
-      const bool live = (int32_t)(h.tail - i) > 0 && q[i & qmask].ref != 0;
-      const bool inrange = (int32_t)(h.tail - i) > 0;
-      const unsigned b = __ballot_sync(FULL, live);
-      const unsigned r = __ballot_sync(FULL, inrange);
-      if (b) {
-        head += (uint32_t)(__ffs(b) - 1);
-        break;
+      if (!b) continue;
+      const int l = __ffs(b) - 1;
+      found.ref = __shfl_sync(FULL, e.ref, l);
+      found.src = __shfl_sync(FULL, e.src, l);
+      found.tag = __shfl_sync(FULL, e.tag, l);
+      found.bytes = __shfl_sync(FULL, e.bytes, l);
+      const uint32_t hidx = base + (uint32_t)l;
+      if (lane == 0) q[hidx & qmask].ref = 0;
+      if (hidx == h.head) {
+        // the next live entry of this chunk becomes the head, else scan on
+        const unsigned after = l == 31 ? 0u : (__ballot_sync(FULL, live) & (~0u << (l + 1)));
+        if (after) {
+          h.head = base + (uint32_t)(__ffs(after) - 1);
+        } else {
+          uint32_t head = base + 32;
+          if ((int32_t)(h.tail - head) <= 0) head = h.tail;
+          while ((int32_t)(h.tail - head) > 0) {
+            const uint32_t i = head + (uint32_t)lane;
+            const bool in2 = (int32_t)(h.tail - i) > 0;
+            const bool lv = in2 && q[i & qmask].ref != 0;
+            const unsigned bl = __ballot_sync(FULL, lv);
+            if (bl) {
+              head += (uint32_t)(__ffs(bl) - 1);
+              break;
+            }
+            head += (uint32_t)__popc(__ballot_sync(FULL, in2));
+          }
+          h.head = head;
+        }
       }
-      head += (uint32_t)__popc(r);
+      __syncwarp();
+      return true;
     }
-    h.head = head;  // every lane keeps the same copy of the queue bounds
-    __syncwarp();
+    return false;
   }
 
   __device__ bool q_push(QEntry* q, QHead& h, uint32_t qmask, QEntry e) {
     if ((h.tail - h.head) > qmask) return false;
     if ((threadIdx.x & 31) == 0) q[h.tail & qmask] = e;
-    h.tail = h.tail + 1;  // all lanes: loop bounds in q_find must stay warp-uniform
+    h.tail = h.tail + 1;  // all lanes: loop bounds in q_take must stay warp-uniform
     __syncwarp();
     return true;
   }
 
-  __device__ void pair(uint64_t sref, uint64_t rref) {
+  // Record a match (lane 0): the receive learns the sender's key, tag and the
+  // delivered bytes (truncated to its capacity); both learn their partner.
+  // Only stores: everything it needs came with the post and the queue entry.
+  __device__ void pair(uint64_t sref, int32_t skey, int32_t stag, int64_t sent, uint64_t rref,
+                       int64_t cap) {
     if ((threadIdx.x & 31) != 0) return;
     DOp* s = op_ref(P, sref);
     DOp* r = op_ref(P, rref);
-    const int64_t sent = s->bytes;
-    const int64_t cap = op_bytes(r->d);
     r->partner = sref;
     r->bytes = sent < cap ? sent : cap;
     r->err = sent > cap ? kErrTruncate : 0;
-    r->msrc = s->d.n32;  // the sender's key: rank and local index
-    r->mtag = s->d.tag;
+    r->msrc = skey;  // the sender's key: rank and local index
+    r->mtag = stag;
     r->lstate = 2;
     r->lround = (int32_t)round;
     s->partner = rref;
@@ -1237,66 +1285,49 @@ struct Ctl {
     atomicOr(&s->pflags, PF_MATCHED);
   }
 
-  // One post of domain d, in key order (warp-cooperative).
-  __device__ void match_post(int g, uint64_t seq, QEntry* pq, QEntry* uq, QHead& ph, QHead& uh,
-                             uint32_t qmask) {
-          const int lane = threadIdx.x & 31;
-          const DOp* o = op_at(P, g, seq);
-          const uint32_t kind = kw_kind(o->d.kw);
-          const uint64_t ref = make_ref(g, seq);
-          if (is_send(kind)) {
-            const int32_t src = o->d.n32, tag = o->d.tag;  // sender key
-            const int64_t hit = q_find(pq, ph, qmask, true, src, tag);
-            if (hit >= 0) {
-              const uint64_t rref = pq[(uint32_t)hit & qmask].ref;
-              q_remove(pq, ph, qmask, (uint32_t)hit);
-              pair(ref, rref);
-            } else if (!q_push(uq, uh, qmask, QEntry{ref, src, tag})) {
-              if (lane == 0) set_error(P, g, kErrNoMem);
-            }
-          } else {
-            const int32_t src = o->d.peer, tag = o->d.tag;
-            const int64_t hit = q_find(uq, uh, qmask, false, src, tag);
-            if (hit >= 0) {
-              const uint64_t sref = uq[(uint32_t)hit & qmask].ref;
-              q_remove(uq, uh, qmask, (uint32_t)hit);
-              pair(sref, ref);
-            } else if (!q_push(pq, ph, qmask, QEntry{ref, src, tag})) {
-              if (lane == 0) set_error(P, g, kErrNoMem);
-            }
-          }
-          __syncwarp();
+  // One post, in key order (warp-cooperative).
+  __device__ void match_rec(const PostRec& p, QEntry* pq, QEntry* uq, QHead& ph, QHead& uh,
+                            uint32_t qmask) {
+    const int lane = threadIdx.x & 31;
+    QEntry e;
+    if (p.send) {
+      if (q_take(pq, ph, qmask, true, p.key, p.tag, e)) {
+        pair(p.ref, p.key, p.tag, p.bytes, e.ref, e.bytes);
+      } else if (!q_push(uq, uh, qmask, QEntry{p.ref, p.key, p.tag, p.bytes})) {
+        if (lane == 0) set_error(P, ref_stream(p.ref), kErrNoMem);
+      }
+    } else {
+      if (q_take(uq, uh, qmask, false, p.key, p.tag, e)) {
+        pair(e.ref, e.src, e.tag, e.bytes, p.ref, p.bytes);
+      } else if (!q_push(pq, ph, qmask, QEntry{p.ref, p.key, p.tag, p.bytes})) {
+        if (lane == 0) set_error(P, ref_stream(p.ref), kErrNoMem);
+      }
+    }
+    __syncwarp();
   }
 
-  // Domain d's posts found by scanning every stream's post list (small rounds).
-  __device__ void match_domain(uint32_t d) {
+  // Small rounds: every post of the round was gathered into shared memory in
+  // key order (stream, then program order); domain d's warp takes its posts
+  // from there.
+  __device__ void match_domain_small(uint32_t d, const PostRec* recs, int total) {
     const int lane = threadIdx.x & 31;
     const uint32_t qmask = (1u << P.qcap_log2) - 1;
     QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
     QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
     QHead ph = P.pqh[d], uh = P.uqh[d];
-    for (int g = 0; g < P.max_streams; ++g) {
-      const int n = sm.cnt[g];
-      if (n == 0) continue;
-      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
-      for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        uint64_t pv = 0;
-        bool mine = false;
-        if (i < n) {
-          pv = posts[i];
-          mine = (uint32_t)(pv >> 40) == d;
-        }
-        unsigned b = __ballot_sync(FULL, mine);
-        while (b) {
-          const int src_lane = __ffs(b) - 1;
-          b &= b - 1;
-          const uint64_t seq = __shfl_sync(FULL, pv, src_lane) & ((1ull << 40) - 1);
-          match_post(g, seq, pq, uq, ph, uh, qmask);
-        }
+    bool any = false;
+    for (int base = 0; base < total; base += 32) {
+      const int i = base + lane;
+      const bool mine = i < total && recs[i].dom == d;
+      unsigned b = __ballot_sync(FULL, mine);
+      while (b) {
+        const int l = __ffs(b) - 1;
+        b &= b - 1;
+        match_rec(recs[base + l], pq, uq, ph, uh, qmask);
+        any = true;
       }
     }
-    if (lane == 0) {
+    if (any && lane == 0) {
       P.pqh[d] = ph;
       P.uqh[d] = uh;
     }
@@ -1312,19 +1343,86 @@ struct Ctl {
     QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
     QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
     QHead ph = P.pqh[d], uh = P.uqh[d];
-    const uint64_t* list = P.dlist + P.dbase[d];
+    const PostRec* list = P.dlist + P.dbase[d];
     for (int base = 0; base < n; base += 32) {
-      const uint64_t pv = base + lane < n ? list[base + lane] : 0;
+      PostRec mine = {0, 0, 0, 0, 0, 0};
+      if (base + lane < n) mine = list[base + lane];
       const int m = (n - base) < 32 ? (n - base) : 32;
       for (int k = 0; k < m; ++k) {
-        const uint64_t v = __shfl_sync(FULL, pv, k);
-        match_post(ref_stream(v), ref_seq(v), pq, uq, ph, uh, qmask);
+        PostRec p;
+        p.ref = __shfl_sync(FULL, mine.ref, k);
+        p.key = __shfl_sync(FULL, mine.key, k);
+        p.tag = __shfl_sync(FULL, mine.tag, k);
+        p.bytes = __shfl_sync(FULL, mine.bytes, k);
+        p.dom = d;
+        p.send = __shfl_sync(FULL, mine.send, k);
+        match_rec(p, pq, uq, ph, uh, qmask);
       }
     }
     if (lane == 0) {
       P.pqh[d] = ph;
       P.uqh[d] = uh;
     }
+  }
+
+  // Domain d's posts found by scanning every stream's post list in global
+  // memory (large rounds of worlds too large for the sort's scratch).
+  __device__ void match_domain_scan(uint32_t d) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t qmask = (1u << P.qcap_log2) - 1;
+    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
+    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
+    QHead ph = P.pqh[d], uh = P.uqh[d];
+    for (int g = 0; g < P.max_streams; ++g) {
+      const int n = sm.cnt[g];
+      if (n == 0) continue;
+      const PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool mine = i < n && posts[i].dom == d;
+        unsigned b = __ballot_sync(FULL, mine);
+        while (b) {
+          const int l = __ffs(b) - 1;
+          b &= b - 1;
+          match_rec(posts[base + l], pq, uq, ph, uh, qmask);
+        }
+      }
+    }
+    if (lane == 0) {
+      P.pqh[d] = ph;
+      P.uqh[d] = uh;
+    }
+  }
+
+  // Small rounds: copy every stream's posts into shared memory, stream after
+  // stream (key order).  Returns the number of posts.
+  __device__ int gather_posts(PostRec* recs) {
+    __shared__ int32_t off[kMaxStreamsPerCta];
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t < 32) {  // exclusive scan of the per-stream post counts by warp 0
+      const int per = (P.max_streams + 31) / 32;
+      const int g0 = t * per;
+      int32_t sum = 0;
+      for (int k = 0; k < per && g0 + k < P.max_streams; ++k) sum += sm.cnt[g0 + k];
+      int32_t x = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, x, o);
+        if (t >= o) x += y;
+      }
+      int32_t b = x - sum;
+      for (int k = 0; k < per && g0 + k < P.max_streams; ++k) {
+        off[g0 + k] = b;
+        b += sm.cnt[g0 + k];
+      }
+    }
+    __syncthreads();
+    for (int g = t; g < P.max_streams; g += nt) {
+      const int n = sm.cnt[g];
+      const PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      for (int i = 0; i < n; ++i) recs[off[g] + i] = posts[i];
+    }
+    __syncthreads();
+    return sm.nposts_round;  // the round's posts, counted as they were made
   }
 
   // Stable counting sort of this round's posts by domain.
@@ -1335,9 +1433,9 @@ struct Ctl {
     // posts per (stream, domain)
     for (int g = t; g < P.max_streams; g += nt) {
       const int n = sm.cnt[g];
-      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      const PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
       int32_t* row = P.cnt2 + (size_t)g * nd;
-      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] += 1;
+      for (int i = 0; i < n; ++i) row[posts[i].dom] += 1;
     }
     __syncthreads();
     // each thread owns a contiguous chunk of domains: per domain, the
@@ -1388,13 +1486,12 @@ struct Ctl {
     // scatter each stream's posts in program order
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
       const int n = sm.cnt[g];
-      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      const PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
       int32_t* row = P.cnt2 + (size_t)g * nd;
       for (int i = 0; i < n; ++i) {
-        const uint64_t pv = posts[i];
-        const uint32_t d = (uint32_t)(pv >> 40);
-        const int32_t k = row[d]++;
-        P.dlist[P.dbase[d] + k] = make_ref(g, pv & ((1ull << 40) - 1));
+        const PostRec pv = posts[i];
+        const int32_t k = row[pv.dom]++;
+        P.dlist[P.dbase[pv.dom] + k] = pv;
       }
     }
   }
@@ -1404,9 +1501,9 @@ struct Ctl {
     const int nd = P.max_comms * P.nranks;
     for (int g = threadIdx.x; g < P.max_streams; g += blockDim.x) {
       const int n = sm.cnt[g];
-      const uint64_t* posts = P.postbuf + ((size_t)g << P.slots_log2);
+      const PostRec* posts = P.postbuf + ((size_t)g << P.slots_log2);
       int32_t* row = P.cnt2 + (size_t)g * nd;
-      for (int i = 0; i < n; ++i) row[(uint32_t)(posts[i] >> 40)] = 0;
+      for (int i = 0; i < n; ++i) row[posts[i].dom] = 0;
     }
   }
 
@@ -1832,8 +1929,7 @@ struct Ctl {
       // stream's cuStreamWaitValue64 polls
       asm volatile("fence.acq_rel.gpu;" ::: "memory");
       st_rlx_sys(&P.done[g], newdone);
-      st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);  // engine clock of this advance
-      st_rlx_sys(&P.sctl[g].done, newdone);
+      sm.smirror[g] = 1;  // done and its clock reach host memory at the end of the tick
       prog = true;
     }
     // how far the stream has executed (non-exclusive: the tick's doorbell pass)
@@ -1860,8 +1956,7 @@ struct Ctl {
     if (rt != S.retire) {
       S.retire = rt;
       S.wl_retired = wlr;
-      st_rlx_sys(&P.sctl[g].wl_retired, wlr);
-      st_rlx_sys(&P.sctl[g].retired, rt);  // descriptors were consumed at ingest, long before
+      sm.smirror[g] = 1;  // descriptors were consumed at ingest, long before
       prog = true;
     }
     return prog;
@@ -1909,8 +2004,7 @@ struct Ctl {
         // before the word the stream's cuStreamWaitValue64 polls
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         st_rlx_sys(&P.done[g], newdone);
-        st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);
-        st_rlx_sys(&P.sctl[g].done, newdone);
+        sm.smirror[g] = 1;
       }
       if (S.flags & SF_EXCLUSIVE) S.reached = pc <= ing ? pc : ing;
       const bool stalled = pc <= ing && S.reached >= pc;
@@ -1944,8 +2038,7 @@ struct Ctl {
     if (lane == 0 && rt != S.retire) {
       S.retire = rt;
       S.wl_retired = wlr;
-      st_rlx_sys(&P.sctl[g].wl_retired, wlr);
-      st_rlx_sys(&P.sctl[g].retired, rt);
+      sm.smirror[g] = 1;
     }
     __syncwarp();
     return prog;
@@ -2121,7 +2214,7 @@ struct Ctl {
       T->ref_r = 0;
       task_publish(T, id);
       atomicOr(&s->pflags, PF_STAGING);
-      atomicAdd((unsigned long long*)&P.wctl->counters[5], 1ull);
+      atomicAdd(&sm.ctr[5], 1ull);
     }
     sm.nstage = 0;
   }
@@ -2220,7 +2313,7 @@ struct Ctl {
       s->state = 2;
       atomicSub(&sm.ready_insts, 1);
       task_publish(T, id);
-      atomicAdd((unsigned long long*)&P.wctl->counters[7], 1ull);
+      atomicAdd(&sm.ctr[7], 1ull);
       sm.any = 1;
     }
   }
@@ -2274,9 +2367,9 @@ struct Ctl {
     }
     if (n_tasks) {
       atomicAdd(&sm.unretired, (int32_t)n_tasks);
-      if (n_msg) atomicAdd((unsigned long long*)&P.wctl->counters[2], n_msg);
-      atomicAdd((unsigned long long*)&P.wctl->counters[3], n_bytes);
-      atomicAdd((unsigned long long*)&P.wctl->counters[4], n_tasks);
+      if (n_msg) atomicAdd(&sm.ctr[2], n_msg);
+      atomicAdd(&sm.ctr[3], n_bytes);
+      atomicAdd(&sm.ctr[4], n_tasks);
     }
   }
 };
@@ -2373,7 +2466,11 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     sm.unretired = 0;  // a launch starts with every task retired or abandoned
     sm.all_dirty = 0;
   }
-  for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 1;
+  for (int g = tid; g < P.max_streams; g += blockDim.x) {
+    sm.sdirty[g] = 1;
+    sm.smirror[g] = 0;
+  }
+  if (tid < 8) sm.ctr[tid] = 0;
   __syncthreads();
   for (int i = tid; i < P.max_comms * P.iw; i += blockDim.x)
     if (P.inst[i].k1 != 0 && P.inst[i].state == 1) atomicAdd(&sm.ready_insts, 1);
@@ -2481,14 +2578,20 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (moved) {
           const int warp = tid >> 5, nw = blockDim.x >> 5;
           const uint32_t nd = (uint32_t)(P.max_comms * P.nranks);
-          if (P.cnt2 && sm.nposts_round >= kSortMinPosts) {
+          // small rounds over few domains match from shared memory (each warp
+          // scans every post for its domains); larger ones from sorted lists
+          if (sm.nposts_round <= kSmallPosts && (uint64_t)sm.nposts_round * nd <= 32768ull) {
+            PostRec* recs = reinterpret_cast<PostRec*>(sm.prec);
+            const int total = C.gather_posts(recs);
+            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain_small(d, recs, total);
+          } else if (P.cnt2) {
             C.sort_posts();
             __syncthreads();
             for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain_sorted(d);
             __syncthreads();
             C.clear_counts();
           } else {
-            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain(d);
+            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain_scan(d);
           }
           __syncthreads();
         }
@@ -2500,7 +2603,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         if (tid == 0) {
           sm.arrivals = 0;
           sh->round = (uint64_t)(C.round + 1);
-          if (moved) atomicAdd((unsigned long long*)&P.wctl->counters[6], 1ull);
+          if (moved) sm.ctr[6] += 1ull;
         }
         C.round += 1;
         __syncthreads();
@@ -2635,6 +2738,19 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       mark(4);
       lap(4);
     }
+    // diagnostic trace: one record per tick (marker 0xFFFFFFFF in the high
+    // word of the third field): start, end, tick number, what it did
+    if (P.trace && tid == 0) {
+      const uint64_t k = atomicAdd((unsigned long long*)P.trace_pos, 1ull);
+      if ((int64_t)k < P.trace_cap) {
+        uint64_t* rec = P.trace + 4 * k;
+        rec[0] = (uint64_t)now;
+        rec[1] = now_ns();
+        rec[2] = (0xFFFFFFFFull << 32) | (uint32_t)ticks;
+        rec[3] = (uint64_t)(ing ? 1 : 0) | (uint64_t)(dirty_now ? 2 : 0) | (uint64_t)(sm.scan_now ? 4 : 0) |
+                 ((uint64_t)(sm.t_alloc - sm.t_retire) << 8) | ((uint64_t)sm.t_used << 32);
+      }
+    }
     // 4. bookkeeping and exit decisions (thread 0)
     if (tid == 0) {
       int decision = 0;  // 0 continue, 1 exit
@@ -2651,7 +2767,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       const bool pending = tasks_live || sm.pending != 0;
       const bool new_in_ring = false;  // rings were drained at the start of this tick
       if (pending || new_in_ring || any) idle_since = now;
-      if (!any && !tasks_live) sm.failed = ld_vol32(&P.wctl->failed);
       // a failed world leaves once its waiters were released by this kernel
       if (sm.failed && sm.released && !tasks_live && !new_in_ring) decision = 1;
       if (!decision && pending && !any && now - last_prog > P.watchdog_ns) {
@@ -2686,6 +2801,20 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     }
     __syncthreads();
     lap(5);
+    // host-visible stream words changed this tick (no fence of this tick follows)
+    for (int g = tid; g < P.max_streams; g += blockDim.x) {
+      if (!sm.smirror[g]) continue;
+      sm.smirror[g] = 0;
+      const SState& S = C.ss[g];
+      st_rlx_sys(&P.sctl[g].done_t, (uint64_t)now);  // engine clock of this tick
+      st_rlx_sys(&P.sctl[g].done, S.done);
+      st_rlx_sys(&P.sctl[g].wl_retired, S.wl_retired);
+      st_rlx_sys(&P.sctl[g].retired, S.retire);
+    }
+    if (tid < 8 && ((ticks & 63) == 0 || sm.flag == 1) && sm.ctr[tid]) {
+      atomicAdd((unsigned long long*)&P.wctl->counters[tid], sm.ctr[tid]);
+      sm.ctr[tid] = 0;
+    }
     if (sm.flag == 1) break;
     if (sm.flag == 2) {
       if (tid == 0) abandon_tasks(P, sm);
@@ -2711,6 +2840,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   __syncthreads();
   // let the movers go; tasks in flight were finished before deciding to exit
   if (tid == 0) {
+    st_rel_gpu32(&sh->exit_flag, 1);
     const int64_t t_exit = (int64_t)now_ns();
     if (t_first_task) {
       const int64_t td = t_tasks_done ? t_tasks_done : t_exit;
@@ -2722,7 +2852,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     atomicAdd((unsigned long long*)&P.wctl->counters[1], (unsigned long long)ticks);
     for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->tick_ns[k], (unsigned long long)tacc[k]);
     for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->sub_ns[k], (unsigned long long)sub[k]);
-    st_rel_gpu32(&sh->exit_flag, 1);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }
 }
@@ -2756,7 +2885,7 @@ __device__ void mover_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf) {
         set_error(P, -1, kErrTimeout);
         sm.flag = 1;
       }
-      __nanosleep(t - idle_t0 > 100000 ? 4000 : 500);
+      __nanosleep(t - idle_t0 > 100000 ? 1000 : 500);
     }
     __syncthreads();
     if (sm.flag) break;
@@ -2850,7 +2979,16 @@ extern "C" int mpxi_engine_launch(const mpxi::EngineParams* p, int nctas, int nt
 // while it has work.
 extern "C" int mpxi_engine_preload(void) {
   cudaFuncAttributes a;
-  return cudaFuncGetAttributes(&a, mpxi::engine_kernel) == cudaSuccess ? 0 : 1;
+  if (cudaFuncGetAttributes(&a, mpxi::engine_kernel) != cudaSuccess) return 1;
+  // A launch that needs more per-thread stack than the context's limit makes
+  // the runtime raise the limit, which waits for the device to go idle: with
+  // streams already waiting on the engine that would never happen.  Raise it
+  // here, before any engine work exists.
+  size_t lim = 0;
+  if (cudaDeviceGetLimit(&lim, cudaLimitStackSize) != cudaSuccess) return 1;
+  if (a.localSizeBytes > lim && cudaDeviceSetLimit(cudaLimitStackSize, a.localSizeBytes) != cudaSuccess)
+    return 1;
+  return 0;
 }
 
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads) {

@@ -386,7 +386,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_door = carve(S * 8), o_done = carve(S * 8);
   const size_t o_ops = carve((size_t)S * slots * sizeof(DOp));
   const size_t o_ss = carve(S * sizeof(SState));
-  const size_t o_post = carve((size_t)S * slots * 8);
+  const size_t o_post = carve((size_t)S * slots * sizeof(PostRec));
   const size_t o_pq = carve((ndom << w->qcap_log2) * sizeof(QEntry));
   const size_t o_uq = carve((ndom << w->qcap_log2) * sizeof(QEntry));
   const size_t o_pqh = carve(ndom * sizeof(QHead)), o_uqh = carve(ndom * sizeof(QHead));
@@ -405,7 +405,9 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_cnt2 = sort_ok ? carve((size_t)S * ndom * 4) : 0;
   const size_t o_dtot = sort_ok ? carve(ndom * 4) : 0;
   const size_t o_dbase = sort_ok ? carve(ndom * 8) : 0;
-  const size_t o_dlist = sort_ok ? carve((size_t)S * slots * 8) : 0;
+  const size_t o_dlist = sort_ok ? carve((size_t)S * slots * sizeof(PostRec)) : 0;
+  const int64_t trace_cap = env_i64("MPX_ENGINE_TRACE", 0);  // diagnostic tile trace records
+  const size_t o_trace = trace_cap > 0 ? carve((size_t)trace_cap * 32 + 8) : 0;
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
   w->dev_bytes = off;
   if (cfg.budget_bytes > 0 && (int64_t)off > cfg.budget_bytes) { world_release(w); return MPX_ERR_NO_MEM; }
@@ -456,7 +458,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.done = (uint64_t*)(base + o_done);
   P.ops = (DOp*)(base + o_ops);
   P.ss = (SState*)(base + o_ss);
-  P.postbuf = (uint64_t*)(base + o_post);
+  P.postbuf = (PostRec*)(base + o_post);
   P.pq = (QEntry*)(base + o_pq);
   P.uq = (QEntry*)(base + o_uq);
   P.pqh = (QHead*)(base + o_pqh);
@@ -474,7 +476,10 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.cnt2 = sort_ok ? (int32_t*)(base + o_cnt2) : nullptr;
   P.dtot = sort_ok ? (int32_t*)(base + o_dtot) : nullptr;
   P.dbase = sort_ok ? (int64_t*)(base + o_dbase) : nullptr;
-  P.dlist = sort_ok ? (uint64_t*)(base + o_dlist) : nullptr;
+  P.dlist = sort_ok ? (PostRec*)(base + o_dlist) : nullptr;
+  P.trace = trace_cap > 0 ? (uint64_t*)(base + o_trace) : nullptr;
+  P.trace_pos = trace_cap > 0 ? (uint64_t*)(base + o_trace + (size_t)trace_cap * 32) : nullptr;
+  P.trace_cap = trace_cap > 0 ? trace_cap : 0;
 
   if (cudaStreamCreateWithFlags(&w->engine_stream, cudaStreamNonBlocking) != cudaSuccess) {
     world_release(w);
@@ -680,6 +685,19 @@ extern "C" int mpx_world_get_error(mpx_world_t w, int* err) {
   if (w->plain) { *err = plain::error(w->plain); return MPX_SUCCESS; }
   *err = __atomic_load_n(&w->wctl->error, __ATOMIC_ACQUIRE);
   return MPX_SUCCESS;
+}
+
+// Diagnostic: copy up to n tile-trace records (4 words each) into out and
+// restart the trace; returns the number of records taken (0 without a trace).
+extern "C" int64_t mpxi_world_trace(mpx_world_t w, uint64_t* out, int64_t n) {
+  if (!w || w->plain || !w->params.trace || !out) return 0;
+  uint64_t pos = 0;
+  if (cudaMemcpy(&pos, w->params.trace_pos, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  const int64_t k = std::min<int64_t>({(int64_t)pos, w->params.trace_cap, n});
+  if (k > 0 && cudaMemcpy(out, w->params.trace, (size_t)k * 32, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  const uint64_t zero = 0;
+  if (cudaMemcpy(w->params.trace_pos, &zero, 8, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+  return k;
 }
 
 extern "C" int mpx_world_get_counters(mpx_world_t w, int64_t* outv, int n) {
@@ -958,6 +976,10 @@ extern "C" int mpx_comm_free(mpx_comm_t* pc) {
   *pc = nullptr;
   return MPX_SUCCESS;
 }
+
+// For the persistent requests (mpx_persist.cpp): whether a communicator's
+// world runs the plain path, which has no nonblocking collectives.
+extern "C" int mpxi_comm_is_plain(mpx_comm_t c) { return c && c->w && c->w->plain ? 1 : 0; }
 
 extern "C" int mpx_comm_rank(mpx_comm_t c, int* rank) {
   if (!c || !rank) return MPX_ERR_ARG;
@@ -1325,7 +1347,32 @@ static mpx_stream_s* request_stream(mpx_request_t r) {
   return w->streams[id];
 }
 
+extern "C" int mpxi_persist_active(mpx_request_t h, mpx_request_t* active);
+extern "C" void mpxi_persist_complete(mpx_request_t h);
+
+static int wait_impl(int n, mpx_request_t* reqs, mpx_status_t* statuses, bool single);
+
+// A persistent request (mpx_*_init, values <= -2) stands for the instance its
+// last start enqueued, or for nothing when inactive (a wait on it then has the
+// empty status).  The wait consumes the instance and leaves the persistent
+// handle valid and inactive.
 static int wait_common(int n, mpx_request_t* reqs, mpx_status_t* statuses, bool single) {
+  bool persistent = false;
+  for (int i = 0; i < n && !persistent; ++i) persistent = reqs[i] <= -2;
+  if (!persistent) return wait_impl(n, reqs, statuses, single);
+  std::vector<mpx_request_t> eff(reqs, reqs + n);
+  for (int i = 0; i < n; ++i)
+    if (reqs[i] <= -2 && mpxi_persist_active(reqs[i], &eff[i]) != MPX_SUCCESS) return MPX_ERR_REQUEST;
+  const int rc = wait_impl(n, eff.data(), statuses, single);
+  if (rc != MPX_SUCCESS) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (reqs[i] <= -2) mpxi_persist_complete(reqs[i]);
+    else reqs[i] = MPX_REQUEST_NULL;
+  }
+  return MPX_SUCCESS;
+}
+
+static int wait_impl(int n, mpx_request_t* reqs, mpx_status_t* statuses, bool single) {
   mpx_world_s* w = nullptr;
   mpx_stream_s* s = nullptr;
   int live = 0;

@@ -144,9 +144,22 @@ struct SState {
 
 struct QEntry {
   uint64_t ref;   // 0 = tombstone
-  int32_t src;    // send: sender rank; recv: source or ANY_SOURCE
+  int32_t src;    // send: sender key; recv: source pattern or ANY_SOURCE
   int32_t tag;    // send: tag; recv: tag or ANY_TAG
+  int64_t bytes;  // send: packed bytes; recv: capacity
 };
+
+// One post of a logical round: what matching needs of the operation, so
+// that matching and pairing read no operation record.
+struct PostRec {
+  uint64_t ref;     // make_ref(stream, seq)
+  int32_t key;      // send: sender key; recv: source pattern or ANY_SOURCE
+  int32_t tag;      // send: tag; recv: tag or ANY_TAG
+  int64_t bytes;    // send: packed bytes; recv: capacity
+  uint32_t dom;     // matching domain (comm slot * ranks + member)
+  uint32_t send;    // 1: a send, 0: a receive
+};
+static_assert(sizeof(PostRec) == 32, "post record");
 
 struct QHead {
   uint32_t head, tail;
@@ -271,14 +284,14 @@ struct EngineParams {
   int32_t* cnt2;              // [max_streams * ndomains] posts per (stream, domain), or null
   int32_t* dtot;              // [ndomains] posts per domain this round
   int64_t* dbase;             // [ndomains] start of each domain's list
-  uint64_t* dlist;            // [max_streams << slots_log2] this round's posts sorted by domain
+  PostRec* dlist;             // [max_streams << slots_log2] this round's posts sorted by domain
   StreamCtl* sctl;            // [max_streams]                 pinned
   WorldCtl* wctl;             //                                pinned
   uint64_t* doorbell;         // [max_streams] device (written by stream memops)
   uint64_t* done;             // [max_streams] device (waited on by stream memops)
   DOp* ops;                   // [max_streams << slots_log2]
   SState* ss;                 // [max_streams]
-  uint64_t* postbuf;          // [max_streams << slots_log2] this round's posts
+  PostRec* postbuf;           // [max_streams << slots_log2] this round's posts
   QEntry* pq;                 // posted receives [ndomains << qcap_log2]
   QEntry* uq;                 // unexpected sends
   QHead* pqh;                 // [ndomains]
@@ -291,6 +304,12 @@ struct EngineParams {
   uint64_t* inst_refs;        // [max_comms * iw * nranks]
   int64_t* next_inst;         // [max_comms * nranks]
   uint64_t* reduce_ptrs;      // [max_comms * iw * 2 * nranks]
+  // diagnostic tile trace (MPX_ENGINE_TRACE entries, or null): one record of
+  // 4 words per tile run by a mover: start and end %globaltimer, task slot <<
+  // 32 | tile, bytes << 8 | unit (bit 7: bulk-copy path)
+  uint64_t* trace;
+  uint64_t* trace_pos;        // next record (atomic)
+  int64_t trace_cap;
   // drain pass: ingest stream g only up to limit[g] (the operations published
   // when the pass was enqueued); nlimit = 0 means no limit
   int32_t nlimit, pad2;

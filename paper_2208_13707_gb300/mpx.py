@@ -185,6 +185,14 @@ _SIGS = {
     "mpx_ireduce_enqueue": [_vp, _vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
     "mpx_iallgather_enqueue": [_vp, _vp, _i64, _i32, _vp, _P(_i64)],
     "mpx_ibarrier_enqueue": [_vp, _P(_i64)],
+    "mpx_allreduce_init": [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_bcast_init": [_vp, _i64, _i32, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_reduce_init": [_vp, _vp, _i64, _i32, ctypes.c_int, ctypes.c_int, _vp, _P(_i64)],
+    "mpx_allgather_init": [_vp, _vp, _i64, _i32, _vp, _P(_i64)],
+    "mpx_barrier_init": [_vp, _P(_i64)],
+    "mpx_start_enqueue": [_P(_i64)],
+    "mpx_startall_enqueue": [ctypes.c_int, _P(_i64)],
+    "mpx_request_free": [_P(_i64)],
     "mpx_get_count": [_P(Status), _i32, _P(_i64)],
     "mpx_saxpy_enqueue": [_i64, _f32, _vp, _vp, _vp],
     "mpx_sendrecv_static": [_vp, _i64, _i32, _vp, _i64, _i32, _vp, _P(_i64)],
@@ -671,3 +679,47 @@ def mpx_serve_run_schedule(cfg: ServeConfig, calls, call_lo, regions, region_byt
     _chk(lib.mpx_serve_run_schedule(ctypes.byref(cfg), ctypes.byref(q), ctypes.byref(r)),
          "mpx_serve_run_schedule")
     return {k: getattr(r, k) for k, _ in ServeResult._fields_}
+
+
+# --- persistent collectives ---------------------------------------------------
+def _persist(fn, name, *args) -> int:
+    r = _i64(-1)
+    _chk(fn(*args, ctypes.byref(r)), name)
+    return r.value
+
+
+def mpx_allreduce_init(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, comm: int) -> int:
+    return _persist(lib.mpx_allreduce_init, "mpx_allreduce_init", sendbuf, recvbuf, count, datatype, op, comm)
+
+
+def mpx_bcast_init(buf: int, count: int, datatype: int, root: int, comm: int) -> int:
+    return _persist(lib.mpx_bcast_init, "mpx_bcast_init", buf, count, datatype, root, comm)
+
+
+def mpx_reduce_init(sendbuf: int, recvbuf: int, count: int, datatype: int, op: int, root: int,
+                    comm: int) -> int:
+    return _persist(lib.mpx_reduce_init, "mpx_reduce_init", sendbuf, recvbuf, count, datatype, op, root,
+                    comm)
+
+
+def mpx_allgather_init(sendbuf: int, recvbuf: int, count: int, datatype: int, comm: int) -> int:
+    return _persist(lib.mpx_allgather_init, "mpx_allgather_init", sendbuf, recvbuf, count, datatype, comm)
+
+
+def mpx_barrier_init(comm: int) -> int:
+    return _persist(lib.mpx_barrier_init, "mpx_barrier_init", comm)
+
+
+def mpx_start_enqueue(request: int) -> None:
+    r = _i64(request)
+    _chk(lib.mpx_start_enqueue(ctypes.byref(r)), "mpx_start_enqueue")
+
+
+def mpx_startall_enqueue(requests) -> None:
+    a = (_i64 * len(requests))(*requests)
+    _chk(lib.mpx_startall_enqueue(len(requests), a), "mpx_startall_enqueue")
+
+
+def mpx_request_free(request: int) -> None:
+    r = _i64(request)
+    _chk(lib.mpx_request_free(ctypes.byref(r)), "mpx_request_free")

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from traffic import gen
 from tests.test_oracle_nonblocking import _crossing, _definitions
 from traffic.program import MODE_FIXED, T_FLOAT, ProgramBuilder
 
@@ -109,3 +110,92 @@ def test_argument_checks():
         mpx.mpx_world_free(w)
         for h in raw:
             mpx.mpx_cuda_stream_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# persistent collectives: mpx_*_init once, mpx_start_enqueue per instance
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["persistent", "drain"])
+def test_persistent_collectives_match_the_oracle(mode):
+    """An in-place int64 allreduce and a broadcast from root 1, each a
+    persistent request started three times, with the root's buffer rewritten
+    by an axpy between broadcast starts: bit-exact with the oracle."""
+    gpu = _gpu()
+    p = gen.persistent_collectives(nranks=4, starts=3, n=4099)
+    ref = oracle.run(p)
+    assert ref.error == 0 and not ref.deadlock
+    out = gpu.run(p, mode=mode, timeout_s=45)
+    assert out.finished and out.world_error == 0
+    for k, (a, b) in enumerate(zip(out.buffers, ref.buffers)):
+        assert np.array_equal(a, b), f"buffer {k} differs"
+
+
+def test_persistent_request_lifecycle():
+    """Start of an active request: MPX_ERR_STATE; free while active:
+    MPX_ERR_PENDING; a wait leaves the handle valid (startable again); a wait
+    on an inactive handle is a no-op; free of an operation's request:
+    MPX_ERR_REQUEST; init on the plain path: MPX_ERR_UNSUPPORTED."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2208_13707_gb300 import mpx
+    for mode in (mpx.ENGINE_PERSISTENT, mpx.ENGINE_PLAIN):
+        cfg = mpx.mpx_world_config_init()
+        cfg.engine_mode = mode
+        cfg.max_streams = 4
+        w = mpx.mpx_world_create(2, cfg)
+        raw = [mpx.mpx_cuda_stream_create() for _ in range(2)]
+        cs = [torch.cuda.ExternalStream(h) for h in raw]
+        ms = [mpx.mpx_stream_create(w, r, raw[r]) for r in range(2)]
+        comm = mpx.mpx_stream_comm_create(w, ms)
+        x = torch.arange(8, dtype=torch.int64, device="cuda").repeat(2, 1)
+        torch.cuda.synchronize()
+        try:
+            if mode == mpx.ENGINE_PLAIN:
+                with pytest.raises(mpx.MpxError) as e:
+                    mpx.mpx_allreduce_init(mpx.IN_PLACE, x[0].data_ptr(), 8, mpx.INT64, mpx.SUM, comm[0])
+                assert e.value.code == mpx.ERR_UNSUPPORTED
+                continue
+            h = [mpx.mpx_allreduce_init(mpx.IN_PLACE, x[r].data_ptr(), 8, mpx.INT64, mpx.SUM, comm[r])
+                 for r in range(2)]
+            assert all(v not in (-1,) and v < -1 for v in h)
+            mpx.mpx_wait_enqueue(h[0])                       # inactive: completes at once
+            for rep in range(2):
+                for r in range(2):
+                    mpx.mpx_start_enqueue(h[r])
+                with pytest.raises(mpx.MpxError) as e:
+                    mpx.mpx_start_enqueue(h[0])
+                assert e.value.code == mpx.ERR_STATE
+                with pytest.raises(mpx.MpxError) as e:
+                    mpx.mpx_request_free(h[0])
+                assert e.value.code == mpx.ERR_PENDING
+                for r in range(2):
+                    mpx.mpx_wait_enqueue(h[r])
+            for s in cs:
+                s.synchronize()
+            assert x.cpu().tolist() == [[4 * v for v in range(8)]] * 2   # two starts: x*2*2
+            q = mpx.mpx_isend_enqueue(x[0].data_ptr(), 1, mpx.INT64, 1, 0, comm[0])
+            with pytest.raises(mpx.MpxError) as e:
+                mpx.mpx_request_free(q)
+            assert e.value.code == mpx.ERR_REQUEST
+            r2 = mpx.mpx_irecv_enqueue(x[1].data_ptr(), 1, mpx.INT64, 0, 0, comm[1])
+            mpx.mpx_wait_enqueue(q)
+            mpx.mpx_wait_enqueue(r2)
+            for s in cs:
+                s.synchronize()
+            for v in h:
+                mpx.mpx_request_free(v)
+        finally:
+            for c in comm:
+                mpx.mpx_comm_free(c)
+            for s in ms:
+                for _ in range(2000):
+                    try:
+                        mpx.mpx_stream_free(s)
+                        break
+                    except mpx.MpxError:
+                        import time
+                        time.sleep(5e-4)
+            mpx.mpx_world_free(w)
+            for h_ in raw:
+                mpx.mpx_cuda_stream_destroy(h_)

@@ -11,8 +11,8 @@ from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
-from .program import (ANY_INDEX, ANY_SOURCE, ANY_TAG, IN_PLACE, MODE_FIXED, MODE_TREE, T_BYTE,
-                      T_DOUBLE, T_FLOAT, T_INT32, T_INT64, BASIC_SIZES, Program,
+from .program import (ANY_INDEX, ANY_SOURCE, ANY_TAG, IALLREDUCE, IBCAST, IN_PLACE, MODE_FIXED,
+                      MODE_TREE, T_BYTE, T_DOUBLE, T_FLOAT, T_INT32, T_INT64, BASIC_SIZES, Program,
                       ProgramBuilder)
 from .rng import Rng
 
@@ -746,4 +746,37 @@ def serving_program(sched: dict) -> Program:
             else:
                 b.allreduce(gs[t], c, regs[t], int(x["off"]), cap, int(x["capture"]),
                             int(x["bytes"]) // 4, T_FLOAT, MODE_FIXED)
+    return b.build()
+
+
+# ----------------------------------------------------------------------------
+# Persistent collectives (MPI-4 MPI_Allreduce_init / MPI_Start in enqueue form)
+# ----------------------------------------------------------------------------
+def persistent_collectives(nranks: int = 4, starts: int = 3, n: int = 1000,
+                           seed: int = SEED_BASE + 3) -> Program:
+    """Every rank creates a persistent in-place int64 allreduce over Y and a
+    persistent fp32 broadcast of B from root 1, then, `starts` times: starts
+    the allreduce, waits, starts the broadcast, waits.  Between broadcast
+    starts the root's B is rewritten by an axpy (B = 0.5 * X + B), so every
+    start must read the buffer as it stands when the stream reaches it."""
+    b = ProgramBuilder(nranks, "persistent")
+    gs = [b.stream(r) for r in range(nranks)]
+    c = b.comm(gs)
+    Y, B, X = [], [], []
+    for r in range(nranks):
+        rng = Rng(seed, 80, r)
+        Y.append(b.buffer(rng.integers(-(1 << 40), 1 << 40, n).astype(np.int64)))
+        B.append(b.buffer(rng.normal(n).astype(np.float32)))
+        X.append(b.buffer(rng.normal(n).astype(np.float32)))
+    ar = [b.persistent(gs[r], IALLREDUCE, c, buf=IN_PLACE, off=0, buf2=Y[r], off2=0, count=n,
+                       type=T_INT64, mode=MODE_FIXED) for r in range(nranks)]
+    bc = [b.persistent(gs[r], IBCAST, c, buf=B[r], off=0, count=n, type=T_FLOAT, peer=1)
+          for r in range(nranks)]
+    for _ in range(starts):
+        for r in range(nranks):
+            b.wait(gs[r], b.start(gs[r], ar[r]))
+            if r == 1:
+                b.axpy(gs[r], 0.5, X[r], 0, B[r], 0, n)
+            b.wait(gs[r], b.start(gs[r], bc[r]))
+    b.meta.update(Y=Y, B=B, X=X, n=n, starts=starts)
     return b.build()

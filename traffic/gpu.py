@@ -105,6 +105,7 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
                 rank_in[(c, int(g))] = r
     engine_stream = torch.cuda.ExternalStream(raw_streams[-1], device=dev)
     req: Dict[int, int] = {}
+    persist: Dict[int, int] = {}   # persistent request id -> handle (created at its first start)
     ops = prog.ops
 
     def retry(fn):
@@ -176,6 +177,19 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
             rb = ptr[int(o["buf2"])] + int(o["off2"])
             sb = mpx.IN_PLACE if b == IN_PLACE else p
             retry(lambda: mpx.mpx_allgather_enqueue(sb, rb, cnt, ty, comm))
+        elif int(o["persist"]) > 0:
+            # a start of a persistent collective: its init call at the first start
+            pid = int(o["persist"]) - 1
+            if pid not in persist:
+                b2 = int(o["buf2"])
+                rb = ptr[b2] + int(o["off2"]) if b2 >= 0 else 0
+                sb = mpx.IN_PLACE if b == IN_PLACE else p
+                persist[pid] = {IALLREDUCE: lambda: mpx.mpx_allreduce_init(sb, rb, cnt, ty, mpx.SUM, comm),
+                                IBCAST: lambda: mpx.mpx_bcast_init(p, cnt, ty, peer, comm),
+                                IREDUCE: lambda: mpx.mpx_reduce_init(sb, rb, cnt, ty, mpx.SUM, peer, comm),
+                                IALLGATHER: lambda: mpx.mpx_allgather_init(sb, rb, cnt, ty, comm)}[k]()
+            retry(lambda: mpx.mpx_start_enqueue(persist[pid]))
+            req[int(j)] = persist[pid]
         elif k == IALLREDUCE:
             rb = ptr[int(o["buf2"])] + int(o["off2"]) if int(o["buf2"]) >= 0 else 0
             sb = mpx.IN_PLACE if b == IN_PLACE else p
@@ -268,6 +282,9 @@ def run(prog: Program, mode: str = "persistent", timeout_s: float = 60.0, exclus
     werr = mpx.mpx_world_get_error(world)
     counters = mpx.mpx_world_get_counters(world)
     extra = {"issue_seconds": t_issue, "drain_passes": passes}
+    if finished:
+        for h in persist.values():  # every start was waited for: the requests are inactive
+            mpx.mpx_request_free(h)
     if finished and not keep_world:
         for c in range(prog.ncomms):
             for h in comms[c]:

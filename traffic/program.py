@@ -46,10 +46,13 @@ ERR_TIMEOUT = 16
 # shared with the oracle's C struct (88 bytes, little endian).  sidx / didx:
 # on a multiplex stream communicator (§3.5) the sender's and the receiver's
 # local stream index (a receive's sidx may be ANY_INDEX); 0 on other comms.
+# persist: k + 1 when a nonblocking collective is a start of persistent
+# request k (MPI-4 persistent collectives, e.g. MPI_Allreduce_init), else 0;
+# the oracle ignores it (a start behaves as the nonblocking call it starts).
 OP_DTYPE = np.dtype({
     "names": ["stream", "kind", "comm", "peer", "tag", "type", "count",
               "buf", "buf2", "off", "off2", "req_lo", "req_n", "status",
-              "mode", "alpha", "sidx", "didx", "pad"],
+              "mode", "alpha", "sidx", "didx", "persist"],
     "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<i8",
                 "<i4", "<i4", "<i8", "<i8", "<i4", "<i4", "<i4",
                 "<i4", "<f4", "<i4", "<i4", "<i4"],
@@ -164,6 +167,7 @@ class ProgramBuilder:
         self.nstatus = 0
         self.issue: List[tuple] = []
         self.meta: dict = {}
+        self.persistents: List[dict] = []
 
     # --- objects ---
     def stream(self, rank: int) -> int:
@@ -312,6 +316,23 @@ class ProgramBuilder:
         return self._op(g, kind=IALLGATHER, comm=comm, buf=sendbuf, off=sendoff, buf2=recvbuf,
                         off2=recvoff, count=count, type=type_)
 
+    # --- persistent collectives (MPI-4: MPI_Allreduce_init / MPI_Start) ---
+    def persistent(self, g, kind, comm, **args) -> int:
+        """A persistent request on stream g for the nonblocking collective
+        `kind` (IALLREDUCE, IBCAST, IREDUCE or IALLGATHER) with fixed
+        arguments (the builder method's keywords).  Records no operation: the
+        request only names what each start() enqueues.  Returns its id."""
+        assert kind in NONBLOCKING_COLLECTIVES
+        self.persistents.append(dict(g=g, kind=kind, comm=comm, args=dict(args)))
+        return len(self.persistents) - 1
+
+    def start(self, g, pid):
+        """Start persistent request pid: its nonblocking collective, enqueued
+        here on g; completed by a wait like any request."""
+        p = self.persistents[pid]
+        assert p["g"] == g, "a persistent request is started on the stream that created it"
+        return self._op(g, kind=p["kind"], comm=p["comm"], persist=pid + 1, **p["args"])
+
     def axpy(self, g, alpha, xbuf, xoff, ybuf, yoff, n):
         """y[i] = alpha*x[i] + y[i] in fp32 with one rounding (fused multiply-add)."""
         return self._op(g, kind=AXPY, alpha=alpha, buf=xbuf, off=xoff, buf2=ybuf,
@@ -347,5 +368,6 @@ class ProgramBuilder:
                        types=np.array(self.types, TYPE_DTYPE),
                        buf_init=self.bufs, reqlist=np.array(reqlist, np.int64),
                        nstatus=self.nstatus, issue_order=issue, name=self.name,
-                       meta=dict(self.meta), comm_mux=[None if m is None else [list(l) for l in m]
-                                                       for m in self.comm_mux])
+                       meta=dict(self.meta, persistents=[dict(p) for p in self.persistents]),
+                       comm_mux=[None if m is None else [list(l) for l in m]
+                                 for m in self.comm_mux])
