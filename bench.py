@@ -470,12 +470,15 @@ def oracle_sample(steps=1, first_step=0):
 
 
 def reference_arm(args, rank, world):
+    """The oracle on the host: W untimed full-size ring steps, then exactly K
+    timed ones (about 1.2 s each, single-threaded)."""
     if rank != 0:
         return
-    steps = max(1, min(args.steps, 2))
+    steps = max(1, args.steps)
+    oracle_sample(max(1, args.warmup))          # warm-up steps, untimed
     value, dt, msgs = oracle_sample(steps)
-    sample = f"{steps} full-size ring step(s): {msgs} messages, 8 axpys of 2^24 each, single thread"
-    line = {"metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": args.gpus, "steps": args.steps,
+    sample = f"{steps} full-size ring steps: {msgs} messages, 8 axpys of 2^24 each per step, single thread"
+    line = {"metric": METRIC, "value": value, "unit": "msgs/s", "n_gpus": args.gpus, "steps": steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "ranks": RANKS, "n": N_AXPY},
@@ -620,7 +623,7 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     return out
 
 
-def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26), R=16, iters=None):
+def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26, 27, 28), R=16, iters=None):
     """Enqueued SUM allreduce among R ranks (one stream each, persistent
     engine): per size, dtype (int64, fp32) and order (fixed, tree), `iters`
     instances back to back after warm-up.  Algorithmic bytes per instance:
@@ -652,7 +655,9 @@ def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26), R=16, iters=None):
                     n = 1 << lg
                     if dt == mpx.INT64:
                         x = xs[:, :n]
-                        x.copy_(torch.round(torch.randn((R, n), device=dev, generator=gen_) * 2.0 ** 40).to(torch.int64))
+                        for r in range(R):  # one rank at a time: small temporaries at 2^28
+                            x[r].copy_(torch.round(torch.randn(n, device=dev, generator=gen_) * 2.0 ** 40)
+                                       .to(torch.int64))
                         y = ys[:, :n]
                     else:
                         x = xs.view(torch.float32)[:, :n]
@@ -661,10 +666,14 @@ def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26), R=16, iters=None):
                     torch.cuda.synchronize()
                     k = iters or max(4, min(200, (1 << 30) // (2 * R * n * esz)))
 
+                    issue = [0.0]
+
                     def run(m):
+                        t_i = time.perf_counter()
                         for _ in range(m):
                             for r in range(R):
                                 mpx.mpx_allreduce_enqueue(x[r].data_ptr(), y[r].data_ptr(), n, dt, mpx.SUM, comm[r])
+                        issue[0] = time.perf_counter() - t_i
                         for c in cs:
                             c.synchronize()
                     run(3)
@@ -672,8 +681,33 @@ def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26), R=16, iters=None):
                     run(k)
                     dt_s = (time.perf_counter() - t0) / k
                     gbs = 2 * R * n * esz / dt_s / 1e9
-                    out.append({"n": n, "dtype": dt_name, "mode": mode_name, "instances": k,
-                                "us_per_instance": 1e6 * dt_s, "gbs": gbs})
+                    e = {"n": n, "dtype": dt_name, "mode": mode_name, "instances": k,
+                         "us_per_instance": 1e6 * dt_s, "gbs": gbs,
+                         "host_issue_us_per_instance": 1e6 * issue[0] / k}
+                    if n <= (1 << 18):
+                        # pipelined: k nonblocking instances per rank, one waitall
+                        # each; device time by CUDA events (the host issues ahead)
+                        def pipe(m):
+                            ev0 = torch.cuda.Event(enable_timing=True)
+                            ev0.record(cs[0])
+                            for c in cs[1:]:
+                                c.wait_event(ev0)
+                            reqs = [[] for _ in range(R)]
+                            for _ in range(m):
+                                for r in range(R):
+                                    reqs[r].append(mpx.mpx_iallreduce_enqueue(x[r].data_ptr(), y[r].data_ptr(),
+                                                                              n, dt, mpx.SUM, comm[r]))
+                            for r in range(R):
+                                mpx.mpx_waitall_enqueue(reqs[r])
+                            ev1 = torch.cuda.Event(enable_timing=True)
+                            for c in cs[1:]:
+                                cs[0].wait_stream(c)
+                            ev1.record(cs[0])
+                            ev1.synchronize()
+                            return ev0.elapsed_time(ev1) * 1e3 / m
+                        pipe(8)
+                        e["pipelined_us_per_instance"] = pipe(min(k, 128))
+                    out.append(e)
         mpx.mpx_world_stop(world, 10000)
     finally:
         for h in comm:
@@ -756,20 +790,118 @@ def host_msgrate(seconds=0.15):
     return out
 
 
-def serving(requests=100000):
+def serving(requests=10_000_000, plain_requests=100_000, curve_requests=200_000,
+            curve=(0.25, 0.5, 0.8, 1.2)):
     """Serving loop: 32 host threads with one MPIX stream each submit
-    requests open-loop (Poisson, mean gap 2 us per thread), sizes Zipf(1.2)
-    over 64 B - 16 MB, 70% p2p / 30% fp32 allreduce over the 32 ranks,
-    admission against a 40 GiB device budget; the same requests through the
-    plain path.  `requests` calls in total (the full workload has 10^7)."""
+    requests open-loop (Poisson, mean gap 2 us per thread: 16 M requests/s
+    offered, over capacity by design), sizes Zipf(1.2) over 64 B - 16 MB,
+    70% p2p / 30% fp32 allreduce over the 32 ranks, admission against a 40 GiB
+    device budget.  The engine runs the full `requests` (10^7); the plain
+    path, which synchronizes its host thread at every blocking call, runs the
+    same workload at `plain_requests`.  The load curve reruns the engine at
+    fractions of its measured capacity (`curve_requests` each), where the
+    latencies describe the engine rather than an over-capacity backlog."""
     from paper_2208_13707_gb300 import mpx
     out = {}
-    for name, mode in (("engine", mpx.ENGINE_PERSISTENT), ("plain", mpx.ENGINE_PLAIN)):
+    for name, mode, n in (("engine", mpx.ENGINE_PERSISTENT, requests),
+                          ("plain", mpx.ENGINE_PLAIN, plain_requests)):
         c = mpx.mpx_serve_config_init()
-        c.requests = requests
+        c.requests = n
         c.engine_mode = mode
         out[name] = mpx.mpx_serve_run(c)
+        out[name]["requests"] = n
     out["requests"] = requests
+    out["speedup_vs_plain"] = out["engine"]["msgs_per_s"] / max(1e-9, out["plain"]["msgs_per_s"])
+    cap = out["engine"]["msgs_per_s"]
+    pts = []
+    for f in curve:
+        c = mpx.mpx_serve_config_init()
+        c.requests = curve_requests
+        c.mean_gap_us = c.nthreads / (f * cap) * 1e6
+        r = mpx.mpx_serve_run(c)
+        pts.append({"offered_fraction_of_capacity": f, "offered_per_s": f * cap,
+                    "mean_gap_us_per_thread": c.mean_gap_us, "requests": curve_requests,
+                    "msgs_per_s": r["msgs_per_s"], "gbs": r["gbs"],
+                    "p50_us": r["p50_us"], "p99_us": r["p99_us"],
+                    "svc_p50_us": r["svc_p50_us"], "svc_p99_us": r["svc_p99_us"],
+                    "admission_waits": r["admission_waits"]})
+    out["load_curve"] = {"capacity_msgs_per_s": cap, "points": pts}
+    return out
+
+
+def tiny_bench(nmsg=1000, reps=3):
+    """C1: 2 ranks, `nmsg` blocking int32 sends (4 B - 16 KB, tags 0-7) on rank
+    0 and blocking receives in a seeded permutation on rank 1.  Engine
+    (resident; eager sends, staged when their receive is not yet posted):
+    msgs/s from CUDA events around the whole sequence, and per receive the
+    time from its stream reaching the call to the call's completion (events
+    recorded just before and after it).  Plain path (host matching, the host
+    thread synchronized per call): host clock over the same calls.  Delivered
+    bytes are checked against the sent ones."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    from traffic import gen, gpu
+    p = gen.tiny_pairs(nmsg=nmsg)
+    sb, rb = p.meta["sbuf"], p.meta["rbuf"]
+    lo = p.stream_op_lo
+    sends, recvs = p.ops[int(lo[0]): int(lo[1])], p.ops[int(lo[1]): int(lo[2])]
+    out = {"messages": nmsg, "payload_bytes": int(p.meta["payload_bytes"])}
+    cfg = mpx.mpx_world_config_init()
+    cfg.max_streams = 4
+    w = mpx.mpx_world_create(2, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(2)]
+    cs = [torch.cuda.ExternalStream(h) for h in raw]
+    ms = [mpx.mpx_stream_create(w, r, raw[r]) for r in range(2)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    src = torch.from_numpy(p.buf_init[sb]).cuda()
+    dst = torch.zeros(p.buf_init[rb].size, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    rates, lat = [], []
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for rep in range(reps + 1):  # the first is a warm-up
+        reach = [ev() for _ in range(nmsg)]
+        done = [ev() for _ in range(nmsg)]
+        start, end0, end = ev(), ev(), ev()
+        start.record(cs[0])
+        cs[1].wait_event(start)
+        for o in sends:
+            mpx.mpx_send_enqueue(src.data_ptr() + int(o["off"]), int(o["count"]), mpx.INT32, 1,
+                                 int(o["tag"]), comm[0])
+        for i, o in enumerate(recvs):
+            reach[i].record(cs[1])
+            mpx.mpx_recv_enqueue(dst.data_ptr() + int(o["off"]), int(o["count"]), mpx.INT32, 0,
+                                 int(o["tag"]), comm[1], 0)
+            done[i].record(cs[1])
+        end0.record(cs[0])
+        cs[1].wait_event(end0)
+        end.record(cs[1])
+        end.synchronize()
+        if rep:
+            rates.append(nmsg / (start.elapsed_time(end) / 1e3))
+            lat += [reach[i].elapsed_time(done[i]) * 1e3 for i in range(nmsg)]
+    assert torch.equal(dst, src.view(torch.uint8)), "tiny: delivered bytes differ from the sent ones"
+    mpx.mpx_world_stop(w, 10000)
+    for c in comm:
+        mpx.mpx_comm_free(c)
+    for s_ in ms:
+        for _ in range(2000):
+            try:
+                mpx.mpx_stream_free(s_)
+                break
+            except mpx.MpxError:
+                time.sleep(5e-4)
+    mpx.mpx_world_free(w)
+    for h in raw:
+        mpx.mpx_cuda_stream_destroy(h)
+    out["engine"] = {"msgs_per_s": float(np.median(rates)), "p50_us": float(np.percentile(lat, 50)),
+                     "p99_us": float(np.percentile(lat, 99)), "timing": "CUDA events"}
+    prates = []
+    for rep in range(reps + 1):
+        r = gpu.run(p, mode="plain", timeout_s=120)
+        assert r.finished and np.array_equal(r.buffers[rb], p.buf_init[sb].view(np.uint8))
+        if rep:
+            prates.append(nmsg / r.seconds)
+    out["plain"] = {"msgs_per_s": float(np.median(prates)), "timing": "host clock"}
     out["speedup_vs_plain"] = out["engine"]["msgs_per_s"] / max(1e-9, out["plain"]["msgs_per_s"])
     return out
 
@@ -809,13 +941,14 @@ def autotune_report():
     return out
 
 
-def profile_steps(kind, launches=3):
+def profile_steps(kind, launches=3, log2n=24):
     """Profile-safe runs for a kernel profiler: the work is a recorded step
     (one CUDA graph: descriptor publication kernel + one engine pass), so no
     stream waits exist for a serialising profiler to block on, and the engine
     pass reads nothing it writes in pinned memory (a replayed pass repeats the
     same work).  kind "allreduce": 16 ranks, one fp32 fixed-order allreduce of
-    2^22 elements each (256 MiB in, 256 MiB out).  kind "batching": the
+    2^log2n elements each (2^24: 1 GiB in, 1 GiB out).  kind "copy": one contiguous
+    1 GiB message between two ranks.  kind "batching": the
     small-message batching step (64 ranks x 4 streams, 65536 messages,
     8 B - 64 KB)."""
     import torch
@@ -833,7 +966,9 @@ def profile_steps(kind, launches=3):
         finally:
             r.close()
         return {"profile_steps": kind, "launches": launches, "messages": 65536}
-    R, n = 16, 1 << 22
+    if kind == "copy":
+        return profile_copy(launches)
+    R, n = 16, 1 << log2n
     dev = torch.device("cuda")
     cfg = mpx.mpx_world_config_init()
     cfg.engine_mode = mpx.ENGINE_DRAIN
@@ -871,6 +1006,56 @@ def profile_steps(kind, launches=3):
         mpx.mpx_cuda_stream_destroy(h)
     assert ok, "profiled allreduce steps failed"
     return {"profile_steps": kind, "launches": launches, "ranks": R, "n": n}
+
+
+def profile_copy(launches=3, nbytes=1 << 30):
+    """One contiguous message of `nbytes` between two ranks as a recorded step
+    (isend, irecv and both waitalls): each launch is one publication kernel
+    and one engine pass that moves the message and completes the waits, with
+    no idle tail and no stream waits.  Checks the delivered bytes."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mpx.ENGINE_DRAIN
+    cfg.max_streams = 4
+    w = mpx.mpx_world_create(2, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(3)]
+    ms = [mpx.mpx_stream_create(w, r, raw[r], mpx.STREAM_EXCLUSIVE) for r in range(2)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    src = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda")
+    dst = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    reqs = np.full(2, -1, np.int64)
+    ops = np.zeros(4, mpx.op_dtype())
+    ops["datatype"] = mpx.BYTE
+    for i, (kind, peer, buf, c, rq) in enumerate(((mpx.OP_ISEND, 1, src, comm[0], 0),
+                                                  (mpx.OP_IRECV, 0, dst, comm[1], 1))):
+        ops[i]["kind"] = kind
+        ops[i]["peer"] = peer
+        ops[i]["count"] = nbytes
+        ops[i]["buf"] = buf.data_ptr()
+        ops[i]["comm"] = c
+        ops[i]["requests"] = reqs.ctypes.data + 8 * rq
+    for i, rq in ((2, 0), (3, 1)):
+        ops[i]["kind"] = mpx.OP_WAITALL
+        ops[i]["count"] = 1
+        ops[i]["requests"] = reqs.ctypes.data + 8 * rq
+    step = mpx.mpx_step_create(w, ops)
+    es = torch.cuda.ExternalStream(raw[2])
+    for _ in range(launches):
+        mpx.mpx_step_launch(step, raw[2])
+    es.synchronize()
+    ok = mpx.mpx_step_get_error(step) == 0 and mpx.mpx_world_get_error(w) == 0 and torch.equal(src, dst)
+    mpx.mpx_step_free(step)
+    for c in comm:
+        mpx.mpx_comm_free(c)
+    for s_ in ms:
+        mpx.mpx_stream_free(s_)
+    mpx.mpx_world_free(w)
+    for h in raw:
+        mpx.mpx_cuda_stream_destroy(h)
+    assert ok, "profiled copy steps failed"
+    return {"profile_steps": "copy", "launches": launches, "bytes": nbytes}
 
 
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
@@ -954,16 +1139,20 @@ def main():
     ap.add_argument("--allreduce-only", action="store_true",
                     help="print only the allreduce bandwidth sweep and the halo exchange")
     ap.add_argument("--no-c4", action="store_true", help="skip the allreduce sweep and the halo exchange")
-    ap.add_argument("--serve-requests", type=int, default=100000,
-                    help="requests of the serving measurement (0 = skip it)")
+    ap.add_argument("--serve-requests", type=int, default=10_000_000,
+                    help="requests of the serving measurement's engine run (0 = skip serving)")
+    ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-pairs (C1) measurement")
+    ap.add_argument("--tiny-only", action="store_true", help="print only the tiny-pairs (C1) measurement")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
     ap.add_argument("--no-host-msgrate", action="store_true",
                     help="skip the host-thread message-rate experiment")
     ap.add_argument("--host-msgrate-only", action="store_true",
                     help="print only the host-thread message-rate experiment (no GPU)")
-    ap.add_argument("--profile-steps", choices=["allreduce", "batching"], default=None,
+    ap.add_argument("--profile-steps", choices=["allreduce", "batching", "copy"], default=None,
                     help="profile-safe recorded steps for a kernel profiler (no benchmark line)")
+    ap.add_argument("--profile-log2n", type=int, default=24,
+                    help="elements per rank (log2) of the profiled allreduce step")
     ap.add_argument("--autotune-only", action="store_true", help="print only the autotuner report")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
@@ -991,10 +1180,13 @@ def main():
         copy_sweep()
         return
     if args.profile_steps:
-        print(json.dumps(profile_steps(args.profile_steps)), flush=True)
+        print(json.dumps(profile_steps(args.profile_steps, log2n=args.profile_log2n)), flush=True)
         return
     if args.autotune_only:
         print(json.dumps({"autotune": autotune_report()}), flush=True)
+        return
+    if args.tiny_only:
+        print(json.dumps({"tiny": tiny_bench()}), flush=True)
         return
     if args.serving_only:
         print(json.dumps({"serving": serving(args.serve_requests)}), flush=True)
@@ -1081,6 +1273,7 @@ def main():
             e["frac_of_peak"] = e["gbs"] / pk
         c4 = {"allreduce": ar, "halo": halo_bench()}
     serve = serving(args.serve_requests) if args.serve_requests else None
+    tiny = None if args.no_tiny else tiny_bench()
     hostr = None if args.no_host_msgrate else host_msgrate()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1115,6 +1308,7 @@ def main():
                 "batching_full": batching_1m,
                 "allreduce_and_halo": c4,
                 "serving": serve,
+                "tiny": tiny,
                 "host_msgrate": hostr,
                 "autotune": tune,
                 "autotune_ring": ring_tune,

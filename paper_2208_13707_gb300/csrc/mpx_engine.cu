@@ -40,6 +40,7 @@ constexpr int kErrTimeout = 16;
 constexpr int kMaxRoundsPerTick = 64;
 constexpr int kMaxStagePerTick = 128;
 constexpr int kMaxDeferred = 512;  // deliveries a scheduling phase sizes together
+constexpr uint64_t kDlvStrided = 1ull << 62;  // deferred delivery with a strided side
 constexpr int kSmallPosts = 256;   // rounds up to this many posts match from shared memory
 constexpr int kTmaStages = 8;   // shared-memory stages of the bulk-copy pipeline
 constexpr int kTmaLead = 4;     // loads in flight ahead of the store being issued
@@ -297,6 +298,11 @@ __device__ __forceinline__ bool is_blocking(uint32_t kw) {
 __device__ void set_error(const EngineParams& P, int g, int err) {
   if (g >= 0) atomicCAS(&P.sctl[g].error, 0, err);
   atomicCAS(&P.wctl->error, 0, err);
+}
+
+// Whether one operation's datatype lays its bytes out contiguously.
+__device__ __forceinline__ bool desc_contig(const Desc& d) {
+  return d.vcount == 1 || d.stride == d.blocklen;
 }
 
 // Packed bytes carried by one operation's datatype.
@@ -1634,9 +1640,12 @@ struct Ctl {
       const int k = atomicAdd(&sm.ndlv, 1);
       if (k < kMaxDeferred) {
         atomicOr(&r->pflags, PF_SCHED);
+        // a strided delivery moves at about 4/7 of a contiguous one's rate per
+        // mover: its bytes weigh 7/4 when the phase's tiles are sized
+        const bool strided = !desc_contig(r->d) || (!from_stage && !desc_contig(s->d));
         sm.dlv_s[k] = sref | (from_stage ? (1ull << 63) : 0ull);
-        sm.dlv_r[k] = rref;
-        atomicAdd(&sm.dlv_bytes, (unsigned long long)r->bytes);
+        sm.dlv_r[k] = rref | (strided ? kDlvStrided : 0ull);
+        atomicAdd(&sm.dlv_bytes, (unsigned long long)r->bytes * (strided ? 7ull : 4ull));
         return true;
       }
       // list full: create this one at once with the default tiling
@@ -2159,12 +2168,18 @@ struct Ctl {
   __device__ void make_deferred() {
     const int n = sm.ndlv < kMaxDeferred ? sm.ndlv : kMaxDeferred;
     if (n == 0) return;
+    // every delivery rounds its tile count up, so the weighted bytes are
+    // spread over the movers left after one tile each: no mover gets a
+    // second tile of this phase's work
     const int64_t movers = P.nctas > 1 ? P.nctas - 1 : 1;
-    const int64_t hint = (int64_t)((sm.dlv_bytes + (unsigned long long)movers - 1) / (unsigned long long)movers);
+    const int64_t share = movers > 2 * (int64_t)n ? movers - n : (movers + 1) / 2;
+    const unsigned long long hw = (sm.dlv_bytes + (unsigned long long)share - 1) / (unsigned long long)share;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t sv = sm.dlv_s[i], rref = sm.dlv_r[i];
+      const uint64_t sv = sm.dlv_s[i], rv = sm.dlv_r[i];
       const bool from_stage = (sv >> 63) != 0;
       const uint64_t sref = sv & ~(1ull << 63);
+      const uint64_t rref = rv & ~kDlvStrided;
+      const int64_t hint = (int64_t)(hw / ((rv & kDlvStrided) ? 7ull : 4ull));
       if (create_deliver(sref, rref, from_stage, true, hint)) continue;
       // undo: the send is reached again (or still staged) and the receive unscheduled
       DOp* r = op_ref(P, rref);
@@ -2294,12 +2309,17 @@ struct Ctl {
       T->nout = nout;
       T->cop = cop;
       T->gcount = n;
-      // about four tiles per engine CTA, within [tile_bytes*8/R, 256 KiB] per rank
+      // k tiles per mover, k the fewest that keeps a tile within 256 KiB per
+      // rank: the tile count never exceeds a whole multiple of the movers (one
+      // tile more than that would make a few movers run a round of their own);
+      // never below tile_bytes*8/R per rank
       const int64_t tmin = P.tile_bytes / (es * (P.nranks < 8 ? 1 : P.nranks / 8));
       const int64_t tmax = ((int64_t)256 << 10) / es;
-      int64_t tile = total / (4 * (int64_t)(P.nctas > 0 ? P.nctas : 1));
-      tile = tile < tmin ? tmin : (tile > tmax ? tmax : tile);
-      tile = tile < 256 ? 256 : (tile & ~(int64_t)255);
+      const int64_t movers = P.nctas > 1 ? P.nctas - 1 : 1;
+      const int64_t per = (total + movers * tmax - 1) / (movers * tmax);
+      int64_t tile = (total + per * movers - 1) / (per * movers);
+      tile = tile < tmin ? tmin : tile;
+      tile = tile < 256 ? 256 : ((tile + 255) & ~(int64_t)255);
       T->tile = tile;
       T->ntiles = (uint32_t)((total + tile - 1) / tile);
       T->nr = (uint32_t)P.nranks;

@@ -4,8 +4,8 @@ benchmark times.
 * Ring exchange (8 ranks, axpy n = 2^24, messages log-uniform 4 KB - 64 MB,
   half vector-typed): three full-size steps through drain passes, every
   buffer compared byte for byte with the oracle.
-* Enqueued allreduce among 16 ranks at n = 2^26 (fp32, fixed and tree
-  order) and n = 2^25 (int64): every rank's output must be identical (a
+* Enqueued allreduce among 16 ranks at n = 2^26 and 2^28 (fp32, fixed and tree
+  order) and n = 2^25 and 2^27 (int64): every rank's output must be identical (a
   property at any size), and sampled elements (both ends, tile edges, random
   positions) must equal what the oracle computes for those elements' inputs:
   bit-exact for int64 and the fixed order, within |y - s| <= 1e-6 * sum|x|
@@ -82,7 +82,8 @@ def _oracle_allreduce(cols, dt, mode):
 
 
 @pytest.mark.parametrize("dt_name,lg,mode", [("f32", 26, "fixed"), ("f32", 26, "tree"),
-                                             ("int64", 25, "fixed")])
+                                             ("int64", 25, "fixed"), ("f32", 28, "fixed"),
+                                             ("int64", 27, "fixed")])
 def test_allreduce_full_size_sampled(dt_name, lg, mode):
     torch = _torch()
     from paper_2208_13707_gb300 import mpx
@@ -94,7 +95,9 @@ def test_allreduce_full_size_sampled(dt_name, lg, mode):
         x = torch.randn((R, n), device=dev, generator=g, dtype=torch.float32)
         dt, tdt, npdt = mpx.FLOAT, T_FLOAT, np.float32
     else:
-        x = torch.round(torch.randn((R, n), device=dev, generator=g) * 2.0 ** 40).to(torch.int64)
+        x = torch.empty((R, n), device=dev, dtype=torch.int64)
+        for r in range(R):  # one rank at a time: small temporaries at 2^27 elements
+            x[r].copy_(torch.round(torch.randn(n, device=dev, generator=g) * 2.0 ** 40).to(torch.int64))
         dt, tdt, npdt = mpx.INT64, T_INT64, np.int64
     y = torch.zeros_like(x)
     cfg = mpx.mpx_world_config_init()
