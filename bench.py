@@ -64,11 +64,11 @@ def whole_job(seconds, units, dist=None, device="cpu"):
 
 # DRAM traffic of the engine pass, from one ncu capture of the ring steps
 # (profiles/engine_ring_exchange_launches.md: dram__bytes_read.sum +
-# dram__bytes_write.sum over six passes = 0.83 of their algorithmic bytes).
+# dram__bytes_write.sum over six passes = 0.82 of their algorithmic bytes).
 # It describes the engine kernel as it was when captured: the source's hash is
 # recorded, and a changed kernel reports no traffic.
 RING_TRAFFIC_RATIO = 0.82
-RING_TRAFFIC_ENGINE_SHA1 = "bf331546ec75db5f"
+RING_TRAFFIC_ENGINE_SHA1 = "6d0c05edde86c229"
 
 
 def ring_traffic(algorithmic_bytes_per_launch):
@@ -153,7 +153,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 class RingBench:
     def __init__(self, ranks=RANKS, n=N_AXPY, max_bytes=MAX_BYTES, tile_bytes=None, engine_ctas=0,
-                 bulk_min=None, mover_schedule=0, persistent=False, plain=False):
+                 bulk_min=None, mover_schedule=0, persistent=False, plain=False, engine_threads=256):
         import torch
         from paper_2208_13707_gb300 import mpx
         self.torch, self.mpx = torch, mpx
@@ -179,6 +179,7 @@ class RingBench:
         cfg.max_comms = 2
         cfg.queue_slots = 1024
         cfg.engine_ctas = engine_ctas
+        cfg.engine_threads = engine_threads
         if tile_bytes:
             cfg.tile_bytes = tile_bytes
         if bulk_min is not None:
@@ -537,6 +538,98 @@ def batching_full(steps=16, warmup=3, nmsg=65536, schedule=None):
     return out
 
 
+def _batch_engine(prog, over, steps, warmup, nmsg, payload):
+    """Persistent engine with batch submission: steps back to back, one wait."""
+    from traffic import gpu
+    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=120, cfg_over=over)
+    try:
+        for _ in range(warmup):
+            r.enqueue()
+        assert r.finish(), "warm-up steps did not finish"
+        r.mpx.mpx_world_stop(r.world, 10000)
+        ctr0 = r.mpx.mpx_world_get_counters(r.world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r.enqueue()
+        t_enq = time.perf_counter() - t0
+        ok = r.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = r.errors()
+        assert ok and werr == 0 and not any(serr), "batched steps failed"
+        r.mpx.mpx_world_stop(r.world, 10000)  # phase times are summed when the engine exits
+        ctr = [a - b for a, b in zip(r.mpx.mpx_world_get_counters(r.world), ctr0)]
+    finally:
+        r.close()
+    phases = {k: ctr[12 + i] / 1e6 for i, k in enumerate(
+        ["ingest", "rounds", "finished_tasks", "completion", "scheduling", "decisions", "own_moves"])}
+    return {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
+            "ms_per_step": 1e3 * dt / steps, "host_enqueue_ms_per_step": 1e3 * t_enq / steps,
+            "payload_gbs": 2 * payload * steps / dt / 1e9,
+            "rounds": int(ctr[6]), "ticks": int(ctr[1]), "staged_sends": int(ctr[5]),
+            "ingest_us_per_descriptor": 1e3 * phases["ingest"] / (len(prog.ops) * steps),
+            "control_ms_by_phase": phases,
+            "control_ms_split": {k: ctr[19 + i] / 1e6 for i, k in enumerate(
+                ["advance", "matching", "collectives", "stream_scheduling", "reduce_and_stage"])}}
+
+
+def _batch_graph(prog, over, steps, warmup, nmsg, payload):
+    """The same step recorded once and replayed as a CUDA graph."""
+    from traffic import gpu
+    gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120, cfg_over=over)
+    try:
+        for _ in range(warmup):
+            gr.enqueue()
+        assert gr.finish(), "graph warm-up did not finish"
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            gr.enqueue()
+        t_enq = time.perf_counter() - t0
+        ok = gr.finish()
+        dt = time.perf_counter() - t0
+        serr, werr = gr.errors()
+        assert ok and werr == 0 and not any(serr), "graph steps failed"
+    finally:
+        gr.close()
+    return {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
+            "ms_per_step": 1e3 * dt / steps, "host_launch_ms_per_step": 1e3 * t_enq / steps,
+            "payload_gbs": 2 * payload * steps / dt / 1e9}
+
+
+def ring_placement(steps, warmup, nmsg=65536, schedule=None):
+    """Where the submission rings live: the small-message batching step
+    (persistent engine and recorded graph) with rings, waitall lists and
+    stream control lines in pinned host memory, then in device memory that
+    the host writes through the coherent link.  Reports msgs/s, the host's
+    enqueue time and the engine's ingest time per descriptor for each."""
+    from paper_2208_13707_gb300 import mpx
+    from traffic import gen
+    prog = gen.batching(nranks=64, streams_per_rank=4, nmsg=nmsg, max_bytes=64 << 10,
+                        laminar=True, seed=gen.SEED_BASE + 2)
+    payload = int(prog.meta["payload_bytes"])
+    out = {"messages_per_step": nmsg, "descriptors_per_step": int(len(prog.ops))}
+    for name, where in (("host", mpx.RINGS_HOST), ("device", mpx.RINGS_DEVICE)):
+        over = {"ring_slots": 4096, "queue_slots": 4096, "ring_placement": where}
+        over.update(schedule or {})
+        try:
+            e = _batch_engine(prog, over, steps, warmup, nmsg, payload)
+            g = _batch_graph(prog, over, steps, warmup, nmsg, payload)
+        except mpx.MpxError as err:
+            if err.code != mpx.ERR_UNSUPPORTED:
+                raise
+            # cudaDevAttr 89 ConcurrentManagedAccess, 101 DirectManagedMemAccessFromHost,
+            # 88 PageableMemoryAccess, 100 PageableMemoryAccessUsesHostPageTables
+            attrs = {k: mpx.device_attr(v) for k, v in (
+                ("concurrent_managed_access", 89), ("direct_managed_mem_access_from_host", 101),
+                ("pageable_memory_access", 88), ("pageable_memory_access_uses_host_page_tables", 100))}
+            out[name] = {"unavailable": "no direct host access to managed device memory", "device_attrs": attrs}
+            continue
+        out[name] = {"engine_msgs_per_s": e["value"], "graph_msgs_per_s": g["value"],
+                     "host_enqueue_ms_per_step": e["host_enqueue_ms_per_step"],
+                     "ingest_us_per_descriptor": e["ingest_us_per_descriptor"],
+                     "ingest_ms_per_step": e["control_ms_by_phase"]["ingest"] / steps}
+    return out
+
+
 def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     """Small-message batching: 64 ranks x 4 MPIX streams (four stream comms),
     `nmsg` messages per step with uniform sources, destinations and tags,
@@ -558,54 +651,8 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     over = {"ring_slots": 4096, "queue_slots": 4096}
     over.update(schedule or {})
     out["schedule"] = dict(schedule or {})
-    r = gpu.BatchRunner(prog, mode="persistent", epoch_barrier=True, timeout_s=120, cfg_over=over)
-    try:
-        for _ in range(warmup):
-            r.enqueue()
-        assert r.finish(), "warm-up steps did not finish"
-        r.mpx.mpx_world_stop(r.world, 10000)
-        ctr0 = r.mpx.mpx_world_get_counters(r.world)
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            r.enqueue()
-        t_enq = time.perf_counter() - t0
-        ok = r.finish()
-        dt = time.perf_counter() - t0
-        serr, werr = r.errors()
-        assert ok and werr == 0 and not any(serr), "batched steps failed"
-        r.mpx.mpx_world_stop(r.world, 10000)  # phase times are summed when the engine exits
-        ctr = [a - b for a, b in zip(r.mpx.mpx_world_get_counters(r.world), ctr0)]
-    finally:
-        r.close()
-    out["engine"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
-                     "ms_per_step": 1e3 * dt / steps, "host_enqueue_ms_per_step": 1e3 * t_enq / steps,
-                     "payload_gbs": 2 * payload * steps / dt / 1e9,
-                     "rounds": int(ctr[6]), "ticks": int(ctr[1]), "staged_sends": int(ctr[5]),
-                     "control_ms_by_phase": {k: ctr[12 + i] / 1e6 for i, k in enumerate(
-                         ["ingest", "rounds", "finished_tasks", "completion", "scheduling",
-                          "decisions", "own_moves"])},
-                     "control_ms_split": {k: ctr[19 + i] / 1e6 for i, k in enumerate(
-                         ["advance", "matching", "collectives", "stream_scheduling",
-                          "reduce_and_stage"])}}
-    # the same step recorded once and replayed as a CUDA graph
-    gr = gpu.BatchRunner(prog, mode="graph", timeout_s=120, cfg_over=over)
-    try:
-        for _ in range(warmup):
-            gr.enqueue()
-        assert gr.finish(), "graph warm-up did not finish"
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            gr.enqueue()
-        t_enq = time.perf_counter() - t0
-        ok = gr.finish()
-        dt = time.perf_counter() - t0
-        serr, werr = gr.errors()
-        assert ok and werr == 0 and not any(serr), "graph steps failed"
-    finally:
-        gr.close()
-    out["graph"] = {"value": nmsg * steps / dt, "unit": "msgs/s", "steps": steps,
-                    "ms_per_step": 1e3 * dt / steps, "host_launch_ms_per_step": 1e3 * t_enq / steps,
-                    "payload_gbs": 2 * payload * steps / dt / 1e9}
+    out["engine"] = _batch_engine(prog, over, steps, warmup, nmsg, payload)
+    out["graph"] = _batch_graph(prog, over, steps, warmup, nmsg, payload)
     q = gpu.BatchRunner(prog, mode="plain", timeout_s=300)
     try:
         q.step()
@@ -912,14 +959,14 @@ def autotune_ring():
     from paper_2208_13707_gb300 import autotune as at
     sizes = [ring_message(step, 0, d)[0] for step in range(8) for d in (0, 1)]
     grid = {"tile_bytes": (64 << 10, 256 << 10, 1 << 20), "bulk_min_bytes": (0, 32 << 10),
-            "engine_ctas": (0,), "engine_threads": (256,), "mover_schedule": (0, 1)}
+            "engine_ctas": (0,), "engine_threads": (256, 512), "mover_schedule": (0, 1)}
     r = at.autotune(sizes, nranks=RANKS, rounds=3, grid=grid)
     best = [t for t in r.table if t["config"] == r.best][0]
     return {"best": r.best, "best_gbs": best["gbs"], "trials": len(r.table),
             "table": [{"config": t["config"], "gbs": t["gbs"]} for t in r.table]}
 
 
-def autotune_report():
+def autotune_report(mixes=("small_8B_64KB", "large_4KB_64MB")):
     """Autotuner on two samples of the workloads' message mixes: small
     (log-uniform 8 B - 64 KB) and large (log-uniform 4 KB - 64 MB, the ring
     exchange's range); best configuration against the default one."""
@@ -930,6 +977,8 @@ def autotune_report():
     rng = np.random.default_rng(0x220813707)
     out = {}
     for name, lo, hi, n in (("small_8B_64KB", 8, 64 << 10, 512), ("large_4KB_64MB", 4096, 64 << 20, 16)):
+        if name not in mixes:
+            continue
         sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.int64).tolist()
         r = at.autotune(sizes, nranks=8, rounds=3, grid=grid)
         default = [t for t in r.table if t["config"] == {"tile_bytes": 64 << 10, "bulk_min_bytes": 32 << 10,
@@ -968,6 +1017,8 @@ def profile_steps(kind, launches=3, log2n=24):
         return {"profile_steps": kind, "launches": launches, "messages": 65536}
     if kind == "copy":
         return profile_copy(launches)
+    if kind == "control":
+        return profile_control(launches)
     R, n = 16, 1 << log2n
     dev = torch.device("cuda")
     cfg = mpx.mpx_world_config_init()
@@ -1058,6 +1109,76 @@ def profile_copy(launches=3, nbytes=1 << 30):
     return {"profile_steps": "copy", "launches": launches, "bytes": nbytes}
 
 
+def profile_control(launches=6):
+    """Drain passes with nothing to do on a one-CTA engine (the control CTA
+    alone): each pass ingests, runs its ticks and exits, so a warp-stall
+    capture sees only the control loop.  No stream waits exist."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mpx.ENGINE_DRAIN
+    cfg.max_streams = 4
+    cfg.engine_ctas = 1
+    w = mpx.mpx_world_create(2, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(3)]
+    ms = [mpx.mpx_stream_create(w, r, raw[r]) for r in range(2)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    es = torch.cuda.ExternalStream(raw[2])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(es)
+    for _ in range(launches):
+        mpx.mpx_world_progress(w, raw[2])
+    ev[1].record(es)
+    es.synchronize()
+    ok = mpx.mpx_world_get_error(w) == 0
+    for c in comm:
+        mpx.mpx_comm_free(c)
+    for s_ in ms:
+        mpx.mpx_stream_free(s_)
+    mpx.mpx_world_free(w)
+    for h in raw:
+        mpx.mpx_cuda_stream_destroy(h)
+    assert ok, "empty passes failed"
+    return {"profile_steps": "control", "launches": launches,
+            "us_per_pass": ev[0].elapsed_time(ev[1]) * 1e3 / launches}
+
+
+def trace_ring(steps=4, warmup=3, max_records=200_000, tile_bytes=None):
+    """The timeline of ring-exchange drain passes: per pass its CUDA-event
+    duration, when the first mover tile started and the last one ended, and
+    each control tick (start and duration in microseconds from the pass's
+    first record, flags: 1 ingest, 2 new events, 4 completion scan; tasks
+    outstanding; tasks made).  Needs MPX_ENGINE_TRACE; sets it when unset."""
+    import os
+    os.environ.setdefault("MPX_ENGINE_TRACE", str(max_records))
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    b = RingBench(tile_bytes=tile_bytes)
+    b.prepare(warmup + steps)
+    out = []
+    try:
+        for k in range(warmup + steps):
+            e = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            b.enqueue_step(k, None, None, e)
+            b.sync_all()
+            t = mpx.engine_trace(b.world, max_records).astype(np.int64)
+            if k < warmup or len(t) == 0:
+                continue
+            tick = (t[:, 2] >> 32) & 0xFFFFFFFF == 0xFFFFFFFF
+            t0 = int(t[:, 0].min())
+            tl = t[~tick]
+            out.append({
+                "step": k, "pass_us": round(e[0].elapsed_time(e[1]) * 1e3, 1),
+                "tiles": int(len(tl)),
+                "tiles_first_start_us": round((int(tl[:, 0].min()) - t0) / 1e3, 1) if len(tl) else None,
+                "tiles_last_end_us": round((int(tl[:, 1].max()) - t0) / 1e3, 1) if len(tl) else None,
+                "ticks": [[round((int(r[0]) - t0) / 1e3, 1), round((int(r[1]) - int(r[0])) / 1e3, 1),
+                           int(r[3]) & 7, (int(r[3]) >> 8) & 0xFFFFFF, int(r[3]) >> 32] for r in t[tick]]})
+    finally:
+        b.close()
+    return out
+
+
 def copy_sweep(sizes_mb=(1, 16, 64, 256, 1024), reps=4):
     """One message per engine pass, per layout and size: the movers' bandwidth
     with the pass's fixed cost included.  Prints one JSON line per case."""
@@ -1125,6 +1246,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-bytes", type=int, default=0)
     ap.add_argument("--engine-ctas", type=int, default=0)
+    ap.add_argument("--engine-threads", type=int, default=256,
+                    help="threads per engine CTA when the schedule is given on the command line")
+    ap.add_argument("--bulk-min-bytes", type=int, default=-1,
+                    help="bulk-copy threshold when the schedule is given on the command line (-1: default)")
+    ap.add_argument("--mover-schedule", type=int, default=0, choices=[0, 1])
     ap.add_argument("--copy-sweep", action="store_true",
                     help="single-message engine passes per layout and size (diagnostic lines, no benchmark line)")
     ap.add_argument("--batch-msgs", type=int, default=65536,
@@ -1142,6 +1268,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10_000_000,
                     help="requests of the serving measurement's engine run (0 = skip serving)")
     ap.add_argument("--no-tiny", action="store_true", help="skip the tiny-pairs (C1) measurement")
+    ap.add_argument("--no-ring-placement", action="store_true",
+                    help="skip the host- vs device-memory submission ring comparison")
+    ap.add_argument("--ring-placement-only", action="store_true",
+                    help="print only the host- vs device-memory submission ring comparison")
     ap.add_argument("--tiny-only", action="store_true", help="print only the tiny-pairs (C1) measurement")
     ap.add_argument("--serving-only", action="store_true", help="print only the serving measurement")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner report")
@@ -1149,11 +1279,14 @@ def main():
                     help="skip the host-thread message-rate experiment")
     ap.add_argument("--host-msgrate-only", action="store_true",
                     help="print only the host-thread message-rate experiment (no GPU)")
-    ap.add_argument("--profile-steps", choices=["allreduce", "batching", "copy"], default=None,
+    ap.add_argument("--profile-steps", choices=["allreduce", "batching", "copy", "control"], default=None,
                     help="profile-safe recorded steps for a kernel profiler (no benchmark line)")
     ap.add_argument("--profile-log2n", type=int, default=24,
                     help="elements per rank (log2) of the profiled allreduce step")
     ap.add_argument("--autotune-only", action="store_true", help="print only the autotuner report")
+    ap.add_argument("--trace-ring", action="store_true",
+                    help="print the control-tick and mover-tile timeline of ring-exchange drain passes "
+                         "(one JSON line per step; diagnostic, no benchmark line)")
     ap.add_argument("--profile-safe", action="store_true",
                     help="run the steps in an order that a kernel-serialising profiler can replay "
                          "(no stream waits); prints no benchmark line")
@@ -1185,6 +1318,10 @@ def main():
     if args.autotune_only:
         print(json.dumps({"autotune": autotune_report()}), flush=True)
         return
+    if args.trace_ring:
+        for rec in trace_ring(steps=args.steps, warmup=args.warmup, tile_bytes=args.tile_bytes or None):
+            print(json.dumps(rec), flush=True)
+        return
     if args.tiny_only:
         print(json.dumps({"tiny": tiny_bench()}), flush=True)
         return
@@ -1202,20 +1339,28 @@ def main():
     if args.batching_full_only:
         print(json.dumps({"batching_full": batching_full()}), flush=True)
         return
-    if args.batching_only:
-        print(json.dumps({"batching_small": batching_small(args.batch_steps, args.warmup,
-                                                           args.batch_msgs)}), flush=True)
+    if args.batching_only or args.ring_placement_only:
+        # the autotuner's choice for the small-message mix, as in the full run
+        small = None if args.no_autotune else autotune_report(("small_8B_64KB",))["small_8B_64KB"]["best"]
+        if args.batching_only:
+            print(json.dumps({"batching_small": batching_small(args.batch_steps, args.warmup,
+                                                               args.batch_msgs, schedule=small)}), flush=True)
+        else:
+            print(json.dumps({"ring_placement": ring_placement(args.batch_steps, args.warmup,
+                                                               args.batch_msgs, schedule=small)}), flush=True)
         return
     if dist is not None:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     # the copy schedule: the autotuner's choice for this workload's message mix
     # (sizes of the ring's own messages), unless given on the command line
-    sched = {"tile_bytes": args.tile_bytes or None, "engine_ctas": args.engine_ctas, "bulk_min": None,
-             "mover_schedule": 0}
+    sched = {"tile_bytes": args.tile_bytes or None, "engine_ctas": args.engine_ctas,
+             "bulk_min": None if args.bulk_min_bytes < 0 else args.bulk_min_bytes,
+             "mover_schedule": args.mover_schedule, "engine_threads": args.engine_threads}
     ring_tune = None
     if not args.no_autotune and not args.tile_bytes and not args.engine_ctas and not args.profile_safe:
         ring_tune = autotune_ring()
         sched = {"tile_bytes": ring_tune["best"]["tile_bytes"], "engine_ctas": ring_tune["best"]["engine_ctas"],
+                 "engine_threads": ring_tune["best"]["engine_threads"],
                  "bulk_min": ring_tune["best"]["bulk_min_bytes"],
                  "mover_schedule": ring_tune["best"]["mover_schedule"]}
     b = RingBench(**sched)
@@ -1263,6 +1408,8 @@ def main():
     small_sched = tune["small_8B_64KB"]["best"] if tune else None
     batching = (batching_small(args.batch_steps, args.warmup, args.batch_msgs, schedule=small_sched)
                 if args.batch_msgs else None)
+    placement = (ring_placement(args.batch_steps, args.warmup, args.batch_msgs, schedule=small_sched)
+                 if args.batch_msgs and not args.no_ring_placement else None)
     batching_1m = None if args.no_batching_full else batching_full(
         schedule=tune["large_4KB_64MB"]["best"] if tune else None)
     c4 = None
@@ -1305,6 +1452,7 @@ def main():
                 "persistent_engine": persistent,
                 "plain_path": plain,
                 "batching_small": batching,
+                "ring_placement": placement,
                 "batching_full": batching_1m,
                 "allreduce_and_halo": c4,
                 "serving": serve,

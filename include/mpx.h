@@ -127,6 +127,15 @@ enum {
                               moves all their tiles (no shared claim point; small messages) */
 };
 
+/* where the submission rings live (mpx_world_config_t.ring_placement) */
+enum {
+  MPX_RINGS_HOST = 0,   /* pinned host memory: the host writes locally, the engine reads across
+                           the chip-to-chip link */
+  MPX_RINGS_DEVICE = 1  /* device memory that the host writes through the coherent chip-to-chip
+                           mapping (managed memory kept on the device); needs a device on which
+                           the host can access managed memory directly, else MPX_ERR_UNSUPPORTED */
+};
+
 /* engine modes (mpx_world_config_t.engine_mode) */
 enum {
   MPX_ENGINE_PERSISTENT = 0, /* one cooperative engine kernel stays resident; relaunched on demand */
@@ -163,7 +172,9 @@ typedef struct {
   int32_t queue_slots;     /* matching queue capacity per (comm, rank) domain, power of two (default 4096) */
   int32_t task_slots;      /* engine task ring, power of two (default 16384) */
   int32_t engine_ctas;     /* engine CTAs; 0 = one per SM */
-  int32_t engine_threads;  /* threads per engine CTA, multiple of 32, <= 512 (default 256) */
+  int32_t engine_threads;  /* threads per engine CTA, multiple of 32, <= 512 (default 256); a
+                              PERSISTENT engine uses at most as many as leave half of each SM's
+                              registers to other kernels (256 in this build) */
   int32_t tile_bytes;      /* copy tile, multiple of 16 (default 65536) */
   int32_t bulk_min_bytes;  /* contiguous tiles at least this large move by TMA bulk copy (default 32768; 0 = never) */
   int32_t reduce_mode;     /* default allreduce order, MPX_REDUCE_* (default FIXED) */
@@ -173,15 +184,22 @@ typedef struct {
   int64_t watchdog_ns;     /* pending work with no progress this long fails with MPX_ERR_TIMEOUT (default 10 s) */
   int64_t idle_exit_ns;    /* persistent engine exits after this long with nothing to do (default 100 ms) */
   int64_t stage_delay_ns;  /* a stalled stream's undeliverable send is staged after this long (default 20 us) */
+  int32_t ring_placement;  /* MPX_RINGS_* : submission rings, waitall lists and stream control
+                              lines (default HOST) */
+  int32_t reserved0;       /* 0 */
 } mpx_world_config_t;
 
 /* Fill *cfg with defaults, then apply MPX_* environment overrides. */
 int mpx_world_config_init(mpx_world_config_t* cfg);
 
 /* Create a world of `nranks` virtual ranks on the current CUDA device.
- * cfg may be NULL (defaults).  Allocates rings and control words in pinned
- * host memory and the engine state, matching queues and staging arena in
- * device memory.  Errors: MPX_ERR_ARG, MPX_ERR_NO_MEM, MPX_ERR_CUDA. */
+ * cfg may be NULL (defaults).  Allocates the submission rings, waitall lists
+ * and stream control words where cfg->ring_placement says (pinned host
+ * memory by default), the world control words in pinned host memory, and the
+ * engine state, matching queues and staging arena in device memory.
+ * Errors: MPX_ERR_ARG, MPX_ERR_NO_MEM, MPX_ERR_CUDA, MPX_ERR_UNSUPPORTED
+ * (MPX_RINGS_DEVICE on a device without direct host access to managed
+ * memory). */
 int mpx_world_create(int nranks, const mpx_world_config_t* cfg, mpx_world_t* world);
 
 /* Stop the engine and free everything.  MPX_ERR_PENDING if streams or
@@ -704,24 +722,22 @@ int mpx_get_count(const mpx_status_t* status, mpx_datatype_t datatype, int64_t* 
 int mpx_saxpy_enqueue(int64_t n, float a, const float* x, float* y, mpx_cuda_stream_t stream);
 
 /* Staged point-to-point copy that allocates nothing.  The paper has no
- * counterpart; it is for callers that cannot call cudaMalloc: code that runs
- * while a stream is being captured into a CUDA graph (an allocation there is
- * not recorded, and cudaMalloc/cudaFree may synchronize the device), code on
- * latency-critical paths that must not risk an implicit device-wide
- * synchronization, and processes whose device memory is entirely carved up
- * in advance.  In stream order on `stream`, the message described by
- * (sendbuf, sendcount, sendtype) is packed into a staging area and unpacked
- * into (recvbuf, recvcount, recvtype); like a matched send/receive it
- * delivers min(message, receive capacity) bytes, and *bytes_delivered (host
- * memory, may be NULL) is set to that number before the call returns.
- * The staging area is a 16 MiB array in the library's device memory (a
- * file-scope __device__ array that every GPU which loads the library holds
- * until the process exits); the call returns MPX_ERR_NO_MEM when more than
- * 16 MiB would be delivered, and allocates nothing itself.  Each device has
- * its own copy of the array.  Its device address is looked up once per
- * device (cudaGetSymbolAddress, with that device current) by mpx_world_create
- * or by the first call on the device, whichever comes first; make that first
- * call before any stream capture.  The address is kept for the life of the
+ * counterpart; it is for callers that cannot call cudaMalloc: code on
+ * latency-critical paths that must not risk the implicit device-wide
+ * synchronization an allocation or a free may bring, and processes whose
+ * device memory is entirely carved up in advance.  In stream order on
+ * `stream`, the message described by (sendbuf, sendcount, sendtype) is
+ * packed into a staging area and unpacked into (recvbuf, recvcount,
+ * recvtype); like a matched send/receive it delivers min(message, receive
+ * capacity) bytes, and *bytes_delivered (host memory, may be NULL) is set to
+ * that number before the call returns.  The staging area is a 16 MiB array
+ * in the library's device memory (a file-scope __device__ array that every
+ * GPU which loads the library holds until the process exits); the call
+ * returns MPX_ERR_NO_MEM when more than 16 MiB would be delivered, and
+ * allocates nothing itself.  Each device has its own copy of the array.  Its
+ * device address is looked up once per device (cudaGetSymbolAddress, with
+ * that device current) by mpx_world_create or by the first call on the
+ * device, whichever comes first.  The address is kept for the life of the
  * process: after a cudaDeviceReset it is stale, and the function must not be
  * called again.  Every call on one device shares that device's array, which
  * keeps the last call's bytes, so calls that overlap on the same device (on

@@ -249,6 +249,11 @@ struct CtaShared {
   uint64_t r0;              // control: task_retire at the start of the retirement scan
   uint64_t own_next;        // mover (per-CTA schedule): next task id this CTA owns
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
+  // control: receives listed (P.cand) for this tick's delivery scheduling;
+  // a failed task creation asks the next tick for a scan of every stream
+  uint32_t ncand;
+  int32_t sched_retry;
+  int32_t sched_all;      // control: this tick's scheduling scans every stream in full
   // control: its own copies of the task-ring words only it writes (task_alloc,
   // task_retire, cq_head); the global words are written through for the movers
   uint64_t c_alloc, c_retire, c_cqh;
@@ -1289,6 +1294,20 @@ struct Ctl {
     s->partner = rref;
     atomicOr(&r->pflags, PF_MATCHED);
     atomicOr(&s->pflags, PF_MATCHED);
+    push_cand(rref);  // deliverable now if both streams have reached their operations
+  }
+
+  // List receive rref for this tick's delivery scheduling (once per tick).
+  __device__ void push_cand(uint64_t rref) {
+    DOp* r = op_ref(P, rref);
+    if (atomicOr(&r->pflags, PF_CAND) & PF_CAND) return;
+    const uint32_t k = atomicAdd(&sm.ncand, 1u);
+    if ((int64_t)k < P.cand_cap) {
+      P.cand[k] = rref;
+    } else {  // list full: every stream is scanned next tick
+      atomicAnd(&r->pflags, ~PF_CAND);
+      sm.sched_retry = 1;
+    }
   }
 
   // One post, in key order (warp-cooperative).
@@ -1676,6 +1695,7 @@ struct Ctl {
     Task* T = task_new(id);
     if (!T) {
       atomicAnd(&r->pflags, ~PF_SCHED);
+      sm.sched_retry = 1;  // ring full: look again next tick
       return false;
     }
     fill_copy(T, src, dst, bytes, tile_hint);
@@ -2161,6 +2181,72 @@ struct Ctl {
     __syncwarp();
   }
 
+  // Whether stream g's stall has lasted long enough for its unmatched-or-
+  // unreached sends to be staged (the condition schedule_op applies per send).
+  __device__ bool staging_due(int g, int64_t now) const {
+    const SState& S = ss[g];
+    if (S.stall_t0 == 0) return false;
+    const int64_t stalled = now - S.stall_t0;
+    return stalled >= P.stage_delay_ns &&
+           (now - sm.last_prog >= P.stage_delay_ns || stalled >= 50 * P.stage_delay_ns);
+  }
+
+  // Event-driven scheduling: a receive's delivery becomes possible only when
+  // it is matched (pair lists it), when its stream reaches it, when its
+  // send's stream reaches the send, or when the send lands in the staging
+  // arena (complete_tasks lists it).  This scan covers the two reach events:
+  // the operations stream g reached since the last scan list their
+  // receives; the others are not looked at again.
+  __device__ void reach_scan(int g) {
+    SState& S = ss[g];
+    const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+    uint64_t seq = S.sreach + 1 > S.retire + 1 ? S.sreach + 1 : S.retire + 1;
+    if (seq > lim) return;
+    uint64_t pf = seq;
+    for (; seq <= lim; ++seq) {
+      if (seq >= pf) pf = prefetch_ops(g, seq, lim);
+      reach_op(g, seq);
+    }
+    S.sreach = lim;
+  }
+
+  __device__ void reach_op(int g, uint64_t seq) {
+    const DOp* o = op_at(P, g, seq);
+    const int32_t f = o->pflags;
+    if (!(f & PF_MATCHED) || (f & PF_SCHED)) return;
+    const uint32_t k = kw_kind(o->d.kw);
+    if (is_recv(k)) push_cand(make_ref(g, seq));
+    else if (is_send(k)) push_cand(o->partner);
+  }
+
+  // The same with one warp per stream: lanes take 32 operations at a time.
+  __device__ void reach_scan_warp(int g) {
+    const int lane = threadIdx.x & 31;
+    SState& S = ss[g];
+    const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+    const uint64_t from = S.sreach + 1 > S.retire + 1 ? S.sreach + 1 : S.retire + 1;
+    for (uint64_t seq = from + (uint64_t)lane; seq <= lim; seq += 32) reach_op(g, seq);
+    __syncwarp();
+    if (lane == 0 && from <= lim) S.sreach = lim;
+    __syncwarp();
+  }
+
+  // Schedule the listed receives (thread per receive); a receive its own
+  // stream has not reached yet is listed again when it is.
+  __device__ void process_cands(int64_t now) {
+    const int64_t n = (int64_t)sm.ncand < P.cand_cap ? (int64_t)sm.ncand : P.cand_cap;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t rref = P.cand[i];
+      const int g = ref_stream(rref);
+      const uint64_t seq = ref_seq(rref);
+      atomicAnd(&op_ref(P, rref)->pflags, ~PF_CAND);
+      const SState& S = ss[g];
+      const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+      if (seq <= S.retire || seq > lim) continue;
+      schedule_op(g, seq, now);
+    }
+  }
+
   // Create the deliveries the scheduling scan deferred, every one with the
   // tile size that spreads the phase's bytes evenly over the movers.  A
   // delivery whose task cannot be created now (ring full) is undone and its
@@ -2186,6 +2272,7 @@ struct Ctl {
       if (!from_stage) atomicAnd(&op_ref(P, sref)->pflags, ~PF_SCHED);
       atomicAnd(&r->pflags, ~PF_SCHED);
       atomicMin((unsigned long long*)&ss[ref_stream(rref)].sched, (unsigned long long)ref_seq(rref));
+      sm.sched_retry = 1;
     }
   }
 
@@ -2356,8 +2443,9 @@ struct Ctl {
         DOp* s = op_ref(P, T->ref_s);
         touch(ref_stream(T->ref_s));
         if (T->action == A_STAGE) {
-          atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
+          const int32_t f = atomicOr(&s->pflags, PF_STAGED | PF_COMPLETE);
           atomicAnd(&s->pflags, ~(PF_SCHED | PF_STAGING));
+          if (f & PF_MATCHED) push_cand(s->partner);  // its receive can take it from the arena
         } else {
           DOp* r = op_ref(P, T->ref_r);
           touch(ref_stream(T->ref_r));
@@ -2498,6 +2586,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   if (tid == 0) {
     C.round = (int64_t)sh->round;
     sm.nstage = 0;
+    sm.ncand = 0;
+    sm.sched_retry = 0;
   }
   __syncthreads();
   C.round = (int64_t)*(volatile uint64_t*)&sh->round;
@@ -2738,16 +2828,45 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         C.task_phase_begin();
         sm.ndlv = 0;
         sm.dlv_bytes = 0;
+        // every stream is scanned in full on the first tick of a launch, every
+        // 64th tick, and after a tick that could not create a listed task
+        sm.sched_all = (ticks & 63) == 0 || sm.sched_retry != 0;
+        sm.sched_retry = 0;
       }
       __syncthreads();
       mark(-1);
+      const bool sched_all = sm.sched_all != 0;
       if (warp_streams) {
         const int warp = tid >> 5, nw = blockDim.x >> 5;
-        for (int g = warp; g < P.max_streams; g += nw) C.stream_schedule_warp(g, now);
+        for (int g = warp; g < P.max_streams; g += nw) {
+          if (sched_all || C.staging_due(g, now)) {
+            C.stream_schedule_warp(g, now);
+            if ((tid & 31) == 0) {
+              SState& S = C.ss[g];
+              const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+              if (lim > S.sreach) S.sreach = lim;
+            }
+            __syncwarp();
+          } else {
+            C.reach_scan_warp(g);
+          }
+        }
       } else {
-        for (int g = tid; g < P.max_streams; g += blockDim.x) C.stream_schedule(g, now);
+        for (int g = tid; g < P.max_streams; g += blockDim.x) {
+          if (sched_all || C.staging_due(g, now)) {
+            C.stream_schedule(g, now);
+            SState& S = C.ss[g];
+            const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+            if (lim > S.sreach) S.sreach = lim;
+          } else {
+            C.reach_scan(g);
+          }
+        }
       }
       __syncthreads();
+      C.process_cands(now);
+      __syncthreads();
+      if (tid == 0) sm.ncand = 0;
       C.make_deferred();
       __syncthreads();
       mark(3);
@@ -3009,6 +3128,12 @@ extern "C" int mpxi_engine_preload(void) {
   if (a.localSizeBytes > lim && cudaDeviceSetLimit(cudaLimitStackSize, a.localSizeBytes) != cudaSuccess)
     return 1;
   return 0;
+}
+
+// Registers per thread of the engine kernel (0 if unknown).
+extern "C" int mpxi_engine_regs(void) {
+  cudaFuncAttributes a;
+  return cudaFuncGetAttributes(&a, mpxi::engine_kernel) == cudaSuccess ? a.numRegs : 0;
 }
 
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads) {

@@ -37,6 +37,7 @@
 using namespace mpxi;
 
 extern "C" int mpxi_engine_max_ctas_per_sm(int nthreads);
+extern "C" int mpxi_engine_regs(void);
 extern "C" int mpxi_engine_preload(void);
 extern "C" int mpxi_saxpy_preload(void);
 extern "C" int mpxi_step_preload(void);
@@ -204,11 +205,13 @@ struct mpx_world_s {
   int device;
   int nsm;
   int slots_log2, wl_log2, qcap_log2, tq_log2, sr_log2, iw;
-  // pinned host memory
+  // submission side: pinned host memory, or managed memory kept on the
+  // device (rings_managed) that the host reaches through the coherent link
   Desc* rings;
   int64_t* waitlists;
   StreamCtl* sctl;
-  WorldCtl* wctl;
+  bool rings_managed;
+  WorldCtl* wctl;     // pinned host memory
   // device memory (one block; see layout in world_create)
   void* dev_block;
   size_t dev_bytes;
@@ -262,6 +265,7 @@ extern "C" int mpx_world_config_init(mpx_world_config_t* c) {
   c->watchdog_ns = env_i64("MPX_WATCHDOG_NS", 10ll * 1000 * 1000 * 1000);
   c->idle_exit_ns = env_i64("MPX_IDLE_EXIT_NS", 100ll * 1000 * 1000);
   c->stage_delay_ns = env_i64("MPX_STAGE_DELAY_NS", 20000);
+  c->ring_placement = (int32_t)env_i64("MPX_RING_PLACEMENT", MPX_RINGS_HOST);
   return MPX_SUCCESS;
 }
 
@@ -281,11 +285,51 @@ static void world_release(mpx_world_s* w) {
   if (w->plain) plain::destroy(w->plain);
   if (w->engine_stream) cudaStreamDestroy(w->engine_stream);
   if (w->dev_block) cudaFree(w->dev_block);
-  if (w->rings) cudaFreeHost(w->rings);
-  if (w->waitlists) cudaFreeHost(w->waitlists);
-  if (w->sctl) cudaFreeHost(w->sctl);
+  for (void* p : {(void*)w->rings, (void*)w->waitlists, (void*)w->sctl}) {
+    if (!p) continue;
+    if (w->rings_managed) cudaFree(p);
+    else cudaFreeHost(p);
+  }
   if (w->wctl) cudaFreeHost(w->wctl);
   delete w;
+}
+
+// Diagnostic: one attribute of the current device (cudaDeviceAttr numbering).
+extern "C" int mpxi_device_attr(int attr, int* value) {
+  int dev = 0;
+  if (!value || cudaGetDevice(&dev) != cudaSuccess) return MPX_ERR_CUDA;
+  return cudaDeviceGetAttribute(value, (cudaDeviceAttr)attr, dev) == cudaSuccess ? MPX_SUCCESS : MPX_ERR_CUDA;
+}
+
+// Device-resident submission side: managed memory whose preferred location
+// is the device, mapped for direct host access (on a coherent chip-to-chip
+// link the host's loads and stores reach device memory without migrating
+// pages), moved to the device before anyone touches it and zeroed there.
+static int alloc_device_rings(mpx_world_s* w, size_t ring_b, size_t wl_b, size_t sctl_b) {
+  int direct = 0, concurrent = 0;
+  if (cudaDeviceGetAttribute(&direct, cudaDevAttrDirectManagedMemAccessFromHost, w->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&concurrent, cudaDevAttrConcurrentManagedAccess, w->device) != cudaSuccess)
+    return MPX_ERR_CUDA;
+  if (!direct || !concurrent) return MPX_ERR_UNSUPPORTED;
+  cudaMemLocation dev{};
+  dev.type = cudaMemLocationTypeDevice;
+  dev.id = w->device;
+  cudaMemLocation host{};
+  host.type = cudaMemLocationTypeHost;
+  host.id = 0;
+  w->rings_managed = true;
+  void** dst[3] = {(void**)&w->rings, (void**)&w->waitlists, (void**)&w->sctl};
+  const size_t bytes[3] = {ring_b, wl_b, sctl_b};
+  for (int k = 0; k < 3; ++k) {
+    if (cudaMallocManaged(dst[k], bytes[k], cudaMemAttachGlobal) != cudaSuccess) return MPX_ERR_NO_MEM;
+    if (cudaMemAdvise(*dst[k], bytes[k], cudaMemAdviseSetPreferredLocation, dev) != cudaSuccess ||
+        cudaMemAdvise(*dst[k], bytes[k], cudaMemAdviseSetAccessedBy, host) != cudaSuccess ||
+        cudaMemAdvise(*dst[k], bytes[k], cudaMemAdviseSetAccessedBy, dev) != cudaSuccess ||
+        cudaMemPrefetchAsync(*dst[k], bytes[k], dev, 0, 0) != cudaSuccess ||
+        cudaMemsetAsync(*dst[k], 0, bytes[k], 0) != cudaSuccess)
+      return MPX_ERR_CUDA;
+  }
+  return cudaStreamSynchronize(0) == cudaSuccess ? MPX_SUCCESS : MPX_ERR_CUDA;
 }
 
 extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mpx_world_t* out) {
@@ -306,6 +350,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   if (cfg.staging_bytes < 4096) return MPX_ERR_ARG;
   if (cfg.mover_schedule != MPX_MOVERS_WORKLIST && cfg.mover_schedule != MPX_MOVERS_PER_CTA)
     return MPX_ERR_ARG;
+  if (cfg.ring_placement != MPX_RINGS_HOST && cfg.ring_placement != MPX_RINGS_DEVICE) return MPX_ERR_ARG;
 
   mpx_world_s* w = new (std::nothrow) mpx_world_s();
   if (!w) return MPX_ERR_NO_MEM;
@@ -347,15 +392,26 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t slots = (size_t)1 << w->slots_log2;
   const size_t ndom = (size_t)cfg.max_comms * nranks;
 
-  // pinned host memory: rings, waitlists, control lines
-  if (cudaHostAlloc((void**)&w->rings, (size_t)S * slots * sizeof(Desc), cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc((void**)&w->waitlists, ((size_t)S << w->wl_log2) * sizeof(int64_t), cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc((void**)&w->sctl, (size_t)S * sizeof(StreamCtl), cudaHostAllocMapped) != cudaSuccess ||
-      cudaHostAlloc((void**)&w->wctl, sizeof(WorldCtl), cudaHostAllocMapped) != cudaSuccess) {
+  // submission rings, waitlists, stream control lines: pinned host memory,
+  // or device memory written by the host through the coherent link
+  const size_t ring_b = (size_t)S * slots * sizeof(Desc);
+  const size_t wl_b = ((size_t)S << w->wl_log2) * sizeof(int64_t);
+  const size_t sctl_b = (size_t)S * sizeof(StreamCtl);
+  if (cfg.ring_placement == MPX_RINGS_DEVICE) {
+    const int rc = alloc_device_rings(w, ring_b, wl_b, sctl_b);
+    if (rc) { world_release(w); return rc; }
+  } else if (cudaHostAlloc((void**)&w->rings, ring_b, cudaHostAllocMapped) != cudaSuccess ||
+             cudaHostAlloc((void**)&w->waitlists, wl_b, cudaHostAllocMapped) != cudaSuccess ||
+             cudaHostAlloc((void**)&w->sctl, sctl_b, cudaHostAllocMapped) != cudaSuccess) {
+    world_release(w);
+    return MPX_ERR_NO_MEM;
+  } else {
+    memset(w->sctl, 0, sctl_b);
+  }
+  if (cudaHostAlloc((void**)&w->wctl, sizeof(WorldCtl), cudaHostAllocMapped) != cudaSuccess) {
     world_release(w);
     return MPX_ERR_NO_MEM;
   }
-  memset(w->sctl, 0, (size_t)S * sizeof(StreamCtl));
   memset(w->wctl, 0, sizeof(WorldCtl));
   w->slot_seq.assign(S, 0);
   w->streams.assign(S, nullptr);
@@ -406,6 +462,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_dtot = sort_ok ? carve(ndom * 4) : 0;
   const size_t o_dbase = sort_ok ? carve(ndom * 8) : 0;
   const size_t o_dlist = sort_ok ? carve((size_t)S * slots * sizeof(PostRec)) : 0;
+  const size_t o_cand = carve((size_t)S * slots * 8);
   const int64_t trace_cap = env_i64("MPX_ENGINE_TRACE", 0);  // diagnostic tile trace records
   const size_t o_trace = trace_cap > 0 ? carve((size_t)trace_cap * 32 + 8) : 0;
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
@@ -450,9 +507,15 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.bulk_min = cfg.bulk_min_bytes;
   P.stage_bytes = cfg.staging_bytes;
   void* dp;
-  cudaHostGetDevicePointer(&dp, w->rings, 0); P.rings = (const Desc*)dp;
-  cudaHostGetDevicePointer(&dp, w->waitlists, 0); P.waitlists = (const int64_t*)dp;
-  cudaHostGetDevicePointer(&dp, w->sctl, 0); P.sctl = (StreamCtl*)dp;
+  if (w->rings_managed) {  // one address for host and device
+    P.rings = w->rings;
+    P.waitlists = w->waitlists;
+    P.sctl = w->sctl;
+  } else {
+    cudaHostGetDevicePointer(&dp, w->rings, 0); P.rings = (const Desc*)dp;
+    cudaHostGetDevicePointer(&dp, w->waitlists, 0); P.waitlists = (const int64_t*)dp;
+    cudaHostGetDevicePointer(&dp, w->sctl, 0); P.sctl = (StreamCtl*)dp;
+  }
   cudaHostGetDevicePointer(&dp, w->wctl, 0); P.wctl = (WorldCtl*)dp;
   P.doorbell = (uint64_t*)(base + o_door);
   P.done = (uint64_t*)(base + o_done);
@@ -477,6 +540,8 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.dtot = sort_ok ? (int32_t*)(base + o_dtot) : nullptr;
   P.dbase = sort_ok ? (int64_t*)(base + o_dbase) : nullptr;
   P.dlist = sort_ok ? (PostRec*)(base + o_dlist) : nullptr;
+  P.cand = (uint64_t*)(base + o_cand);
+  P.cand_cap = (int64_t)S * (int64_t)slots;
   P.trace = trace_cap > 0 ? (uint64_t*)(base + o_trace) : nullptr;
   P.trace_pos = trace_cap > 0 ? (uint64_t*)(base + o_trace + (size_t)trace_cap * 32) : nullptr;
   P.trace_cap = trace_cap > 0 ? trace_cap : 0;
@@ -486,7 +551,15 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
     return MPX_ERR_CUDA;
   }
   w->engine_threads = cfg.engine_threads;
-  int per_sm = mpxi_engine_max_ctas_per_sm(cfg.engine_threads);
+  if (cfg.engine_mode == MPX_ENGINE_PERSISTENT) {
+    // a resident engine leaves at least half of each SM's registers to the
+    // application's kernels: with all of them taken, a kernel enqueued before
+    // a send never runs, its doorbell never rings and the engine waits for it
+    const int regs = mpxi_engine_regs();
+    const int cap = regs > 0 ? std::max(64, (32768 / regs) & ~31) : 256;
+    w->engine_threads = std::min(w->engine_threads, cap);
+  }
+  int per_sm = mpxi_engine_max_ctas_per_sm(w->engine_threads);
   if (per_sm < 1) { world_release(w); return MPX_ERR_CUDA; }
   int ctas = cfg.engine_ctas > 0 ? cfg.engine_ctas : w->nsm;
   ctas = std::min(ctas, per_sm * w->nsm);

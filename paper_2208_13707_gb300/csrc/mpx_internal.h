@@ -106,7 +106,8 @@ enum : int32_t {
   PF_DELIVERED = 8,   // payload is in the receive buffer (send or recv side)
   PF_COMPLETE = 16,   // completion visible to the stream (send: staged or delivered)
   PF_WAITED = 32,     // a completed wait covered this request
-  PF_STAGING = 64     // staging task in flight
+  PF_STAGING = 64,    // staging task in flight
+  PF_CAND = 128       // receive: listed for this tick's delivery scheduling
 };
 
 struct alignas(64) DOp {
@@ -135,6 +136,7 @@ struct SState {
   uint64_t done;       // last completion word value written
   uint64_t reached;    // stream has executed up to this seq (doorbell)
   uint64_t wl_retired; // waitlist entries finished
+  uint64_t sreach;     // the scheduler has seen this stream reach every seq up to here
   int64_t stall_t0;    // globaltimer when the current physical stall began (0: none)
   int32_t flags;       // copy of StreamCtl.flags
   int32_t rank;
@@ -285,6 +287,8 @@ struct EngineParams {
   int32_t* dtot;              // [ndomains] posts per domain this round
   int64_t* dbase;             // [ndomains] start of each domain's list
   PostRec* dlist;             // [max_streams << slots_log2] this round's posts sorted by domain
+  uint64_t* cand;             // [cand_cap] receives whose delivery may have become possible this tick
+  int64_t cand_cap;
   StreamCtl* sctl;            // [max_streams]                 pinned
   WorldCtl* wctl;             //                                pinned
   uint64_t* doorbell;         // [max_streams] device (written by stream memops)

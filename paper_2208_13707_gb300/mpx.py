@@ -30,6 +30,7 @@ REDUCE_FIXED, REDUCE_TREE = 0, 1
 STREAM_DEFAULT, STREAM_EXCLUSIVE = 0, 1
 ENGINE_PERSISTENT, ENGINE_DRAIN, ENGINE_PLAIN = 0, 1, 2
 MOVERS_WORKLIST, MOVERS_PER_CTA = 0, 1
+RINGS_HOST, RINGS_DEVICE = 0, 1
 REQUEST_NULL = -1
 IN_PLACE = 1
 ERRORS = {0: "SUCCESS", 1: "ERR_ARG", 2: "ERR_RANK", 3: "ERR_TAG", 4: "ERR_TYPE", 5: "ERR_COMM",
@@ -54,7 +55,8 @@ class WorldConfig(ctypes.Structure):
                 ("reduce_mode", ctypes.c_int32), ("mover_schedule", ctypes.c_int32),
                 ("staging_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
                 ("watchdog_ns", ctypes.c_int64), ("idle_exit_ns", ctypes.c_int64),
-                ("stage_delay_ns", ctypes.c_int64)]
+                ("stage_delay_ns", ctypes.c_int64), ("ring_placement", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 (OP_SEND, OP_RECV, OP_ISEND, OP_IRECV, OP_WAIT, OP_WAITALL, OP_ALLREDUCE, OP_BCAST, OP_REDUCE,
@@ -268,6 +270,35 @@ def mpx_world_get_counters(world: int) -> list:
     a = (_i64 * 26)()
     _chk(lib.mpx_world_get_counters(world, a, 26), "mpx_world_get_counters")
     return list(a)
+
+
+lib.mpxi_world_trace.argtypes = [_vp, _vp, _i64]
+lib.mpxi_world_trace.restype = _i64
+lib.mpxi_device_attr.argtypes = [ctypes.c_int, _P(ctypes.c_int)]
+lib.mpxi_device_attr.restype = ctypes.c_int
+
+
+def device_attr(attr: int) -> int:
+    """Diagnostic: cudaDeviceGetAttribute(attr) of the current device."""
+    v = ctypes.c_int()
+    _chk(lib.mpxi_device_attr(attr, ctypes.byref(v)), "mpxi_device_attr")
+    return v.value
+
+
+def engine_trace(world: int, max_records: int = 1 << 16):
+    """Diagnostic: the engine's timeline records since the last call, as a
+    (k, 4) uint64 array, and restart the trace.  Needs the environment variable
+    MPX_ENGINE_TRACE (record capacity) set before the world is created; empty
+    otherwise.  A mover tile writes (start ns, end ns, task << 32 | tile,
+    bytes << 8 | kind bits); a control tick writes (start ns, end ns,
+    0xFFFFFFFF << 32 | tick, what it did: bit 0 ingest, bit 1 new events,
+    bit 2 completion scan, bits 8-31 tasks outstanding, bits 32+ tasks made)."""
+    import numpy as np
+    out = np.zeros((max_records, 4), np.uint64)
+    k = lib.mpxi_world_trace(world, out.ctypes.data, max_records)
+    if k < 0:
+        raise MpxError(ERR_CUDA, "mpxi_world_trace")
+    return out[:k]
 
 
 # --- streams and communicators ---

@@ -60,6 +60,50 @@ def test_ring_exchange_small(mode):
     _compare(p, mode=mode)
 
 
+def test_resident_engine_leaves_room_for_compute_kernels():
+    """A resident engine asked for 512 threads per CTA would take every
+    register of every SM (128 per thread), and the axpy each rank runs before
+    its sends could never start.  The world caps a resident engine's threads
+    so that half the registers stay free; the ring steps then finish (a
+    short watchdog turns a regression into a world error, not a hang)."""
+    p = gen.ring_exchange(nranks=8, n=1 << 12, steps=2, min_bytes=256, max_bytes=64 << 10)
+    _compare(p, mode="persistent", cfg_over={"engine_threads": 512, "watchdog_ns": 3_000_000_000})
+
+
+def _device_rings_or_skip():
+    from paper_2208_13707_gb300 import mpx
+    cfg = mpx.mpx_world_config_init()
+    cfg.ring_placement = mpx.RINGS_DEVICE
+    cfg.max_streams = 2
+    try:
+        w = mpx.mpx_world_create(1, cfg)
+    except mpx.MpxError as e:
+        if e.code == mpx.ERR_UNSUPPORTED:
+            pytest.skip("no direct host access to managed device memory")
+        raise
+    mpx.mpx_world_free(w)
+
+
+@pytest.mark.parametrize("mode", ["persistent", "drain"])
+def test_ring_exchange_with_rings_in_device_memory(mode):
+    """Submission rings, waitall lists and stream control lines in device
+    memory written by the host through the coherent link: same outcome."""
+    _gpu()
+    _device_rings_or_skip()
+    from paper_2208_13707_gb300 import mpx
+    p = gen.ring_exchange(nranks=8, n=1 << 12, steps=4, min_bytes=256, max_bytes=256 << 10)
+    _compare(p, mode=mode, cfg_over={"ring_placement": mpx.RINGS_DEVICE})
+
+
+def test_batching_with_rings_in_device_memory():
+    _gpu()
+    _device_rings_or_skip()
+    from paper_2208_13707_gb300 import mpx
+    p = gen.batching(nranks=8, streams_per_rank=2, nmsg=2000, max_bytes=4096, laminar=True,
+                     seed=gen.SEED_BASE + 11)
+    _compare(p, mode="persistent", cfg_over={"ring_placement": mpx.RINGS_DEVICE})
+
+
 @pytest.mark.parametrize("schedule", [1])
 def test_ring_exchange_per_cta_movers(schedule):
     """Multi-tile messages and vector layouts with each mover owning its tasks."""

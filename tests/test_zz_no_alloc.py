@@ -1,7 +1,6 @@
 """mpx_sendrecv_static: the staged copy that allocates nothing, for callers
-that cannot call cudaMalloc (code running while a stream is captured into a
-CUDA graph, paths that must not risk a device-wide synchronization, processes
-whose device memory is carved up in advance).
+that cannot call cudaMalloc (paths that must not risk a device-wide
+synchronization, processes whose device memory is carved up in advance).
 
 Its output must equal what the engine's send/receive path delivers for the
 same layouts, byte for byte, on two calls in a row (the calls share the one
