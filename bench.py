@@ -568,8 +568,9 @@ def _batch_engine(prog, over, steps, warmup, nmsg, payload):
             "rounds": int(ctr[6]), "ticks": int(ctr[1]), "staged_sends": int(ctr[5]),
             "ingest_us_per_descriptor": 1e3 * phases["ingest"] / (len(prog.ops) * steps),
             "control_ms_by_phase": phases,
-            "control_ms_split": {k: ctr[19 + i] / 1e6 for i, k in enumerate(
-                ["advance", "matching", "collectives", "stream_scheduling", "reduce_and_stage"])}}
+            "control_ms_split": dict({k: ctr[19 + i] / 1e6 for i, k in enumerate(
+                ["advance", "matching", "collectives", "stream_scheduling", "reduce_and_stage"])},
+                matching_sort=ctr[26] / 1e6)}
 
 
 def _batch_graph(prog, over, steps, warmup, nmsg, payload):
@@ -1148,7 +1149,10 @@ def trace_ring(steps=4, warmup=3, max_records=200_000, tile_bytes=None):
     duration, when the first mover tile started and the last one ended, and
     each control tick (start and duration in microseconds from the pass's
     first record, flags: 1 ingest, 2 new events, 4 completion scan; tasks
-    outstanding; tasks made).  Needs MPX_ENGINE_TRACE; sets it when unset."""
+    outstanding; tasks made), and per tick the microseconds from its start at
+    the ends of ingest, rounds, finished tasks, completion, scheduling scans,
+    listed receives, deferred deliveries and scheduling (0: not reached).
+    Needs MPX_ENGINE_TRACE; sets it when unset."""
     import os
     os.environ.setdefault("MPX_ENGINE_TRACE", str(max_records))
     import torch
@@ -1164,16 +1168,19 @@ def trace_ring(steps=4, warmup=3, max_records=200_000, tile_bytes=None):
             t = mpx.engine_trace(b.world, max_records).astype(np.int64)
             if k < warmup or len(t) == 0:
                 continue
-            tick = (t[:, 2] >> 32) & 0xFFFFFFFF == 0xFFFFFFFF
+            hi = (t[:, 2] >> 32) & 0xFFFFFFFF
+            tick, phases = hi == 0xFFFFFFFF, hi == 0xFFFFFFFE
             t0 = int(t[:, 0].min())
-            tl = t[~tick]
+            tl = t[~tick & ~phases]
             out.append({
                 "step": k, "pass_us": round(e[0].elapsed_time(e[1]) * 1e3, 1),
                 "tiles": int(len(tl)),
                 "tiles_first_start_us": round((int(tl[:, 0].min()) - t0) / 1e3, 1) if len(tl) else None,
                 "tiles_last_end_us": round((int(tl[:, 1].max()) - t0) / 1e3, 1) if len(tl) else None,
                 "ticks": [[round((int(r[0]) - t0) / 1e3, 1), round((int(r[1]) - int(r[0])) / 1e3, 1),
-                           int(r[3]) & 7, (int(r[3]) >> 8) & 0xFFFFFF, int(r[3]) >> 32] for r in t[tick]]})
+                           int(r[3]) & 7, (int(r[3]) >> 8) & 0xFFFFFF, int(r[3]) >> 32] for r in t[tick]],
+                "tick_phase_ends_us": [[(int(r[w]) >> sh) & 0xFFFF for w in (1, 3) for sh in (0, 16, 32, 48)]
+                                       for r in t[phases]]})
     finally:
         b.close()
     return out

@@ -248,8 +248,9 @@ int mpx_world_get_error(mpx_world_t world, int* first_error);
  * [16] scheduling, [17] decisions, [18] the control CTA's own data movement;
  * finer, in ns: [19] stream advance, [20] matching, [21] collectives (parts
  * of [13]), [22] per-stream scheduling, [23] reductions and staging (parts of
- * [16]); [24] logical rounds run, [25] ticks that ran rounds.
- * n is the array length (<= 26 filled). */
+ * [16]); [24] logical rounds run, [25] ticks that ran rounds; [26] the
+ * domain sort of large rounds (part of [20]).
+ * n is the array length (<= 27 filled). */
 int mpx_world_get_counters(mpx_world_t world, int64_t* out, int n);
 
 /* MPIX_Stream_create (§3.1) for virtual rank `rank`, backed by a CUDA

@@ -249,9 +249,11 @@ struct CtaShared {
   uint64_t r0;              // control: task_retire at the start of the retirement scan
   uint64_t own_next;        // mover (per-CTA schedule): next task id this CTA owns
   int32_t ready_insts;    // control: allreduce instances logically complete, not yet scheduled
-  // control: receives listed (P.cand) for this tick's delivery scheduling;
-  // a failed task creation asks the next tick for a scan of every stream
-  uint32_t ncand;
+  // control: receives listed for delivery scheduling, a FIFO over P.cand
+  // (absolute positions [cand_h, cand_t)); an overflow asks the next tick
+  // for a scan of every stream
+  unsigned long long cand_h, cand_t;
+  int32_t cand_go;
   int32_t sched_retry;
   int32_t sched_all;      // control: this tick's scheduling scans every stream in full
   // control: its own copies of the task-ring words only it writes (task_alloc,
@@ -1218,52 +1220,85 @@ struct Ctl {
   __device__ bool q_take(QEntry* q, QHead& h, uint32_t qmask, bool is_send_post, int32_t src,
                          int32_t tag, QEntry& found) {
     const int lane = threadIdx.x & 31;
-    for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32) {
-      const uint32_t idx = base + (uint32_t)lane;
-      const bool inr = (int32_t)(h.tail - idx) > 0;
-      QEntry e = {0, 0, 0, 0};
-      if (inr) e = q[idx & qmask];
-      const bool live = inr && e.ref != 0;
-      bool hit = false;
-      if (live) {
-        if (is_send_post)  // a posted receive accepting (src, tag)
-          hit = src_accepts(e.src, src) && (e.tag == kAnyTag || e.tag == tag);
-        else  // an unexpected send the receive (src, tag) accepts
-          hit = src_accepts(src, e.src) && (tag == kAnyTag || tag == e.tag);
+    // four chunks of 32 entries per step, loaded together (one round trip
+    // for the 128 oldest entries instead of four)
+    constexpr int kChunks = 4;
+    for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32 * kChunks) {
+      // (reference, source, tag) of each entry; the bytes of the one taken
+      uint64_t ref[kChunks];
+      int2 st[kChunks];
+      bool live[kChunks], hit[kChunks];
+#pragma unroll
+      for (int j = 0; j < kChunks; ++j) {
+        const uint32_t idx = base + (uint32_t)(32 * j + lane);
+        ref[j] = 0;
+        st[j] = make_int2(0, 0);
+        if ((int32_t)(h.tail - idx) > 0) {
+          const QEntry* qe = &q[idx & qmask];
+          ref[j] = qe->ref;
+          st[j] = *reinterpret_cast<const int2*>(&qe->src);
+        }
       }
-      const unsigned b = __ballot_sync(FULL, hit);
-      if (!b) continue;
-      const int l = __ffs(b) - 1;
-      found.ref = __shfl_sync(FULL, e.ref, l);
-      found.src = __shfl_sync(FULL, e.src, l);
-      found.tag = __shfl_sync(FULL, e.tag, l);
-      found.bytes = __shfl_sync(FULL, e.bytes, l);
-      const uint32_t hidx = base + (uint32_t)l;
-      if (lane == 0) q[hidx & qmask].ref = 0;
-      if (hidx == h.head) {
-        // the next live entry of this chunk becomes the head, else scan on
-        const unsigned after = l == 31 ? 0u : (__ballot_sync(FULL, live) & (~0u << (l + 1)));
-        if (after) {
-          h.head = base + (uint32_t)(__ffs(after) - 1);
-        } else {
-          uint32_t head = base + 32;
-          if ((int32_t)(h.tail - head) <= 0) head = h.tail;
-          while ((int32_t)(h.tail - head) > 0) {
-            const uint32_t i = head + (uint32_t)lane;
-            const bool in2 = (int32_t)(h.tail - i) > 0;
-            const bool lv = in2 && q[i & qmask].ref != 0;
-            const unsigned bl = __ballot_sync(FULL, lv);
-            if (bl) {
-              head += (uint32_t)(__ffs(bl) - 1);
-              break;
+#pragma unroll
+      for (int j = 0; j < kChunks; ++j) {
+        live[j] = ref[j] != 0;
+        hit[j] = false;
+        if (live[j]) {
+          if (is_send_post)  // a posted receive accepting (src, tag)
+            hit[j] = src_accepts(st[j].x, src) && (st[j].y == kAnyTag || st[j].y == tag);
+          else  // an unexpected send the receive (src, tag) accepts
+            hit[j] = src_accepts(src, st[j].x) && (tag == kAnyTag || tag == st[j].y);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kChunks; ++j) {
+        const unsigned b = __ballot_sync(FULL, hit[j]);
+        if (!b) continue;
+        const int l = __ffs(b) - 1;
+        const uint32_t hidx = base + (uint32_t)(32 * j + l);
+        found.ref = __shfl_sync(FULL, ref[j], l);
+        found.src = __shfl_sync(FULL, st[j].x, l);
+        found.tag = __shfl_sync(FULL, st[j].y, l);
+        found.bytes = q[hidx & qmask].bytes;
+        if (lane == 0) q[hidx & qmask].ref = 0;
+        if (hidx == h.head) {
+          // the next live entry among those loaded becomes the head, else scan on
+          uint32_t head = 0;
+          bool got = false;
+          const unsigned after = l == 31 ? 0u : (__ballot_sync(FULL, live[j]) & (~0u << (l + 1)));
+          if (after) {
+            head = base + (uint32_t)(32 * j + __ffs(after) - 1);
+            got = true;
+          }
+#pragma unroll
+          for (int jj = 0; jj < kChunks; ++jj) {
+            if (jj <= j) continue;
+            const unsigned bl = __ballot_sync(FULL, live[jj]);
+            if (!got && bl) {
+              head = base + (uint32_t)(32 * jj + __ffs(bl) - 1);
+              got = true;
             }
-            head += (uint32_t)__popc(__ballot_sync(FULL, in2));
+          }
+          if (!got) {
+            head = base + 32 * kChunks;
+            if ((int32_t)(h.tail - head) <= 0) head = h.tail;
+            while ((int32_t)(h.tail - head) > 0) {
+              const uint32_t i = head + (uint32_t)lane;
+              const bool in2 = (int32_t)(h.tail - i) > 0;
+              const bool lv = in2 && q[i & qmask].ref != 0;
+              const unsigned bl = __ballot_sync(FULL, lv);
+              if (bl) {
+                head += (uint32_t)(__ffs(bl) - 1);
+                break;
+              }
+              head += (uint32_t)__popc(__ballot_sync(FULL, in2));
+            }
           }
           h.head = head;
         }
+        __syncwarp();
+        return true;
       }
-      __syncwarp();
-      return true;
     }
     return false;
   }
@@ -1278,10 +1313,16 @@ struct Ctl {
 
   // Record a match (lane 0): the receive learns the sender's key, tag and the
   // delivered bytes (truncated to its capacity); both learn their partner.
-  // Only stores: everything it needs came with the post and the queue entry.
+  // Only stores and non-returning atomics: everything it needs came with the
+  // post and the queue entry.
   __device__ void pair(uint64_t sref, int32_t skey, int32_t stag, int64_t sent, uint64_t rref,
                        int64_t cap) {
     if ((threadIdx.x & 31) != 0) return;
+    pair_store(sref, skey, stag, sent, rref, cap);
+  }
+  // (any lane, for one pair)
+  __device__ void pair_store(uint64_t sref, int32_t skey, int32_t stag, int64_t sent, uint64_t rref,
+                             int64_t cap) {
     DOp* s = op_ref(P, sref);
     DOp* r = op_ref(P, rref);
     r->partner = sref;
@@ -1292,19 +1333,29 @@ struct Ctl {
     r->lstate = 2;
     r->lround = (int32_t)round;
     s->partner = rref;
-    atomicOr(&r->pflags, PF_MATCHED);
     atomicOr(&s->pflags, PF_MATCHED);
-    push_cand(rref);  // deliverable now if both streams have reached their operations
+    // deliverable now if both streams have reached their operations: listed
+    // at once (an unmatched receive is never listed, so no check is needed)
+    atomicOr(&r->pflags, PF_MATCHED | PF_CAND);
+    const unsigned long long k = atomicAdd(&sm.cand_t, 1ull);
+    if (k - sm.cand_h < (unsigned long long)P.cand_cap) {
+      P.cand[k & (unsigned long long)(P.cand_cap - 1)] = rref;
+    } else {
+      P.cand[k & (unsigned long long)(P.cand_cap - 1)] = 0;
+      atomicAnd(&r->pflags, ~PF_CAND);
+      sm.sched_retry = 1;
+    }
   }
 
-  // List receive rref for this tick's delivery scheduling (once per tick).
+  // List receive rref for delivery scheduling (at most once at a time).
   __device__ void push_cand(uint64_t rref) {
     DOp* r = op_ref(P, rref);
     if (atomicOr(&r->pflags, PF_CAND) & PF_CAND) return;
-    const uint32_t k = atomicAdd(&sm.ncand, 1u);
-    if ((int64_t)k < P.cand_cap) {
-      P.cand[k] = rref;
-    } else {  // list full: every stream is scanned next tick
+    const unsigned long long k = atomicAdd(&sm.cand_t, 1ull);
+    if (k - sm.cand_h < (unsigned long long)P.cand_cap) {
+      P.cand[k & (unsigned long long)(P.cand_cap - 1)] = rref;
+    } else {  // cannot happen while every receive is listed at most once
+      P.cand[k & (unsigned long long)(P.cand_cap - 1)] = 0;
       atomicAnd(&r->pflags, ~PF_CAND);
       sm.sched_retry = 1;
     }
@@ -1388,6 +1439,179 @@ struct Ctl {
       P.pqh[d] = ph;
       P.uqh[d] = uh;
     }
+  }
+
+  // The same with the domain's two queues mirrored in shared memory: the
+  // (source, tag) of every entry between head and tail is read once, and the
+  // posts are matched in order against the mirror alone; what that decides
+  // in global memory (reading and tombstoning the entries taken, recording
+  // the pairs, appending what stays queued) is done afterwards by all lanes
+  // at once.  An entry appended and taken within the round never reaches
+  // global memory.  Needs room in `wbuf` for each queue's live span plus the
+  // domain's posts; else returns false having changed nothing.
+  // Warp-cooperative.
+  static constexpr int32_t kTombTag = INT32_MIN;
+  static constexpr uint16_t kOld = 0xFFFF;  // mirror entry that came from global memory
+  __device__ int mirror_find(const int2* k, uint32_t hl, uint32_t tl, bool is_send_post, int32_t src,
+                             int32_t tag) const {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = hl; base < tl; base += 32) {
+      const uint32_t i = base + (uint32_t)lane;
+      bool hit = false;
+      if (i < tl) {
+        const int2 e = k[i];
+        if (e.y != kTombTag) {
+          if (is_send_post)  // a posted receive accepting (src, tag)
+            hit = src_accepts(e.x, src) && (e.y == kAnyTag || e.y == tag);
+          else  // an unexpected send the receive (src, tag) accepts
+            hit = src_accepts(src, e.x) && (tag == kAnyTag || tag == e.y);
+        }
+      }
+      const unsigned b = __ballot_sync(FULL, hit);
+      if (b) return (int)(base + (uint32_t)(__ffs(b) - 1));
+    }
+    return -1;
+  }
+  // the first live mirror entry at or after hl (tl if none)
+  __device__ uint32_t mirror_next_live(const int2* k, uint32_t hl, uint32_t tl) const {
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = hl; base < tl; base += 32) {
+      const uint32_t i = base + (uint32_t)lane;
+      const unsigned b = __ballot_sync(FULL, i < tl && k[i].y != kTombTag);
+      if (b) return base + (uint32_t)(__ffs(b) - 1);
+    }
+    return tl;
+  }
+  __device__ bool match_domain_mirror(uint32_t d, uint8_t* wbuf, uint32_t wbytes) {
+    const int lane = threadIdx.x & 31;
+    const int32_t n = P.dtot[d];
+    if (n == 0) return true;
+    if (n > 32767) return false;
+    // per queue: keys (8 B) and where each entry came from (2 B); the pairs (4 B each)
+    if ((int64_t)wbytes < 4 * (int64_t)n + 160) return false;
+    const uint32_t cap = (((wbytes - 4u * (uint32_t)n) / 20u) & ~7u);
+    QHead ph = P.pqh[d], uh = P.uqh[d];
+    const uint32_t lp = ph.tail - ph.head, lu = uh.tail - uh.head;
+    if ((uint64_t)lp + (uint64_t)n > cap || (uint64_t)lu + (uint64_t)n > cap) return false;
+    int2* kp = reinterpret_cast<int2*>(wbuf);
+    int2* ku = kp + cap;
+    uint16_t* op = reinterpret_cast<uint16_t*>(ku + cap);  // kOld, or the post that appended it
+    uint16_t* ou = op + cap;
+    uint32_t* mt = reinterpret_cast<uint32_t*>(ou + cap);  // post << 16 | send << 15 | position
+    const uint32_t qmask = (1u << P.qcap_log2) - 1;
+    QEntry* pq = P.pq + ((size_t)d << P.qcap_log2);
+    QEntry* uq = P.uq + ((size_t)d << P.qcap_log2);
+    for (uint32_t i = (uint32_t)lane; i < lp; i += 32) {
+      const QEntry* e = &pq[(ph.head + i) & qmask];
+      kp[i] = e->ref ? make_int2(e->src, e->tag) : make_int2(0, kTombTag);
+      op[i] = kOld;
+    }
+    for (uint32_t i = (uint32_t)lane; i < lu; i += 32) {
+      const QEntry* e = &uq[(uh.head + i) & qmask];
+      ku[i] = e->ref ? make_int2(e->src, e->tag) : make_int2(0, kTombTag);
+      ou[i] = kOld;
+    }
+    __syncwarp();
+    uint32_t hp = 0, tp = lp, hu = 0, tu = lu;  // mirror positions (0 = the queue's head)
+    uint32_t nm = 0;
+    const PostRec* list = P.dlist + P.dbase[d];
+    for (int base = 0; base < n; base += 32) {
+      int2 mk = make_int2(0, 0);
+      uint32_t msend = 0;
+      if (base + lane < n) {
+        mk = make_int2(list[base + lane].key, list[base + lane].tag);
+        msend = list[base + lane].send;
+      }
+      const int m = (n - base) < 32 ? (n - base) : 32;
+      for (int k = 0; k < m; ++k) {
+        const int32_t pkey = __shfl_sync(FULL, mk.x, k);
+        const int32_t ptag = __shfl_sync(FULL, mk.y, k);
+        const bool send = __shfl_sync(FULL, msend, k) != 0;
+        const uint32_t pi = (uint32_t)(base + k);
+        int2* tk = send ? kp : ku;  // the queue to take from
+        uint32_t& th = send ? hp : hu;
+        const uint32_t tt = send ? tp : tu;
+        const int f = mirror_find(tk, th, tt, send, pkey, ptag);
+        if (f >= 0) {
+          if (lane == 0) {
+            tk[f].y = kTombTag;
+            mt[nm] = (pi << 16) | (send ? 0x8000u : 0u) | (uint32_t)f;
+          }
+          ++nm;
+          __syncwarp();
+          if ((uint32_t)f == th) th = mirror_next_live(tk, th + 1, tt);
+        } else {
+          int2* ak = send ? ku : kp;  // the queue to append to
+          uint16_t* ao = send ? ou : op;
+          const uint32_t ah = send ? hu : hp;
+          uint32_t& at = send ? tu : tp;
+          if (at - ah > qmask) {  // queue full: the post stays unmatched
+            if (lane == 0) set_error(P, ref_stream(list[pi].ref), kErrNoMem);
+          } else {
+            if (lane == 0) {
+              ak[at] = make_int2(pkey, ptag);
+              ao[at] = (uint16_t)pi;
+            }
+            at = at + 1;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // global effects, every lane a pair or an entry at a time
+    for (uint32_t i = (uint32_t)lane; i < nm; i += 32) {
+      const uint32_t rec = mt[i];
+      const uint32_t pi = rec >> 16, f = rec & 0x7FFFu;
+      const bool send = (rec & 0x8000u) != 0;
+      const PostRec& p = list[pi];
+      const uint16_t o = send ? op[f] : ou[f];
+      uint64_t eref;
+      int32_t esrc, etag;
+      int64_t ebytes;
+      if (o == kOld) {  // taken from global memory: read, then tombstone
+        QEntry* qe = send ? &pq[(ph.head + f) & qmask] : &uq[(uh.head + f) & qmask];
+        const QEntry e = *qe;
+        eref = e.ref;
+        esrc = e.src;
+        etag = e.tag;
+        ebytes = e.bytes;
+        qe->ref = 0;
+      } else {  // appended by an earlier post of this round
+        const PostRec& q = list[o];
+        eref = q.ref;
+        esrc = q.key;
+        etag = q.tag;
+        ebytes = q.bytes;
+      }
+      if (send) pair_store(p.ref, p.key, p.tag, p.bytes, eref, ebytes);
+      else pair_store(eref, esrc, etag, ebytes, p.ref, p.bytes);
+    }
+    // entries appended this round: the live ones are written out, the taken
+    // ones leave a tombstone (the queue's tail moved over them)
+    for (uint32_t i = lp + (uint32_t)lane; i < tp; i += 32) {
+      QEntry* qe = &pq[(ph.head + i) & qmask];
+      if (kp[i].y == kTombTag) {
+        qe->ref = 0;
+      } else {
+        const PostRec& q = list[op[i]];
+        *qe = QEntry{q.ref, q.key, q.tag, q.bytes};
+      }
+    }
+    for (uint32_t i = lu + (uint32_t)lane; i < tu; i += 32) {
+      QEntry* qe = &uq[(uh.head + i) & qmask];
+      if (ku[i].y == kTombTag) {
+        qe->ref = 0;
+      } else {
+        const PostRec& q = list[ou[i]];
+        *qe = QEntry{q.ref, q.key, q.tag, q.bytes};
+      }
+    }
+    if (lane == 0) {
+      P.pqh[d] = QHead{ph.head + hp, ph.head + tp};
+      P.uqh[d] = QHead{uh.head + hu, uh.head + tu};
+    }
+    __syncwarp();
+    return true;
   }
 
   // Domain d's posts found by scanning every stream's post list in global
@@ -1694,8 +1918,7 @@ struct Ctl {
     uint64_t id;
     Task* T = task_new(id);
     if (!T) {
-      atomicAnd(&r->pflags, ~PF_SCHED);
-      sm.sched_retry = 1;  // ring full: look again next tick
+      atomicAnd(&r->pflags, ~PF_SCHED);  // ring full (task_new raised ntask_full)
       return false;
     }
     fill_copy(T, src, dst, bytes, tile_hint);
@@ -2231,20 +2454,41 @@ struct Ctl {
     __syncwarp();
   }
 
-  // Schedule the listed receives (thread per receive); a receive its own
-  // stream has not reached yet is listed again when it is.
+  // Schedule the listed receives in list order, a thread per receive and a
+  // block of them at a time, until this phase's task slots are spoken for
+  // (the rest stay listed).  A receive its own stream has not reached yet is
+  // listed again when it is; one whose task cannot be created is listed
+  // again at once (behind the entries listed now).
   __device__ void process_cands(int64_t now) {
-    const int64_t n = (int64_t)sm.ncand < P.cand_cap ? (int64_t)sm.ncand : P.cand_cap;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t rref = P.cand[i];
-      const int g = ref_stream(rref);
-      const uint64_t seq = ref_seq(rref);
-      atomicAnd(&op_ref(P, rref)->pflags, ~PF_CAND);
-      const SState& S = ss[g];
-      const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
-      if (seq <= S.retire || seq > lim) continue;
-      schedule_op(g, seq, now);
+    const unsigned long long t = sm.cand_t;
+    const unsigned long long mask = (unsigned long long)(P.cand_cap - 1);
+    unsigned long long base = sm.cand_h;
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0)
+        sm.cand_go = base < t && (int64_t)sm.t_used + (int64_t)sm.ndlv < (int64_t)sm.t_avail;
+      __syncthreads();
+      if (!sm.cand_go) break;
+      const unsigned long long i = base + threadIdx.x;
+      if (i < t) {
+        const uint64_t rref = P.cand[i & mask];
+        if (rref != 0) {
+          const int g = ref_stream(rref);
+          const uint64_t seq = ref_seq(rref);
+          const SState& S = ss[g];
+          if (seq > S.retire) {  // (a retired receive's slot may hold a newer operation)
+            atomicAnd(&op_ref(P, rref)->pflags, ~PF_CAND);
+            const uint64_t lim = S.reached < S.ingested ? S.reached : S.ingested;
+            // once the ring ran out in this phase an unsettled receive is
+            // listed again (its task may be what could not be created)
+            if (seq <= lim && !schedule_op(g, seq, now) && sm.ntask_full) push_cand(rref);
+          }
+        }
+      }
+      base += blockDim.x;
     }
+    if (threadIdx.x == 0) sm.cand_h = base < t ? base : t;
+    __syncthreads();
   }
 
   // Create the deliveries the scheduling scan deferred, every one with the
@@ -2272,7 +2516,7 @@ struct Ctl {
       if (!from_stage) atomicAnd(&op_ref(P, sref)->pflags, ~PF_SCHED);
       atomicAnd(&r->pflags, ~PF_SCHED);
       atomicMin((unsigned long long*)&ss[ref_stream(rref)].sched, (unsigned long long)ref_seq(rref));
-      sm.sched_retry = 1;
+      push_cand(rref);
     }
   }
 
@@ -2586,7 +2830,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   if (tid == 0) {
     C.round = (int64_t)sh->round;
     sm.nstage = 0;
-    sm.ncand = 0;
+    sm.cand_h = *(volatile unsigned long long*)&sh->cand_h;
+    sm.cand_t = *(volatile unsigned long long*)&sh->cand_t;
     sm.sched_retry = 0;
   }
   __syncthreads();
@@ -2640,6 +2885,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         tp = t;
       }
     };
+    // diagnostic trace: microseconds from the tick's start at its phase ends
+    uint16_t at_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto stamp = [&](int k) {
+      if (P.trace && tid == 0) {
+        const int64_t d = ((int64_t)now_ns() - now) / 1000;
+        at_us[k] = (uint16_t)(d > 65535 ? 65535 : d < 1 ? 1 : d);
+      }
+    };
     // 1. ingest
     const bool ing = C.ingest();
     if (ing) {
@@ -2648,6 +2901,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     }
     __syncthreads();
     lap(0);
+    stamp(0);
     // every thread takes its branch from one snapshot of the flags: thread 0
     // clears `dirty` below, and a warp that read it after that would skip the
     // rounds and meet the others' barriers at different points of the tick
@@ -2697,7 +2951,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
           } else if (P.cnt2) {
             C.sort_posts();
             __syncthreads();
-            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw) C.match_domain_sorted(d);
+            if (tid == 0 && timing) sub[7] += now_ns() - ts;  // (inside the matching time)
+            // with movers present this CTA never copies: its bulk-copy stages
+            // hold each warp's queue mirrors
+            const uint32_t wbytes = (uint32_t)(((size_t)kTmaStages * kTmaChunk / (size_t)nw) & ~(size_t)15);
+            uint8_t* wbuf = gridDim.x > 1 ? buf + (size_t)warp * wbytes : nullptr;
+            for (uint32_t d = (uint32_t)warp; d < nd; d += (uint32_t)nw)
+              if (!wbuf || !C.match_domain_mirror(d, wbuf, wbytes)) C.match_domain_sorted(d);
             __syncthreads();
             C.clear_counts();
           } else {
@@ -2725,6 +2985,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     }
     lap(1);
+    stamp(1);
     if (!failed_now) {
       // 3. finished tasks, then per-stream completion and retirement
       if (tid == 0) {
@@ -2799,6 +3060,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
       __syncthreads();
       lap(2);
+      stamp(2);
       int phys = 0, pend = 0;
       if (tid == 0) sm.pending = 0;
       __syncthreads();
@@ -2824,6 +3086,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       __syncthreads();
       for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 0;
       lap(3);
+      stamp(3);
       if (tid == 0) {
         C.task_phase_begin();
         sm.ndlv = 0;
@@ -2863,12 +3126,15 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
           }
         }
       }
-      __syncthreads();
+      stamp(4);
       C.process_cands(now);
-      __syncthreads();
-      if (tid == 0) sm.ncand = 0;
+      stamp(5);
       C.make_deferred();
       __syncthreads();
+      // a full scan that ran out of task slots leaves its receives to the next
+      // tick's full scan (the scans list nothing they could not schedule)
+      if (tid == 0 && sched_all && sm.ntask_full) sm.sched_retry = 1;
+      stamp(6);
       mark(3);
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
@@ -2876,6 +3142,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if (tid == 0) C.task_phase_end();
       mark(4);
       lap(4);
+      stamp(7);
     }
     // diagnostic trace: one record per tick (marker 0xFFFFFFFF in the high
     // word of the third field): start, end, tick number, what it did
@@ -2888,6 +3155,19 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         rec[2] = (0xFFFFFFFFull << 32) | (uint32_t)ticks;
         rec[3] = (uint64_t)(ing ? 1 : 0) | (uint64_t)(dirty_now ? 2 : 0) | (uint64_t)(sm.scan_now ? 4 : 0) |
                  ((uint64_t)(sm.t_alloc - sm.t_retire) << 8) | ((uint64_t)sm.t_used << 32);
+      }
+      // its phase ends (marker 0xFFFFFFFE): us from the tick's start after
+      // ingest, rounds, finished tasks, completion, scheduling scans, listed
+      // receives, deferred deliveries, end of scheduling (0: not reached)
+      const uint64_t k2 = atomicAdd((unsigned long long*)P.trace_pos, 1ull);
+      if ((int64_t)k2 < P.trace_cap) {
+        uint64_t* rec = P.trace + 4 * k2;
+        rec[0] = (uint64_t)now;
+        rec[1] = (uint64_t)at_us[0] | ((uint64_t)at_us[1] << 16) | ((uint64_t)at_us[2] << 32) |
+                 ((uint64_t)at_us[3] << 48);
+        rec[2] = (0xFFFFFFFEull << 32) | (uint32_t)ticks;
+        rec[3] = (uint64_t)at_us[4] | ((uint64_t)at_us[5] << 16) | ((uint64_t)at_us[6] << 32) |
+                 ((uint64_t)at_us[7] << 48);
       }
     }
     // 4. bookkeeping and exit decisions (thread 0)
@@ -2976,6 +3256,10 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     for (int g = tid; g < P.max_streams; g += blockDim.x) P.ss[g] = C.ss[g];
     __threadfence();
   }
+  if (tid == 0) {  // receives still listed stay listed for the next launch
+    sh->cand_h = sm.cand_h;
+    sh->cand_t = sm.cand_t;
+  }
   __syncthreads();
   // let the movers go; tasks in flight were finished before deciding to exit
   if (tid == 0) {
@@ -2990,7 +3274,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     atomicAdd((unsigned long long*)&P.wctl->phase[3], (unsigned long long)ticks);
     atomicAdd((unsigned long long*)&P.wctl->counters[1], (unsigned long long)ticks);
     for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->tick_ns[k], (unsigned long long)tacc[k]);
-    for (int k = 0; k < 7; ++k) atomicAdd((unsigned long long*)&P.wctl->sub_ns[k], (unsigned long long)sub[k]);
+    for (int k = 0; k < 8; ++k) atomicAdd((unsigned long long*)&P.wctl->sub_ns[k], (unsigned long long)sub[k]);
     if (P.mode == 0) st_rel_sys32(&P.wctl->state, ENG_STOPPED);
   }
 }

@@ -462,7 +462,9 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   const size_t o_dtot = sort_ok ? carve(ndom * 4) : 0;
   const size_t o_dbase = sort_ok ? carve(ndom * 8) : 0;
   const size_t o_dlist = sort_ok ? carve((size_t)S * slots * sizeof(PostRec)) : 0;
-  const size_t o_cand = carve((size_t)S * slots * 8);
+  size_t cand_cap = 1;  // a power of two at least the operations in flight
+  while (cand_cap < (size_t)S * slots) cand_cap <<= 1;
+  const size_t o_cand = carve(cand_cap * 8);
   const int64_t trace_cap = env_i64("MPX_ENGINE_TRACE", 0);  // diagnostic tile trace records
   const size_t o_trace = trace_cap > 0 ? carve((size_t)trace_cap * 32 + 8) : 0;
   const size_t o_stage = carve((size_t)cfg.staging_bytes);
@@ -541,7 +543,7 @@ extern "C" int mpx_world_create(int nranks, const mpx_world_config_t* cfg_in, mp
   P.dbase = sort_ok ? (int64_t*)(base + o_dbase) : nullptr;
   P.dlist = sort_ok ? (PostRec*)(base + o_dlist) : nullptr;
   P.cand = (uint64_t*)(base + o_cand);
-  P.cand_cap = (int64_t)S * (int64_t)slots;
+  P.cand_cap = (int64_t)cand_cap;
   P.trace = trace_cap > 0 ? (uint64_t*)(base + o_trace) : nullptr;
   P.trace_pos = trace_cap > 0 ? (uint64_t*)(base + o_trace + (size_t)trace_cap * 32) : nullptr;
   P.trace_cap = trace_cap > 0 ? trace_cap : 0;
@@ -775,12 +777,13 @@ extern "C" int64_t mpxi_world_trace(mpx_world_t w, uint64_t* out, int64_t n) {
 
 extern "C" int mpx_world_get_counters(mpx_world_t w, int64_t* outv, int n) {
   if (!w || !outv || n < 0) return MPX_ERR_ARG;
-  for (int i = 0; i < n && i < 26; ++i) {
+  for (int i = 0; i < n && i < 27; ++i) {
     if (w->plain) outv[i] = i < 19 ? plain::counter(w->plain, i) : 0;
     else if (i < 8) outv[i] = (int64_t)__atomic_load_n(&w->wctl->counters[i], __ATOMIC_ACQUIRE);
     else if (i < 12) outv[i] = (int64_t)__atomic_load_n(&w->wctl->phase[i - 8], __ATOMIC_ACQUIRE);
     else if (i < 19) outv[i] = (int64_t)__atomic_load_n(&w->wctl->tick_ns[i - 12], __ATOMIC_ACQUIRE);
-    else outv[i] = (int64_t)__atomic_load_n(&w->wctl->sub_ns[i - 19], __ATOMIC_ACQUIRE);
+    else if (i < 26) outv[i] = (int64_t)__atomic_load_n(&w->wctl->sub_ns[i - 19], __ATOMIC_ACQUIRE);
+    else outv[i] = (int64_t)__atomic_load_n(&w->wctl->sub_ns[7], __ATOMIC_ACQUIRE);
   }
   return MPX_SUCCESS;
 }

@@ -242,7 +242,8 @@ struct alignas(128) Shared {
   // staging ring allocator (control-owned)
   uint64_t st_head, st_tail;     // arena byte offsets (monotone)
   uint64_t sr_head, sr_tail;     // StageRec ring indices
-  uint64_t pad2[6];
+  uint64_t cand_h, cand_t;       // delivery-scheduling list (EngineParams.cand), kept across launches
+  uint64_t pad2[4];
   // completion queue: the CTA that finishes a task's last tile appends the
   // task's slot (movers: cq_tail); the control CTA consumes (cq_head)
   uint64_t cq_head;
@@ -287,8 +288,8 @@ struct EngineParams {
   int32_t* dtot;              // [ndomains] posts per domain this round
   int64_t* dbase;             // [ndomains] start of each domain's list
   PostRec* dlist;             // [max_streams << slots_log2] this round's posts sorted by domain
-  uint64_t* cand;             // [cand_cap] receives whose delivery may have become possible this tick
-  int64_t cand_cap;
+  uint64_t* cand;             // [cand_cap] FIFO of receives whose delivery may have become possible
+  int64_t cand_cap;           // a power of two
   StreamCtl* sctl;            // [max_streams]                 pinned
   WorldCtl* wctl;             //                                pinned
   uint64_t* doorbell;         // [max_streams] device (written by stream memops)

@@ -267,8 +267,8 @@ def mpx_world_get_error(world: int) -> int:
 
 
 def mpx_world_get_counters(world: int) -> list:
-    a = (_i64 * 26)()
-    _chk(lib.mpx_world_get_counters(world, a, 26), "mpx_world_get_counters")
+    a = (_i64 * 27)()
+    _chk(lib.mpx_world_get_counters(world, a, 27), "mpx_world_get_counters")
     return list(a)
 
 
@@ -292,7 +292,11 @@ def engine_trace(world: int, max_records: int = 1 << 16):
     otherwise.  A mover tile writes (start ns, end ns, task << 32 | tile,
     bytes << 8 | kind bits); a control tick writes (start ns, end ns,
     0xFFFFFFFF << 32 | tick, what it did: bit 0 ingest, bit 1 new events,
-    bit 2 completion scan, bits 8-31 tasks outstanding, bits 32+ tasks made)."""
+    bit 2 completion scan, bits 8-31 tasks outstanding, bits 32+ tasks made)
+    and then (start ns, four 16-bit phase ends, 0xFFFFFFFE << 32 | tick, four
+    more): microseconds from the tick's start at the ends of ingest, rounds,
+    finished tasks, completion, scheduling scans, listed receives, deferred
+    deliveries and scheduling (0: phase not reached)."""
     import numpy as np
     out = np.zeros((max_records, 4), np.uint64)
     k = lib.mpxi_world_trace(world, out.ctypes.data, max_records)
