@@ -255,6 +255,7 @@ struct CtaShared {
   unsigned long long cand_h, cand_t;
   int32_t cand_go;
   int32_t sched_retry;
+  uint16_t at_us[8];      // control, diagnostic trace: phase ends of the current tick
   int32_t sched_all;      // control: this tick's scheduling scans every stream in full
   // control: its own copies of the task-ring words only it writes (task_alloc,
   // task_retire, cq_head); the global words are written through for the movers
@@ -1220,85 +1221,52 @@ struct Ctl {
   __device__ bool q_take(QEntry* q, QHead& h, uint32_t qmask, bool is_send_post, int32_t src,
                          int32_t tag, QEntry& found) {
     const int lane = threadIdx.x & 31;
-    // four chunks of 32 entries per step, loaded together (one round trip
-    // for the 128 oldest entries instead of four)
-    constexpr int kChunks = 4;
-    for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32 * kChunks) {
-      // (reference, source, tag) of each entry; the bytes of the one taken
-      uint64_t ref[kChunks];
-      int2 st[kChunks];
-      bool live[kChunks], hit[kChunks];
-#pragma unroll
-      for (int j = 0; j < kChunks; ++j) {
-        const uint32_t idx = base + (uint32_t)(32 * j + lane);
-        ref[j] = 0;
-        st[j] = make_int2(0, 0);
-        if ((int32_t)(h.tail - idx) > 0) {
-          const QEntry* qe = &q[idx & qmask];
-          ref[j] = qe->ref;
-          st[j] = *reinterpret_cast<const int2*>(&qe->src);
-        }
+    for (uint32_t base = h.head; (int32_t)(h.tail - base) > 0; base += 32) {
+      const uint32_t idx = base + (uint32_t)lane;
+      const bool inr = (int32_t)(h.tail - idx) > 0;
+      QEntry e = {0, 0, 0, 0};
+      if (inr) e = q[idx & qmask];
+      const bool live = inr && e.ref != 0;
+      bool hit = false;
+      if (live) {
+        if (is_send_post)  // a posted receive accepting (src, tag)
+          hit = src_accepts(e.src, src) && (e.tag == kAnyTag || e.tag == tag);
+        else  // an unexpected send the receive (src, tag) accepts
+          hit = src_accepts(src, e.src) && (tag == kAnyTag || tag == e.tag);
       }
-#pragma unroll
-      for (int j = 0; j < kChunks; ++j) {
-        live[j] = ref[j] != 0;
-        hit[j] = false;
-        if (live[j]) {
-          if (is_send_post)  // a posted receive accepting (src, tag)
-            hit[j] = src_accepts(st[j].x, src) && (st[j].y == kAnyTag || st[j].y == tag);
-          else  // an unexpected send the receive (src, tag) accepts
-            hit[j] = src_accepts(src, st[j].x) && (tag == kAnyTag || tag == st[j].y);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kChunks; ++j) {
-        const unsigned b = __ballot_sync(FULL, hit[j]);
-        if (!b) continue;
-        const int l = __ffs(b) - 1;
-        const uint32_t hidx = base + (uint32_t)(32 * j + l);
-        found.ref = __shfl_sync(FULL, ref[j], l);
-        found.src = __shfl_sync(FULL, st[j].x, l);
-        found.tag = __shfl_sync(FULL, st[j].y, l);
-        found.bytes = q[hidx & qmask].bytes;
-        if (lane == 0) q[hidx & qmask].ref = 0;
-        if (hidx == h.head) {
-          // the next live entry among those loaded becomes the head, else scan on
-          uint32_t head = 0;
-          bool got = false;
-          const unsigned after = l == 31 ? 0u : (__ballot_sync(FULL, live[j]) & (~0u << (l + 1)));
-          if (after) {
-            head = base + (uint32_t)(32 * j + __ffs(after) - 1);
-            got = true;
-          }
-#pragma unroll
-          for (int jj = 0; jj < kChunks; ++jj) {
-            if (jj <= j) continue;
-            const unsigned bl = __ballot_sync(FULL, live[jj]);
-            if (!got && bl) {
-              head = base + (uint32_t)(32 * jj + __ffs(bl) - 1);
-              got = true;
+      const unsigned b = __ballot_sync(FULL, hit);
+      if (!b) continue;
+      const int l = __ffs(b) - 1;
+      found.ref = __shfl_sync(FULL, e.ref, l);
+      found.src = __shfl_sync(FULL, e.src, l);
+      found.tag = __shfl_sync(FULL, e.tag, l);
+      found.bytes = __shfl_sync(FULL, e.bytes, l);
+      const uint32_t hidx = base + (uint32_t)l;
+      if (lane == 0) q[hidx & qmask].ref = 0;
+      if (hidx == h.head) {
+        // the next live entry of this chunk becomes the head, else scan on
+        const unsigned after = l == 31 ? 0u : (__ballot_sync(FULL, live) & (~0u << (l + 1)));
+        if (after) {
+          h.head = base + (uint32_t)(__ffs(after) - 1);
+        } else {
+          uint32_t head = base + 32;
+          if ((int32_t)(h.tail - head) <= 0) head = h.tail;
+          while ((int32_t)(h.tail - head) > 0) {
+            const uint32_t i = head + (uint32_t)lane;
+            const bool in2 = (int32_t)(h.tail - i) > 0;
+            const bool lv = in2 && q[i & qmask].ref != 0;
+            const unsigned bl = __ballot_sync(FULL, lv);
+            if (bl) {
+              head += (uint32_t)(__ffs(bl) - 1);
+              break;
             }
-          }
-          if (!got) {
-            head = base + 32 * kChunks;
-            if ((int32_t)(h.tail - head) <= 0) head = h.tail;
-            while ((int32_t)(h.tail - head) > 0) {
-              const uint32_t i = head + (uint32_t)lane;
-              const bool in2 = (int32_t)(h.tail - i) > 0;
-              const bool lv = in2 && q[i & qmask].ref != 0;
-              const unsigned bl = __ballot_sync(FULL, lv);
-              if (bl) {
-                head += (uint32_t)(__ffs(bl) - 1);
-                break;
-              }
-              head += (uint32_t)__popc(__ballot_sync(FULL, in2));
-            }
+            head += (uint32_t)__popc(__ballot_sync(FULL, in2));
           }
           h.head = head;
         }
-        __syncwarp();
-        return true;
       }
+      __syncwarp();
+      return true;
     }
     return false;
   }
@@ -1847,9 +1815,10 @@ struct Ctl {
     uint32_t U = 16;
     if (C != kContig) {
       auto bad = [&](uint32_t u) {
-        if ((C % u) || (src.base % u) || (dst.base % u)) return true;
-        if (src.seg != kContig && ((src.stride % u) || (src.extent % u))) return true;
-        if (dst.seg != kContig && ((dst.stride % u) || (dst.extent % u))) return true;
+        const uint64_t m = u - 1;  // (u is a power of two)
+        if (((uint64_t)C & m) || (src.base & m) || (dst.base & m)) return true;
+        if (src.seg != kContig && (((uint64_t)src.stride & m) || ((uint64_t)src.extent & m))) return true;
+        if (dst.seg != kContig && (((uint64_t)dst.stride & m) || ((uint64_t)dst.extent & m))) return true;
         return false;
       };
       while (U > 1 && bad(U)) U >>= 1;
@@ -2459,7 +2428,23 @@ struct Ctl {
   // (the rest stay listed).  A receive its own stream has not reached yet is
   // listed again when it is; one whose task cannot be created is listed
   // again at once (behind the entries listed now).
-  __device__ void process_cands(int64_t now) {
+  __device__ void process_cands(int64_t now, bool after_full_scan) {
+    __syncthreads();
+    if (sm.cand_h == sm.cand_t) return;  // (uniform: read after the barrier, changed by no one here)
+    if (after_full_scan) {
+      // this tick's full scan already scheduled every reached receive it
+      // could: the list is only unlisted
+      const unsigned long long t = sm.cand_t, mask = (unsigned long long)(P.cand_cap - 1);
+      for (unsigned long long i = sm.cand_h + threadIdx.x; i < t; i += blockDim.x) {
+        const uint64_t rref = P.cand[i & mask];
+        if (rref != 0 && ref_seq(rref) > ss[ref_stream(rref)].retire)
+          atomicAnd(&op_ref(P, rref)->pflags, ~PF_CAND);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) sm.cand_h = t;
+      __syncthreads();
+      return;
+    }
     const unsigned long long t = sm.cand_t;
     const unsigned long long mask = (unsigned long long)(P.cand_cap - 1);
     unsigned long long base = sm.cand_h;
@@ -2886,11 +2871,12 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
     };
     // diagnostic trace: microseconds from the tick's start at its phase ends
-    uint16_t at_us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (P.trace && tid == 0)
+      for (int k = 0; k < 8; ++k) sm.at_us[k] = 0;
     auto stamp = [&](int k) {
       if (P.trace && tid == 0) {
         const int64_t d = ((int64_t)now_ns() - now) / 1000;
-        at_us[k] = (uint16_t)(d > 65535 ? 65535 : d < 1 ? 1 : d);
+        sm.at_us[k] = (uint16_t)(d > 65535 ? 65535 : d < 1 ? 1 : d);
       }
     };
     // 1. ingest
@@ -2939,7 +2925,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         __syncthreads();
         mark(0);
         const bool moved = sm.flag != 0;
-        if (moved) {
+        // (a round that only moved streams past waits posted nothing to match)
+        if (moved && sm.nposts_round > 0) {
           const int warp = tid >> 5, nw = blockDim.x >> 5;
           const uint32_t nd = (uint32_t)(P.max_comms * P.nranks);
           // small rounds over few domains match from shared memory (each warp
@@ -3127,7 +3114,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         }
       }
       stamp(4);
-      C.process_cands(now);
+      C.process_cands(now, sched_all);
       stamp(5);
       C.make_deferred();
       __syncthreads();
@@ -3163,11 +3150,11 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       if ((int64_t)k2 < P.trace_cap) {
         uint64_t* rec = P.trace + 4 * k2;
         rec[0] = (uint64_t)now;
-        rec[1] = (uint64_t)at_us[0] | ((uint64_t)at_us[1] << 16) | ((uint64_t)at_us[2] << 32) |
-                 ((uint64_t)at_us[3] << 48);
+        rec[1] = (uint64_t)sm.at_us[0] | ((uint64_t)sm.at_us[1] << 16) | ((uint64_t)sm.at_us[2] << 32) |
+                 ((uint64_t)sm.at_us[3] << 48);
         rec[2] = (0xFFFFFFFEull << 32) | (uint32_t)ticks;
-        rec[3] = (uint64_t)at_us[4] | ((uint64_t)at_us[5] << 16) | ((uint64_t)at_us[6] << 32) |
-                 ((uint64_t)at_us[7] << 48);
+        rec[3] = (uint64_t)sm.at_us[4] | ((uint64_t)sm.at_us[5] << 16) | ((uint64_t)sm.at_us[6] << 32) |
+                 ((uint64_t)sm.at_us[7] << 48);
       }
     }
     // 4. bookkeeping and exit decisions (thread 0)
