@@ -671,6 +671,67 @@ def batching_small(steps, warmup, nmsg=65536, plain_steps=3, schedule=None):
     return out
 
 
+def allreduce_recorded(log2_sizes=(10, 14, 18), R=16, m=64, reps=5):
+    """The small-instance floor without the host: one recorded step (a CUDA
+    graph: descriptor publication kernel + one engine pass) holding m
+    blocking SUM allreduces per rank, back to back on exclusive streams;
+    CUDA events around each launch on the engine stream.  Per size and dtype:
+    the median launch time / m, and the same for a step of one instance."""
+    import torch
+    from paper_2208_13707_gb300 import mpx
+    dev = torch.device("cuda")
+    cfg = mpx.mpx_world_config_init()
+    cfg.engine_mode = mpx.ENGINE_DRAIN
+    cfg.max_streams = R
+    w = mpx.mpx_world_create(R, cfg)
+    raw = [mpx.mpx_cuda_stream_create() for _ in range(R + 1)]
+    ms = [mpx.mpx_stream_create(w, i, raw[i], mpx.STREAM_EXCLUSIVE) for i in range(R)]
+    comm = mpx.mpx_stream_comm_create(w, ms)
+    es = torch.cuda.ExternalStream(raw[R])
+    out = []
+    try:
+        for dt_name, dt, tdt in (("int64", mpx.INT64, torch.int64), ("f32", mpx.FLOAT, torch.float32)):
+            for lg in log2_sizes:
+                n = 1 << lg
+                x = (torch.randn((R, n), device=dev) * 1000).to(tdt)
+                y = torch.zeros_like(x)
+                torch.cuda.synchronize()
+                e = {"n": n, "dtype": dt_name, "instances_per_step": m}
+                for k in (m, 1):
+                    ops = np.zeros(R * k, mpx.op_dtype())
+                    ops["kind"] = mpx.OP_ALLREDUCE
+                    ops["datatype"] = dt
+                    ops["count"] = n
+                    ops["op"] = mpx.SUM
+                    ops["buf"] = np.repeat([x[r].data_ptr() for r in range(R)], k)
+                    ops["recvbuf"] = np.repeat([y[r].data_ptr() for r in range(R)], k)
+                    ops["comm"] = np.repeat(comm, k)
+                    step = mpx.mpx_step_create(w, ops)
+                    t = []
+                    for rep in range(reps + 2):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(es)
+                        mpx.mpx_step_launch(step, raw[R])
+                        e1.record(es)
+                        e1.synchronize()
+                        if rep >= 2:
+                            t.append(e0.elapsed_time(e1) * 1e3)
+                    assert mpx.mpx_step_get_error(step) == 0 and mpx.mpx_world_get_error(w) == 0
+                    mpx.mpx_step_free(step)
+                    e["us_per_instance" if k == m else "us_step_of_one"] = float(np.median(t)) / k
+                out.append(e)
+    finally:
+        for c in comm:
+            mpx.mpx_comm_free(c)
+        for s_ in ms:
+            mpx.mpx_stream_free(s_)
+        mpx.mpx_world_free(w)
+        for h in raw:
+            mpx.mpx_cuda_stream_destroy(h)
+    return out
+
+
 def allreduce_bw(log2_sizes=(10, 14, 18, 22, 24, 26, 27, 28), R=16, iters=None):
     """Enqueued SUM allreduce among R ranks (one stream each, persistent
     engine): per size, dtype (int64, fp32) and order (fixed, tree), `iters`
@@ -1340,8 +1401,8 @@ def main():
         ar = allreduce_bw()
         for e in ar:
             e["frac_of_peak"] = e["gbs"] / pk
-        print(json.dumps({"allreduce": ar, "halo": halo_bench(), "peak_gbs": pk, "peak_source": pkind}),
-              flush=True)
+        print(json.dumps({"allreduce": ar, "allreduce_recorded": allreduce_recorded(), "halo": halo_bench(),
+                          "peak_gbs": pk, "peak_source": pkind}), flush=True)
         return
     if args.batching_full_only:
         print(json.dumps({"batching_full": batching_full()}), flush=True)
@@ -1425,7 +1486,7 @@ def main():
         ar = allreduce_bw()
         for e in ar:
             e["frac_of_peak"] = e["gbs"] / pk
-        c4 = {"allreduce": ar, "halo": halo_bench()}
+        c4 = {"allreduce": ar, "allreduce_recorded": allreduce_recorded(), "halo": halo_bench()}
     serve = serving(args.serve_requests) if args.serve_requests else None
     tiny = None if args.no_tiny else tiny_bench()
     hostr = None if args.no_host_msgrate else host_msgrate()

@@ -39,6 +39,10 @@ constexpr int kErrTruncate = 15;
 constexpr int kErrTimeout = 16;
 constexpr int kMaxRoundsPerTick = 64;
 constexpr int kMaxStagePerTick = 128;
+// collective instances this small (inputs read, bytes) are reduced by the
+// control CTA itself in the tick that finds them ready, up to this many a tick
+constexpr int64_t kFastReduceBytes = 256 << 10;
+constexpr int kMaxFastReduces = 4;
 constexpr int kMaxDeferred = 512;  // deliveries a scheduling phase sizes together
 constexpr uint64_t kDlvStrided = 1ull << 62;  // deferred delivery with a strided side
 constexpr int kSmallPosts = 256;   // rounds up to this many posts match from shared memory
@@ -256,6 +260,15 @@ struct CtaShared {
   int32_t cand_go;
   int32_t sched_retry;
   uint16_t at_us[8];      // control, diagnostic trace: phase ends of the current tick
+  // control: small instances this tick's scheduling reduces in place (their
+  // tasks are built here and never published)
+  int32_t nfast;
+  Task fast_task[kMaxFastReduces];
+  // control: something this tick can have made schedulable (new descriptors,
+  // rounds, finished tasks, a doorbell or completion change); the oldest stall
+  int32_t ev;
+  int32_t sched_skip;
+  unsigned long long min_stall;
   int32_t sched_all;      // control: this tick's scheduling scans every stream in full
   // control: its own copies of the task-ring words only it writes (task_alloc,
   // task_retire, cq_head); the global words are written through for the movers
@@ -2615,8 +2628,15 @@ struct Ctl {
       for (uint32_t r = 0; r < nin; ++r) aligned = aligned && (ptrs[r] & 15) == 0;
       for (uint32_t r = 0; r < nout; ++r) aligned = aligned && (ptrs[R + r] & 15) == 0;
       if (cop == CO_GATHER && ((n * es) & 15) != 0) aligned = false;  // block starts
-      uint64_t id;
-      Task* T = task_new(id);
+      // a small instance is reduced by this CTA right after the scan (no
+      // mover, no completion queue: its streams see it complete next tick)
+      int fk = -1;
+      if (gridDim.x > 1 && (int64_t)nin * total * es <= kFastReduceBytes) {
+        fk = atomicAdd(&sm.nfast, 1);
+        if (fk >= kMaxFastReduces) fk = -1;
+      }
+      uint64_t id = 0;
+      Task* T = fk >= 0 ? &sm.fast_task[fk] : task_new(id);
       if (!T) continue;
       T->type = T_REDUCE;
       T->action = A_REDUCE;
@@ -2648,10 +2668,46 @@ struct Ctl {
       T->chunk = 0;
       s->state = 2;
       atomicSub(&sm.ready_insts, 1);
-      task_publish(T, id);
+      if (fk >= 0) {
+        T->tile = (total + 255) & ~(int64_t)255;  // one tile: the whole instance
+        T->ntiles = 1;
+      } else {
+        task_publish(T, id);
+      }
       atomicAdd(&sm.ctr[7], 1ull);
       sm.any = 1;
     }
+  }
+
+  // The instances schedule_reduce kept for this CTA: every thread reduces,
+  // then each instance completes as a finished reduction task would.
+  __device__ void run_fast_reduces(uint8_t* buf) {
+    __syncthreads();
+    const int n = sm.nfast < kMaxFastReduces ? sm.nfast : kMaxFastReduces;
+    for (int f = 0; f < n; ++f) {
+      const Task& T = sm.fast_task[f];
+      reduce_tile(sm, buf, T, 0u, P);
+      __threadfence();  // (the outputs before the instance's completion, as a mover's tile)
+      __syncthreads();
+      InstSlot* s = &P.inst[T.ref_s];
+      const uint64_t* refs = P.inst_refs + (size_t)T.ref_s * P.nranks;
+      for (int r = threadIdx.x; r < P.nranks; r += blockDim.x) {
+        atomicOr(&op_ref(P, refs[r])->pflags, PF_COMPLETE | PF_DELIVERED);
+        touch(ref_stream(refs[r]));
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s->state = 0;
+        s->arrived = 0;
+        __threadfence();
+        atomicExch((unsigned long long*)&s->k1, 0ull);
+        sm.dirty = 1;  // a stream may wait for this instance slot
+        sm.ctr[3] += (unsigned long long)(T.bytes * base_size(T.dtype) * P.nranks);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sm.nfast = 0;
+    __syncthreads();
   }
 
   // --- 4. finished tasks (thread per completion-queue entry) ---
@@ -2815,6 +2871,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   if (tid == 0) {
     C.round = (int64_t)sh->round;
     sm.nstage = 0;
+    sm.nfast = 0;
     sm.cand_h = *(volatile unsigned long long*)&sh->cand_h;
     sm.cand_t = *(volatile unsigned long long*)&sh->cand_t;
     sm.sched_retry = 0;
@@ -3034,15 +3091,24 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         }
       }
       // doorbells: how far each non-exclusive stream has executed; a change is
-      // an event for that stream's completion scan
+      // an event for that stream's completion scan (and the oldest stall is
+      // noted for the staging rule)
+      if (tid == 0) {
+        sm.ev = ing || dirty_now || cq_h != cq_t;
+        sm.min_stall = ~0ull;
+      }
+      __syncthreads();
       for (int g = tid; g < P.max_streams; g += blockDim.x) {
         SState& S = C.ss[g];
-        if ((S.flags & SF_EXCLUSIVE) || (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested)) continue;
+        if (!(S.flags & SF_ACTIVE) && S.retire >= S.ingested) continue;
+        if (S.stall_t0 != 0) atomicMin(&sm.min_stall, (unsigned long long)S.stall_t0);
+        if (S.flags & SF_EXCLUSIVE) continue;
         uint64_t db;
         asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(db) : "l"(&P.doorbell[g]) : "memory");
         if (db != S.reached) {
           S.reached = db;
           sm.sdirty[g] = 1;
+          sm.ev = 1;
         }
       }
       __syncthreads();
@@ -3068,12 +3134,29 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
           if (S.retire < S.ingested) pend = 1;
         }
       }
-      if (phys) atomicOr(&sm.any, 1);
+      if (phys) {
+        atomicOr(&sm.any, 1);
+        sm.ev = 1;
+      }
       if (pend) atomicOr(&sm.pending, 1);
       __syncthreads();
       for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 0;
       lap(3);
       stamp(3);
+      // an idle tick skips scheduling: nothing became reachable, matched,
+      // staged, listed or ready, no full scan is due and no stall has lasted
+      // long enough for staging
+      if (tid == 0) {
+        const bool stall_due = sm.min_stall != ~0ull && now - (int64_t)sm.min_stall >= P.stage_delay_ns &&
+                               (now - sm.last_prog >= P.stage_delay_ns ||
+                                now - (int64_t)sm.min_stall >= 50 * P.stage_delay_ns);
+        sm.sched_skip = !sm.ev && !stall_due && (ticks & 63) != 0 && sm.sched_retry == 0 &&
+                        sm.cand_h == sm.cand_t && sm.ready_insts == 0 && sm.nstage == 0;
+        if (sm.sched_skip) sm.t_used = 0;  // (no tasks made this tick)
+      }
+      __syncthreads();
+    }
+    if (!failed_now && !sm.sched_skip) {
       if (tid == 0) {
         C.task_phase_begin();
         sm.ndlv = 0;
@@ -3125,7 +3208,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       mark(3);
       C.schedule_reduce();
       if (tid == 0) C.make_stage_tasks();
-      __syncthreads();
+      C.run_fast_reduces(buf);
       if (tid == 0) C.task_phase_end();
       mark(4);
       lap(4);
