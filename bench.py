@@ -1028,6 +1028,32 @@ def autotune_ring():
             "table": [{"config": t["config"], "gbs": t["gbs"]} for t in r.table]}
 
 
+def confirm_ring_schedule(ring_tune, top=4, warmup=3, steps=12):
+    """The autotuner ranks schedules by their copy rate on the ring's message
+    sizes alone; the step also pays the engine's control time, which depends
+    on the tile count.  Its `top` schedules, and the default tiling, are
+    timed on a few real ring steps each (the bench's own steps, CUDA events)
+    and the fastest step wins."""
+    ranked = sorted(ring_tune["table"], key=lambda t: -t["gbs"])
+    cands = [t["config"] for t in ranked[:top]]
+    default = {"bulk_min_bytes": 32 << 10, "engine_ctas": 0, "engine_threads": 256, "mover_schedule": 0,
+               "tile_bytes": 64 << 10}
+    if default not in cands:
+        cands.append(default)
+    trials = []
+    for c in cands:
+        sched = {"tile_bytes": c["tile_bytes"], "engine_ctas": c["engine_ctas"], "engine_threads": c["engine_threads"],
+                 "bulk_min": c["bulk_min_bytes"], "mover_schedule": c["mover_schedule"]}
+        b = RingBench(**sched)
+        try:
+            res = b.run(warmup, steps)
+        finally:
+            b.close()
+        trials.append({"config": c, "ms_per_step": res["total_ms"] / steps})
+    best = min(trials, key=lambda t: t["ms_per_step"])
+    return best["config"], trials
+
+
 def autotune_report(mixes=("small_8B_64KB", "large_4KB_64MB")):
     """Autotuner on two samples of the workloads' message mixes: small
     (log-uniform 8 B - 64 KB) and large (log-uniform 4 KB - 64 MB, the ring
@@ -1427,10 +1453,12 @@ def main():
     ring_tune = None
     if not args.no_autotune and not args.tile_bytes and not args.engine_ctas and not args.profile_safe:
         ring_tune = autotune_ring()
-        sched = {"tile_bytes": ring_tune["best"]["tile_bytes"], "engine_ctas": ring_tune["best"]["engine_ctas"],
-                 "engine_threads": ring_tune["best"]["engine_threads"],
-                 "bulk_min": ring_tune["best"]["bulk_min_bytes"],
-                 "mover_schedule": ring_tune["best"]["mover_schedule"]}
+        chosen, ring_tune["step_trials"] = confirm_ring_schedule(ring_tune)
+        ring_tune["chosen"] = chosen
+        sched = {"tile_bytes": chosen["tile_bytes"], "engine_ctas": chosen["engine_ctas"],
+                 "engine_threads": chosen["engine_threads"],
+                 "bulk_min": chosen["bulk_min_bytes"],
+                 "mover_schedule": chosen["mover_schedule"]}
     b = RingBench(**sched)
     if args.profile_safe:
         b.run_profile_safe(args.warmup, args.steps)
@@ -1502,7 +1530,8 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "ranks": b.R, "n": b.n, "messages_per_step": 2 * b.R,
                            "copy_schedule": {k: v for k, v in sched.items()},
-                           "schedule_source": "autotuner" if ring_tune else "defaults / command line",
+                           "schedule_source": ("autotuner top 4 + default, confirmed on 12 ring steps each"
+                                               if ring_tune else "defaults / command line"),
                            "engine": "drain pass per step (mpx_world_progress after the step's axpys)",
                            "l2": "inputs larger than L2 (>1.5 GB touched per step)",
                            "parallelism": f"replicas x{world_size}"},

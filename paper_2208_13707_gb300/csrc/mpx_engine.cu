@@ -269,6 +269,7 @@ struct CtaShared {
   int32_t ev;
   int32_t sched_skip;
   unsigned long long min_stall;
+  unsigned long long tacc[8], sub[8];  // control, thread 0: phase timers of this launch
   int32_t sched_all;      // control: this tick's scheduling scans every stream in full
   // control: its own copies of the task-ring words only it writes (task_alloc,
   // task_retire, cq_head); the global words are written through for the movers
@@ -785,6 +786,9 @@ __device__ bool reduce_span_bulk(CtaShared& sm, uint8_t* buf, const uint64_t* in
 // Elements [e_in, e_in + n) of the inputs combined into elements
 // [e_out, e_out + n) of the outputs: bulk copies through shared memory for the
 // 16-byte part when every address allows, else 16-byte vectors, else elements.
+// kBulk: the staged bulk-copy path may be taken (movers); the control CTA's
+// small reductions use the direct loads only (less code inlined there)
+template <bool kBulk>
 __device__ void reduce_span(CtaShared& sm, uint8_t* buf, const Task& T, const uint64_t* in,
                             int nin, int64_t e_in, const uint64_t* out, int nout, int64_t e_out,
                             int64_t n, bool sum, const EngineParams& P) {
@@ -797,7 +801,7 @@ __device__ void reduce_span(CtaShared& sm, uint8_t* buf, const Task& T, const ui
   if (T.unit == 16) {
     const int64_t per = 16 / es;
     const int64_t nv = n / per;
-    if (nv > 0 && bulk_reduce_chunk(nin) >= 256) {
+    if (kBulk && nv > 0 && bulk_reduce_chunk(nin) >= 256) {
       if (!reduce_span_bulk(sm, buf, in, nin, e_in * es, out, nout, e_out * es, dt, tree, sum,
                             nv * 16, P))
         return;
@@ -846,6 +850,7 @@ __device__ void reduce_span(CtaShared& sm, uint8_t* buf, const Task& T, const ui
 // One tile of a collective task: a SUM (allreduce, reduce), a copy of one
 // input (broadcast), or, for an allgather, the copies of the input blocks the
 // tile covers (element e of the outputs comes from input e / gcount).
+template <bool kBulk>
 __device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t k,
                             const EngineParams& P) {
   const int64_t e0 = (int64_t)k * T.tile;
@@ -858,12 +863,12 @@ __device__ void reduce_tile(CtaShared& sm, uint8_t* buf, const Task& T, uint32_t
     for (int64_t a = e0; a < e1;) {
       const int64_t s = a / n;
       const int64_t b = e1 < (s + 1) * n ? e1 : (s + 1) * n;
-      reduce_span(sm, buf, T, ptrs + s, 1, a - s * n, out, (int)T.nout, a, b - a, false, P);
+      reduce_span<kBulk>(sm, buf, T, ptrs + s, 1, a - s * n, out, (int)T.nout, a, b - a, false, P);
       a = b;
     }
     return;
   }
-  reduce_span(sm, buf, T, ptrs, (int)T.nin, e0, out, (int)T.nout, e0, e1 - e0, T.cop == CO_SUM, P);
+  reduce_span<kBulk>(sm, buf, T, ptrs, (int)T.nin, e0, out, (int)T.nout, e0, e1 - e0, T.cop == CO_SUM, P);
 }
 
 // Claim one tile: thread 0 fetch-and-adds the claim word of the task at
@@ -955,7 +960,7 @@ __device__ void run_claimed(const EngineParams& P, CtaShared& sm, uint8_t* buf) 
   } else if (T.type == T_COPY) {
     copy_tile(sm, buf, T, sm.claim_tile, P);
   } else if (T.type == T_REDUCE) {
-    reduce_tile(sm, buf, T, sm.claim_tile, P);
+    reduce_tile<true>(sm, buf, T, sm.claim_tile, P);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -2683,10 +2688,11 @@ struct Ctl {
   // then each instance completes as a finished reduction task would.
   __device__ void run_fast_reduces(uint8_t* buf) {
     __syncthreads();
+    if (sm.nfast == 0) return;  // (uniform: read after the barrier, changed by no one here)
     const int n = sm.nfast < kMaxFastReduces ? sm.nfast : kMaxFastReduces;
     for (int f = 0; f < n; ++f) {
       const Task& T = sm.fast_task[f];
-      reduce_tile(sm, buf, T, 0u, P);
+      reduce_tile<false>(sm, buf, T, 0u, P);
       __threadfence();  // (the outputs before the instance's completion, as a mover's tile)
       __syncthreads();
       InstSlot* s = &P.inst[T.ref_s];
@@ -2889,8 +2895,13 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
   const int64_t t_launch = last_prog;
   const uint64_t alloc0 = sm.c_alloc;
   int64_t t_first_task = 0, t_tasks_done = 0;
-  uint64_t tacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  uint64_t sub[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // finer split (thread 0)
+  // (thread 0's phase timers live in shared memory: registers are scarce here)
+  unsigned long long* tacc = sm.tacc;
+  unsigned long long* sub = sm.sub;  // finer split
+  if (tid < 8) {
+    tacc[tid] = 0;
+    sub[tid] = 0;
+  }
   uint64_t ts = 0;
   const bool timing = P.timing != 0;
   auto mark = [&](int k) {  // thread 0: time since the last mark into sub[k]
