@@ -3172,8 +3172,9 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         C.task_phase_begin();
         sm.ndlv = 0;
         sm.dlv_bytes = 0;
-        // every stream is scanned in full on the first tick of a launch, every
-        // 64th tick, and after a tick that could not create a listed task
+        // every stream is scanned in full every 64th tick and after a full scan
+        // that ran out of task slots (the list and the reach points carry over
+        // from launch to launch)
         sm.sched_all = (ticks & 63) == 0 || sm.sched_retry != 0;
         sm.sched_retry = 0;
       }
