@@ -267,6 +267,7 @@ struct CtaShared {
   // control: something this tick can have made schedulable (new descriptors,
   // rounds, finished tasks, a doorbell or completion change); the oldest stall
   int32_t ev;
+  int32_t ev_carry;       // control: the last completion scans or finished tasks changed something
   int32_t sched_skip;
   unsigned long long min_stall;
   unsigned long long tacc[8], sub[8];  // control, thread 0: phase timers of this launch
@@ -2878,6 +2879,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     C.round = (int64_t)sh->round;
     sm.nstage = 0;
     sm.nfast = 0;
+    sm.ev_carry = 1;  // the first tick always schedules
     sm.cand_h = *(volatile unsigned long long*)&sh->cand_h;
     sm.cand_t = *(volatile unsigned long long*)&sh->cand_t;
     sm.sched_retry = 0;
@@ -3042,70 +3044,14 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
     lap(1);
     stamp(1);
     if (!failed_now) {
-      // 3. finished tasks, then per-stream completion and retirement
+      // 3. doorbells: how far each non-exclusive stream has executed; a change
+      // is an event for scheduling and for that stream's completion scan (and
+      // the oldest stall is noted for the staging rule)
       if (tid == 0) {
-        sm.t_retire = sm.c_cqh;
-        sm.t_alloc = ld_acq_gpu(&sh->cq_tail);
-        // the scans below can move something only after new completions, or
-        // while processed tasks wait for the movers' head to pass them
-        sm.scan_now = sm.t_alloc != sm.t_retire || sm.unretired > 0;
-        sm.all_dirty = (ticks & 63) == 0;  // a periodic full completion scan
-      }
-      __syncthreads();
-      const uint64_t cq_h = sm.t_retire, cq_t = sm.t_alloc;
-      if (cq_h != cq_t) C.complete_tasks(cq_h, cq_t);
-      if (sm.scan_now) {
-        if (tid == 0) {
-          sm.scan_a = cq_t;
-          const uint64_t r0 = sm.c_retire;
-          const uint64_t a = sm.c_alloc;
-          // a slot is reused only after the movers' head has passed its task
-          // (per-CTA schedule: its owner read the record before the last tile
-          // finished, so a processed task can be retired at once)
-          const uint64_t head = P.movers_per_cta && gridDim.x > 1 ? a : ld_acq_gpu(&sh->task_head);
-          uint64_t lim = a < head ? a : head;
-          if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
-          sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
-          sm.scan_b = lim;
-        }
-        __syncthreads();
-        // parallel: the completion-queue head moves over processed entries,
-        // task_retire over processed tasks (a window of 8 per thread a tick)
-        const uint64_t mask = (1ull << P.tq_log2) - 1, qmask = cq_mask(P);
-        for (uint64_t pos = cq_h + tid; pos < cq_t; pos += blockDim.x)
-          if (P.cq[pos & qmask] != kCqDone) {
-            atomicMin((unsigned long long*)&sm.scan_a, (unsigned long long)pos);
-            break;
-          }
-        const uint64_t r0 = sm.r0, lim = sm.scan_b;
-        for (uint64_t id = r0 + tid; id < lim; id += blockDim.x) {
-          const Task& T = P.tasks[id & mask];
-          if (T.type != 0 || claim_idp(T.claim) != id_tag(id)) {
-            atomicMin((unsigned long long*)&sm.scan_b, (unsigned long long)id);
-            break;
-          }
-        }
-        __syncthreads();
-        const uint64_t newh = sm.scan_a;
-        for (uint64_t pos = cq_h + tid; pos < newh; pos += blockDim.x) P.cq[pos & qmask] = 0;
-        if (tid == 0) {
-          if (newh != sm.c_cqh) {
-            sm.c_cqh = newh;
-            sh->cq_head = newh;
-          }
-          if (sm.scan_b != sm.c_retire) {
-            sm.unretired -= (int32_t)(sm.scan_b - sm.c_retire);
-            sm.c_retire = sm.scan_b;
-            sh->task_retire = sm.scan_b;
-          }
-          C.stage_reclaim();
-        }
-      }
-      // doorbells: how far each non-exclusive stream has executed; a change is
-      // an event for that stream's completion scan (and the oldest stall is
-      // noted for the staging rule)
-      if (tid == 0) {
-        sm.ev = ing || dirty_now || cq_h != cq_t;
+        // (what the previous tick's finished tasks and completion scans
+        // changed was carried over in ev_carry)
+        sm.ev = ing || dirty_now || sm.ev_carry;
+        sm.ev_carry = 0;
         sm.min_stall = ~0ull;
       }
       __syncthreads();
@@ -3123,37 +3069,6 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
         }
       }
       __syncthreads();
-      lap(2);
-      stamp(2);
-      int phys = 0, pend = 0;
-      if (tid == 0) sm.pending = 0;
-      __syncthreads();
-      // only streams with an event since their last scan (every stream on
-      // the periodic full scan): nothing else can change a completion word
-      const bool all = sm.all_dirty != 0;
-      if (warp_streams) {
-        const int warp = tid >> 5, nw = blockDim.x >> 5;
-        for (int g = warp; g < P.max_streams; g += nw) {
-          if ((all || sm.sdirty[g]) && C.stream_physical_warp(g, now)) phys = 1;
-          const SState& S = C.ss[g];
-          if (S.retire < S.ingested) pend = 1;
-        }
-      } else {
-        for (int g = tid; g < P.max_streams; g += blockDim.x) {
-          if ((all || sm.sdirty[g]) && C.stream_physical(g, now)) phys = 1;
-          const SState& S = C.ss[g];
-          if (S.retire < S.ingested) pend = 1;
-        }
-      }
-      if (phys) {
-        atomicOr(&sm.any, 1);
-        sm.ev = 1;
-      }
-      if (pend) atomicOr(&sm.pending, 1);
-      __syncthreads();
-      for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 0;
-      lap(3);
-      stamp(3);
       // an idle tick skips scheduling: nothing became reachable, matched,
       // staged, listed or ready, no full scan is due and no stall has lasted
       // long enough for staging
@@ -3167,6 +3082,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
       __syncthreads();
     }
+    // 4. scheduling
     if (!failed_now && !sm.sched_skip) {
       if (tid == 0) {
         C.task_phase_begin();
@@ -3226,6 +3142,100 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       lap(4);
       stamp(7);
     }
+    if (!failed_now) {
+      // 5. finished tasks, then per-stream completion and retirement (after
+      // scheduling: a tick's first tasks start before these scans run)
+      if (tid == 0) {
+        sm.t_retire = sm.c_cqh;
+        sm.t_alloc = ld_acq_gpu(&sh->cq_tail);
+        // the scans below can move something only after new completions, or
+        // while processed tasks wait for the movers' head to pass them
+        sm.scan_now = sm.t_alloc != sm.t_retire || sm.unretired > 0;
+        sm.all_dirty = (ticks & 63) == 0;  // a periodic full completion scan
+      }
+      __syncthreads();
+      const uint64_t cq_h = sm.t_retire, cq_t = sm.t_alloc;
+      if (cq_h != cq_t) C.complete_tasks(cq_h, cq_t);
+      if (tid == 0 && cq_h != cq_t) sm.ev_carry = 1;
+      if (sm.scan_now) {
+        if (tid == 0) {
+          sm.scan_a = cq_t;
+          const uint64_t r0 = sm.c_retire;
+          const uint64_t a = sm.c_alloc;
+          // a slot is reused only after the movers' head has passed its task
+          // (per-CTA schedule: its owner read the record before the last tile
+          // finished, so a processed task can be retired at once)
+          const uint64_t head = P.movers_per_cta && gridDim.x > 1 ? a : ld_acq_gpu(&sh->task_head);
+          uint64_t lim = a < head ? a : head;
+          if (lim > r0 + 8ull * blockDim.x) lim = r0 + 8ull * blockDim.x;
+          sm.r0 = r0;  // (sm.t_retire still holds the queue head other warps may be reading)
+          sm.scan_b = lim;
+        }
+        __syncthreads();
+        // parallel: the completion-queue head moves over processed entries,
+        // task_retire over processed tasks (a window of 8 per thread a tick)
+        const uint64_t mask = (1ull << P.tq_log2) - 1, qmask = cq_mask(P);
+        for (uint64_t pos = cq_h + tid; pos < cq_t; pos += blockDim.x)
+          if (P.cq[pos & qmask] != kCqDone) {
+            atomicMin((unsigned long long*)&sm.scan_a, (unsigned long long)pos);
+            break;
+          }
+        const uint64_t r0 = sm.r0, lim = sm.scan_b;
+        for (uint64_t id = r0 + tid; id < lim; id += blockDim.x) {
+          const Task& T = P.tasks[id & mask];
+          if (T.type != 0 || claim_idp(T.claim) != id_tag(id)) {
+            atomicMin((unsigned long long*)&sm.scan_b, (unsigned long long)id);
+            break;
+          }
+        }
+        __syncthreads();
+        const uint64_t newh = sm.scan_a;
+        for (uint64_t pos = cq_h + tid; pos < newh; pos += blockDim.x) P.cq[pos & qmask] = 0;
+        if (tid == 0) {
+          if (newh != sm.c_cqh) {
+            sm.c_cqh = newh;
+            sh->cq_head = newh;
+          }
+          if (sm.scan_b != sm.c_retire) {
+            sm.unretired -= (int32_t)(sm.scan_b - sm.c_retire);
+            sm.c_retire = sm.scan_b;
+            sh->task_retire = sm.scan_b;
+          }
+          C.stage_reclaim();
+        }
+      }
+      lap(2);
+      stamp(2);
+      int phys = 0, pend = 0;
+      if (tid == 0) sm.pending = 0;
+      __syncthreads();
+      // only streams with an event since their last scan (every stream on
+      // the periodic full scan): nothing else can change a completion word
+      const bool all = sm.all_dirty != 0;
+      if (warp_streams) {
+        const int warp = tid >> 5, nw = blockDim.x >> 5;
+        for (int g = warp; g < P.max_streams; g += nw) {
+          if ((all || sm.sdirty[g]) && C.stream_physical_warp(g, now)) phys = 1;
+          const SState& S = C.ss[g];
+          if (S.retire < S.ingested) pend = 1;
+        }
+      } else {
+        for (int g = tid; g < P.max_streams; g += blockDim.x) {
+          if ((all || sm.sdirty[g]) && C.stream_physical(g, now)) phys = 1;
+          const SState& S = C.ss[g];
+          if (S.retire < S.ingested) pend = 1;
+        }
+      }
+      if (phys) {
+        atomicOr(&sm.any, 1);
+        sm.ev_carry = 1;
+      }
+      if (pend) atomicOr(&sm.pending, 1);
+      __syncthreads();
+      for (int g = tid; g < P.max_streams; g += blockDim.x) sm.sdirty[g] = 0;
+      lap(3);
+      stamp(3);
+    }
     // diagnostic trace: one record per tick (marker 0xFFFFFFFF in the high
     // word of the third field): start, end, tick number, what it did
     if (P.trace && tid == 0) {
@@ -3252,7 +3262,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
                  ((uint64_t)sm.at_us[7] << 48);
       }
     }
-    // 4. bookkeeping and exit decisions (thread 0)
+    // 6. bookkeeping and exit decisions (thread 0)
     if (tid == 0) {
       int decision = 0;  // 0 continue, 1 exit
       const bool any = sm.any != 0;
@@ -3324,7 +3334,7 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       __syncthreads();
       continue;
     }
-    // 5. move data only when no mover CTA exists (a tile would stall the
+    // 7. move data only when no mover CTA exists (a tile would stall the
     // control loop); back off when there is nothing to do
     if (gridDim.x == 1 && claim_tile(P, sm)) {
       run_claimed(P, sm, buf);
