@@ -268,6 +268,7 @@ struct CtaShared {
   // rounds, finished tasks, a doorbell or completion change); the oldest stall
   int32_t ev;
   int32_t ev_carry;       // control: the last completion scans or finished tasks changed something
+  int32_t resched;        // control: the completion scans moved an exclusive stream's reach point
   int32_t sched_skip;
   unsigned long long min_stall;
   unsigned long long tacc[8], sub[8];  // control, thread 0: phase timers of this launch
@@ -2173,7 +2174,13 @@ struct Ctl {
       prog = true;
     }
     // how far the stream has executed (non-exclusive: the tick's doorbell pass)
-    if (S.flags & SF_EXCLUSIVE) S.reached = pc <= S.ingested ? pc : S.ingested;
+    if (S.flags & SF_EXCLUSIVE) {
+      const uint64_t nr = pc <= S.ingested ? pc : S.ingested;
+      if (nr != S.reached) {
+        S.reached = nr;
+        sm.resched = 1;  // newly reached operations: schedule them in this tick
+      }
+    }
     // stall clock: the stream sits at blocking op pc
     const bool stalled = pc <= S.ingested && S.reached >= pc;
     if (stalled) {
@@ -2246,7 +2253,13 @@ struct Ctl {
         st_rlx_sys(&P.done[g], newdone);
         sm.smirror[g] = 1;
       }
-      if (S.flags & SF_EXCLUSIVE) S.reached = pc <= ing ? pc : ing;
+      if (S.flags & SF_EXCLUSIVE) {
+        const uint64_t nr = pc <= ing ? pc : ing;
+        if (nr != S.reached) {
+          S.reached = nr;
+          sm.resched = 1;  // newly reached operations: schedule them in this tick
+        }
+      }
       const bool stalled = pc <= ing && S.reached >= pc;
       if (stalled) {
         if (S.stall_t0 == 0 || advanced) S.stall_t0 = now;
@@ -3082,8 +3095,11 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       }
       __syncthreads();
     }
-    // 4. scheduling
-    if (!failed_now && !sm.sched_skip) {
+    // 4. scheduling, then 5. finished tasks and completion; when those scans
+    // move an exclusive stream's reach point (its previous blocking operation
+    // completed), scheduling runs once more in the same tick
+    for (int pass = 0;; ++pass) {
+    if (!failed_now && (pass > 0 || !sm.sched_skip)) {
       if (tid == 0) {
         C.task_phase_begin();
         sm.ndlv = 0;
@@ -3142,7 +3158,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       lap(4);
       stamp(7);
     }
-    if (!failed_now) {
+    if (!failed_now && pass == 0) {
+      if (tid == 0) sm.resched = 0;
       // 5. finished tasks, then per-stream completion and retirement (after
       // scheduling: a tick's first tasks start before these scans run)
       if (tid == 0) {
@@ -3236,6 +3253,12 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       lap(3);
       stamp(3);
     }
+    if (pass > 0 || failed_now) break;
+    __syncthreads();
+    if (!sm.resched) break;
+    __syncthreads();
+    if (tid == 0) sm.resched = 0;
+    }
     // diagnostic trace: one record per tick (marker 0xFFFFFFFF in the high
     // word of the third field): start, end, tick number, what it did
     if (P.trace && tid == 0) {
@@ -3272,7 +3295,8 @@ __device__ void control_loop(const EngineParams& P, CtaShared& sm, uint8_t* buf)
       const uint64_t a = sm.c_alloc;
       const uint64_t rt = sm.c_retire;
       const bool tasks_live = rt != a;
-      if (any || tasks_live) sm.last_prog = now;
+      // (stamped at the end of the tick: a long tick is not a quiet engine)
+      if (any || tasks_live) sm.last_prog = (int64_t)now_ns();
       if (a != alloc0 && t_first_task == 0) t_first_task = now;
       if (a != alloc0 && !tasks_live) t_tasks_done = now;
       const bool pending = tasks_live || sm.pending != 0;
