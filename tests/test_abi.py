@@ -82,6 +82,23 @@ def test_config_defaults_and_validation():
     with pytest.raises(mpx.MpxError) as e:
         mpx.mpx_world_create(2, bad)
     assert e.value.code == mpx.ERR_ARG
+    # submission rings in pinned host memory unless asked otherwise; an unknown
+    # placement is refused before any CUDA call
+    assert c.ring_placement == mpx.RINGS_HOST and c.reserved0 == 0
+    bad = mpx.mpx_world_config_init()
+    bad.ring_placement = 7
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_world_create(2, bad)
+    assert e.value.code == mpx.ERR_ARG
+
+
+def test_diagnostic_entry_points_are_bound():
+    """The engine trace and the device-attribute query are diagnostics of the
+    library (not part of the header's API): bound, and without a world the
+    trace is empty."""
+    from paper_2208_13707_gb300 import mpx
+    assert callable(mpx.engine_trace) and callable(mpx.device_attr)
+    assert mpx.lib.mpxi_world_trace(None, None, 0) == 0
 
 
 def test_sendrecv_static_rejects_bad_arguments_before_touching_the_gpu():
