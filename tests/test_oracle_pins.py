@@ -220,6 +220,7 @@ def test_any_source_takes_lowest_stream_first_in_round():
     o = oracle.run(p)
     # posts of round 1 in key order: rank0's two receives, rank1's send, rank2's send
     assert list(o.buffers[r]) == [1] * 4 + [2] * 4
+    assert (match_set(o.match, p), False) in legal_outcomes(p)  # and MPI allows it
 
 
 def test_round_model_hand_worked_wildcard_order():
@@ -246,6 +247,7 @@ def test_round_model_hand_worked_wildcard_order():
     assert not o.deadlock
     assert list(o.buffers[r]) == [0xA] * 4 + [0xB] * 4 + [0xC] * 4
     assert list(o.post_round[:3]) == [1, 2, 2]
+    assert (match_set(o.match, p), False) in legal_outcomes(p)  # and MPI allows it
 
 
 def test_round_model_causal_order_beats_stream_order():
