@@ -137,6 +137,35 @@ def test_truncation_takes_capacity_and_reports_error():
     assert (s["source"], s["tag"], s["error"], s["bytes"]) == (0, 5, ERR_TRUNCATE, 24)
 
 
+def test_zero_count_messages_match_in_order_and_move_nothing():
+    """MPI: a message of count 0 matches like any other (by source, tag and
+    order); it moves no bytes and its status carries the source, the tag and
+    0 bytes.  A receive of capacity 0 that takes a longer message delivers
+    nothing and reports MPI_ERR_TRUNCATE."""
+    b = ProgramBuilder(2)
+    g0, g1 = b.stream(0), b.stream(1)
+    c = b.comm([g0, g1])
+    src = b.buffer(np.arange(1, 17, dtype=np.uint8))
+    dst = b.buffer(np.full(16, 0xEE, np.uint8))
+    st = b.status_slots(3)
+    b.send(g0, c, src, 0, 0, T_FLOAT, 1, 7)                     # op 0: empty, tag 7
+    b.send(g0, c, src, 0, 4, T_BYTE, 1, 7)                      # op 1: 4 bytes, tag 7
+    b.send(g0, c, src, 4, 2, T_INT32, 1, 9)                     # op 2: 8 bytes, tag 9
+    b.recv(g1, c, dst, 0, 4, T_BYTE, 0, 7, st)                  # op 3: the first tag-7 message
+    b.recv(g1, c, dst, 0, 4, T_BYTE, ANY_SOURCE, ANY_TAG, st + 1)  # op 4: the next message
+    b.recv(g1, c, dst, 8, 0, T_INT32, 0, 9, st + 2)             # op 5: capacity 0
+    p = b.build()
+    o = oracle.run(p)
+    assert o.error == 0 and not o.deadlock
+    assert [int(o.match[k]) for k in range(3)] == [3, 4, 5]
+    got = [(int(s["source"]), int(s["tag"]), int(s["error"]), int(s["bytes"]))
+           for s in o.status[st: st + 3]]
+    assert got == [(0, 7, 0, 0), (0, 7, 0, 4), (0, 9, ERR_TRUNCATE, 0)]
+    expect = np.full(16, 0xEE, np.uint8)
+    expect[:4] = [1, 2, 3, 4]
+    assert np.array_equal(o.buffers[dst], expect)
+
+
 # ---------------------------------------------------------------------------
 # matching: closed form, exhaustive enumeration, invariants
 # ---------------------------------------------------------------------------
