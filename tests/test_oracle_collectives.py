@@ -122,3 +122,64 @@ def test_mismatched_collective_kinds_are_an_error():
     b.bcast(gs[1], c, x[1], 0, n, T_INT64, 0)
     o = oracle.run(b.build())
     assert o.error != 0
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes: each must be caught by the pins above
+# ---------------------------------------------------------------------------
+COLL_MUTANTS = [
+    # the broadcast copies rank 0's elements whatever the root
+    ("const Op& root = p.ops[arr[(size_t)o0.peer]];", "const Op& root = p.ops[arr[0]];"),
+    # the gathered blocks land in reverse rank order
+    ("std::memcpy(at(o.buf2, o.off2) + (int64_t)s * bytes, block[s].data(), (size_t)bytes);",
+     "std::memcpy(at(o.buf2, o.off2) + (int64_t)s * bytes, block[R - 1 - s].data(), (size_t)bytes);"),
+    # an in-place gather takes block 0 of each receive buffer as the contribution
+    ("const int64_t so = o.buf == kInPlace ? o.off2 + (int64_t)s * bytes : o.off;",
+     "const int64_t so = o.buf == kInPlace ? o.off2 : o.off;"),
+    # a reduce writes every rank's receive buffer
+    ("const bool writes = root < 0 || (int)k == root;", "const bool writes = true;"),
+    # a reduce writes rank 0's receive buffer instead of the root's
+    ("const bool writes = root < 0 || (int)k == root;", "const bool writes = root < 0 || k == 0;"),
+]
+
+
+def _collective_checks():
+    for root in (0, 3):
+        yield lambda root=root: test_bcast_copies_the_root_everywhere(root)
+    for dt in (T_INT64, T_FLOAT):
+        for in_place in (False, True):
+            yield lambda dt=dt, ip=in_place: test_reduce_sums_into_the_root_only(dt, ip)
+    for in_place in (False, True):
+        yield lambda ip=in_place: test_allgather_concatenates_in_rank_order(ip)
+    yield test_collective_kinds_share_the_instance_order
+
+
+@pytest.mark.parametrize("k", range(len(COLL_MUTANTS)))
+def test_planted_collective_mistake_is_caught(k, tmp_path, monkeypatch):
+    import importlib
+    import os
+    import shutil
+    import sys
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "mpx_oracle.cpp")).read()
+    old, new = COLL_MUTANTS[k]
+    assert old in src
+    d = tmp_path / "oracle"
+    d.mkdir()
+    (d / "mpx_oracle.cpp").write_text(src.replace(old, new, 1))
+    shutil.copy(oracle.__file__, d / "__init__.py")
+    monkeypatch.syspath_prepend(str(tmp_path))
+    saved = sys.modules.pop("oracle")
+    try:
+        mutant = importlib.import_module("oracle")
+        assert mutant.__file__.startswith(str(tmp_path))
+        monkeypatch.setitem(globals(), "oracle", mutant)
+        caught = False
+        for fn in _collective_checks():
+            try:
+                fn()
+            except AssertionError:
+                caught = True
+                break
+        assert caught, f"mutant {k} survived"
+    finally:
+        sys.modules["oracle"] = saved

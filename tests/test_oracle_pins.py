@@ -572,6 +572,17 @@ MUTANTS = [
      "return r.done_round[j] >= 0 && r.done_round[j] <= round;"),
     # truncation reported on the wrong side
     ("st.error = sent > cap ? kErrTruncate : 0;", "st.error = sent < cap ? kErrTruncate : 0;"),
+    # fp32 fixed-order fold over the ranks after the first in reverse order
+    ("for (size_t k = 1; k < R; ++k) acc = acc + load<float>(in[k], i);",
+     "for (size_t k = R - 1; k >= 1; --k) acc = acc + load<float>(in[k], i);"),
+    # tree-mode reference sum drops rank 0's term
+    ("for (size_t k = 0; k < R; ++k) acc += (double)load<float>(in[k], i);",
+     "for (size_t k = 1; k < R; ++k) acc += (double)load<float>(in[k], i);"),
+    # axpy rounded twice (product, then sum) instead of once
+    ("y = std::fma(o.alpha, x, y);", "y = o.alpha * x + y;"),
+    # a send request's status carries rank 0 instead of MPI_ANY_SOURCE
+    ("st.source = kAnySource;  // empty status for send requests",
+     "st.source = 0;  // empty status for send requests"),
 ]
 
 
@@ -598,6 +609,9 @@ def test_planted_mistake_is_caught(k, tmp_path, monkeypatch):
                   test_truncation_takes_capacity_and_reports_error,
                   test_validity_checker_rejects_overtaking, test_ring_exchange_matches_numpy_restatement,
                   test_round_model_hand_worked_wildcard_order, test_any_source_takes_lowest_stream_first_in_round,
+                  test_zero_count_messages_match_in_order_and_move_nothing,
+                  test_allreduce_fp32_fixed_is_left_fold, test_allreduce_fp32_tree_mode_and_reference_sum,
+                  test_axpy_single_rounding, test_send_request_status_is_the_empty_status,
                   lambda: [test_outcome_is_among_all_legal_outcomes(s) for s in range(60)]]
         caught = False
         for fn in checks:
