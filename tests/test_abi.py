@@ -252,3 +252,47 @@ def test_serve_run_rejects_bad_configs_without_a_gpu():
     with pytest.raises(mpx.MpxError) as e:
         mpx.mpx_serve_run(c)
     assert e.value.code == mpx.ERR_ARG
+
+
+def _header_constants():
+    """Every enum constant of include/mpx.h (MPX_ prefix, upper case)."""
+    src = open(os.path.join(ROOT, "include", "mpx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = []
+    for body in re.findall(r"\benum\s*\{(.*?)\}", src, flags=re.S):
+        for item in body.split(","):
+            m = re.match(r"\s*(MPX_[A-Z0-9_]+)\b", item)
+            if m:
+                names.append(m.group(1))
+    return names
+
+
+def test_constants_match_the_binding(tmp_path):
+    """Each MPX_* constant as the C compiler evaluates it equals the binding's
+    value of the same name without the prefix, and the traffic program format
+    uses the header's wildcard and status error values."""
+    import subprocess
+    from paper_2208_13707_gb300 import mpx
+    from traffic import program
+    names = _header_constants()
+    assert len(names) > 60
+    macros = ["MPX_REQUEST_NULL"]
+    src = tmp_path / "c.c"
+    src.write_text('#include <stdio.h>\n#include "mpx.h"\nint main(void){\n' +
+                   "".join(f'  printf("{n} %lld\\n", (long long)({n}));\n' for n in names + macros) +
+                   '  printf("MPX_IN_PLACE %lld\\n", (long long)(size_t)MPX_IN_PLACE);\n'
+                   "  return 0;\n}\n")
+    exe = tmp_path / "c"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    wrong = [(n, int(v), getattr(mpx, n[4:], None)) for n, v in got.items()
+             if getattr(mpx, n[4:], None) != int(v)]
+    assert wrong == [], "binding constants that differ from include/mpx.h (name, C, Python)"
+    assert (program.ANY_SOURCE, program.ANY_TAG, program.ANY_INDEX) == (
+        int(got["MPX_ANY_SOURCE"]), int(got["MPX_ANY_TAG"]), int(got["MPX_ANY_INDEX"]))
+    assert (program.ERR_TRUNCATE, program.ERR_TIMEOUT) == (
+        int(got["MPX_ERR_TRUNCATE"]), int(got["MPX_ERR_TIMEOUT"]))
+    assert [program.T_BYTE, program.T_INT32, program.T_INT64, program.T_FLOAT, program.T_DOUBLE] == [
+        int(got[n]) for n in ("MPX_BYTE", "MPX_INT32", "MPX_INT64", "MPX_FLOAT", "MPX_DOUBLE")]
