@@ -506,6 +506,29 @@ def test_allreduce_fp32_fixed_is_left_fold():
             assert abs(float(acc[i]) - exact) <= gamma * mag + 1e-45
 
 
+def test_allreduce_fp64_fixed_is_left_fold():
+    """fp64 SUM in fixed order: ((x0 + x1) + x2) + ... in rank order, one
+    rounding per addition, within the sequential-summation bound of the exact
+    sum (Higham, Accuracy and Stability of Numerical Algorithms, §4.2)."""
+    R, n = 16, 777
+    p = gen.allreduce_suite(nranks=R, sizes=(n,), dtypes=(T_DOUBLE,), modes=(MODE_FIXED,))
+    o = oracle.run(p)
+    assert o.error == 0 and not o.deadlock
+    for inst, xs, outs in _instances(p, o):
+        fl = [x.view(np.float64) for x in xs]
+        acc = fl[0].copy()
+        for k in range(1, R):
+            acc = acc + fl[k]
+        for out in outs:
+            assert np.array_equal(out.view(np.float64), acc)
+        u = 2.0 ** -53
+        gamma = (R - 1) * u / (1 - (R - 1) * u)
+        for i in range(0, n, 7):
+            exact = sum((Fraction(float(f[i])) for f in fl), Fraction(0))
+            mag = sum(abs(float(f[i])) for f in fl)
+            assert abs(Fraction(float(acc[i])) - exact) <= Fraction(gamma * mag)
+
+
 def test_allreduce_fp32_tree_mode_and_reference_sum():
     p = gen.allreduce_suite(nranks=16, sizes=(512,), dtypes=(T_FLOAT,), modes=(MODE_TREE,),
                             in_place=True)
@@ -575,6 +598,9 @@ MUTANTS = [
     # fp32 fixed-order fold over the ranks after the first in reverse order
     ("for (size_t k = 1; k < R; ++k) acc = acc + load<float>(in[k], i);",
      "for (size_t k = R - 1; k >= 1; --k) acc = acc + load<float>(in[k], i);"),
+    # fp64 fixed-order fold drops the last rank's term
+    ("for (size_t k = 1; k < R; ++k) acc = acc + load<double>(in[k], i);",
+     "for (size_t k = 1; k + 1 < R; ++k) acc = acc + load<double>(in[k], i);"),
     # tree-mode reference sum drops rank 0's term
     ("for (size_t k = 0; k < R; ++k) acc += (double)load<float>(in[k], i);",
      "for (size_t k = 1; k < R; ++k) acc += (double)load<float>(in[k], i);"),
@@ -611,6 +637,7 @@ def test_planted_mistake_is_caught(k, tmp_path, monkeypatch):
                   test_round_model_hand_worked_wildcard_order, test_any_source_takes_lowest_stream_first_in_round,
                   test_zero_count_messages_match_in_order_and_move_nothing,
                   test_allreduce_fp32_fixed_is_left_fold, test_allreduce_fp32_tree_mode_and_reference_sum,
+                  test_allreduce_fp64_fixed_is_left_fold,
                   test_axpy_single_rounding, test_send_request_status_is_the_empty_status,
                   lambda: [test_outcome_is_among_all_legal_outcomes(s) for s in range(60)]]
         caught = False
