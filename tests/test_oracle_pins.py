@@ -252,6 +252,63 @@ def test_any_source_takes_lowest_stream_first_in_round():
     assert (match_set(o.match, p), False) in legal_outcomes(p)  # and MPI allows it
 
 
+@pytest.mark.parametrize("seed", range(24))
+def test_any_source_one_round_closed_form(seed):
+    """Reading A1/A2 fixed for a whole family.  Every rank posts only
+    nonblocking calls before its waitall, so everything is posted in round 1
+    with key (1, stream id, program index); rank q posts M receives with
+    (ANY_SOURCE, ANY_TAG) and the others send it M messages in all.  Sends from
+    streams before q's wait as unexpected messages in key order and q's
+    receives take them in that order; the later streams' sends find q's
+    remaining receives in posting order.  Either way receive j takes the j-th
+    send to q in (stream id, program index) order, wherever q's stream sits;
+    stream ids are drawn independently of ranks, so rank order cannot stand in
+    for it."""
+    rng = np.random.default_rng(0x5EED + seed)
+    R = int(rng.integers(3, 7))
+    q = int(rng.integers(0, R))
+    b = ProgramBuilder(R)
+    gid = {}
+    for r in rng.permutation(R):
+        gid[int(r)] = b.stream(int(r))
+    c = b.comm([gid[r] for r in range(R)])
+    sends = []                  # (stream id, program index, rank, tag, payload)
+    val = 1
+    reqs = {r: [] for r in range(R)}
+    for r in range(R):
+        if r == q:
+            continue
+        for _ in range(int(rng.integers(0, 4))):
+            n = int(rng.integers(1, 9))
+            payload = np.arange(val, val + n, dtype=np.int32)
+            val += n
+            tag = int(rng.integers(0, 4))
+            h = b.isend(gid[r], c, b.buffer(payload), 0, n, T_INT32, q, tag)
+            reqs[r].append(h)
+            sends.append((gid[r], h[1], r, tag, payload))
+    M = len(sends)
+    rbuf = b.buffer(np.full(8 * max(M, 1), -1, np.int32))
+    for j in range(M):
+        reqs[q].append(b.irecv(gid[q], c, rbuf, 32 * j, 8, T_INT32, ANY_SOURCE, ANY_TAG))
+    st = b.status_slots(max(M, 1))
+    for r in range(R):
+        if reqs[r]:
+            b.waitall(gid[r], reqs[r], st if r == q else -1)
+    p = b.build()
+    o = oracle.run(p)
+    assert o.error == 0 and not o.deadlock
+    order = sorted(sends, key=lambda x: (x[0], x[1]))
+    got = o.buffers[rbuf].view(np.int32)
+    for j, (g, k, r, tag, payload) in enumerate(order):
+        recv_op = int(p.stream_op_lo[gid[q]]) + j
+        assert int(o.match[int(p.stream_op_lo[g]) + k]) == recv_op
+        n = len(payload)
+        assert np.array_equal(got[8 * j: 8 * j + n], payload) and np.all(got[8 * j + n: 8 * j + 8] == -1)
+        s_ = o.status[st + j]
+        assert (int(s_["source"]), int(s_["tag"]), int(s_["error"]), int(s_["bytes"])) == (r, tag, 0, 4 * n)
+    assert validity_violations(p, o.match, require_complete=True) == []
+
+
 def test_round_model_hand_worked_wildcard_order():
     """Hand-worked under the round reading: rank 0 isends A then waits, then
     sends C; rank 1 sends B; rank 2 posts three ANY_SOURCE receives.
@@ -636,6 +693,7 @@ def test_planted_mistake_is_caught(k, tmp_path, monkeypatch):
                   test_validity_checker_rejects_overtaking, test_ring_exchange_matches_numpy_restatement,
                   test_round_model_hand_worked_wildcard_order, test_any_source_takes_lowest_stream_first_in_round,
                   test_zero_count_messages_match_in_order_and_move_nothing,
+                  lambda: [test_any_source_one_round_closed_form(s) for s in range(24)],
                   test_allreduce_fp32_fixed_is_left_fold, test_allreduce_fp32_tree_mode_and_reference_sum,
                   test_allreduce_fp64_fixed_is_left_fold,
                   test_axpy_single_rounding, test_send_request_status_is_the_empty_status,
