@@ -296,3 +296,43 @@ def test_constants_match_the_binding(tmp_path):
         int(got["MPX_ERR_TRUNCATE"]), int(got["MPX_ERR_TIMEOUT"]))
     assert [program.T_BYTE, program.T_INT32, program.T_INT64, program.T_FLOAT, program.T_DOUBLE] == [
         int(got[n]) for n in ("MPX_BYTE", "MPX_INT32", "MPX_INT64", "MPX_FLOAT", "MPX_DOUBLE")]
+
+
+_NULL_CALLS = r'''
+import ctypes, sys
+lib = ctypes.CDLL(sys.argv[1])
+for item in sys.argv[2:]:
+    name, nargs = item.split(":")
+    f = getattr(lib, name)
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p] * int(nargs)
+    print(name, end=" ", flush=True)
+    print(f(*([None] * int(nargs))), flush=True)
+'''
+
+
+def test_null_handles_and_zero_sizes_return_codes(lib):
+    """Every entry point called with null pointers, null handles and zero
+    sizes returns an error code without crashing and without touching a GPU;
+    only calls that a zero count makes no-ops (waitall and startall of no
+    requests, an empty batch, an axpy of no elements, a zero-byte static
+    copy) succeed.  One child process makes every call in turn, so a crash
+    names the call."""
+    import subprocess
+    import sys
+    src = open(os.path.join(ROOT, "include", "mpx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"\bint\s+(mpx_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src)
+    assert len(decls) == len(_declared())
+    items = [f"{n}:{0 if a.strip() in ('', 'void') else len(a.split(','))}" for n, a in decls]
+    path = os.path.join(ROOT, "paper_2208_13707_gb300", "_lib", "libmpx.so")
+    r = subprocess.run([sys.executable, "-c", _NULL_CALLS, path, *items], capture_output=True,
+                       text=True, timeout=300, env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    lines = r.stdout.splitlines()
+    assert r.returncode == 0, f"crashed in {lines[-1] if lines else '?'}: {r.stderr[-300:]}"
+    got = dict(line.split() for line in lines)
+    assert len(got) == len(decls)
+    no_ops = {"mpx_waitall_enqueue", "mpx_startall_enqueue", "mpx_enqueue_batch",
+              "mpx_saxpy_enqueue", "mpx_sendrecv_static", "mpx_version"}
+    ok = sorted(n for n, v in got.items() if int(v) == 0)
+    assert set(ok) <= no_ops, f"calls that succeed on null arguments: {sorted(set(ok) - no_ops)}"
