@@ -336,3 +336,40 @@ def test_null_handles_and_zero_sizes_return_codes(lib):
               "mpx_saxpy_enqueue", "mpx_sendrecv_static", "mpx_version"}
     ok = sorted(n for n, v in got.items() if int(v) == 0)
     assert set(ok) <= no_ops, f"calls that succeed on null arguments: {sorted(set(ok) - no_ops)}"
+
+
+def test_datatype_registry_from_many_threads():
+    """Derived datatypes are process-wide: threads that create, check and free
+    vector types at the same time get distinct live handles whose size and
+    extent are their own (ctypes releases the interpreter lock during each
+    call, so the calls overlap in the library)."""
+    import threading
+    from paper_2208_13707_gb300 import mpx
+    errors, live = [], {}
+    lock = threading.Lock()
+
+    def worker(t):
+        try:
+            for k in range(300):
+                vc, bl = 1 + (t + k) % 7, 1 + k % 5
+                st = bl + t % 3
+                h = mpx.mpx_type_vector(vc, bl, st, mpx.INT32)
+                with lock:
+                    if h in live:
+                        errors.append(f"handle {h} handed out twice")
+                    live[h] = t
+                if mpx.mpx_type_size(h) != 4 * vc * bl or \
+                        mpx.mpx_type_extent(h) != 4 * ((vc - 1) * st + bl):
+                    errors.append(f"type {h} of thread {t} changed")
+                with lock:
+                    del live[h]
+                mpx.mpx_type_free(h)
+        except Exception as e:      # reported below
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(8)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert errors == []
