@@ -1146,7 +1146,7 @@ extern "C" int mpx_get_count(const mpx_status_t* st, mpx_datatype_t t, int64_t* 
   int64_t sz;
   int rc = mpx_type_size(t, &sz);
   if (rc) return rc;
-  *count = (sz > 0 && st->bytes % sz == 0) ? st->bytes / sz : MPX_UNDEFINED;
+  *count = (sz > 0 && st->bytes % sz == 0) ? st->bytes / sz : (int64_t)MPX_UNDEFINED;
   return MPX_SUCCESS;
 }
 
