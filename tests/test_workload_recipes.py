@@ -4,6 +4,9 @@ Every workload is drawn from splitmix64 (Steele, Lea, Flood, "Fast splittable
 pseudorandom number generators", OOPSLA 2014).  These checks fix the
 generator to the published outputs of that algorithm, and each workload
 builder to the distribution and the structure it claims:
+  - tiny pairs: 1,000 blocking int32 sends of U[1, 4096] elements with tags
+    U[0, 7], received by blocking receives in a random order that keeps each
+    tag's order;
   - ring exchange (§6, Listing 4's axpy between the exchanges): sizes
     log-uniform over 4 KB - 64 MB, the four layout pairs equally likely, the
     vector type MPI_Type_vector(nb, 64, 128) of fp32;
@@ -27,7 +30,8 @@ import pytest
 
 from traffic import gen
 from traffic.program import (ALLREDUCE, ANY_SOURCE, ANY_TAG, AXPY, IRECV, ISEND, MODE_FIXED,
-                             MODE_TREE, T_BYTE, T_FLOAT, T_INT32, T_INT64, WAITALL, type_size)
+                             MODE_TREE, RECV, SEND, T_BYTE, T_FLOAT, T_INT32, T_INT64, WAITALL,
+                             type_size)
 from traffic.rng import Rng
 
 
@@ -94,6 +98,32 @@ def test_uniform_integers_and_normal_draws():
     i = np.arange(1, n + 1)
     d = max(np.max(i / n - phi), np.max(phi - (i - 1) / n))
     assert d < 1.95 / math.sqrt(n), f"Box-Muller draws: KS distance {d:.5f} from N(0,1)"
+
+
+# ---------------------------------------------------------------------------
+# tiny pairs
+# ---------------------------------------------------------------------------
+def test_tiny_pairs_recipe():
+    nmsg = 1000
+    p = gen.tiny_pairs(nmsg=nmsg)
+    s0 = p.ops[p.stream_op_lo[0]: p.stream_op_lo[1]]
+    s1 = p.ops[p.stream_op_lo[1]: p.stream_op_lo[2]]
+    assert len(s0) == len(s1) == nmsg
+    assert np.all(s0["kind"] == SEND) and np.all(s1["kind"] == RECV)
+    assert np.all(s0["type"] == T_INT32) and np.all(s0["peer"] == 1) and np.all(s1["peer"] == 0)
+    counts, tags, order = p.meta["counts"], p.meta["tags"], p.meta["recv_order"]
+    assert counts.min() >= 1 and counts.max() <= 4096
+    assert abs(counts.mean() - 2048.5) < 5 * math.sqrt((4096 ** 2 - 1) / 12 / nmsg)
+    tc = np.bincount(tags, minlength=8)
+    assert len(tc) == 8 and all(_within(int(c), nmsg, 1 / 8) for c in tc)
+    assert sorted(order) == list(range(nmsg))
+    # each receive names exactly its message, and a tag's messages are received in send order
+    assert np.array_equal(s1["count"], counts[order]) and np.array_equal(s1["tag"], tags[order])
+    for t in range(8):
+        mine = [int(m) for m in order if tags[m] == t]
+        assert mine == sorted(mine)
+    # the interleaving of the tags is random: most receives are out of send order
+    assert np.count_nonzero(np.asarray(order) != np.arange(nmsg)) > nmsg // 2
 
 
 # ---------------------------------------------------------------------------
