@@ -373,3 +373,62 @@ def test_datatype_registry_from_many_threads():
     for th in threads:
         th.join()
     assert errors == []
+
+
+_CONFIG_FIELDS = {   # field: (environment variable, default documented in include/mpx.h)
+    "engine_mode": ("MPX_ENGINE_MODE", 0), "max_streams": ("MPX_MAX_STREAMS", 64),
+    "ring_slots": ("MPX_RING_SLOTS", 4096), "max_comms": ("MPX_MAX_COMMS", 8),
+    "queue_slots": ("MPX_QUEUE_SLOTS", 4096), "task_slots": ("MPX_TASK_SLOTS", 16384),
+    "engine_ctas": ("MPX_ENGINE_CTAS", 0), "engine_threads": ("MPX_ENGINE_THREADS", 256),
+    "tile_bytes": ("MPX_TILE_BYTES", 65536), "bulk_min_bytes": ("MPX_BULK_MIN_BYTES", 32768),
+    "reduce_mode": ("MPX_REDUCE_MODE", 0), "mover_schedule": ("MPX_MOVER_SCHEDULE", 0),
+    "staging_bytes": ("MPX_STAGING_BYTES", 256 << 20), "budget_bytes": ("MPX_BUDGET_BYTES", 0),
+    "watchdog_ns": ("MPX_WATCHDOG_NS", 10 ** 10), "idle_exit_ns": ("MPX_IDLE_EXIT_NS", 10 ** 8),
+    "stage_delay_ns": ("MPX_STAGE_DELAY_NS", 20000), "ring_placement": ("MPX_RING_PLACEMENT", 0),
+}
+
+_CONFIG_DUMP = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2208_13707_gb300 import mpx
+c = mpx.mpx_world_config_init()
+print(json.dumps({f: getattr(c, f) for f, _ in c._fields_}))
+'''
+
+
+def _config_in_env(env_over):
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if not k.startswith("MPX_")}
+    env.update(env_over)
+    r = subprocess.run([sys.executable, "-c", _CONFIG_DUMP, ROOT], capture_output=True, text=True,
+                       env=env, timeout=120, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_config_defaults_are_the_documented_ones_and_env_overrides_each_field():
+    got = _config_in_env({})
+    assert {f: got[f] for f in _CONFIG_FIELDS} == {f: d for f, (_, d) in _CONFIG_FIELDS.items()}
+    over = {env: str(d + 1 if d else 7) for f, (env, d) in _CONFIG_FIELDS.items()}
+    got = _config_in_env(over)
+    assert {f: got[f] for f in _CONFIG_FIELDS} == {f: int(over[env]) for f, (env, _) in _CONFIG_FIELDS.items()}
+
+
+@pytest.mark.parametrize("field,value", [
+    ("max_streams", 0), ("max_streams", 1025), ("ring_slots", 8), ("queue_slots", 48),
+    ("queue_slots", 16), ("task_slots", 32), ("max_comms", 0), ("max_comms", 65536),
+    ("tile_bytes", 128), ("tile_bytes", 4100), ("engine_threads", 32), ("engine_threads", 544),
+    ("engine_threads", 100), ("engine_mode", 3), ("engine_mode", -1), ("staging_bytes", 4095),
+    ("mover_schedule", 2), ("ring_placement", -1)])
+def test_world_config_out_of_range_is_refused_before_any_cuda_call(field, value):
+    from paper_2208_13707_gb300 import mpx
+    cfg = mpx.mpx_world_config_init()
+    setattr(cfg, field, value)
+    with pytest.raises(mpx.MpxError) as e:
+        mpx.mpx_world_create(2, cfg)
+    assert e.value.code == mpx.ERR_ARG
+    for n in (0, 4097):
+        with pytest.raises(mpx.MpxError) as e:
+            mpx.mpx_world_create(n, None)
+        assert e.value.code == mpx.ERR_ARG
